@@ -1,0 +1,145 @@
+"""Seeded synthetic workloads (inputs only; none of the sampler's arithmetic lives here).
+
+Both the CUDA path and the CPU oracle receive problems built here, as plain dicts:
+  {"X": (N, n_cov) float64, "y": (N,) float64, "lik": "bernoulli"|"gaussian", "noise_var": float,
+   "kernels": [{"kind": "se"|"linear"|"overlap", "cols": tuple, "jitter": float,
+                "prior_a": (a_c, a_theta), "prior_b": (b_c, b_theta)}, ...],
+   "sample_hypers": bool, "u_fixed": (2n,) or None}
+
+The latent functions behind the labels are drawn in weight space, so no kernel matrix is formed:
+  SE       random Fourier features (Rahimi and Recht 2007), 4096 features:
+           f(x) = sqrt(2c/M) sum_j cos(w_j . x + b_j), w_j ~ N(0, I / l^2), b_j ~ U[0, 2 pi)
+  linear   f(x) = sqrt(c) (w . x + sqrt(b) w_0),  w ~ N(0, I)
+  overlap  exp(-h/l) = prod over columns of (rho + (1 - rho) [x_i = x'_i]), rho = exp(-1/l):
+           per-column features [sqrt(rho), sqrt(1 - rho) e_category], tensor product over columns,
+           f = w . phi(x), w ~ N(0, I)
+The paper's own workloads (a 500-sample simulated logistic problem, Sec. 2.5, and the NMES data,
+Sec. 2.6, which is not available here) are stood in for by these generators, with the paper's
+sizes (N = 500, continuous / binary / ordinal covariates) where they apply.
+"""
+import numpy as np
+
+DEFAULT_PRIOR_A = (2.0, 2.0)
+DEFAULT_PRIOR_B = (2.0, 2.0)
+DEFAULT_JITTER = 1e-6
+
+
+def _kernel(kind, cols):
+    return {"kind": kind, "cols": tuple(int(c) for c in cols), "jitter": DEFAULT_JITTER,
+            "prior_a": DEFAULT_PRIOR_A, "prior_b": DEFAULT_PRIOR_B}
+
+
+def _rff_draw(rng, X, lengthscale, amplitude, n_features=4096):
+    W = rng.standard_normal((n_features, X.shape[1])) / lengthscale
+    b = rng.uniform(0.0, 2.0 * np.pi, n_features)
+    return np.sqrt(2.0 * amplitude / n_features) * np.cos(X @ W.T + b).sum(axis=1)
+
+
+def _linear_draw(rng, X, amplitude, offset):
+    w = rng.standard_normal(X.shape[1])
+    w0 = rng.standard_normal()
+    return np.sqrt(amplitude) * (X @ w + np.sqrt(offset) * w0)
+
+
+def _overlap_draw(rng, X, amplitude, lengthscale, n_levels):
+    rho = np.exp(-1.0 / lengthscale)
+    cols = X.shape[1]
+    feats = np.ones((X.shape[0], 1))
+    for c in range(cols):
+        phi = np.zeros((X.shape[0], n_levels + 1))
+        phi[:, 0] = np.sqrt(rho)
+        phi[np.arange(X.shape[0]), 1 + X[:, c].astype(int)] = np.sqrt(1.0 - rho)
+        feats = (feats[:, :, None] * phi[:, None, :]).reshape(X.shape[0], -1)
+    w = rng.standard_normal(feats.shape[1])
+    return np.sqrt(amplitude) * feats @ w
+
+
+def _bernoulli(rng, F):
+    return (rng.uniform(size=F.shape) < 1.0 / (1.0 + np.exp(-F))).astype(np.float64)
+
+
+def gp_classification(N, seed=0, lengthscale=0.5, amplitude=1.0):
+    """GP binary classification: x ~ U[-1, 1]^2, SE kernel (log amplitude, log lengthscale),
+    f_true from the GP at (lengthscale, amplitude), y ~ Bernoulli(sigmoid(f_true)).
+    N = 50 gives d = 52; N = 400 gives d = 402."""
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(-1.0, 1.0, (N, 2))
+    f = _rff_draw(rng, X, lengthscale, amplitude)
+    y = _bernoulli(rng, f)
+    return {"X": X, "y": y, "lik": "bernoulli", "noise_var": 1.0,
+            "kernels": [_kernel("se", (0, 1))], "sample_hypers": True, "u_fixed": None,
+            "f_true": f}
+
+
+def gp_regression(N, seed=0, lengthscale=0.5, amplitude=1.0, noise_var=0.1, sample_hypers=False):
+    """Gaussian-likelihood GP regression on x ~ U[-1, 1]^2 (closed-form posterior when the
+    hyperparameters are held fixed at u_fixed = (log amplitude, log lengthscale))."""
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(-1.0, 1.0, (N, 2))
+    f = _rff_draw(rng, X, lengthscale, amplitude)
+    y = f + np.sqrt(noise_var) * rng.standard_normal(N)
+    u_fixed = None if sample_hypers else np.array([np.log(amplitude), np.log(lengthscale)])
+    return {"X": X, "y": y, "lik": "gaussian", "noise_var": noise_var,
+            "kernels": [_kernel("se", (0, 1))], "sample_hypers": sample_hypers,
+            "u_fixed": u_fixed, "f_true": f}
+
+
+def propensity(N, seed=0, n_kernels=3):
+    """Additive multiple-kernel propensity model (the NMES-like stand-in): 8 covariates,
+    4 continuous ~ N(0,1) (cols 0-3), 2 binary ~ Bernoulli(0.5) (cols 4-5), 2 ordinal uniform on
+    {0..4} (cols 6-7). Kernels, in order: SE on the continuous, linear on the binary,
+    categorical-overlap on the ordinal (the first n_kernels of them). Treatment
+    ~ Bernoulli(sigmoid(sum of the GP draws)) with every amplitude, lengthscale and offset 1."""
+    rng = np.random.default_rng(seed)
+    Xc = rng.standard_normal((N, 4))
+    Xb = (rng.uniform(size=(N, 2)) < 0.5).astype(np.float64)
+    Xo = rng.integers(0, 5, size=(N, 2)).astype(np.float64)
+    X = np.concatenate([Xc, Xb, Xo], axis=1)
+    draws = [_rff_draw(rng, Xc, 1.0, 1.0), _linear_draw(rng, Xb, 1.0, 1.0),
+             _overlap_draw(rng, Xo, 1.0, 1.0, 5)]
+    kernels = [_kernel("se", (0, 1, 2, 3)), _kernel("linear", (4, 5)), _kernel("overlap", (6, 7))]
+    F = np.sum(draws[:n_kernels], axis=0)
+    y = _bernoulli(rng, F)
+    return {"X": X, "y": y, "lik": "bernoulli", "noise_var": 1.0,
+            "kernels": kernels[:n_kernels], "sample_hypers": True, "u_fixed": None, "f_true": F}
+
+
+def uneven_batch(n_problems=128, seed=0, n_min=32, n_max=512):
+    """Problems of uneven dimension: N ~ U{n_min..n_max}, 1-3 kernels (SE, linear, overlap in that
+    order) on the propensity covariates; problem i uses seed + i."""
+    out = []
+    for i in range(n_problems):
+        rng = np.random.default_rng(seed + i)
+        N = int(rng.integers(n_min, n_max + 1))
+        nk = int(rng.integers(1, 4))
+        out.append(propensity(N, seed=seed + i, n_kernels=nk))
+    return out
+
+
+def dims(problem):
+    N = problem["X"].shape[0]
+    n = len(problem["kernels"])
+    return N, n, n * N + (2 * n if problem["sample_hypers"] else 0)
+
+
+def initial_state(problem, n_chains):
+    """f = 0 and u = 0 (amplitude = lengthscale = 1) for every chain, as an (n_chains, d) array."""
+    _, _, d = dims(problem)
+    return np.zeros((n_chains, d))
+
+
+def random_state(problem, n_chains, seed, f_scale=0.5, u_scale=0.3):
+    """Random positions for parity tests: f ~ N(0, f_scale^2), u ~ N(0, u_scale^2)."""
+    rng = np.random.default_rng(seed)
+    _, _, d = dims(problem)
+    q = f_scale * rng.standard_normal((n_chains, d))
+    N, n, _ = dims(problem)
+    if problem["sample_hypers"]:
+        q[:, n * N:] = u_scale * rng.standard_normal((n_chains, 2 * n))
+    return q
+
+
+def random_momentum(problem, n_chains, seed):
+    rng = np.random.default_rng(seed)
+    _, _, d = dims(problem)
+    return rng.standard_normal((n_chains, d))
