@@ -1,0 +1,193 @@
+/*
+ * rmhmc.h - C ABI of the B300 (sm_103a) SoftAbs-RMHMC library for hierarchical Gaussian-process
+ * models (Hayakawa and Asai, "Fast Riemannian-manifold Hamiltonian Monte Carlo for hierarchical
+ * Gaussian-process models").
+ *
+ * Model (Sec. 2.1, Eq. data_likelihood with J = 1, Eq. BMKL, Eq. hpar_prior), dual form:
+ *   F = sum_k f_k, f_k ~ N(0, K_k(u_k)) over the N inputs, y_m | F_m ~ Bernoulli(sigmoid(F_m)) or
+ *   N(F_m, noise_var); u_k = (log c_k, log theta_k) with theta = exp(u) ~ InvGamma(a, b) per
+ *   hyperparameter; tempered posterior P_tau ∝ P(y | F)^tau * prior (Sec. "MC integration for BME").
+ *   Position q = (f_1[0:N], ..., f_n[0:N], u_1[0:2], ..., u_n[0:2]), d = nN + 2n
+ *   (d = nN when the hyperparameters are held fixed).
+ *   Kernels:  SE      k = c (exp(-|x - x'|^2 / (2 theta^2)) + jitter [same sample])
+ *             LINEAR  k = c (x . x' + theta + jitter [same sample])
+ *             OVERLAP k = c (exp(-#mismatching columns / theta) + jitter [same sample])
+ * Sampler (Sec. 2.2, Algorithm 1): Hamiltonian of Eq. Hamiltonian with the soft-absolute metric
+ *   G = Psi g(Lambda) Psi^T of the Hessian H = Psi Lambda Psi^T; generalized leapfrog of
+ *   Eq. leapfrog with n_fp fixed-point iterations for each implicit half; gradient terms through
+ *   the Betancourt contractions W1, W2 (Eq. d3_transform, Eq. Betancourt_formula); eigenvectors
+ *   carried across substeps by warm-started Jacobi (Sec. 2.4).
+ *
+ * Conventions
+ *   - Every pointer argument is owned by the caller. Arguments named *_dev are device pointers
+ *     (e.g. torch CUDA tensors) on the device that was current at rmhmc_init_model; *_host are
+ *     host pointers. Arrays are row-major, float64 unless stated, chain-major (n_chains x ...).
+ *   - The model owns its device copies, per-chain state and workspaces until rmhmc_free_model.
+ *   - Calls enqueue work on the stream given at init and return without synchronising, except
+ *     where stated; read outputs after synchronising that stream.
+ *   - The return value is the call-level status. Per-chain numerical failures (a kernel matrix
+ *     that is not positive definite, a non-finite value, Jacobi that did not converge) never abort
+ *     a call: they are reported per chain in status_dev and, inside rmhmc_sample, make the
+ *     proposal rejected.
+ */
+#ifndef RMHMC_H
+#define RMHMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RMHMC_OK = 0,
+  RMHMC_EINVAL = 1,     /* bad argument (sizes, kinds, null pointers) */
+  RMHMC_ENOMEM = 2,     /* device allocation failed */
+  RMHMC_ECUDA = 3,      /* a CUDA runtime call failed */
+  RMHMC_ENOTCONV = 4,   /* per chain: Jacobi did not reach the tolerance within max_sweeps */
+  RMHMC_ENONFINITE = 5, /* per chain: a non-finite Hamiltonian or position */
+  RMHMC_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+  RMHMC_ENOTIMPL = 7,   /* option not implemented in this build */
+  RMHMC_ENOTPD = 8      /* per chain: a kernel matrix lost positive definiteness (Cholesky) */
+} rmhmc_status;
+
+/* per-chain status bits written to status_dev / chain_status_dev (0 = healthy) */
+#define RMHMC_CHAIN_NOTPD 1
+#define RMHMC_CHAIN_NOTCONV 2
+#define RMHMC_CHAIN_NONFINITE 4
+
+typedef enum { RMHMC_LIK_BERNOULLI_LOGIT = 0, RMHMC_LIK_GAUSSIAN = 1 } rmhmc_lik;
+typedef enum { RMHMC_K_SE = 0, RMHMC_K_LINEAR = 1, RMHMC_K_OVERLAP = 2 } rmhmc_kernel_kind;
+typedef enum { RMHMC_G_COTH = 0, RMHMC_G_SQRT = 1 } rmhmc_gkind;
+typedef enum { RMHMC_FP64 = 0, RMHMC_MIXED = 1 } rmhmc_precision;
+
+#define RMHMC_MAX_COLS 16
+#define RMHMC_MAX_KERNELS 3
+
+/* One GP component (Eq. BMKL): kernel kind, the input columns it reads, the jitter and the
+ * InvGamma(a, b) hyperpriors (Eq. hpar_prior) on (c, theta). */
+typedef struct {
+  int kind;                   /* rmhmc_kernel_kind */
+  int n_cols;                 /* 1..RMHMC_MAX_COLS */
+  int cols[RMHMC_MAX_COLS];   /* column indices into X */
+  double jitter;              /* > 0; K = c (K~ + jitter I) */
+  double prior_a[2];          /* shape of InvGamma on (c, theta) */
+  double prior_b[2];          /* scale of InvGamma on (c, theta) */
+} rmhmc_kernel_desc;
+
+/* The data and model. X, y, kernels and u_fixed are host pointers, read during
+ * rmhmc_init_model only. */
+typedef struct {
+  int N;                        /* number of inputs, 1..1024 */
+  int n_cov;                    /* columns of X */
+  const double* X;              /* host, N x n_cov */
+  const double* y;              /* host, N (0/1 for Bernoulli) */
+  int lik;                      /* rmhmc_lik */
+  double noise_var;             /* Gaussian likelihood variance */
+  int n_kernels;                /* 1..RMHMC_MAX_KERNELS */
+  const rmhmc_kernel_desc* kernels;
+  int sample_hypers;            /* 1: q includes u; 0: u held at u_fixed */
+  const double* u_fixed;        /* host, 2 n_kernels, used when sample_hypers == 0 */
+} rmhmc_model_desc;
+
+/* Integrator and geometry settings. The geometry fields (g_kind, alpha, jacobi_tol, max_sweeps,
+ * reorth_every, precision) must be the same in every call on a model as in rmhmc_set_state. */
+typedef struct {
+  double eps;          /* leapfrog step size (Eq. leapfrog) */
+  int n_leapfrog;      /* leapfrogs per MH proposal (C in Algorithm 1) */
+  int n_fp;            /* fixed-point iterations for each implicit half-step, >= 1 */
+  int g_kind;          /* rmhmc_gkind: g = l coth(alpha l) or sqrt(1/alpha^2 + l^2) */
+  double alpha;        /* soft-abs sharpness (kappa = 1 / alpha for the sqrt map) */
+  double jacobi_tol;   /* zeta: stop when ||offdiag(M)||_F <= zeta ||M||_F (Sec. 2.4) */
+  int max_sweeps;      /* Jacobi sweep limit per eigen-update */
+  int reorth_every;    /* Gram-Schmidt of Psi every this many eigen-updates (Sec. 2.4); 0 = never */
+  int precision;       /* rmhmc_precision; only RMHMC_FP64 in this build */
+} rmhmc_integrator;
+
+typedef struct rmhmc_model rmhmc_model;
+
+/* Validate the description, copy X, y and the kernel descriptors to the device and allocate the
+ * per-chain state for n_chains chains (positions, momenta, eigenvectors, workspaces).
+ * tau_host: n_chains inverse temperatures in (0, 1] (NULL = all 1). cuda_stream: a cudaStream_t
+ * (NULL = legacy default stream). On success *out owns the device memory.
+ * Errors: EINVAL (bad sizes/kinds), ENOMEM, ECUDA. */
+rmhmc_status rmhmc_init_model(const rmhmc_model_desc* desc, int n_chains, const double* tau_host,
+                              void* cuda_stream, rmhmc_model** out);
+
+/* Set every chain's position (q_dev: n_chains x d) and momentum (p_dev: n_chains x d, may be
+ * NULL = zero) and evaluate the geometry there: U, its gradient, Hessian (Eq. d_Hamiltonian
+ * derivatives), a cold-start Jacobi eigendecomposition from Psi = I (Sec. 2.4), and the
+ * third-derivative operator of Sec. 2.3. Errors: EINVAL, ECUDA. */
+rmhmc_status rmhmc_set_state(rmhmc_model* m, const rmhmc_integrator* integ, const double* q_dev,
+                             const double* p_dev);
+
+/* Advance every chain by n_steps generalized leapfrogs (Eq. leapfrog) from the model's state,
+ * then copy the state out. p_in_dev (n_chains x d, may be NULL): momenta to start from instead of
+ * the model's current ones (the geometry depends on q only, so nothing is recomputed). Outputs:
+ * q_dev, p_dev (n_chains x d), H_dev (n_chains, Eq. Hamiltonian at the end), status_dev
+ * (n_chains ints, RMHMC_CHAIN_* bits); each may be NULL. Errors: EINVAL, ECUDA. */
+rmhmc_status rmhmc_leapfrog(rmhmc_model* m, const rmhmc_integrator* integ, int n_steps,
+                            const double* p_in_dev, double* q_dev, double* p_dev, double* H_dev,
+                            int* status_dev);
+
+/* Algorithm 1 for n_burn + n_iter iterations from the model's state: momentum p = G^{1/2} z with
+ * z from Philox4x64-10 (key (seed, chain), counter (block, iteration, 0, 0)), n_leapfrog
+ * leapfrogs, Metropolis-Hastings with r from counter (0, iteration, 1, 0) (accept iff
+ * log r < H0 - H1). Iteration numbers continue across calls on the same model. The last n_iter
+ * iterations are recorded: q_samples_dev (n_iter x n_chains x d), logp_dev (n_iter x n_chains,
+ * log P_tau(q) = -U(q)), accept_dev (n_iter x n_chains ints), sweeps_dev (n_iter x n_chains ints,
+ * Jacobi sweeps in that iteration's trajectory), chain_status_dev (n_chains ints, OR of the
+ * RMHMC_CHAIN_* bits seen). Any output pointer may be NULL. The host enqueues iteration by
+ * iteration; the call returns after enqueueing. Errors: EINVAL, ECUDA. */
+rmhmc_status rmhmc_sample(rmhmc_model* m, const rmhmc_integrator* integ, int n_iter, int n_burn,
+                          uint64_t seed, double* q_samples_dev, double* logp_dev, int* accept_dev,
+                          int* sweeps_dev, int* chain_status_dev);
+
+/* Copy out the geometry at the current state (for checks and diagnostics): U_dev (n_chains),
+ * dU_dev (n_chains x d), hess_dev (n_chains x d x d, Hessian of U), lam_dev (n_chains x d,
+ * eigenvalues in the solver's order), G_dev (n_chains x d x d, the soft-abs metric), sweeps_dev
+ * (n_chains ints, sweeps of the last eigen-update). Any pointer may be NULL. */
+rmhmc_status rmhmc_geometry(rmhmc_model* m, double* U_dev, double* dU_dev, double* hess_dev,
+                            double* lam_dev, double* G_dev, int* sweeps_dev);
+
+/* At the current position and a given momentum p_dev (n_chains x d): dHdq_dev = dH/dq
+ * (dU + 1/2 tr(W2 dH_i) - 1/2 tr(W1 dH_i), Eq. Betancourt_formula with the sign of the derivative
+ * of Eq. Hamiltonian), Ginv_p_dev = G^-1 p = dH/dp, H_dev = Eq. Hamiltonian. NULL skips an output. */
+rmhmc_status rmhmc_hamiltonian_grad(rmhmc_model* m, const double* p_dev, double* dHdq_dev,
+                                    double* Ginv_p_dev, double* H_dev);
+
+/* Kernel-level profile (for measurement; not part of the method). While enabled, every kernel
+ * launch of the model is bracketed by CUDA events on the model's stream and counted in one of
+ * RMHMC_PROF_NCAT categories (names from rmhmc_profile_category), with the algorithmic FLOPs of
+ * the work it must do (GEMM 2mnk on the unpadded sizes, halved for symmetric outputs; Cholesky
+ * and triangular inverse N^3/3; Jacobi 8 d^3 per sweep actually performed). rmhmc_profile(m, 1)
+ * resets and starts, rmhmc_profile(m, 0) stops. rmhmc_profile_read synchronises the stream and
+ * writes per-category milliseconds, FLOPs and launch counts (host arrays of RMHMC_PROF_NCAT). */
+#define RMHMC_PROF_NCAT 8
+rmhmc_status rmhmc_profile(rmhmc_model* m, int enable);
+rmhmc_status rmhmc_profile_read(rmhmc_model* m, double* ms_host, double* flops_host,
+                                long long* launches_host);
+const char* rmhmc_profile_category(int i);
+
+/* Measure this GPU's FP64 FMA throughput (a roofline denominator, not part of the method): runs a
+ * dependent-chain DFMA kernel on every SM for about ms_target milliseconds on cuda_stream and writes
+ * the achieved TFLOP/s (2 flops per FMA) to *tflops_host. Synchronises the stream. */
+rmhmc_status rmhmc_fp64_peak(void* cuda_stream, int ms_target, double* tflops_host);
+
+/* Dimension d of q, and number of chains. */
+int rmhmc_dim(const rmhmc_model* m);
+int rmhmc_n_chains(const rmhmc_model* m);
+
+/* Release the model's device memory (synchronises its stream first). NULL is a no-op. */
+void rmhmc_free_model(rmhmc_model* m);
+
+/* Static string for a status code. */
+const char* rmhmc_status_string(rmhmc_status s);
+
+/* Library build identifier, e.g. "rmhmc sm_103a fp64". */
+const char* rmhmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RMHMC_H */

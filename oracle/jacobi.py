@@ -3,8 +3,11 @@ Sec. 2.4 / Sec. 3.1, never for the oracle's own geometry, which uses LAPACK eigh
 
 Sec. 2.4: with Psi from the previous point, M = Psi^T H Psi is diagonal up to O(eps); cyclic Jacobi
 drives its off-diagonal part to the tolerance zeta, M = Q diag(lambda) Q^T, and Psi <- Psi Q.
-Stopping rule: sweeps continue while ||offdiag(M)||_F > zeta ||M||_F (checked before every sweep,
-so an already-diagonal M takes 0 sweeps), up to max_sweeps.
+Stopping rule (the tolerance zeta is not defined further in Sec. 2.4; relative reading): sweeps
+continue while some |m_jl| > max(zeta sqrt(|m_jj m_ll|), 4 u ||M||_F) (u = 2^-53; the floor is
+the rounding level rotations leave behind), checked before every sweep (an already diagonal M
+takes 0 sweeps), up to max_sweeps; the Frobenius reading ||offdiag||_F > zeta ||M||_F is
+available as rule='frobenius'.
 Each rotation is the symmetric 2x2 Schur decomposition (Golub and Van Loan, "Matrix
 Computations", Sec. 8.5): for the pair (j, l) with M_jl != 0,
   theta = (M_ll - M_jj) / (2 M_jl),  t = sign(theta) / (|theta| + sqrt(1 + theta^2)),
@@ -20,15 +23,35 @@ def offdiag_norm(M):
     return float(np.sqrt(np.sum(off * off)))
 
 
-def jacobi_eigh(H, Psi0=None, tol=1e-13, max_sweeps=30):
-    """Returns (lam, Psi, sweeps). Psi0 = None is the cold start Psi0 = I."""
+U_ROUND = 2.0 ** -53
+
+
+def relative_offdiag(M, tol):
+    """max over j != l of |m_jl| / max(tol sqrt(|m_jj m_ll|), 4 u ||M||_F); <= 1 is converged."""
+    d = np.abs(np.diag(M))
+    floor = 4.0 * U_ROUND * np.linalg.norm(M)
+    den = np.maximum(tol * np.sqrt(np.outer(d, d)), max(floor, 1e-300))
+    R = np.abs(M) / den
+    np.fill_diagonal(R, 0.0)
+    return float(R.max()) if R.size else 0.0
+
+
+def jacobi_eigh(H, Psi0=None, tol=1e-13, max_sweeps=30, rule="relative"):
+    """Returns (lam, Psi, sweeps). Psi0 = None is the cold start Psi0 = I.
+    rule 'relative': continue while some |m_jl| > max(tol sqrt(|m_jj m_ll|), 4 u ||M||_F) (the
+    rule the CUDA path uses); rule 'frobenius': continue while ||offdiag(M)||_F > tol ||M||_F."""
     H = np.asarray(H, dtype=np.float64)
     d = H.shape[0]
     Psi = np.eye(d) if Psi0 is None else np.array(Psi0, dtype=np.float64)
     M = Psi.T @ H @ Psi
     M = 0.5 * (M + M.T)
     sweeps = 0
-    while offdiag_norm(M) > tol * np.linalg.norm(M) and sweeps < max_sweeps:
+    def unconverged(M):
+        if rule == "frobenius":
+            return offdiag_norm(M) > tol * np.linalg.norm(M)
+        return relative_offdiag(M, tol) > 1.0
+
+    while unconverged(M) and sweeps < max_sweeps:
         for j in range(d - 1):
             for l in range(j + 1, d):
                 mjl = M[j, l]

@@ -10,7 +10,7 @@ Coordinates q = (f_1[0:N], ..., f_n[0:N], u_1[0:2], ..., u_n[0:2]); d = nN + 2n,
 hyperparameters are held fixed.
 
 U(q) = tau * sum_m l(F_m, y_m)
-       + sum_k [ 1/2 f_k^T K_k^-1 f_k + 1/2 log|K_k| + N/2 log 2pi ]
+       + sum_k [ 1/2 f_k^T K_k^-1 f_k + 1/2 log|K_k| + N/2 log 2pi ]     (f^T K^-1 f = |L^-1 f|^2)
        - sum_{k,h} log p(u_kh),      log p(u) = a log b - lgamma(a) - a u - b exp(-u)
 
 Likelihoods (exact negative log likelihoods):
@@ -22,10 +22,12 @@ coordinate); stacking all slices gives the full tensor the Betancourt formula co
 (Eq. Betancourt_formula). The hyperparameter terms the paper omits in Sec. 2.3 are written out
 here in full.
 """
+from contextlib import contextmanager
 from dataclasses import dataclass, field
 from math import lgamma, log, pi
 
 import numpy as np
+import scipy.linalg as sla
 
 from .kernels import dK, kernel_derivs
 
@@ -68,6 +70,17 @@ class GPModel:
         return self.n * self.N + self.P
 
 
+def from_problem(problem):
+    """GPModel from a workload dict (keys X, y, lik, noise_var, kernels, sample_hypers, u_fixed)."""
+    ks = [KernelSpec(kind=k["kind"], cols=tuple(k["cols"]), jitter=k["jitter"],
+                     prior_a=tuple(k["prior_a"]), prior_b=tuple(k["prior_b"]))
+          for k in problem["kernels"]]
+    return GPModel(X=np.asarray(problem["X"], dtype=np.float64),
+                   y=np.asarray(problem["y"], dtype=np.float64), kernels=ks,
+                   lik=problem["lik"], noise_var=problem["noise_var"],
+                   sample_hypers=problem["sample_hypers"], u_fixed=problem["u_fixed"])
+
+
 def split(model, q):
     """Latent blocks f (n x N) and hyperparameters u (n x 2)."""
     q = np.asarray(q, dtype=np.float64)
@@ -102,6 +115,22 @@ def lik_derivs(model, F):
     raise ValueError(model.lik)
 
 
+_INVERSE = {"method": "lu"}
+
+
+@contextmanager
+def inverse_method(method):
+    """Evaluate K^-1 and alpha with LAPACK's LU ('lu', the default) or Cholesky ('cholesky')
+    routines. Both are backward stable; their difference measures how far cond(K) lets two valid
+    FP64 evaluations of the same quantity drift apart (used to calibrate parity tolerances)."""
+    old = _INVERSE["method"]
+    _INVERSE["method"] = method
+    try:
+        yield
+    finally:
+        _INVERSE["method"] = old
+
+
 class KernelState:
     """Per-kernel quantities at q: K and its u_1-derivatives, K^-1, alpha = K^-1 f."""
 
@@ -109,10 +138,19 @@ class KernelState:
         self.mats = kernel_derivs(spec.kind, Xk, u, spec.jitter)
         K = self.mats[0]
         self.L = np.linalg.cholesky(K)
-        self.Kinv = np.linalg.inv(K)
+        if _INVERSE["method"] == "cholesky":
+            cf = (self.L, True)
+            self.Kinv = sla.cho_solve(cf, np.eye(len(f)), check_finite=False)
+            self.alpha = sla.cho_solve(cf, f, check_finite=False)
+        else:
+            self.Kinv = np.linalg.inv(K)
+            self.alpha = np.linalg.solve(K, f)
         self.Kinv = 0.5 * (self.Kinv + self.Kinv.T)
-        self.alpha = np.linalg.solve(K, f)
         self.logdet = 2.0 * np.sum(np.log(np.diag(self.L)))
+        # f^T K^-1 f = |L^-1 f|^2 by forward substitution (backward stable; the product f . alpha
+        # loses ~cond(K) u relative accuracy to cancellation)
+        t = sla.solve_triangular(self.L, f, lower=True, check_finite=False)
+        self.quad = float(t @ t)
 
     def d(self, *idx):
         return dK(self.mats, idx)
@@ -139,7 +177,7 @@ def potential(model, q, tau=1.0):
     l0, _, _, _ = lik_derivs(model, F)
     U = tau * np.sum(l0)
     for k, s in enumerate(st):
-        U += 0.5 * f[k] @ s.alpha + 0.5 * s.logdet + 0.5 * model.N * LOG2PI
+        U += 0.5 * s.quad + 0.5 * s.logdet + 0.5 * model.N * LOG2PI
     if model.sample_hypers:
         for k, spec in enumerate(model.kernels):
             for h in range(2):

@@ -1,0 +1,467 @@
+// Warm-started ("dynamically programmed") Jacobi eigendecomposition, Sec. 2.4.
+//
+// Given Psi from the previous point, M = Psi^T H Psi is nearly diagonal; cyclic Jacobi drives its
+// off-diagonal part below the tolerance zeta and the accumulated rotations update Psi <- Psi Q. This is
+// the parallel (round-robin) block form of cyclic Jacobi: the indices are cut into nb blocks of 8;
+// in each of the nb - 1 rounds of a sweep the blocks are paired by the circle method and every
+// pair's 16 x 16 diagonal sub-problem is diagonalised exactly by an inner cyclic Jacobi (one warp,
+// shared memory), giving an orthogonal V_P; then all pairs are applied at once as the two-sided
+// block transform M[P, Q] <- V_P^T M[P, Q] V_Q (only P <= Q is computed; the mirror is written),
+// and Psi^T[P, :] <- V_P^T Psi^T[P, :]. One thread-block cluster works on one chain; the rounds
+// are separated by hardware cluster barriers, so the whole eigen-update (all sweeps) is one launch
+// with no host round trip. M and Psi^T live in global memory (they stay in the 126 MB L2 for the
+// batch sizes used); accesses are 64-byte row segments, and loads bypass L1 (ld.global.cg) so that
+// writes by other CTAs of the cluster are seen after each barrier.
+//
+// Stopping rule (relative per pair, with a rounding floor): sweeps continue while some
+// |m_jl| > max(zeta sqrt(|m_jj m_ll|), 4 u ||M||_F) (checked before each sweep, so an unchanged
+// basis costs 0 sweeps), up to max_sweeps; hitting the limit marks the chain RMHMC_CHAIN_NOTCONV.
+// A Frobenius rule ||offdiag||_F <= zeta ||M||_F would leave couplings of ~zeta ||H|| between the
+// small eigenpairs, which dominate G^-1; the floor stops the rule from chasing rounding noise
+// (rotations against entries of size ||M|| leave couplings of ~u ||M|| behind).
+// Each 2 x 2 rotation is the symmetric Schur decomposition (Golub and Van Loan, Matrix
+// Computations, Sec. 8.5).
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rmhmc {
+
+namespace {
+
+constexpr int NW = 8;            // warps per CTA
+constexpr int SB = kJacSB;       // 16
+constexpr int BL = kJacBlk;      // 8
+constexpr int SBP = SB + 1;
+constexpr int MAX_INNER = 8;
+constexpr int WARP_SMEM = 4 * SB * SBP;  // doubles per warp
+
+__device__ __forceinline__ void circle_pair(int r, int p, int nb, int& I, int& J) {
+  const int m1 = nb - 1;
+  if (p == 0) {
+    I = r;
+    J = nb - 1;
+  } else {
+    I = (r + p) % m1;
+    J = (r - p + m1) % m1;
+  }
+}
+
+__device__ __forceinline__ int gidx(int I, int J, int t) { return t < BL ? I * BL + t : J * BL + (t - BL); }
+
+// Symmetric Schur rotation zeroing A_ab: returns (c, s) with J = [[c, s], [-s, c]] on (a, b).
+__device__ __forceinline__ void schur2(double app, double aqq, double apq, double& c, double& s) {
+  if (fabs(apq) < 1e-300) {
+    c = 1.0;
+    s = 0.0;
+    return;
+  }
+  const double theta = (aqq - app) / (2.0 * apq);
+  double t;
+  if (fabs(theta) > 1e150) t = 0.5 / theta;
+  else t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = t * c;
+}
+
+// Inner exact solve of one 16 x 16 sub-problem by a single warp: A <- V^T A V diagonal. Returns
+// false when the block already met the tolerance (then V = I exactly and A is unchanged).
+__device__ bool inner_solve(double* A, double* V, double* cs, double tol2, double floor2) {
+  const int lane = threadIdx.x & 31;
+  bool rotated = false;
+  for (int e = lane; e < SB * SB; e += 32) V[(e / SB) * SBP + e % SB] = (e / SB == e % SB) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int it = 0; it < MAX_INNER; ++it) {
+    double crit = 0.0;
+    for (int e = lane; e < SB * SB; e += 32) {
+      const int i = e / SB, j = e % SB;
+      const double v = A[i * SBP + j];
+      if (i != j && v != 0.0)
+        crit = fmax(crit, v * v / fmax(tol2 * fabs(A[i * SBP + i] * A[j * SBP + j]), fmax(floor2, 1e-300)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) crit = fmax(crit, __shfl_xor_sync(0xffffffffu, crit, o));
+    if (!(crit > 1.0)) break;
+    rotated = true;
+    for (int r = 0; r < SB - 1; ++r) {
+      if (lane < SB / 2) {
+        int a, b;
+        circle_pair(r, lane, SB, a, b);
+        double c, s;
+        schur2(A[a * SBP + a], A[b * SBP + b], A[a * SBP + b], c, s);
+        cs[2 * lane] = c;
+        cs[2 * lane + 1] = s;
+      }
+      __syncwarp();
+      // rows: A <- J^T A
+      for (int task = lane; task < (SB / 2) * SB; task += 32) {
+        const int pr = task / SB, u = task % SB;
+        int a, b;
+        circle_pair(r, pr, SB, a, b);
+        const double c = cs[2 * pr], s = cs[2 * pr + 1];
+        const double xa = A[a * SBP + u], xb = A[b * SBP + u];
+        A[a * SBP + u] = c * xa - s * xb;
+        A[b * SBP + u] = s * xa + c * xb;
+      }
+      __syncwarp();
+      // columns: A <- A J, and V <- V J
+      for (int task = lane; task < (SB / 2) * SB; task += 32) {
+        const int pr = task / SB, t = task % SB;
+        int a, b;
+        circle_pair(r, pr, SB, a, b);
+        const double c = cs[2 * pr], s = cs[2 * pr + 1];
+        const double xa = A[t * SBP + a], xb = A[t * SBP + b];
+        A[t * SBP + a] = c * xa - s * xb;
+        A[t * SBP + b] = s * xa + c * xb;
+        const double va = V[t * SBP + a], vb = V[t * SBP + b];
+        V[t * SBP + a] = c * va - s * vb;
+        V[t * SBP + b] = s * va + c * vb;
+      }
+      __syncwarp();
+      if (lane < SB / 2) {
+        int a, b;
+        circle_pair(r, lane, SB, a, b);
+        if (cs[2 * lane + 1] != 0.0) {
+          A[a * SBP + b] = 0.0;
+          A[b * SBP + a] = 0.0;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  return rotated;
+}
+
+// Y = Vp^T X Vq, all 16 x 16 in shared memory (a null Vp or Vq stands for the identity); T is
+// scratch.
+__device__ __forceinline__ void tile_transform(const double* X, const double* Vp, const double* Vq,
+                                               double* T, double* Y) {
+  const int lane = threadIdx.x & 31;
+  const int t = lane >> 1, u0 = (lane & 1) * 8;
+  const double* src = X;
+  if (Vq) {
+    double acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = 0.0;
+#pragma unroll 4
+    for (int v = 0; v < SB; ++v) {
+      const double x = X[t * SBP + v];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = fma(x, Vq[v * SBP + u0 + j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) T[t * SBP + u0 + j] = acc[j];
+    __syncwarp();
+    src = T;
+  }
+  double acc[8];
+  if (Vp) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = 0.0;
+#pragma unroll 4
+    for (int v = 0; v < SB; ++v) {
+      const double p = Vp[v * SBP + t];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = fma(p, src[v * SBP + u0 + j], acc[j]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = src[t * SBP + u0 + j];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) Y[t * SBP + u0 + j] = acc[j];
+  __syncwarp();
+}
+
+__device__ __forceinline__ void load_v(double* dst, const double* src) {
+  const int lane = threadIdx.x & 31;
+  for (int e = lane; e < SB * SB; e += 32) dst[(e / SB) * SBP + e % SB] = __ldcg(src + e);
+}
+
+__global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, double* __restrict__ Pb,
+                                                   double* __restrict__ lamb, int dp, double tol,
+                                                   int max_sweeps, int* __restrict__ status,
+                                                   int* __restrict__ sweeps_out,
+                                                   int* __restrict__ sweeps_acc,
+                                                   double* __restrict__ Vb, double* __restrict__ Db,
+                                                   double* __restrict__ slotsb,
+                                                   int* __restrict__ flagsb) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int chain = blockIdx.x / C;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nb = dp / BL, np = nb / 2;
+  if (status[chain] != 0) {
+    if (rank == 0 && tid == 0) sweeps_out[chain] = 0;
+    return;  // uniform for the whole cluster
+  }
+  double* M = Mb + (long long)chain * dp * dp;
+  double* P = Pb + (long long)chain * dp * dp;
+  double* V = Vb + (long long)chain * np * SB * SB;
+  double* D = Db + (long long)chain * np * SB * SB;
+  double* slots = slotsb + (long long)chain * 64;
+  int* flags = flagsb + (long long)chain * np;
+  extern __shared__ double smem[];
+  double* ws = smem + warp * WARP_SMEM;
+  double* X = ws;
+  double* Tt = ws + SB * SBP;
+  double* Va = ws + 2 * SB * SBP;
+  double* Vq = ws + 3 * SB * SBP;
+  __shared__ double red[2][NW];
+  __shared__ double cs[NW][SB];
+
+  const int gw = rank * NW + warp, nwt = C * NW;
+  const int nMjobs = np * (np + 1) / 2, nct = dp / SB;
+  int sweeps = 0;
+  bool converged = false;
+  for (;;) {
+    // ---- convergence test. Pass 1: ||M||_F^2. Pass 2: max over j != l of
+    //      m_jl^2 / max(zeta^2 |m_jj m_ll|, floor^2), floor = 4 u ||M||_F (rounding level)
+    double tot = 0.0;
+    for (long long e = (long long)rank * blockDim.x + tid; e < (long long)dp * dp;
+         e += (long long)C * blockDim.x) {
+      const double v = __ldcg(M + e);
+      tot = fma(v, v, tot);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) red[0][warp] = tot;
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0;
+      for (int w = 0; w < NW; ++w) a += red[0][w];
+      __stcg(slots + (sweeps & 1) * 32 + 2 * rank, a);
+    }
+    cluster.sync();
+    tot = 0.0;
+    for (int r = 0; r < C; ++r) tot += __ldcg(slots + (sweeps & 1) * 32 + 2 * r);
+    const double floor2 = 16.0 * 1.2325951644078310e-32 * tot;  // (4 u)^2 ||M||_F^2, u = 2^-53
+    double crit = 0.0, bad = isfinite(tot) ? 0.0 : 1.0;
+    for (long long e = (long long)rank * blockDim.x + tid; e < (long long)dp * dp;
+         e += (long long)C * blockDim.x) {
+      const int j = (int)(e / dp), l = (int)(e % dp);
+      if (j == l) continue;
+      const double v = __ldcg(M + e);
+      if (v == 0.0) continue;
+      const double den = fabs(__ldcg(M + (long long)j * dp + j) * __ldcg(M + (long long)l * dp + l));
+      const double r = v * v / fmax(tol * tol * den, fmax(floor2, 1e-300));
+      if (!(r <= 1e308)) bad = 1.0;
+      crit = fmax(crit, r);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      crit = fmax(crit, __shfl_xor_sync(0xffffffffu, crit, o));
+      bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, o));
+    }
+    __syncthreads();
+    if (lane == 0) { red[0][warp] = crit; red[1][warp] = bad; }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < NW; ++w) { a = fmax(a, red[0][w]); b = fmax(b, red[1][w]); }
+      __stcg(slots + (sweeps & 1) * 32 + 16 + 2 * rank, a);
+      __stcg(slots + (sweeps & 1) * 32 + 16 + 2 * rank + 1, b);
+    }
+    cluster.sync();
+    crit = 0.0;
+    bad = 0.0;
+    for (int r = 0; r < C; ++r) {
+      crit = fmax(crit, __ldcg(slots + (sweeps & 1) * 32 + 16 + 2 * r));
+      bad = fmax(bad, __ldcg(slots + (sweeps & 1) * 32 + 16 + 2 * r + 1));
+    }
+    if (bad != 0.0) break;
+    if (crit <= 1.0) { converged = true; break; }
+    if (sweeps >= max_sweeps) break;
+    const double itol2 = 1e-4 * tol * tol;  // inner problems are solved 100x tighter
+
+    for (int r = 0; r < nb - 1; ++r) {
+      // ---- phase 1: exact 16 x 16 solves, one warp per block pair
+      for (int p = gw; p < np; p += nwt) {
+        int I, J;
+        circle_pair(r, p, nb, I, J);
+        for (int e = lane; e < SB * SB; e += 32) {
+          const int a = e / SB, b = e % SB;
+          X[a * SBP + b] = __ldcg(M + (long long)gidx(I, J, a) * dp + gidx(I, J, b));
+        }
+        __syncwarp();
+        const bool rot = inner_solve(X, Va, cs[warp], itol2, floor2);
+        if (rot) {
+          for (int e = lane; e < SB * SB; e += 32) {
+            const int a = e / SB, b = e % SB;
+            __stcg(V + (long long)p * SB * SB + e, Va[a * SBP + b]);
+            __stcg(D + (long long)p * SB * SB + e, X[a * SBP + b]);
+          }
+        }
+        if (lane == 0) __stcg(flags + p, rot ? 1 : 0);
+        __syncwarp();
+      }
+      cluster.sync();
+      // ---- phase 2: apply all rotations to M (P <= Q tiles) and to the rows of Psi^T
+      for (int job = gw; job < nMjobs + np * nct; job += nwt) {
+        if (job < nMjobs) {
+          int Q = (int)((sqrt(8.0 * job + 1.0) - 1.0) * 0.5);
+          while (Q * (Q + 1) / 2 > job) --Q;
+          while ((Q + 1) * (Q + 2) / 2 <= job) ++Q;
+          const int Pp = job - Q * (Q + 1) / 2;
+          const int fP = __ldcg(flags + Pp), fQ = __ldcg(flags + Q);
+          if (!fP && !fQ) continue;  // both rotations are exactly I: the tile is unchanged
+          int I1, J1, I2, J2;
+          circle_pair(r, Pp, nb, I1, J1);
+          circle_pair(r, Q, nb, I2, J2);
+          if (Pp == Q) {
+            for (int e = lane; e < SB * SB; e += 32) {
+              const int a = e / SB, b = e % SB;
+              __stcg(M + (long long)gidx(I1, J1, a) * dp + gidx(I1, J1, b),
+                     __ldcg(D + (long long)Pp * SB * SB + e));
+            }
+          } else {
+            for (int e = lane; e < SB * SB; e += 32) {
+              const int a = e / SB, b = e % SB;
+              X[a * SBP + b] = __ldcg(M + (long long)gidx(I1, J1, a) * dp + gidx(I2, J2, b));
+            }
+            if (fP) load_v(Va, V + (long long)Pp * SB * SB);
+            if (fQ) load_v(Vq, V + (long long)Q * SB * SB);
+            __syncwarp();
+            tile_transform(X, fP ? Va : nullptr, fQ ? Vq : nullptr, Tt, X);
+            const int t = lane >> 1, u0 = (lane & 1) * 8;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              __stcg(M + (long long)gidx(I1, J1, t) * dp + gidx(I2, J2, u0 + j), X[t * SBP + u0 + j]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              __stcg(M + (long long)gidx(I2, J2, t) * dp + gidx(I1, J1, u0 + j), X[(u0 + j) * SBP + t]);
+          }
+          __syncwarp();
+        } else {
+          const int pj = job - nMjobs;
+          const int Pp = pj / nct, ct = pj % nct;
+          if (!__ldcg(flags + Pp)) continue;
+          int I1, J1;
+          circle_pair(r, Pp, nb, I1, J1);
+          for (int e = lane; e < SB * SB; e += 32) {
+            const int a = e / SB, b = e % SB;
+            X[a * SBP + b] = __ldcg(P + (long long)gidx(I1, J1, a) * dp + ct * SB + b);
+          }
+          load_v(Va, V + (long long)Pp * SB * SB);
+          __syncwarp();
+          tile_transform(X, Va, nullptr, Tt, X);
+          const int t = lane >> 1, u0 = (lane & 1) * 8;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            __stcg(P + (long long)gidx(I1, J1, t) * dp + ct * SB + u0 + j, X[t * SBP + u0 + j]);
+          __syncwarp();
+        }
+      }
+      cluster.sync();
+    }
+    ++sweeps;
+  }
+  for (int i = rank * blockDim.x + tid; i < dp; i += C * blockDim.x)
+    lamb[(long long)chain * dp + i] = __ldcg(M + (long long)i * dp + i);
+  if (rank == 0 && tid == 0) {
+    sweeps_out[chain] = sweeps;
+    if (sweeps_acc) sweeps_acc[chain] += sweeps;
+    if (!converged) atomicOr(&status[chain], RMHMC_CHAIN_NOTCONV);
+  }
+}
+
+// Right-looking modified Gram-Schmidt on the first d rows of Psi^T, one cluster per chain:
+// at step j every later row k loses its component along row j (using ||row_j||^2, so row j need
+// not be normalised yet); the rows are normalised at the end.
+__global__ void __launch_bounds__(NW * 32) k_mgs(double* __restrict__ Pb, int dp, int d,
+                                                const int* __restrict__ eig_count, int every) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int chain = blockIdx.x / C;
+  const int cnt = eig_count[chain];
+  if (every <= 0 || cnt <= 0 || (cnt % every) != 0) return;  // uniform per cluster
+  double* P = Pb + (long long)chain * dp * dp;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int gw = rank * NW + warp, nwt = C * NW;
+  for (int j = 0; j + 1 < d; ++j) {
+    const double* rj = P + (long long)j * dp;
+    for (int k = j + 1 + gw; k < d; k += nwt) {
+      double* rk = P + (long long)k * dp;
+      double nj = 0.0, dot = 0.0;
+      for (int c = lane; c < dp; c += 32) {
+        const double a = __ldcg(rj + c);
+        nj += a * a;
+        dot += a * __ldcg(rk + c);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        nj += __shfl_xor_sync(0xffffffffu, nj, o);
+        dot += __shfl_xor_sync(0xffffffffu, dot, o);
+      }
+      const double coef = dot / nj;
+      for (int c = lane; c < dp; c += 32) __stcg(rk + c, __ldcg(rk + c) - coef * __ldcg(rj + c));
+    }
+    cluster.sync();
+  }
+  for (int k = gw; k < d; k += nwt) {
+    double* rk = P + (long long)k * dp;
+    double nk = 0.0;
+    for (int c = lane; c < dp; c += 32) {
+      const double a = __ldcg(rk + c);
+      nk += a * a;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nk += __shfl_xor_sync(0xffffffffu, nk, o);
+    const double inv = 1.0 / sqrt(nk);
+    for (int c = lane; c < dp; c += 32) __stcg(rk + c, __ldcg(rk + c) * inv);
+  }
+}
+
+template <typename K, typename... Args>
+cudaError_t launch_cluster(K kernel, int n_chains, int C, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n_chains * C, 1, 1);
+  cfg.blockDim = dim3(NW * 32, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+}  // namespace
+
+int jacobi_cluster_size(int n_chains) {
+  if (n_chains <= 18) return 8;
+  if (n_chains <= 37) return 4;
+  if (n_chains <= 74) return 2;
+  return 1;
+}
+
+void jacobi_f64(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,
+                double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
+                JacobiWork w, int cluster) {
+  (void)d;
+  const size_t smem = (size_t)NW * WARP_SMEM * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  launch_cluster(k_jacobi, n_chains, cluster, smem, s, M, PsiT, lam, dp, tol, max_sweeps, status,
+                 sweeps_out, sweeps_acc, w.V, w.D, w.slots, w.flags);
+}
+
+void mgs_rows_f64(cudaStream_t s, double* PsiT, int dp, int d, int n_chains, const int* eig_count,
+                  int every, int cluster) {
+  if (every <= 0) return;
+  launch_cluster(k_mgs, n_chains, cluster, 0, s, PsiT, dp, d, eig_count, every);
+}
+
+}  // namespace rmhmc

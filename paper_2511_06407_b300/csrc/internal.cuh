@@ -1,0 +1,101 @@
+// Internal declarations shared by the CUDA translation units of librmhmc (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rmhmc.h"
+
+namespace rmhmc {
+
+constexpr int kMaxN = 1024;       // inputs per problem (FP64 path)
+constexpr int kJacBlk = 8;        // Jacobi index block b; a rotated pair of blocks is 16 x 16
+constexpr int kJacSB = 2 * kJacBlk;
+constexpr int kStatSlots = 32;    // per (chain, kernel) scalar slots
+
+// per (chain, kernel) scalar slot indices (see model kernels)
+enum Stat {
+  ST_LOGDET = 0,  // log|K|
+  ST_FA,          // f . alpha
+  ST_AB,          // alpha . beta          (alpha^T D1 alpha)
+  ST_AE2,         // alpha . eps2          (alpha^T D2 alpha)
+  ST_AE3,         // alpha . eps3          (alpha^T D3 alpha)
+  ST_AD,          // alpha . delta         (alpha^T D1 K^-1 D1 alpha ... via delta = D1 gamma)
+  ST_GB,          // gamma . beta
+  ST_GD,          // gamma . delta
+  ST_GE2,         // gamma . eps2
+  ST_TRS,         // tr(S)     = <K^-1, D1>
+  ST_TRS2,        // tr(S^2)
+  ST_TRS3,        // tr(S^3)
+  ST_TRR2,        // <K^-1, D2>
+  ST_TRR3,        // <K^-1, D3>
+  ST_TRSR2,       // <A1, D2> = tr(K^-1 D1 K^-1 D2)
+  ST_COUNT
+};
+
+struct KernelDev {
+  int kind;
+  int n_cols;
+  int cols[RMHMC_MAX_COLS];
+  double jitter;
+  double a[2];
+  double b[2];
+};
+
+struct ModelDev {
+  int N, n, P, d, dp, ncov, lik, sample_hypers, n_chains;
+  double noise_var;
+  const double* X;        // N x ncov
+  const double* y;        // N
+  const double* u_fixed;  // 2n
+  const double* tau;      // n_chains
+  KernelDev k[RMHMC_MAX_KERNELS];
+};
+
+struct GeomDev {
+  int g_kind;
+  double alpha;
+};
+
+// ---------------------------------------------------------------- linear algebra (linalg.cu)
+// Batched FP64 GEMM: C_b = alpha op(A_b) op(B_b) + beta C_b, row-major. op(A) is m x k, op(B) is
+// k x n. sym: m == n and the product is symmetric: only tiles on/below the diagonal are computed
+// and mirrored. tri: A and B are op()-views of lower-triangular factors with (op(A) op(B))_ij
+// summing over k >= max(i, j) only (used for K^-1 = L^-T L^-1).
+void gemm_f64(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
+              int lda, long long sA, const double* B, int ldb, long long sB, double beta, double* C,
+              int ldc, long long sC, int batch, bool sym, bool tri);
+// In-place lower Cholesky of batch N x N matrices (row-major, ld = N); writes log|K| to
+// logdet[b * logdet_stride] and sets status bit RMHMC_CHAIN_NOTPD in status[b / per_chain].
+void cholesky_f64(cudaStream_t s, double* A, int N, int batch, double* logdet, int logdet_stride,
+                  int* status, int per_chain);
+// t = L^-1 f and a = L^-T t (= K^-1 f) by substitution, per (batch) factor L.
+void cholsolve_f64(cudaStream_t s, const double* L, const double* f, double* t, double* a, int N,
+                   int batch);
+// X = L^-1 (lower triangular) for batch matrices.
+void trinv_lower_f64(cudaStream_t s, const double* L, double* X, int N, int batch);
+// y_b = op(A_b) x_b for batch N x N (ld) matrices; row-major.
+void gemv_f64(cudaStream_t s, bool ta, int rows, int cols, const double* A, int lda, long long sA,
+              const double* x, long long sx, double* y, long long sy, int batch, double alpha,
+              double beta);
+
+// ---------------------------------------------------------------- eigen (eigen.cu)
+// Warm-started block-Jacobi on M (dp x dp per chain, symmetric), rotating PsiT's rows alongside;
+// writes lam (dp per chain) and the sweep count; sets RMHMC_CHAIN_NOTCONV on failure. Chains
+// whose status is nonzero on entry are skipped.
+struct JacobiWork {
+  double* V;      // n_chains x (nb/2) x 256
+  double* D;      // n_chains x (nb/2) x 256
+  double* slots;  // n_chains x 64
+  int* flags;     // n_chains x (nb/2): pair rotated in the current round
+};
+void jacobi_f64(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,
+                double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
+                JacobiWork w, int cluster);
+// Modified Gram-Schmidt on the first d rows of PsiT (dp x dp per chain), for chains whose
+// eig_count is a positive multiple of every (0 = never).
+void mgs_rows_f64(cudaStream_t s, double* PsiT, int dp, int d, int n_chains, const int* eig_count,
+                  int every, int cluster);
+int jacobi_cluster_size(int n_chains);
+
+// ---------------------------------------------------------------- model kernels (model.cu side)
+}  // namespace rmhmc

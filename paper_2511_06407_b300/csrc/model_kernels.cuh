@@ -1,0 +1,471 @@
+// Device kernels of the model layer: kernel matrices, likelihood maps, hyperparameter statistics,
+// Hessian assembly, the third-derivative contraction and the soft-abs map. Included once, by
+// rmhmc.cu.
+#pragma once
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace rmhmc {
+namespace dev {
+
+constexpr double LOG2PI = 1.8378770664093454835606594728112;
+
+__device__ __forceinline__ double hyper_u(const ModelDev& md, const double* q, int dp, int c, int k,
+                                          int h) {
+  return md.sample_hypers ? q[(long long)c * dp + md.n * md.N + 2 * k + h] : md.u_fixed[2 * k + h];
+}
+
+// K(x_i, x_j) and its first three derivatives in u_1 = log theta (Eq. BMKL kernels, log-parametrised).
+// Every derivative in u_0 = log c returns the same value, so these four cover all mixed derivatives.
+__device__ __forceinline__ void kern_derivs(const KernelDev& kd, const double* __restrict__ X, int ncov,
+                                            int i, int j, double c, double th, double D[4]) {
+  const double* xi = X + (long long)i * ncov;
+  const double* xj = X + (long long)j * ncov;
+  const double diag = (i == j) ? c * kd.jitter : 0.0;
+  if (kd.kind == RMHMC_K_SE) {
+    double sq = 0.0;
+    for (int t = 0; t < kd.n_cols; ++t) {
+      const double dd = xi[kd.cols[t]] - xj[kd.cols[t]];
+      sq = fma(dd, dd, sq);
+    }
+    const double r = sq / (th * th);
+    const double E = c * exp(-0.5 * r);
+    D[0] = E + diag;
+    D[1] = E * r;
+    D[2] = E * (r * r - 2.0 * r);
+    D[3] = E * (r * r * r - 6.0 * r * r + 4.0 * r);
+  } else if (kd.kind == RMHMC_K_LINEAR) {
+    double g = 0.0;
+    for (int t = 0; t < kd.n_cols; ++t) g = fma(xi[kd.cols[t]], xj[kd.cols[t]], g);
+    D[0] = c * (g + th) + diag;
+    D[1] = c * th;
+    D[2] = D[1];
+    D[3] = D[1];
+  } else {
+    double h = 0.0;
+    for (int t = 0; t < kd.n_cols; ++t) h += (xi[kd.cols[t]] != xj[kd.cols[t]]) ? 1.0 : 0.0;
+    const double s = h / th;
+    const double E = c * exp(-s);
+    D[0] = E + diag;
+    D[1] = E * s;
+    D[2] = E * (s * s - s);
+    D[3] = E * (s * s * s - 3.0 * s * s + s);
+  }
+}
+
+// K and D1 = dK/du_1 for every (chain, kernel): grid (tiles, n, C).
+__global__ void k_assemble(ModelDev md, const double* __restrict__ q, int dp, double* __restrict__ K,
+                           double* __restrict__ D1) {
+  const int k = blockIdx.y, c = blockIdx.z, N = md.N;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)N * N) return;
+  const int i = (int)(e / N), j = (int)(e % N);
+  const double cc = exp(hyper_u(md, q, dp, c, k, 0)), th = exp(hyper_u(md, q, dp, c, k, 1));
+  double D[4];
+  kern_derivs(md.k[k], md.X, md.ncov, i, j, cc, th, D);
+  const long long o = ((long long)c * md.n + k) * N * N + e;
+  K[o] = D[0];
+  D1[o] = D[1];
+}
+
+// Latent blocks f_k packed contiguously per (chain, kernel), and tau-scaled likelihood maps of
+// F = sum_k f_k (Sec. 2.5 logistic / Gaussian): l, l', l'', l''' per (chain, sample).
+__global__ void k_lik(ModelDev md, const double* __restrict__ q, int dp, double* __restrict__ fpk,
+                      double* __restrict__ l0, double* __restrict__ l1, double* __restrict__ l2,
+                      double* __restrict__ l3) {
+  const int c = blockIdx.y, N = md.N;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= N) return;
+  const double* qc = q + (long long)c * dp;
+  double F = 0.0;
+  for (int k = 0; k < md.n; ++k) {
+    const double f = qc[k * N + m];
+    fpk[((long long)c * md.n + k) * N + m] = f;
+    F += f;
+  }
+  const double tau = md.tau[c], y = md.y[m];
+  double a0, a1, a2, a3;
+  if (md.lik == RMHMC_LIK_BERNOULLI_LOGIT) {
+    const double s = 1.0 / (1.0 + exp(-F));
+    a0 = fmax(F, 0.0) + log1p(exp(-fabs(F))) - y * F;
+    a1 = s - y;
+    a2 = s * (1.0 - s);
+    a3 = a2 * (1.0 - 2.0 * s);
+  } else {
+    const double v = md.noise_var;
+    a0 = (y - F) * (y - F) / (2.0 * v) + 0.5 * log(2.0 * M_PI * v);
+    a1 = (F - y) / v;
+    a2 = 1.0 / v;
+    a3 = 0.0;
+  }
+  const long long o = (long long)c * N + m;
+  l0[o] = tau * a0;
+  l1[o] = tau * a1;
+  l2[o] = tau * a2;
+  l3[o] = tau * a3;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+  return s;  // valid in thread 0
+}
+
+// Per (chain, kernel) vectors and scalars the Hessian (THIRD = false) and the third-derivative
+// operator (THIRD = true) need, with S = K^-1 D1, A1 = S K^-1, S2 = S S (D2, D3 regenerated).
+// On entry `beta` holds t = L^-1 f (used for f . alpha = |t|^2) and is then overwritten:
+//   beta = D1 a, eps2 = D2 a, eps3 = D3 a, gamma = K^-1 beta (= S a), delta = D1 gamma,
+//   fuu11 = K^-1 (2 delta - eps2);  scalars in the Stat slots.
+template <bool THIRD>
+__global__ void __launch_bounds__(256) k_stats(ModelDev md, const double* __restrict__ q, int dp,
+                                               const double* __restrict__ D1b,
+                                               const double* __restrict__ Kinvb,
+                                               const double* __restrict__ Sb,
+                                               const double* __restrict__ A1b,
+                                               const double* __restrict__ S2b,
+                                               const double* __restrict__ fpk,
+                                               const double* __restrict__ alphab,
+                                               double* __restrict__ betab, double* __restrict__ gammab,
+                                               double* __restrict__ eps2b, double* __restrict__ eps3b,
+                                               double* __restrict__ deltab,
+                                               double* __restrict__ fuu11b, double* __restrict__ stats) {
+  const int b = blockIdx.x, n = md.n, N = md.N;
+  const int c = b / n, k = b % n;
+  const long long mo = (long long)b * N * N, vo = (long long)b * N;
+  const double* Kinv = Kinvb + mo;
+  const double* D1 = D1b + mo;
+  const double* S = Sb + mo;
+  const double* al = alphab + vo;
+  const double* f = fpk + vo;
+  double* beta = betab + vo;
+  double* gam = gammab + vo;
+  double* eps2 = eps2b + vo;
+  double* eps3 = eps3b + vo;
+  double* del = deltab + vo;
+  double* fuu = fuu11b + vo;
+  double* st = stats + (long long)b * kStatSlots;
+  const double cc = exp(hyper_u(md, q, dp, c, k, 0)), th = exp(hyper_u(md, q, dp, c, k, 1));
+  __shared__ double sh[32];
+  double fa = 0, ab = 0, ae2 = 0, ae3 = 0, trS = 0, trR2 = 0, trR3 = 0, trSR2 = 0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double bi = 0, e2 = 0, e3 = 0;
+    for (int j = 0; j < N; ++j) {
+      double D[4];
+      kern_derivs(md.k[k], md.X, md.ncov, j, i, cc, th, D);
+      const double aj = al[j];
+      const double kij = Kinv[(long long)j * N + i];
+      bi = fma(D[1], aj, bi);
+      e2 = fma(D[2], aj, e2);
+      trS = fma(kij, D[1], trS);
+      trR2 = fma(kij, D[2], trR2);
+      if (THIRD) {
+        e3 = fma(D[3], aj, e3);
+        trR3 = fma(kij, D[3], trR3);
+        trSR2 = fma(A1b[mo + (long long)j * N + i], D[2], trSR2);
+      }
+    }
+    // on entry beta holds t = L^-1 f, so f . alpha = f^T K^-1 f = |t|^2 (a sum of squares)
+    const double ti = beta[i];
+    fa = fma(ti, ti, fa);
+    beta[i] = bi;
+    eps2[i] = e2;
+    if (THIRD) eps3[i] = e3;
+    ab = fma(al[i], bi, ab);
+    ae2 = fma(al[i], e2, ae2);
+    if (THIRD) ae3 = fma(al[i], e3, ae3);
+  }
+  __syncthreads();
+  double gb = 0, ge2 = 0, trS2 = 0, trS3 = 0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double gi = 0, s2 = 0, s3 = 0;
+    for (int j = 0; j < N; ++j) {
+      gi = fma(Kinv[(long long)j * N + i], beta[j], gi);
+      const double sji = S[(long long)j * N + i];
+      s2 = fma(S[(long long)i * N + j], sji, s2);
+      if (THIRD) s3 = fma(S2b[mo + (long long)i * N + j], sji, s3);
+    }
+    gam[i] = gi;
+    gb = fma(gi, beta[i], gb);
+    ge2 = fma(gi, eps2[i], ge2);
+    trS2 += s2;
+    trS3 += s3;
+  }
+  double ad = 0, gd = 0;
+  if (THIRD) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      double di = 0;
+      for (int j = 0; j < N; ++j) di = fma(D1[(long long)j * N + i], gam[j], di);
+      del[i] = di;
+      ad = fma(al[i], di, ad);
+      gd = fma(gam[i], di, gd);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      double v = 0;
+      for (int j = 0; j < N; ++j) v = fma(Kinv[(long long)j * N + i], 2.0 * del[j] - eps2[j], v);
+      fuu[i] = v;
+    }
+  }
+  double r;
+  r = block_sum(fa, sh);    if (threadIdx.x == 0) st[ST_FA] = r;
+  r = block_sum(ab, sh);    if (threadIdx.x == 0) st[ST_AB] = r;
+  r = block_sum(ae2, sh);   if (threadIdx.x == 0) st[ST_AE2] = r;
+  r = block_sum(gb, sh);    if (threadIdx.x == 0) st[ST_GB] = r;
+  r = block_sum(ge2, sh);   if (threadIdx.x == 0) st[ST_GE2] = r;
+  r = block_sum(trS, sh);   if (threadIdx.x == 0) st[ST_TRS] = r;
+  r = block_sum(trS2, sh);  if (threadIdx.x == 0) st[ST_TRS2] = r;
+  r = block_sum(trR2, sh);  if (threadIdx.x == 0) st[ST_TRR2] = r;
+  if (THIRD) {
+    r = block_sum(ae3, sh);   if (threadIdx.x == 0) st[ST_AE3] = r;
+    r = block_sum(ad, sh);    if (threadIdx.x == 0) st[ST_AD] = r;
+    r = block_sum(gd, sh);    if (threadIdx.x == 0) st[ST_GD] = r;
+    r = block_sum(trS3, sh);  if (threadIdx.x == 0) st[ST_TRS3] = r;
+    r = block_sum(trR3, sh);  if (threadIdx.x == 0) st[ST_TRR3] = r;
+    r = block_sum(trSR2, sh); if (threadIdx.x == 0) st[ST_TRSR2] = r;
+  }
+}
+
+__device__ __forceinline__ double log_prior_u(double a, double b, double u) {
+  return a * log(b) - lgamma(a) - a * u - b * exp(-u);
+}
+
+// U = -log P_tau(q) and dU/dq for every chain (one CTA per chain).
+__global__ void __launch_bounds__(256) k_udu(ModelDev md, const double* __restrict__ q, int dp,
+                                             const double* __restrict__ l0,
+                                             const double* __restrict__ l1,
+                                             const double* __restrict__ alphab,
+                                             const double* __restrict__ stats,
+                                             double* __restrict__ U, double* __restrict__ dU) {
+  const int c = blockIdx.x, N = md.N, n = md.n;
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int m = threadIdx.x; m < N; m += blockDim.x) s += l0[(long long)c * N + m];
+  for (int e = threadIdx.x; e < n * N; e += blockDim.x) {
+    const int k = e / N, m = e % N;
+    dU[(long long)c * dp + e] = l1[(long long)c * N + m] + alphab[((long long)c * n + k) * N + m];
+  }
+  for (int e = md.d + threadIdx.x; e < dp; e += blockDim.x) dU[(long long)c * dp + e] = 0.0;
+  const double tot = block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    double Uc = tot;
+    for (int k = 0; k < n; ++k) {
+      const double* st = stats + ((long long)c * n + k) * kStatSlots;
+      Uc += 0.5 * st[ST_FA] + 0.5 * st[ST_LOGDET] + 0.5 * N * LOG2PI;
+      if (md.sample_hypers) {
+        const KernelDev& kd = md.k[k];
+        const double u0 = hyper_u(md, q, dp, c, k, 0), u1 = hyper_u(md, q, dp, c, k, 1);
+        Uc -= log_prior_u(kd.a[0], kd.b[0], u0) + log_prior_u(kd.a[1], kd.b[1], u1);
+        const long long base = (long long)c * dp + n * N + 2 * k;
+        dU[base] = -0.5 * st[ST_FA] + 0.5 * N + kd.a[0] - kd.b[0] * exp(-u0);
+        dU[base + 1] = -0.5 * st[ST_AB] + 0.5 * st[ST_TRS] + kd.a[1] - kd.b[1] * exp(-u1);
+      }
+    }
+    U[c] = Uc;
+  }
+}
+
+// Hessian of U (d x d inside the dp x dp padded storage; padding is zero):
+//   H[f_a, f_b] = diag(tau l'') + [a = b] K_a^-1
+//   H[f_k, u_k0] = -alpha_k, H[f_k, u_k1] = -gamma_k  (= -K^-1 K_h alpha)
+//   H[u_k, u_k] = [[ fa/2 + b0 e^-u0,  ab/2 ], [ ab/2,  gb - ae2/2 + trR2/2 - trS2/2 + b1 e^-u1 ]]
+__global__ void k_hessian(ModelDev md, const double* __restrict__ q, int dp,
+                          const double* __restrict__ Kinvb, const double* __restrict__ l2,
+                          const double* __restrict__ alphab, const double* __restrict__ gammab,
+                          const double* __restrict__ stats, double* __restrict__ H) {
+  const int c = blockIdx.y, N = md.N, n = md.n, nN = n * N, d = md.d;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)dp * dp) return;
+  const int r = (int)(e / dp), s = (int)(e % dp);
+  double v = 0.0;
+  if (r < d && s < d) {
+    if (r < nN && s < nN) {
+      const int a = r / N, i = r % N, bb = s / N, j = s % N;
+      if (a == bb) v += Kinvb[(((long long)c * n + a) * N + i) * N + j];
+      if (i == j) v += l2[(long long)c * N + i];
+    } else if (r < nN || s < nN) {
+      const int fr = r < nN ? r : s, ur = (r < nN ? s : r) - nN;
+      const int a = fr / N, i = fr % N, k = ur / 2, h = ur % 2;
+      if (a == k) {
+        const long long vo = ((long long)c * n + k) * N + i;
+        v = h == 0 ? -alphab[vo] : -gammab[vo];
+      }
+    } else {
+      const int ur = r - nN, us = s - nN;
+      const int k = ur / 2, h1 = ur % 2, k2 = us / 2, h2 = us % 2;
+      if (k == k2) {
+        const double* st = stats + ((long long)c * n + k) * kStatSlots;
+        const KernelDev& kd = md.k[k];
+        if (h1 == 0 && h2 == 0)
+          v = 0.5 * st[ST_FA] + kd.b[0] * exp(-hyper_u(md, q, dp, c, k, 0));
+        else if (h1 != h2)
+          v = 0.5 * st[ST_AB];
+        else
+          v = st[ST_GB] - 0.5 * st[ST_AE2] + 0.5 * st[ST_TRR2] - 0.5 * st[ST_TRS2] +
+              kd.b[1] * exp(-hyper_u(md, q, dp, c, k, 1));
+      }
+    }
+  }
+  H[(long long)c * dp * dp + e] = v;
+}
+
+// d^3 U / du_j du_k du_l for the two hyperparameters of one kernel (j, k, l in {0, 1}), from the
+// scalars in the Stat slots. With gamma_0 = alpha, gamma_1 = gamma, K_0 = K, K_1 = D1,
+// K_{..} = D_{number of 1 indices}, S_0 = I, S_1 = S:
+//   - g_j K_k g_l - g_k K_j g_l - g_k K_l g_j + (K_jk a) g_l + g_k (K_jl a) + (K_kl a) g_j
+//   - a K_jkl a / 2 - tr(S_j K^-1 K_kl) / 2 + tr(K^-1 K_jkl) / 2 + tr(S_j S_k S_l) / 2
+//   + tr(S_k S_j S_l) / 2 - tr(K^-1 K_jk S_l) / 2 - tr(S_k K^-1 K_jl) / 2 - [j = k = l] b e^-u
+__device__ __forceinline__ double g_k_g(const double* st, int x, int y, int z) {
+  const int yz = y + z;  // K_y gamma_z: 0 -> f, 1 -> beta, 2 -> delta
+  if (x == 0) return yz == 0 ? st[ST_FA] : (yz == 1 ? st[ST_AB] : st[ST_AD]);
+  return yz == 0 ? st[ST_AB] : (yz == 1 ? st[ST_GB] : st[ST_GD]);
+}
+__device__ __forceinline__ double km_a_g(const double* st, int m, int l) {
+  // (K_m alpha) . gamma_l, K_m alpha: 0 -> f, 1 -> beta, 2 -> eps2
+  if (l == 0) return m == 0 ? st[ST_FA] : (m == 1 ? st[ST_AB] : st[ST_AE2]);
+  return m == 0 ? st[ST_AB] : (m == 1 ? st[ST_GB] : st[ST_GE2]);
+}
+__device__ __forceinline__ double tr_skm(const double* st, int N, int x, int m) {
+  // tr(S_x K^-1 K_m), m = number of 1 indices (0..2)
+  if (x == 0) return m == 0 ? (double)N : (m == 1 ? st[ST_TRS] : st[ST_TRR2]);
+  return m == 0 ? st[ST_TRS] : (m == 1 ? st[ST_TRS2] : st[ST_TRSR2]);
+}
+__device__ __forceinline__ double tr_km(const double* st, int N, int m) {
+  return m == 0 ? (double)N : (m == 1 ? st[ST_TRS] : (m == 2 ? st[ST_TRR2] : st[ST_TRR3]));
+}
+__device__ __forceinline__ double tr_spow(const double* st, int N, int m) {
+  return m == 0 ? (double)N : (m == 1 ? st[ST_TRS] : (m == 2 ? st[ST_TRS2] : st[ST_TRS3]));
+}
+__device__ __forceinline__ double a_km_a(const double* st, int m) {
+  return m == 0 ? st[ST_FA] : (m == 1 ? st[ST_AB] : (m == 2 ? st[ST_AE2] : st[ST_AE3]));
+}
+__device__ double uuu(const double* st, int N, int j, int k, int l, double b_e) {
+  double v = -g_k_g(st, j, k, l) - g_k_g(st, k, j, l) - g_k_g(st, k, l, j);
+  v += km_a_g(st, j + k, l) + km_a_g(st, j + l, k) + km_a_g(st, k + l, j);
+  v -= 0.5 * a_km_a(st, j + k + l);
+  v -= 0.5 * tr_skm(st, N, j, k + l);
+  v += 0.5 * tr_km(st, N, j + k + l);
+  v += tr_spow(st, N, j + k + l);
+  v -= 0.5 * tr_skm(st, N, l, j + k);
+  v -= 0.5 * tr_skm(st, N, k, j + l);
+  if (j == k && k == l) v -= b_e;
+  return v;
+}
+
+// v_i = tr(W dH_i) for every coordinate i of one (chain, kernel), W = W2 - W1 (Eq. Betancourt_formula
+// contracted with the third derivatives in the model's structure, Sec. 2.3; all O(N^2)):
+//   i = f_{k,m}:  tau l'''_m sum_{a,b} W[f_a m, f_b m] - 2 (K^-1 w_0 + A1 w_1)_m
+//                 + W_00 alpha_m + 2 W_01 gamma_m + W_11 fuu11_m,        w_h = W[f_k, u_kh]
+//   i = u_{k,j}:  -<W[f_k, f_k], A_j> + 2 sum_h <w_h, fuu_{j h}> + sum_{h h'} W_{h h'} uuu(j, h, h')
+//   with A_0 = K^-1, A_1 = A1, fuu_00 = alpha, fuu_01 = gamma, fuu_11 = fuu11.
+__global__ void __launch_bounds__(256) k_contract(ModelDev md, const double* __restrict__ q, int dp,
+                                                  const double* __restrict__ Wb,
+                                                  const double* __restrict__ Kinvb,
+                                                  const double* __restrict__ A1b,
+                                                  const double* __restrict__ l3,
+                                                  const double* __restrict__ alphab,
+                                                  const double* __restrict__ gammab,
+                                                  const double* __restrict__ fuu11b,
+                                                  const double* __restrict__ stats,
+                                                  double* __restrict__ vout) {
+  const int b = blockIdx.x, n = md.n, N = md.N, nN = n * N;
+  const int c = b / n, k = b % n;
+  const double* W = Wb + (long long)c * dp * dp;
+  const long long mo = (long long)b * N * N, vo = (long long)b * N;
+  const double* Kinv = Kinvb + mo;
+  const double* A1 = A1b + mo;
+  const double* al = alphab + vo;
+  const double* ga = gammab + vo;
+  const double* fu = fuu11b + vo;
+  double* v = vout + (long long)c * dp;
+  const bool hyp = md.sample_hypers != 0;
+  extern __shared__ double shm[];
+  double* w0 = shm;
+  double* w1 = shm + N;
+  __shared__ double sh[32];
+  const int u0i = nN + 2 * k, u1i = nN + 2 * k + 1;
+  if (hyp) {
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      w0[r] = W[(long long)(k * N + r) * dp + u0i];
+      w1[r] = W[(long long)(k * N + r) * dp + u1i];
+    }
+  }
+  __syncthreads();
+  double W00 = 0, W01 = 0, W11 = 0;
+  if (hyp) {
+    W00 = W[(long long)u0i * dp + u0i];
+    W01 = W[(long long)u0i * dp + u1i];
+    W11 = W[(long long)u1i * dp + u1i];
+  }
+  double dot00 = 0, dot01 = 0, dot11 = 0, trA0 = 0, trA1 = 0;
+  for (int m = threadIdx.x; m < N; m += blockDim.x) {
+    double diag = 0.0;
+    for (int a = 0; a < n; ++a)
+      for (int bb = 0; bb < n; ++bb) diag += W[(long long)(a * N + m) * dp + bb * N + m];
+    double val = l3[(long long)c * N + m] * diag;
+    if (hyp) {
+      double k0 = 0.0, k1 = 0.0;
+      for (int r = 0; r < N; ++r) {
+        k0 = fma(Kinv[(long long)r * N + m], w0[r], k0);
+        k1 = fma(A1[(long long)r * N + m], w1[r], k1);
+      }
+      val += -2.0 * (k0 + k1) + W00 * al[m] + 2.0 * W01 * ga[m] + W11 * fu[m];
+      dot00 = fma(w0[m], al[m], dot00);
+      dot01 = fma(w1[m], ga[m], dot01);
+      dot11 = fma(w1[m], fu[m], dot11);
+      // <W[f_k, f_k], A_j>: column m of the block
+      double t0 = 0.0, t1 = 0.0;
+      for (int r = 0; r < N; ++r) {
+        const double wr = W[(long long)(k * N + r) * dp + k * N + m];
+        t0 = fma(wr, Kinv[(long long)r * N + m], t0);
+        t1 = fma(wr, A1[(long long)r * N + m], t1);
+      }
+      trA0 += t0;
+      trA1 += t1;
+    }
+    v[k * N + m] = val;
+  }
+  if (!hyp) return;
+  double w0a = 0, w0g = 0, w1a = 0;
+  for (int m = threadIdx.x; m < N; m += blockDim.x) {
+    w0a = fma(w0[m], al[m], w0a);
+    w0g = fma(w0[m], ga[m], w0g);
+    w1a = fma(w1[m], al[m], w1a);
+  }
+  const double s_w0a = block_sum(w0a, sh);
+  const double s_w0g = block_sum(w0g, sh);
+  const double s_w1a = block_sum(w1a, sh);
+  const double s_w1g = block_sum(dot01, sh);
+  const double s_w1f = block_sum(dot11, sh);
+  const double s_trA0 = block_sum(trA0, sh);
+  const double s_trA1 = block_sum(trA1, sh);
+  (void)dot00;
+  if (threadIdx.x == 0) {
+    const double* st = stats + (long long)b * kStatSlots;
+    const KernelDev& kd = md.k[k];
+    const double be0 = kd.b[0] * exp(-hyper_u(md, q, dp, c, k, 0));
+    const double be1 = kd.b[1] * exp(-hyper_u(md, q, dp, c, k, 1));
+    const double Wh[2][2] = {{W00, W01}, {W01, W11}};
+    // <w_h, fuu_{j h}>: fuu_00 = alpha, fuu_01 = fuu_10 = gamma, fuu_11 = fuu11
+    const double wf[2][2] = {{s_w0a, s_w1g}, {s_w0g, s_w1f}};  // [j][h]
+    (void)s_w1a;
+    for (int j = 0; j < 2; ++j) {
+      double val = -(j == 0 ? s_trA0 : s_trA1) + 2.0 * (wf[j][0] + wf[j][1]);
+      const double bej = j == 0 ? be0 : be1;
+      for (int h = 0; h < 2; ++h)
+        for (int h2 = 0; h2 < 2; ++h2) val += Wh[h][h2] * uuu(st, N, j, h, h2, bej);
+      v[nN + 2 * k + j] = val;
+    }
+  }
+}
+
+}  // namespace dev
+}  // namespace rmhmc

@@ -1,0 +1,904 @@
+// librmhmc: C ABI, per-chain state and the generalized-leapfrog / Algorithm 1 orchestration of
+// the plain-FP64 SoftAbs-RMHMC path (declared in include/rmhmc.h).
+//
+// Every step of the path runs in the CUDA kernels of this library, enqueued on the model's
+// stream; the host only sequences launches. Internal vectors use the padded dimension dp (a
+// multiple of 16 >= d, zero in the padding) so that the d x d matrices tile evenly for the
+// Jacobi blocks.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
+
+#include "internal.cuh"
+#include "model_kernels.cuh"
+
+using namespace rmhmc;
+
+namespace {
+
+// ------------------------------------------------------------------------------- device helpers
+
+// Soft-absolute map (Sec. 2.2): g(l) = l coth(alpha l) or sqrt(1/alpha^2 + l^2), and g'(l).
+// coth form, x = alpha l:  |x| < 1e-3 Laurent series of x coth x (and of its derivative);
+// |x| > 20 saturated (g = |l|, g' = sign l); |x| <= 1 g' = (sinh 2x - 2x) / (2 sinh^2 x) with
+// sinh y - y summed from its Taylor series (no cancellation); otherwise g = l / tanh x,
+// g' = 1/tanh x - x / sinh^2 x.
+__device__ __forceinline__ double sinh_minus_identity(double y) {
+  const double y2 = y * y;
+  double term = y * y2 / 6.0, sum = 0.0;
+  for (int k = 1; k <= 12; ++k) {
+    sum += term;
+    term *= y2 / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
+  }
+  return sum;
+}
+
+__device__ __forceinline__ void softabs(double lam, double alpha, int kind, double& g, double& gp) {
+  if (kind == RMHMC_G_SQRT) {
+    const double kap = 1.0 / alpha;
+    const double r = sqrt(kap * kap + lam * lam);
+    g = r;
+    gp = lam / r;
+    return;
+  }
+  const double x = alpha * lam, ax = fabs(x);
+  if (ax < 1e-3) {
+    const double x2 = x * x;
+    g = (1.0 + x2 / 3.0 - x2 * x2 / 45.0 + 2.0 * x2 * x2 * x2 / 945.0) / alpha;
+    gp = 2.0 * x / 3.0 - 4.0 * x * x2 / 45.0 + 4.0 * x * x2 * x2 / 315.0;
+  } else if (ax > 20.0) {
+    g = fabs(lam);
+    gp = lam > 0.0 ? 1.0 : -1.0;
+  } else {
+    const double th = tanh(x), sh = sinh(x);
+    g = lam / th;
+    gp = (ax <= 1.0) ? sinh_minus_identity(2.0 * x) / (2.0 * sh * sh) : 1.0 / th - x / (sh * sh);
+  }
+}
+
+// Divided difference T_jl of Eq. d3_transform; near-equal eigenvalues take g' at the midpoint.
+__device__ __forceinline__ double tdiv(double lj, double ll, double gj, double gl, double alpha,
+                                       int kind) {
+  const double sc = fmax(1.0, fmax(fabs(lj), fabs(ll)));
+  if (fabs(lj - ll) <= 1e-7 * sc) {
+    double g, gp;
+    softabs(0.5 * (lj + ll), alpha, kind, g, gp);
+    return gp;
+  }
+  return (gj - gl) / (lj - ll);
+}
+
+__global__ void k_softabs(const double* __restrict__ lam, double* __restrict__ g,
+                          double* __restrict__ gp, int dp, int d, int C, double alpha, int kind) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)C * dp) return;
+  const int i = (int)(e % dp);
+  double a = 1.0, b = 0.0;
+  if (i < d) softabs(lam[e], alpha, kind, a, b);
+  g[e] = a;
+  gp[e] = b;
+}
+
+// C = diag(g'/g) - (b b^T) o T on the first d indices (zero elsewhere), b = t / g:
+// Psi C Psi^T = W2 - W1 (Eq. Betancourt_formula).
+__global__ void k_build_c(const double* __restrict__ t, const double* __restrict__ lam,
+                          const double* __restrict__ g, const double* __restrict__ gp,
+                          double* __restrict__ Cm, int dp, int d, double alpha, int kind) {
+  const int c = blockIdx.y;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)dp * dp) return;
+  const int j = (int)(e / dp), l = (int)(e % dp);
+  double v = 0.0;
+  if (j < d && l < d) {
+    const long long o = (long long)c * dp;
+    const double bj = t[o + j] / g[o + j], bl = t[o + l] / g[o + l];
+    const double T = (j == l) ? gp[o + j] : tdiv(lam[o + j], lam[o + l], g[o + j], g[o + l], alpha, kind);
+    v = -bj * bl * T;
+    if (j == l) v += gp[o + j] / g[o + j];
+  }
+  Cm[(long long)c * dp * dp + e] = v;
+}
+
+// t_i <- t_i * s(g_i) on the first d entries (s = 1/g or sqrt(g)), zero in the padding.
+__global__ void k_scale_g(double* __restrict__ t, const double* __restrict__ g, int dp, int d, int C,
+                          int mode) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)C * dp) return;
+  const int i = (int)(e % dp);
+  t[e] = (i < d) ? (mode == 0 ? t[e] / g[e] : t[e] * sqrt(g[e])) : 0.0;
+}
+
+// out = a + s * b (vectors of C x dp)
+__global__ void k_axpy(double* __restrict__ out, const double* __restrict__ a,
+                       const double* __restrict__ b, double s, long long n) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = a[e] + s * b[e];
+}
+
+// out = a + s * (b + c)
+__global__ void k_axpy2(double* __restrict__ out, const double* __restrict__ a,
+                        const double* __restrict__ b, const double* __restrict__ cc, double s,
+                        long long n) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = a[e] + s * (b[e] + cc[e]);
+}
+
+// Strided copy between the caller's d-stride layout and the internal dp-stride layout.
+__global__ void k_restride(double* __restrict__ dst, int dst_ld, const double* __restrict__ src,
+                           int src_ld, int d, int C) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)C * dst_ld) return;
+  const int c = (int)(e / dst_ld), i = (int)(e % dst_ld);
+  dst[e] = (i < d && src) ? src[(long long)c * src_ld + i] : 0.0;
+}
+
+__global__ void k_set_identity(double* __restrict__ A, int dp, int C) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)C * dp * dp) return;
+  const long long r = e % ((long long)dp * dp);
+  A[e] = (r / dp == r % dp) ? 1.0 : 0.0;
+}
+
+// H(q, p) of Eq. Hamiltonian per chain: U + (d log 2pi + sum log g) / 2 + p . (G^-1 p) / 2.
+__global__ void __launch_bounds__(256) k_hamiltonian(const double* __restrict__ U,
+                                                     const double* __restrict__ g,
+                                                     const double* __restrict__ p,
+                                                     const double* __restrict__ ginvp, int dp, int d,
+                                                     double* __restrict__ Ham) {
+  const int c = blockIdx.x;
+  __shared__ double sh[32];
+  double lg = 0.0, quad = 0.0;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    const long long o = (long long)c * dp + i;
+    lg += log(g[o]);
+    quad = fma(p[o], ginvp[o], quad);
+  }
+  const double a = dev::block_sum(lg, sh);
+  const double b = dev::block_sum(quad, sh);
+  if (threadIdx.x == 0) Ham[c] = U[c] + 0.5 * (d * dev::LOG2PI + a) + 0.5 * b;
+}
+
+// Philox4x64-10 (Salmon et al., SC'11) with the published multipliers and Weyl increments.
+__device__ __forceinline__ void philox(uint64_t x[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t lo0 = M0 * x[0], hi0 = __umul64hi(M0, x[0]);
+    const uint64_t lo1 = M1 * x[2], hi1 = __umul64hi(M1, x[2]);
+    const uint64_t n0 = hi1 ^ x[1] ^ k0, n2 = hi0 ^ x[3] ^ k1;
+    x[0] = n0;
+    x[1] = lo1;
+    x[2] = n2;
+    x[3] = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+}
+
+// Momentum normals: block b of (seed, chain, iteration) gives z[4b..4b+3] by Box-Muller.
+__global__ void k_normals(double* __restrict__ z, int dp, int d, int C, uint64_t seed, uint64_t iter) {
+  const int c = blockIdx.y;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (4 * b >= dp) return;
+  uint64_t x[4] = {(uint64_t)b, iter, 0ull, 0ull};
+  philox(x, seed, (uint64_t)c);
+  for (int pr = 0; pr < 2; ++pr) {
+    const double u1 = (double)((x[2 * pr] >> 11) + 1) * 0x1.0p-53;
+    const double u2 = (double)(x[2 * pr + 1] >> 11) * 0x1.0p-53;
+    const double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    const int i0 = 4 * b + 2 * pr;
+    if (i0 < dp) z[(long long)c * dp + i0] = (i0 < d) ? r * cs : 0.0;
+    if (i0 + 1 < dp) z[(long long)c * dp + i0 + 1] = (i0 + 1 < d) ? r * sn : 0.0;
+  }
+}
+
+// Metropolis-Hastings decision per chain (Algorithm 1): r from counter (0, iteration, 1, 0).
+__global__ void k_accept(const double* __restrict__ H0, const double* __restrict__ H1,
+                         int* __restrict__ status, int* __restrict__ acc, int C, uint64_t seed,
+                         uint64_t iter, int* __restrict__ acc_out, int* __restrict__ sweeps_out,
+                         const int* __restrict__ sweeps_acc, int* __restrict__ chain_status) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  uint64_t x[4] = {0ull, iter, 1ull, 0ull};
+  philox(x, seed, (uint64_t)c);
+  const double r = (double)(x[0] >> 11) * 0x1.0p-53;
+  int st = status[c];
+  if (!isfinite(H1[c])) st |= RMHMC_CHAIN_NONFINITE;
+  const int a = (st == 0) && (log(r) < H0[c] - H1[c]);
+  acc[c] = a;
+  if (acc_out) acc_out[c] = a;
+  if (sweeps_out) sweeps_out[c] = sweeps_acc[c];
+  if (chain_status) chain_status[c] |= st;
+  status[c] = 0;
+}
+
+// Rejected chains return to the saved position and eigenvectors.
+__global__ void k_restore(const int* __restrict__ acc, double* __restrict__ q,
+                          const double* __restrict__ q_save, double* __restrict__ PsiT,
+                          const double* __restrict__ PsiT_save, int* __restrict__ eig_count,
+                          const int* __restrict__ eig_save, int dp) {
+  const int c = blockIdx.y;
+  if (acc[c]) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long o = (long long)c * dp * dp;
+  if (e < (long long)dp * dp) PsiT[o + e] = PsiT_save[o + e];
+  if (e < dp) q[(long long)c * dp + e] = q_save[(long long)c * dp + e];
+  if (e == 0) eig_count[c] = eig_save[c];
+}
+
+// eig_count += 1 per chain; sweeps_total += sweeps of the eigen-update just done
+__global__ void k_inc(int* __restrict__ v, int C, int* __restrict__ tot, const int* __restrict__ last) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < C) {
+    v[c] += 1;
+    tot[c] += last[c];
+  }
+}
+
+__global__ void k_record(const double* __restrict__ q, const double* __restrict__ U, int dp, int d,
+                         int C, double* __restrict__ qs, double* __restrict__ logp) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)C * d) return;
+  const int c = (int)(e / d), i = (int)(e % d);
+  if (qs) qs[e] = q[(long long)c * dp + i];
+  if (logp && i == 0) logp[c] = -U[c];
+}
+
+// dst (C x d x d) <- the leading d x d block of src (C x dp x dp)
+__global__ void k_compact(double* __restrict__ dst, const double* __restrict__ src, int dp, int d, int C) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)C * d * d) return;
+  const long long c = e / ((long long)d * d), r = e % ((long long)d * d);
+  dst[e] = src[c * dp * dp + (r / d) * dp + r % d];
+}
+
+// Y = diag(g) PsiT on the first d rows (zero below)
+__global__ void k_scale_rows(double* __restrict__ Y, const double* __restrict__ PsiT,
+                             const double* __restrict__ g, int dp, int d) {
+  const int c = blockIdx.y;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)dp * dp) return;
+  const int r = (int)(e / dp);
+  const long long o = (long long)c * dp * dp + e;
+  Y[o] = r < d ? g[(long long)c * dp + r] * PsiT[o] : 0.0;
+}
+
+// Eight independent FMA chains per thread: enough instruction-level parallelism to keep the FP64
+// pipe busy; the result is kept live through a data-dependent store that never happens.
+__global__ void k_dfma_peak(double* __restrict__ sink, int iters, double b, double c) {
+  double a0 = threadIdx.x * 1e-3, a1 = a0 + 1.0, a2 = a0 + 2.0, a3 = a0 + 3.0;
+  double a4 = a0 + 4.0, a5 = a0 + 5.0, a6 = a0 + 6.0, a7 = a0 + 7.0;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
+      a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
+    }
+  }
+  const double s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (s == 12345.678) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------ the model
+
+struct rmhmc_model {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  ModelDev md{};
+  int N = 0, n = 0, P = 0, d = 0, dp = 0, C = 0;
+  int cluster = 1;
+  bool has_state = false;
+  int g_kind = 0, max_sweeps = 30, reorth_every = 10, precision = 0;
+  double alpha = 1e6, tol = 1e-13;
+  uint64_t iter = 0;
+  std::vector<void*> allocs;
+  // per (chain, kernel) N x N
+  double *KL, *D1, *Kinv, *S, *Aux, *S2;
+  // per (chain, kernel) N-vectors
+  double *fpk, *alpha_, *beta, *gamma, *eps2, *eps3, *delta, *fuu11;
+  double* stats;
+  // per chain N-vectors
+  double *l0, *l1, *l2, *l3;
+  // per chain dp x dp
+  double *H, *M, *PsiT, *W, *Y, *PsiT_save;
+  // per chain dp-vectors
+  double *q, *p, *ph, *q0, *v0, *vk, *t1, *dU, *dHdq, *lam, *g, *gp, *q_save, *z, *vtr, *xin;
+  // per chain scalars
+  double *U, *Ham0, *Ham1;
+  int *status, *sweeps_last, *sweeps_acc, *eig_count, *eig_save, *acc, *sweeps_total;
+  JacobiWork jw;
+  // kernel-level profile (rmhmc_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_next = 0;
+  struct Rec { int cat; size_t a, b; };
+  std::vector<Rec> recs;
+  double prof_flops[RMHMC_PROF_NCAT] = {};
+  long long prof_launch[RMHMC_PROF_NCAT] = {};
+};
+
+namespace {
+
+enum Cat { CAT_GEMM = 0, CAT_JACOBI, CAT_CHOL, CAT_TRINV, CAT_MODEL, CAT_CONTRACT, CAT_VECTOR, CAT_MGS };
+const char* kCatNames[RMHMC_PROF_NCAT] = {"gemm_f64", "jacobi_f64", "cholesky_f64", "trinv_f64",
+                                          "model", "contract", "vector", "mgs_f64"};
+
+// Brackets one launch site with CUDA events on the model's stream while profiling is enabled.
+struct ProfScope {
+  rmhmc_model* m;
+  int cat;
+  size_t a = 0;
+  bool on = false, once = true;
+  ProfScope(rmhmc_model* mm, int c, double flops) : m(mm), cat(c) {
+    if (!m->prof) return;
+    m->prof_flops[c] += flops;
+    m->prof_launch[c] += 1;
+    if (m->ev_next + 2 > m->ev.size()) return;
+    a = m->ev_next;
+    m->ev_next += 2;
+    cudaEventRecord(m->ev[a], m->stream);
+    on = true;
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(m->ev[a + 1], m->stream);
+    m->recs.push_back({cat, a, a + 1});
+  }
+};
+#define PROF(m, cat, flops) for (ProfScope _ps((m), (cat), (flops)); _ps.once; _ps.once = false)
+
+inline double gemm_flops(double mm, double nn, double kk, bool sym, bool tri) {
+  if (tri) return mm * mm * mm / 3.0;
+  return sym ? mm * (mm + 1.0) * kk : 2.0 * mm * nn * kk;
+}
+
+template <typename T>
+rmhmc_status dalloc(rmhmc_model* m, T** p, size_t count) {
+  void* ptr = nullptr;
+  if (cudaMalloc(&ptr, count * sizeof(T) + 16) != cudaSuccess) return RMHMC_ENOMEM;
+  cudaMemsetAsync(ptr, 0, count * sizeof(T) + 16, m->stream);
+  m->allocs.push_back(ptr);
+  *p = (T*)ptr;
+  return RMHMC_OK;
+}
+
+rmhmc_status check_launch() {
+  return cudaGetLastError() == cudaSuccess ? RMHMC_OK : RMHMC_ECUDA;
+}
+
+// --- geometry at the current q: U, dU, Hessian, warm-started eigendecomposition, g(lambda);
+//     with `third`, also the third-derivative operator (A1, S^2 and the F-phase statistics).
+void eval_geometry(rmhmc_model* m, bool third) {
+  cudaStream_t s = m->stream;
+  const int N = m->N, n = m->n, C = m->C, dp = m->dp, d = m->d;
+  const long long NN = (long long)N * N;
+  const int B = C * n;
+  const double Nf = N, df = d, Bf = B, Cf = C;
+  PROF(m, CAT_MODEL, 0)
+  dev::k_assemble<<<dim3(nblk(NN), n, C), 256, 0, s>>>(m->md, m->q, dp, m->KL, m->D1);
+  PROF(m, CAT_MODEL, 0)
+  dev::k_lik<<<dim3(nblk(N), C), 256, 0, s>>>(m->md, m->q, dp, m->fpk, m->l0, m->l1, m->l2, m->l3);
+  PROF(m, CAT_CHOL, Bf * Nf * Nf * Nf / 3.0)
+  cholesky_f64(s, m->KL, N, B, m->stats + ST_LOGDET, kStatSlots, m->status, n);
+  PROF(m, CAT_TRINV, Bf * Nf * Nf * Nf / 3.0)
+  trinv_lower_f64(s, m->KL, m->Aux, N, B);
+  // K^-1 = L^-T L^-1 (symmetric; the sum runs over k >= max(i, j) only)
+  PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, true, true))
+  gemm_f64(s, true, false, N, N, N, 1.0, m->Aux, N, NN, m->Aux, N, NN, 0.0, m->Kinv, N, NN, B, true, true);
+  // t = L^-1 f (kept in beta for f . alpha = |t|^2) and alpha = L^-T t by substitution
+  PROF(m, CAT_VECTOR, 2.0 * Bf * Nf * Nf)
+  cholsolve_f64(s, m->KL, m->fpk, m->beta, m->alpha_, N, B);
+  PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, false, false))
+  gemm_f64(s, false, false, N, N, N, 1.0, m->Kinv, N, NN, m->D1, N, NN, 0.0, m->S, N, NN, B, false, false);
+  if (third) {
+    PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, true, false))
+    gemm_f64(s, false, false, N, N, N, 1.0, m->S, N, NN, m->Kinv, N, NN, 0.0, m->Aux, N, NN, B, true, false);
+    PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, false, false))
+    gemm_f64(s, false, false, N, N, N, 1.0, m->S, N, NN, m->S, N, NN, 0.0, m->S2, N, NN, B, false, false);
+    PROF(m, CAT_MODEL, 0)
+    dev::k_stats<true><<<B, 256, 0, s>>>(m->md, m->q, dp, m->D1, m->Kinv, m->S, m->Aux, m->S2, m->fpk,
+                                         m->alpha_, m->beta, m->gamma, m->eps2, m->eps3, m->delta,
+                                         m->fuu11, m->stats);
+  } else {
+    PROF(m, CAT_MODEL, 0)
+    dev::k_stats<false><<<B, 256, 0, s>>>(m->md, m->q, dp, m->D1, m->Kinv, m->S, m->Aux, m->S2, m->fpk,
+                                          m->alpha_, m->beta, m->gamma, m->eps2, m->eps3, m->delta,
+                                          m->fuu11, m->stats);
+  }
+  PROF(m, CAT_MODEL, 0)
+  dev::k_udu<<<C, 256, 0, s>>>(m->md, m->q, dp, m->l0, m->l1, m->alpha_, m->stats, m->U, m->dU);
+  const long long DD = (long long)dp * dp;
+  PROF(m, CAT_MODEL, 0)
+  dev::k_hessian<<<dim3(nblk(DD), C), 256, 0, s>>>(m->md, m->q, dp, m->Kinv, m->l2, m->alpha_,
+                                                   m->gamma, m->stats, m->H);
+  // Sec. 2.4: Gram-Schmidt of Psi every reorth_every eigen-updates, then M = Psi^T H Psi
+  if (m->reorth_every > 0) {
+    PROF(m, CAT_MGS, 0)
+    mgs_rows_f64(s, m->PsiT, dp, d, C, m->eig_count, m->reorth_every, m->cluster);
+  }
+  PROF(m, CAT_GEMM, Cf * gemm_flops(df, df, df, false, false))
+  gemm_f64(s, false, true, dp, dp, dp, 1.0, m->H, dp, DD, m->PsiT, dp, DD, 0.0, m->Y, dp, DD, C, false, false);
+  PROF(m, CAT_GEMM, Cf * gemm_flops(df, df, df, true, false))
+  gemm_f64(s, false, false, dp, dp, dp, 1.0, m->PsiT, dp, DD, m->Y, dp, DD, 0.0, m->M, dp, DD, C, true, false);
+  PROF(m, CAT_JACOBI, 0)
+  jacobi_f64(s, m->M, m->PsiT, m->lam, dp, d, C, m->tol, m->max_sweeps, m->status, m->sweeps_last,
+             m->sweeps_acc, m->jw, m->cluster);
+  PROF(m, CAT_VECTOR, 0)
+  k_inc<<<nblk(C), 256, 0, s>>>(m->eig_count, C, m->sweeps_total, m->sweeps_last);
+  PROF(m, CAT_VECTOR, 0)
+  k_softabs<<<nblk((long long)C * dp), 256, 0, s>>>(m->lam, m->g, m->gp, dp, d, C, m->alpha, m->g_kind);
+}
+
+// out = G^-1 x = Psi diag(1/g) Psi^T x
+void ginv(rmhmc_model* m, const double* x, double* out) {
+  cudaStream_t s = m->stream;
+  const int dp = m->dp, C = m->C;
+  const long long DD = (long long)dp * dp;
+  const double v2 = 2.0 * C * (double)m->d * m->d;
+  PROF(m, CAT_VECTOR, v2)
+  gemv_f64(s, false, dp, dp, m->PsiT, dp, DD, x, dp, m->t1, dp, C, 1.0, 0.0);
+  PROF(m, CAT_VECTOR, 0)
+  k_scale_g<<<nblk((long long)C * dp), 256, 0, s>>>(m->t1, m->g, dp, m->d, C, 0);
+  PROF(m, CAT_VECTOR, v2)
+  gemv_f64(s, true, dp, dp, m->PsiT, dp, DD, m->t1, dp, out, dp, C, 1.0, 0.0);
+}
+
+// out = dH/dq(q, x) = dU + tr((W2 - W1) dH_i) / 2
+void grad_h(rmhmc_model* m, const double* x, double* out) {
+  cudaStream_t s = m->stream;
+  const int dp = m->dp, C = m->C, N = m->N, n = m->n;
+  const long long DD = (long long)dp * dp;
+  const double df = m->d, Cf = C;
+  PROF(m, CAT_VECTOR, 2.0 * Cf * df * df)
+  gemv_f64(s, false, dp, dp, m->PsiT, dp, DD, x, dp, m->t1, dp, C, 1.0, 0.0);
+  PROF(m, CAT_VECTOR, 0)
+  k_build_c<<<dim3(nblk(DD), C), 256, 0, s>>>(m->t1, m->lam, m->g, m->gp, m->M, dp, m->d, m->alpha, m->g_kind);
+  // W = Psi C Psi^T = PsiT^T (C PsiT)
+  PROF(m, CAT_GEMM, Cf * gemm_flops(df, df, df, false, false))
+  gemm_f64(s, false, false, dp, dp, dp, 1.0, m->M, dp, DD, m->PsiT, dp, DD, 0.0, m->Y, dp, DD, C, false, false);
+  PROF(m, CAT_GEMM, Cf * gemm_flops(df, df, df, true, false))
+  gemm_f64(s, true, false, dp, dp, dp, 1.0, m->PsiT, dp, DD, m->Y, dp, DD, 0.0, m->W, dp, DD, C, true, false);
+  PROF(m, CAT_CONTRACT, 0)
+  dev::k_contract<<<C * n, 256, 2 * N * sizeof(double), s>>>(m->md, m->q, dp, m->W, m->Kinv, m->Aux,
+                                                             m->l3, m->alpha_, m->gamma, m->fuu11,
+                                                             m->stats, m->vtr);
+  PROF(m, CAT_VECTOR, 0)
+  k_axpy<<<nblk((long long)C * dp), 256, 0, s>>>(out, m->dU, m->vtr, 0.5, (long long)C * dp);
+}
+
+void hamiltonian(rmhmc_model* m, const double* x, double* Ham) {
+  ginv(m, x, m->vk);
+  PROF(m, CAT_VECTOR, 0)
+  k_hamiltonian<<<m->C, 256, 0, m->stream>>>(m->U, m->g, x, m->vk, m->dp, m->d, Ham);
+}
+
+// One generalized leapfrog (Eq. leapfrog) from the geometry at q (third-derivative operator ready).
+void leapfrog_step(rmhmc_model* m, double eps, int n_fp) {
+  cudaStream_t s = m->stream;
+  const long long nv = (long long)m->C * m->dp;
+  const unsigned g = nblk(nv);
+  cudaMemcpyAsync(m->ph, m->p, nv * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  for (int k = 0; k < n_fp; ++k) {
+    grad_h(m, m->ph, m->dHdq);
+    PROF(m, CAT_VECTOR, 0)
+    k_axpy<<<g, 256, 0, s>>>(m->ph, m->p, m->dHdq, -0.5 * eps, nv);
+  }
+  ginv(m, m->ph, m->v0);
+  cudaMemcpyAsync(m->q0, m->q, nv * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  for (int k = 0; k < n_fp; ++k) {
+    if (k == 0) {
+      PROF(m, CAT_VECTOR, 0)
+      k_axpy2<<<g, 256, 0, s>>>(m->q, m->q0, m->v0, m->v0, 0.5 * eps, nv);
+    } else {
+      eval_geometry(m, false);
+      ginv(m, m->ph, m->vk);
+      PROF(m, CAT_VECTOR, 0)
+      k_axpy2<<<g, 256, 0, s>>>(m->q, m->q0, m->v0, m->vk, 0.5 * eps, nv);
+    }
+  }
+  eval_geometry(m, true);
+  grad_h(m, m->ph, m->dHdq);
+  PROF(m, CAT_VECTOR, 0)
+  k_axpy<<<g, 256, 0, s>>>(m->p, m->ph, m->dHdq, -0.5 * eps, nv);
+}
+
+rmhmc_status check_integ(const rmhmc_model* m, const rmhmc_integrator* in, bool for_state) {
+  if (!in) return RMHMC_EINVAL;
+  if (in->precision != RMHMC_FP64) return RMHMC_ENOTIMPL;
+  if (in->g_kind != RMHMC_G_COTH && in->g_kind != RMHMC_G_SQRT) return RMHMC_EINVAL;
+  if (!(in->alpha > 0.0) || !(in->jacobi_tol > 0.0) || in->max_sweeps < 0 || in->reorth_every < 0)
+    return RMHMC_EINVAL;
+  if (!for_state) {
+    if (!m->has_state) return RMHMC_EINVAL;
+    if (in->g_kind != m->g_kind || in->alpha != m->alpha || in->jacobi_tol != m->tol ||
+        in->max_sweeps != m->max_sweeps || in->reorth_every != m->reorth_every)
+      return RMHMC_EINVAL;
+    if (!(in->eps > 0.0) || in->n_fp < 1) return RMHMC_EINVAL;
+  }
+  return RMHMC_OK;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char* rmhmc_status_string(rmhmc_status s) {
+  switch (s) {
+    case RMHMC_OK: return "ok";
+    case RMHMC_EINVAL: return "invalid argument";
+    case RMHMC_ENOMEM: return "device allocation failed";
+    case RMHMC_ECUDA: return "CUDA runtime error";
+    case RMHMC_ENOTCONV: return "Jacobi did not converge";
+    case RMHMC_ENONFINITE: return "non-finite value";
+    case RMHMC_ETIMEOUT: return "bounded device wait gave up";
+    case RMHMC_ENOTIMPL: return "not implemented in this build";
+    case RMHMC_ENOTPD: return "kernel matrix not positive definite";
+  }
+  return "unknown status";
+}
+
+const char* rmhmc_version(void) { return "rmhmc sm_103a fp64"; }
+
+rmhmc_status rmhmc_fp64_peak(void* cuda_stream, int ms_target, double* tflops_host) {
+  if (!tflops_host || ms_target < 1) return RMHMC_EINVAL;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 4, threads = 256;
+  double* sink = nullptr;
+  if (cudaMalloc(&sink, (size_t)blocks * threads * sizeof(double)) != cudaSuccess) return RMHMC_ENOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int iters = 64;
+  float ms = 0.f;
+  k_dfma_peak<<<blocks, threads, 0, s>>>(sink, 8, 0.9999, 1e-7);
+  for (int rep = 0; rep < 12; ++rep) {
+    cudaEventRecord(e0, s);
+    k_dfma_peak<<<blocks, threads, 0, s>>>(sink, iters, 0.9999, 1e-7);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms >= 0.5f * ms_target || !(ms > 1e-3f)) break;
+    iters = (int)fmin(1e7, iters * fmin(100.0, fmax(2.0, 0.8 * ms_target / ms)));
+  }
+  const double flops = 2.0 * blocks * threads * (double)iters * 16.0 * 8.0;
+  *tflops_host = ms > 1e-3f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  return cudaGetLastError() == cudaSuccess ? RMHMC_OK : RMHMC_ECUDA;
+}
+
+const char* rmhmc_profile_category(int i) {
+  return (i >= 0 && i < RMHMC_PROF_NCAT) ? kCatNames[i] : "";
+}
+
+rmhmc_status rmhmc_profile(rmhmc_model* m, int enable) {
+  if (!m) return RMHMC_EINVAL;
+  if (enable) {
+    if (m->ev.empty()) {
+      m->ev.resize(1 << 15);
+      for (auto& e : m->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return RMHMC_ECUDA;
+    }
+    m->ev_next = 0;
+    m->recs.clear();
+    for (int i = 0; i < RMHMC_PROF_NCAT; ++i) {
+      m->prof_flops[i] = 0.0;
+      m->prof_launch[i] = 0;
+    }
+    cudaMemsetAsync(m->sweeps_total, 0, m->C * sizeof(int), m->stream);
+  }
+  m->prof = enable != 0;
+  return RMHMC_OK;
+}
+
+rmhmc_status rmhmc_profile_read(rmhmc_model* m, double* ms_host, double* flops_host,
+                                long long* launches_host) {
+  if (!m) return RMHMC_EINVAL;
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) return RMHMC_ECUDA;
+  double ms[RMHMC_PROF_NCAT] = {};
+  for (const auto& r : m->recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, m->ev[r.a], m->ev[r.b]) == cudaSuccess) ms[r.cat] += t;
+  }
+  std::vector<int> sw(m->C);
+  cudaMemcpy(sw.data(), m->sweeps_total, m->C * sizeof(int), cudaMemcpyDeviceToHost);
+  double sweeps = 0.0;
+  for (int v : sw) sweeps += v;
+  const double d = m->d;
+  for (int i = 0; i < RMHMC_PROF_NCAT; ++i) {
+    if (ms_host) ms_host[i] = ms[i];
+    if (flops_host) flops_host[i] = (i == CAT_JACOBI) ? sweeps * 8.0 * d * d * d : m->prof_flops[i];
+    if (launches_host) launches_host[i] = m->prof_launch[i];
+  }
+  return RMHMC_OK;
+}
+
+int rmhmc_dim(const rmhmc_model* m) { return m ? m->d : -1; }
+int rmhmc_n_chains(const rmhmc_model* m) { return m ? m->C : -1; }
+
+void rmhmc_free_model(rmhmc_model* m) {
+  if (!m) return;
+  cudaStreamSynchronize(m->stream);
+  for (void* p : m->allocs) cudaFree(p);
+  for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+  delete m;
+}
+
+rmhmc_status rmhmc_init_model(const rmhmc_model_desc* desc, int n_chains, const double* tau_host,
+                              void* cuda_stream, rmhmc_model** out) {
+  if (!desc || !out || n_chains < 1 || n_chains > 65535) return RMHMC_EINVAL;
+  *out = nullptr;
+  if (desc->N < 1 || desc->N > kMaxN || desc->n_cov < 1 || !desc->X || !desc->y) return RMHMC_EINVAL;
+  if (desc->n_kernels < 1 || desc->n_kernels > RMHMC_MAX_KERNELS || !desc->kernels) return RMHMC_EINVAL;
+  if (desc->lik != RMHMC_LIK_BERNOULLI_LOGIT && desc->lik != RMHMC_LIK_GAUSSIAN) return RMHMC_EINVAL;
+  if (desc->lik == RMHMC_LIK_GAUSSIAN && !(desc->noise_var > 0.0)) return RMHMC_EINVAL;
+  if (!desc->sample_hypers && !desc->u_fixed) return RMHMC_EINVAL;
+  for (int k = 0; k < desc->n_kernels; ++k) {
+    const rmhmc_kernel_desc& kd = desc->kernels[k];
+    if (kd.kind < 0 || kd.kind > 2 || kd.n_cols < 1 || kd.n_cols > RMHMC_MAX_COLS) return RMHMC_EINVAL;
+    if (!(kd.jitter > 0.0)) return RMHMC_EINVAL;
+    for (int t = 0; t < kd.n_cols; ++t)
+      if (kd.cols[t] < 0 || kd.cols[t] >= desc->n_cov) return RMHMC_EINVAL;
+    for (int h = 0; h < 2; ++h)
+      if (!(kd.prior_a[h] > 0.0) || !(kd.prior_b[h] > 0.0)) return RMHMC_EINVAL;
+  }
+  if (tau_host)
+    for (int c = 0; c < n_chains; ++c)
+      if (!(tau_host[c] >= 0.0) || tau_host[c] > 1.0) return RMHMC_EINVAL;
+
+  rmhmc_model* m = new rmhmc_model();
+  cudaGetDevice(&m->device);
+  m->stream = (cudaStream_t)cuda_stream;
+  m->N = desc->N;
+  m->n = desc->n_kernels;
+  m->P = desc->sample_hypers ? 2 * m->n : 0;
+  m->d = m->n * m->N + m->P;
+  m->dp = ((m->d + kJacSB - 1) / kJacSB) * kJacSB;
+  m->C = n_chains;
+  m->cluster = jacobi_cluster_size(n_chains);
+  ModelDev& md = m->md;
+  md.N = m->N;
+  md.n = m->n;
+  md.P = m->P;
+  md.d = m->d;
+  md.dp = m->dp;
+  md.ncov = desc->n_cov;
+  md.lik = desc->lik;
+  md.sample_hypers = desc->sample_hypers ? 1 : 0;
+  md.n_chains = n_chains;
+  md.noise_var = desc->noise_var;
+  for (int k = 0; k < m->n; ++k) {
+    const rmhmc_kernel_desc& kd = desc->kernels[k];
+    md.k[k].kind = kd.kind;
+    md.k[k].n_cols = kd.n_cols;
+    for (int t = 0; t < RMHMC_MAX_COLS; ++t) md.k[k].cols[t] = t < kd.n_cols ? kd.cols[t] : 0;
+    md.k[k].jitter = kd.jitter;
+    for (int h = 0; h < 2; ++h) {
+      md.k[k].a[h] = kd.prior_a[h];
+      md.k[k].b[h] = kd.prior_b[h];
+    }
+  }
+  const int N = m->N, n = m->n, C = m->C, dp = m->dp;
+  const size_t NN = (size_t)N * N, DD = (size_t)dp * dp;
+  const size_t B = (size_t)C * n;
+  rmhmc_status st = RMHMC_OK;
+#define ALLOC(ptr, cnt) \
+  if (st == RMHMC_OK) st = dalloc(m, &(ptr), (cnt))
+  double *X = nullptr, *y = nullptr, *uf = nullptr, *tau = nullptr;
+  ALLOC(X, (size_t)N * desc->n_cov);
+  ALLOC(y, (size_t)N);
+  ALLOC(uf, (size_t)2 * n);
+  ALLOC(tau, (size_t)C);
+  ALLOC(m->KL, B * NN);
+  ALLOC(m->D1, B * NN);
+  ALLOC(m->Kinv, B * NN);
+  ALLOC(m->S, B * NN);
+  ALLOC(m->Aux, B * NN);
+  ALLOC(m->S2, B * NN);
+  ALLOC(m->fpk, B * N);
+  ALLOC(m->alpha_, B * N);
+  ALLOC(m->beta, B * N);
+  ALLOC(m->gamma, B * N);
+  ALLOC(m->eps2, B * N);
+  ALLOC(m->eps3, B * N);
+  ALLOC(m->delta, B * N);
+  ALLOC(m->fuu11, B * N);
+  ALLOC(m->stats, B * kStatSlots);
+  ALLOC(m->l0, (size_t)C * N);
+  ALLOC(m->l1, (size_t)C * N);
+  ALLOC(m->l2, (size_t)C * N);
+  ALLOC(m->l3, (size_t)C * N);
+  ALLOC(m->H, C * DD);
+  ALLOC(m->M, C * DD);
+  ALLOC(m->PsiT, C * DD);
+  ALLOC(m->W, C * DD);
+  ALLOC(m->Y, C * DD);
+  ALLOC(m->PsiT_save, C * DD);
+  double** vecs[] = {&m->q, &m->p, &m->ph, &m->q0, &m->v0, &m->vk, &m->t1, &m->dU, &m->dHdq,
+                     &m->lam, &m->g, &m->gp, &m->q_save, &m->z, &m->vtr, &m->xin};
+  for (double** v : vecs) ALLOC(*v, (size_t)C * dp);
+  ALLOC(m->U, (size_t)C);
+  ALLOC(m->Ham0, (size_t)C);
+  ALLOC(m->Ham1, (size_t)C);
+  int** ivecs[] = {&m->status, &m->sweeps_last, &m->sweeps_acc, &m->eig_count, &m->eig_save, &m->acc,
+                   &m->sweeps_total};
+  for (int** v : ivecs) ALLOC(*v, (size_t)C);
+  const int np = dp / kJacBlk / 2;
+  ALLOC(m->jw.V, (size_t)C * np * 256);
+  ALLOC(m->jw.D, (size_t)C * np * 256);
+  ALLOC(m->jw.slots, (size_t)C * 64);
+  ALLOC(m->jw.flags, (size_t)C * np);
+#undef ALLOC
+  if (st != RMHMC_OK) {
+    rmhmc_free_model(m);
+    return st;
+  }
+  std::vector<double> tauv(C, 1.0);
+  if (tau_host) memcpy(tauv.data(), tau_host, C * sizeof(double));
+  std::vector<double> ufv(2 * n, 0.0);
+  if (!desc->sample_hypers) memcpy(ufv.data(), desc->u_fixed, 2 * n * sizeof(double));
+  cudaError_t e = cudaMemcpyAsync(X, desc->X, (size_t)N * desc->n_cov * sizeof(double),
+                                  cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(y, desc->y, N * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(uf, ufv.data(), 2 * n * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tau, tauv.data(), C * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) {
+    rmhmc_free_model(m);
+    return RMHMC_ECUDA;
+  }
+  md.X = X;
+  md.y = y;
+  md.u_fixed = uf;
+  md.tau = tau;
+  *out = m;
+  return RMHMC_OK;
+}
+
+rmhmc_status rmhmc_set_state(rmhmc_model* m, const rmhmc_integrator* integ, const double* q_dev,
+                             const double* p_dev) {
+  if (!m || !q_dev) return RMHMC_EINVAL;
+  rmhmc_status st = check_integ(m, integ, true);
+  if (st != RMHMC_OK) return st;
+  m->g_kind = integ->g_kind;
+  m->alpha = integ->alpha;
+  m->tol = integ->jacobi_tol;
+  m->max_sweeps = integ->max_sweeps;
+  m->reorth_every = integ->reorth_every;
+  m->precision = integ->precision;
+  cudaStream_t s = m->stream;
+  const int C = m->C, dp = m->dp, d = m->d;
+  k_restride<<<nblk((long long)C * dp), 256, 0, s>>>(m->q, dp, q_dev, d, d, C);
+  k_restride<<<nblk((long long)C * dp), 256, 0, s>>>(m->p, dp, p_dev, d, d, C);
+  cudaMemsetAsync(m->status, 0, C * sizeof(int), s);
+  cudaMemsetAsync(m->eig_count, 0, C * sizeof(int), s);
+  cudaMemsetAsync(m->sweeps_acc, 0, C * sizeof(int), s);
+  k_set_identity<<<nblk((long long)C * dp * dp), 256, 0, s>>>(m->PsiT, dp, C);
+  eval_geometry(m, true);
+  m->has_state = true;
+  return check_launch();
+}
+
+rmhmc_status rmhmc_leapfrog(rmhmc_model* m, const rmhmc_integrator* integ, int n_steps,
+                            const double* p_in_dev, double* q_dev, double* p_dev, double* H_dev,
+                            int* status_dev) {
+  if (!m || n_steps < 0) return RMHMC_EINVAL;
+  rmhmc_status st = check_integ(m, integ, false);
+  if (st != RMHMC_OK) return st;
+  cudaStream_t s = m->stream;
+  const int C = m->C, dp = m->dp, d = m->d;
+  if (p_in_dev) {
+    PROF(m, CAT_VECTOR, 0)
+    k_restride<<<nblk((long long)C * dp), 256, 0, s>>>(m->p, dp, p_in_dev, d, d, C);
+  }
+  for (int i = 0; i < n_steps; ++i) leapfrog_step(m, integ->eps, integ->n_fp);
+  if (q_dev) {
+    PROF(m, CAT_VECTOR, 0)
+    k_restride<<<nblk((long long)C * d), 256, 0, s>>>(q_dev, d, m->q, dp, d, C);
+  }
+  if (p_dev) {
+    PROF(m, CAT_VECTOR, 0)
+    k_restride<<<nblk((long long)C * d), 256, 0, s>>>(p_dev, d, m->p, dp, d, C);
+  }
+  if (H_dev) hamiltonian(m, m->p, H_dev);
+  if (status_dev) cudaMemcpyAsync(status_dev, m->status, C * sizeof(int), cudaMemcpyDeviceToDevice, s);
+  return check_launch();
+}
+
+rmhmc_status rmhmc_sample(rmhmc_model* m, const rmhmc_integrator* integ, int n_iter, int n_burn,
+                          uint64_t seed, double* q_samples_dev, double* logp_dev, int* accept_dev,
+                          int* sweeps_dev, int* chain_status_dev) {
+  if (!m || n_iter < 0 || n_burn < 0) return RMHMC_EINVAL;
+  rmhmc_status st = check_integ(m, integ, false);
+  if (st != RMHMC_OK) return st;
+  if (integ->n_leapfrog < 1) return RMHMC_EINVAL;
+  cudaStream_t s = m->stream;
+  const int C = m->C, dp = m->dp, d = m->d;
+  const long long nv = (long long)C * dp, DD = (long long)dp * dp;
+  if (chain_status_dev) cudaMemsetAsync(chain_status_dev, 0, C * sizeof(int), s);
+  for (int it = 0; it < n_burn + n_iter; ++it) {
+    const uint64_t l = m->iter++;
+    const bool rec = it >= n_burn;
+    const long long ro = rec ? (long long)(it - n_burn) : 0;
+    // p = G^{1/2} z (symmetric root)
+    k_normals<<<dim3(nblk((dp + 3) / 4, 128), C), 128, 0, s>>>(m->z, dp, d, C, seed, l);
+    gemv_f64(s, false, dp, dp, m->PsiT, dp, DD, m->z, dp, m->t1, dp, C, 1.0, 0.0);
+    k_scale_g<<<nblk(nv), 256, 0, s>>>(m->t1, m->g, dp, d, C, 1);
+    gemv_f64(s, true, dp, dp, m->PsiT, dp, DD, m->t1, dp, m->p, dp, C, 1.0, 0.0);
+    hamiltonian(m, m->p, m->Ham0);
+    cudaMemcpyAsync(m->q_save, m->q, nv * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(m->PsiT_save, m->PsiT, C * DD * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(m->eig_save, m->eig_count, C * sizeof(int), cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(m->sweeps_acc, 0, C * sizeof(int), s);
+    for (int L = 0; L < integ->n_leapfrog; ++L) leapfrog_step(m, integ->eps, integ->n_fp);
+    hamiltonian(m, m->p, m->Ham1);
+    k_accept<<<nblk(C), 256, 0, s>>>(m->Ham0, m->Ham1, m->status, m->acc, C, seed, l,
+                                     (rec && accept_dev) ? accept_dev + ro * C : nullptr,
+                                     (rec && sweeps_dev) ? sweeps_dev + ro * C : nullptr,
+                                     m->sweeps_acc, chain_status_dev);
+    k_restore<<<dim3(nblk(DD), C), 256, 0, s>>>(m->acc, m->q, m->q_save, m->PsiT, m->PsiT_save,
+                                                m->eig_count, m->eig_save, dp);
+    eval_geometry(m, true);
+    if (rec && (q_samples_dev || logp_dev))
+      k_record<<<nblk((long long)C * d), 256, 0, s>>>(m->q, m->U, dp, d, C,
+                                                       q_samples_dev ? q_samples_dev + ro * C * d : nullptr,
+                                                       logp_dev ? logp_dev + ro * C : nullptr);
+  }
+  return check_launch();
+}
+
+rmhmc_status rmhmc_geometry(rmhmc_model* m, double* U_dev, double* dU_dev, double* hess_dev,
+                            double* lam_dev, double* G_dev, int* sweeps_dev) {
+  if (!m || !m->has_state) return RMHMC_EINVAL;
+  cudaStream_t s = m->stream;
+  const int C = m->C, dp = m->dp, d = m->d;
+  const long long DD = (long long)dp * dp;
+  if (U_dev) cudaMemcpyAsync(U_dev, m->U, C * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (dU_dev) k_restride<<<nblk((long long)C * d), 256, 0, s>>>(dU_dev, d, m->dU, dp, d, C);
+  if (lam_dev) k_restride<<<nblk((long long)C * d), 256, 0, s>>>(lam_dev, d, m->lam, dp, d, C);
+  if (sweeps_dev) cudaMemcpyAsync(sweeps_dev, m->sweeps_last, C * sizeof(int), cudaMemcpyDeviceToDevice, s);
+  if (hess_dev) k_compact<<<nblk((long long)C * d * d), 256, 0, s>>>(hess_dev, m->H, dp, d, C);
+  if (G_dev) {
+    // G = Psi diag(g) Psi^T = PsiT^T (diag(g) PsiT), built in scratch and compacted
+    k_scale_rows<<<dim3(nblk(DD), C), 256, 0, s>>>(m->Y, m->PsiT, m->g, dp, d);
+    gemm_f64(s, true, false, dp, dp, dp, 1.0, m->PsiT, dp, DD, m->Y, dp, DD, 0.0, m->W, dp, DD, C, true, false);
+    k_compact<<<nblk((long long)C * d * d), 256, 0, s>>>(G_dev, m->W, dp, d, C);
+  }
+  return check_launch();
+}
+
+rmhmc_status rmhmc_hamiltonian_grad(rmhmc_model* m, const double* p_dev, double* dHdq_dev,
+                                    double* Ginv_p_dev, double* H_dev) {
+  if (!m || !m->has_state || !p_dev) return RMHMC_EINVAL;
+  cudaStream_t s = m->stream;
+  const int C = m->C, dp = m->dp, d = m->d;
+  k_restride<<<nblk((long long)C * dp), 256, 0, s>>>(m->xin, dp, p_dev, d, d, C);
+  if (dHdq_dev) {
+    grad_h(m, m->xin, m->dHdq);
+    k_restride<<<nblk((long long)C * d), 256, 0, s>>>(dHdq_dev, d, m->dHdq, dp, d, C);
+  }
+  if (Ginv_p_dev) {
+    ginv(m, m->xin, m->v0);
+    k_restride<<<nblk((long long)C * d), 256, 0, s>>>(Ginv_p_dev, d, m->v0, dp, d, C);
+  }
+  if (H_dev) hamiltonian(m, m->xin, H_dev);
+  return check_launch();
+}
+
+}  // extern "C"

@@ -1,0 +1,256 @@
+"""Thin ctypes binding of librmhmc (include/rmhmc.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts workload dicts and torch CUDA
+tensors into the C structs and device pointers the ABI takes, and raises on a non-OK status.
+There is no fallback: if librmhmc.so is missing or fails to load, every call raises.
+"""
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_uint64, c_void_p
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librmhmc.so")
+
+MAX_COLS = 16
+KINDS = {"se": 0, "linear": 1, "overlap": 2}
+LIKS = {"bernoulli": 0, "gaussian": 1}
+GKINDS = {"coth": 0, "sqrt": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+CHAIN_NOTPD, CHAIN_NOTCONV, CHAIN_NONFINITE = 1, 2, 4
+PROF_NCAT = 8
+
+
+class KernelDesc(ctypes.Structure):
+    _fields_ = [("kind", c_int), ("n_cols", c_int), ("cols", c_int * MAX_COLS), ("jitter", c_double),
+                ("prior_a", c_double * 2), ("prior_b", c_double * 2)]
+
+
+class ModelDesc(ctypes.Structure):
+    _fields_ = [("N", c_int), ("n_cov", c_int), ("X", POINTER(c_double)), ("y", POINTER(c_double)),
+                ("lik", c_int), ("noise_var", c_double), ("n_kernels", c_int),
+                ("kernels", POINTER(KernelDesc)), ("sample_hypers", c_int),
+                ("u_fixed", POINTER(c_double))]
+
+
+class IntegratorC(ctypes.Structure):
+    _fields_ = [("eps", c_double), ("n_leapfrog", c_int), ("n_fp", c_int), ("g_kind", c_int),
+                ("alpha", c_double), ("jacobi_tol", c_double), ("max_sweeps", c_int),
+                ("reorth_every", c_int), ("precision", c_int)]
+
+
+@dataclass
+class Integrator:
+    """Leapfrog and geometry settings (rmhmc_integrator)."""
+    eps: float = 0.1
+    n_leapfrog: int = 10
+    n_fp: int = 6
+    g_kind: str = "coth"
+    alpha: float = 1e6
+    jacobi_tol: float = 1e-13
+    max_sweeps: int = 30
+    reorth_every: int = 10
+    precision: str = "fp64"
+
+    def c(self):
+        return IntegratorC(self.eps, self.n_leapfrog, self.n_fp, GKINDS[self.g_kind], self.alpha,
+                           self.jacobi_tol, self.max_sweeps, self.reorth_every,
+                           PRECISIONS[self.precision])
+
+
+class RmhmcError(RuntimeError):
+    pass
+
+
+_lib_handle = None
+
+
+def lib():
+    """Load librmhmc.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(LIB_PATH):
+        raise RmhmcError(f"{LIB_PATH} is missing: build it with `python -m paper_2511_06407_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    L.rmhmc_init_model.argtypes = [POINTER(ModelDesc), c_int, POINTER(c_double), c_void_p,
+                                   POINTER(c_void_p)]
+    L.rmhmc_set_state.argtypes = [c_void_p, POINTER(IntegratorC), c_void_p, c_void_p]
+    L.rmhmc_leapfrog.argtypes = [c_void_p, POINTER(IntegratorC), c_int, c_void_p, c_void_p,
+                                 c_void_p, c_void_p, c_void_p]
+    L.rmhmc_sample.argtypes = [c_void_p, POINTER(IntegratorC), c_int, c_int, c_uint64, c_void_p,
+                               c_void_p, c_void_p, c_void_p, c_void_p]
+    L.rmhmc_geometry.argtypes = [c_void_p] + [c_void_p] * 6
+    L.rmhmc_hamiltonian_grad.argtypes = [c_void_p] + [c_void_p] * 4
+    L.rmhmc_dim.argtypes = [c_void_p]
+    L.rmhmc_dim.restype = c_int
+    L.rmhmc_n_chains.argtypes = [c_void_p]
+    L.rmhmc_n_chains.restype = c_int
+    L.rmhmc_free_model.argtypes = [c_void_p]
+    L.rmhmc_free_model.restype = None
+    L.rmhmc_profile.argtypes = [c_void_p, c_int]
+    L.rmhmc_profile.restype = c_int
+    L.rmhmc_profile_read.argtypes = [c_void_p, POINTER(c_double), POINTER(c_double),
+                                     POINTER(ctypes.c_longlong)]
+    L.rmhmc_profile_read.restype = c_int
+    L.rmhmc_profile_category.argtypes = [c_int]
+    L.rmhmc_profile_category.restype = c_char_p
+    L.rmhmc_fp64_peak.argtypes = [c_void_p, c_int, POINTER(c_double)]
+    L.rmhmc_fp64_peak.restype = c_int
+    L.rmhmc_version.argtypes = []
+    L.rmhmc_status_string.argtypes = [c_int]
+    L.rmhmc_status_string.restype = c_char_p
+    L.rmhmc_version.restype = c_char_p
+    for name in ("rmhmc_init_model", "rmhmc_set_state", "rmhmc_leapfrog", "rmhmc_sample",
+                 "rmhmc_geometry", "rmhmc_hamiltonian_grad"):
+        getattr(L, name).restype = c_int
+    _lib_handle = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise RmhmcError(f"rmhmc status {rc}: {lib().rmhmc_status_string(rc).decode()}")
+
+
+def _ptr(t, shape=None, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise RmhmcError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise RmhmcError(f"expected dtype {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise RmhmcError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Model:
+    """One problem (a workload dict) with n_chains chains on the current CUDA device/stream."""
+
+    def __init__(self, problem, n_chains, tau=None, stream=None):
+        import torch
+        L = lib()
+        X = np.ascontiguousarray(problem["X"], dtype=np.float64)
+        y = np.ascontiguousarray(problem["y"], dtype=np.float64)
+        ks = (KernelDesc * len(problem["kernels"]))()
+        for i, k in enumerate(problem["kernels"]):
+            cols = list(k["cols"])
+            ks[i].kind = KINDS[k["kind"]]
+            ks[i].n_cols = len(cols)
+            for j, cidx in enumerate(cols):
+                ks[i].cols[j] = int(cidx)
+            ks[i].jitter = float(k["jitter"])
+            ks[i].prior_a[0], ks[i].prior_a[1] = (float(v) for v in k["prior_a"])
+            ks[i].prior_b[0], ks[i].prior_b[1] = (float(v) for v in k["prior_b"])
+        uf = None
+        if not problem["sample_hypers"]:
+            uf = np.ascontiguousarray(problem["u_fixed"], dtype=np.float64)
+        desc = ModelDesc(X.shape[0], X.shape[1], X.ctypes.data_as(POINTER(c_double)),
+                         y.ctypes.data_as(POINTER(c_double)), LIKS[problem["lik"]],
+                         float(problem["noise_var"]), len(problem["kernels"]), ks,
+                         1 if problem["sample_hypers"] else 0,
+                         uf.ctypes.data_as(POINTER(c_double)) if uf is not None else None)
+        tau_arr = None
+        if tau is not None:
+            tau_arr = np.ascontiguousarray(np.broadcast_to(np.asarray(tau, dtype=np.float64), (n_chains,)))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = c_void_p()
+        _check(L.rmhmc_init_model(ctypes.byref(desc), int(n_chains),
+                                  tau_arr.ctypes.data_as(POINTER(c_double)) if tau_arr is not None else None,
+                                  c_void_p(stream.cuda_stream), ctypes.byref(handle)))
+        self._h = handle
+        self.d = L.rmhmc_dim(self._h)
+        self.n_chains = L.rmhmc_n_chains(self._h)
+        self.integ = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rmhmc_free_model(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _integ(self, integ):
+        integ = integ or self.integ or Integrator()
+        return integ, integ.c()
+
+    def set_state(self, q, p=None, integ=None):
+        import torch
+        integ, ic = self._integ(integ)
+        self.integ = integ
+        sh = (self.n_chains, self.d)
+        _check(lib().rmhmc_set_state(self._h, ctypes.byref(ic), _ptr(q, sh, torch.float64),
+                                     _ptr(p, sh, torch.float64)))
+
+    def leapfrog(self, n_steps, q_out=None, p_out=None, H_out=None, status_out=None, integ=None,
+                 p_in=None):
+        import torch
+        integ, ic = self._integ(integ)
+        sh = (self.n_chains, self.d)
+        _check(lib().rmhmc_leapfrog(self._h, ctypes.byref(ic), int(n_steps),
+                                    _ptr(p_in, sh, torch.float64),
+                                    _ptr(q_out, sh, torch.float64), _ptr(p_out, sh, torch.float64),
+                                    _ptr(H_out, (self.n_chains,), torch.float64),
+                                    _ptr(status_out, (self.n_chains,), torch.int32)))
+
+    def sample(self, n_iter, n_burn, seed, q_samples=None, logp=None, accept=None, sweeps=None,
+               chain_status=None, integ=None):
+        import torch
+        integ, ic = self._integ(integ)
+        C, d = self.n_chains, self.d
+        _check(lib().rmhmc_sample(self._h, ctypes.byref(ic), int(n_iter), int(n_burn), int(seed),
+                                  _ptr(q_samples, (n_iter, C, d), torch.float64),
+                                  _ptr(logp, (n_iter, C), torch.float64),
+                                  _ptr(accept, (n_iter, C), torch.int32),
+                                  _ptr(sweeps, (n_iter, C), torch.int32),
+                                  _ptr(chain_status, (C,), torch.int32)))
+
+    def geometry(self, U=None, dU=None, hess=None, lam=None, G=None, sweeps=None):
+        import torch
+        C, d = self.n_chains, self.d
+        f64 = torch.float64
+        _check(lib().rmhmc_geometry(self._h, _ptr(U, (C,), f64), _ptr(dU, (C, d), f64),
+                                    _ptr(hess, (C, d, d), f64), _ptr(lam, (C, d), f64),
+                                    _ptr(G, (C, d, d), f64), _ptr(sweeps, (C,), torch.int32)))
+
+    def hamiltonian_grad(self, p, dHdq=None, Ginv_p=None, H=None):
+        import torch
+        C, d = self.n_chains, self.d
+        f64 = torch.float64
+        _check(lib().rmhmc_hamiltonian_grad(self._h, _ptr(p, (C, d), f64), _ptr(dHdq, (C, d), f64),
+                                            _ptr(Ginv_p, (C, d), f64), _ptr(H, (C,), f64)))
+
+
+    def profile(self, enable=True):
+        _check(lib().rmhmc_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{category: (ms, flops, launches)} since profile(True); synchronises the stream."""
+        n = PROF_NCAT
+        ms, fl, ln = (c_double * n)(), (c_double * n)(), (ctypes.c_longlong * n)()
+        _check(lib().rmhmc_profile_read(self._h, ms, fl, ln))
+        return {lib().rmhmc_profile_category(i).decode(): (ms[i], fl[i], int(ln[i])) for i in range(n)}
+
+
+def fp64_peak_tflops(ms_target=200, stream=None):
+    """Measured FP64 FMA throughput of the current GPU (TFLOP/s)."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    out = c_double()
+    _check(lib().rmhmc_fp64_peak(c_void_p(stream.cuda_stream), int(ms_target), ctypes.byref(out)))
+    return out.value
+
+
+def version():
+    return lib().rmhmc_version().decode()

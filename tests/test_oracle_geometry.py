@@ -1,9 +1,10 @@
 """Pins for the oracle's SoftAbs map and Riemannian geometry: mpmath reference values, closed-form
 limits, finite differences of the metric and the Hamiltonian, and the positive-definite special
 case (CPU only)."""
-import mpmath
 import numpy as np
 import pytest
+
+mpmath = pytest.importorskip("mpmath")
 
 from oracle import model as mdl
 from oracle.geometry import Geometry

@@ -4,7 +4,6 @@ import numpy as np
 import pytest
 import scipy.stats as st
 from scipy.spatial.distance import cdist
-from sklearn.gaussian_process.kernels import RBF, DotProduct
 
 from oracle import model as mdl
 from oracle.kernels import kernel_derivs
@@ -39,6 +38,7 @@ PROBLEMS = _problems()
 
 @pytest.mark.parametrize("u", [(0.3, -0.2), (-0.5, 0.6)])
 def test_se_kernel_matches_sklearn(u):
+    RBF = pytest.importorskip("sklearn.gaussian_process.kernels").RBF
     X = np.random.default_rng(0).uniform(-1, 1, (9, 2))
     K, D1, _, _ = kernel_derivs("se", X, u, 1e-6)
     c, ell = np.exp(u[0]), np.exp(u[1])
@@ -49,6 +49,7 @@ def test_se_kernel_matches_sklearn(u):
 
 
 def test_linear_kernel_matches_sklearn():
+    DotProduct = pytest.importorskip("sklearn.gaussian_process.kernels").DotProduct
     X = (np.random.default_rng(1).uniform(size=(8, 2)) < 0.5).astype(float)
     u = (0.2, -0.4)
     K, D1, _, _ = kernel_derivs("linear", X, u, 1e-6)
@@ -141,3 +142,42 @@ def test_third_derivatives_fd(pi, oracle_model):
     # a third-derivative tensor is symmetric in all three indices
     np.testing.assert_allclose(T3, T3.transpose(1, 0, 2), atol=1e-10 * np.abs(T3).max())
     np.testing.assert_allclose(T3, T3.transpose(2, 1, 0), atol=1e-10 * np.abs(T3).max())
+
+
+@pytest.mark.parametrize("state", ["zero", "random"])
+def test_potential_matches_40_digit_evaluation(oracle_model, state):
+    """U of an ill-conditioned problem (SE kernel, jitter 1e-6, cond(K) ~ 1e7) against the same
+    definition evaluated in 40-digit arithmetic (mpmath Cholesky), at f = 0 and at a random point
+    off the prior manifold (huge K^-1 f): to within the first-order error that rounding K to FP64
+    already commits (tests/conftest.potential_rounding_bound; 2e-11 relative at f = 0, 1e-9 at the
+    random point)."""
+    from conftest import potential_rounding_bound
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    prob = wl.gp_classification(24, seed=0)
+    m = oracle_model(prob)
+    q = wl.random_state(prob, 1, seed=10)[0]
+    if state == "zero":
+        q[:] = 0.0
+    f, u = mdl.split(m, q)
+    X, N = m.X, m.N
+    c, th = mp.e ** mp.mpf(u[0, 0]), mp.e ** mp.mpf(u[0, 1])
+    K = mp.matrix(N, N)
+    for i in range(N):
+        for j in range(N):
+            sq = sum((mp.mpf(X[i, k]) - mp.mpf(X[j, k])) ** 2 for k in range(2))
+            K[i, j] = c * mp.e ** (-sq / (2 * th * th)) + (c * mp.mpf(1e-6) if i == j else 0)
+    L = mp.cholesky(K)
+    t = mp.lu_solve(L, mp.matrix([mp.mpf(v) for v in f[0]]))
+    quad = sum(t[i] ** 2 for i in range(N))
+    logdet = 2 * sum(mp.log(L[i, i]) for i in range(N))
+    lik = sum(mp.log(1 + mp.e ** mp.mpf(f[0][i])) - mp.mpf(m.y[i]) * mp.mpf(f[0][i]) for i in range(N))
+    pri = sum(2 * mp.log(2) - mp.loggamma(2) - 2 * mp.mpf(u[0, h]) - 2 * mp.e ** (-mp.mpf(u[0, h]))
+              for h in range(2))
+    exact = float(lik + quad / 2 + logdet / 2 + mp.mpf(N) / 2 * mp.log(2 * mp.pi) - pri)
+    assert np.linalg.cond(kernel_derivs("se", X, u[0], 1e-6)[0]) > 1e5
+    err = abs(mdl.potential(m, q) - exact)
+    bound = potential_rounding_bound(m, q)
+    assert err <= max(1e-12 * abs(exact), bound), (err, bound)
+    # a dropped or wrong term would be orders of magnitude above the bound
+    assert bound < 1e-8 * abs(exact)
