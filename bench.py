@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 from paper_2511_06407_b300 import workloads as wl  # noqa: E402
 
-N_INPUTS, N_CHAINS, EPS, N_FP = 400, 64, 0.01, 6
+N_INPUTS, N_CHAINS, EPS, N_FP = 400, 64, 0.005, 6
 SUBSTEPS_PER_LEAPFROG = 2 * N_FP + 1
 METRIC = "RMHMC leapfrog substeps/s"
 UNIT = "substeps/s"
@@ -105,15 +105,23 @@ def oracle_leapfrogs(seconds, max_leapfrogs=None):
     from oracle.model import from_problem
     prob = wl.gp_classification(N_INPUTS, seed=0)
     m = from_problem(prob)
-    q = np.zeros(m.d)
-    geo = Geometry(m, q, 1.0)
-    p = geo.sqrtG_z(np.random.default_rng(0).standard_normal(m.d))
+    rng = np.random.default_rng(0)
+    geo0 = Geometry(m, np.zeros(m.d), 1.0)
+    q, geo = np.zeros(m.d), geo0
+    p = geo.sqrtG_z(rng.standard_normal(m.d))
     n, t0 = 0, time.perf_counter()
     while True:
-        q, p, geo = leapfrog(m, q, p, EPS, N_FP, geo=geo)
-        n += 1
+        try:
+            with np.errstate(all="ignore"):
+                q, p, geo = leapfrog(m, q, p, EPS, N_FP, geo=geo)
+            n += 1
+        except np.linalg.LinAlgError:
+            # the trajectory left the region where K is positive definite: restart from f = 0,
+            # u = 0 with a fresh momentum (only completed leapfrogs are counted)
+            q, geo = np.zeros(m.d), geo0
+            p = geo.sqrtG_z(rng.standard_normal(m.d))
         el = time.perf_counter() - t0
-        if el >= seconds or (max_leapfrogs and n >= max_leapfrogs):
+        if (el >= seconds and n > 0) or (max_leapfrogs and n >= max_leapfrogs):
             break
     return SUBSTEPS_PER_LEAPFROG * n / el, n, el
 

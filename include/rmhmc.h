@@ -60,6 +60,13 @@ typedef enum { RMHMC_LIK_BERNOULLI_LOGIT = 0, RMHMC_LIK_GAUSSIAN = 1 } rmhmc_lik
 typedef enum { RMHMC_K_SE = 0, RMHMC_K_LINEAR = 1, RMHMC_K_OVERLAP = 2 } rmhmc_kernel_kind;
 typedef enum { RMHMC_G_COTH = 0, RMHMC_G_SQRT = 1 } rmhmc_gkind;
 typedef enum { RMHMC_FP64 = 0, RMHMC_MIXED = 1 } rmhmc_precision;
+/* Jacobi stopping rules (u = 2^-53, floor = 4 u ||M||_F, d_min = min_i |m_ii|): sweeps continue
+ * while some pair j != l has
+ *   METRIC:   |m_jl| > max(zeta |m_jj m_ll| / d_min, floor)  -- first-order error of G^-1, W1, W2
+ *             and log|G| below zeta relative; eigenvalues inside near-degenerate clusters are
+ *             left mixed (the metric is insensitive to that), which saves most sweeps
+ *   RELATIVE: |m_jl| > max(zeta sqrt(|m_jj m_ll|), floor)   -- every eigenpair resolved */
+typedef enum { RMHMC_JACOBI_METRIC = 0, RMHMC_JACOBI_RELATIVE = 1 } rmhmc_jacobi_rule;
 
 #define RMHMC_MAX_COLS 16
 #define RMHMC_MAX_KERNELS 3
@@ -91,17 +98,19 @@ typedef struct {
 } rmhmc_model_desc;
 
 /* Integrator and geometry settings. The geometry fields (g_kind, alpha, jacobi_tol, max_sweeps,
- * reorth_every, precision) must be the same in every call on a model as in rmhmc_set_state. */
+ * reorth_every, precision, jacobi_rule) must be the same in every call on a model as in
+ * rmhmc_set_state. */
 typedef struct {
   double eps;          /* leapfrog step size (Eq. leapfrog) */
   int n_leapfrog;      /* leapfrogs per MH proposal (C in Algorithm 1) */
   int n_fp;            /* fixed-point iterations for each implicit half-step, >= 1 */
   int g_kind;          /* rmhmc_gkind: g = l coth(alpha l) or sqrt(1/alpha^2 + l^2) */
   double alpha;        /* soft-abs sharpness (kappa = 1 / alpha for the sqrt map) */
-  double jacobi_tol;   /* zeta: stop when ||offdiag(M)||_F <= zeta ||M||_F (Sec. 2.4) */
+  double jacobi_tol;   /* zeta, the tolerance of Sec. 2.4 (see jacobi_rule for how it is applied) */
   int max_sweeps;      /* Jacobi sweep limit per eigen-update */
   int reorth_every;    /* Gram-Schmidt of Psi every this many eigen-updates (Sec. 2.4); 0 = never */
   int precision;       /* rmhmc_precision; only RMHMC_FP64 in this build */
+  int jacobi_rule;     /* rmhmc_jacobi_rule: when M = Psi^T H Psi counts as diagonal */
 } rmhmc_integrator;
 
 typedef struct rmhmc_model rmhmc_model;

@@ -26,11 +26,16 @@ def offdiag_norm(M):
 U_ROUND = 2.0 ** -53
 
 
-def relative_offdiag(M, tol):
-    """max over j != l of |m_jl| / max(tol sqrt(|m_jj m_ll|), 4 u ||M||_F); <= 1 is converged."""
+def relative_offdiag(M, tol, rule="relative"):
+    """max over j != l of |m_jl| / max(tol * den_jl, 4 u ||M||_F); <= 1 is converged.
+    den_jl = sqrt(|m_jj m_ll|) ('relative') or |m_jj m_ll| / min_i |m_ii| ('metric')."""
     d = np.abs(np.diag(M))
     floor = 4.0 * U_ROUND * np.linalg.norm(M)
-    den = np.maximum(tol * np.sqrt(np.outer(d, d)), max(floor, 1e-300))
+    if rule == "metric":
+        den = np.outer(d, d) / max(d.min(), 1e-300)
+    else:
+        den = np.sqrt(np.outer(d, d))
+    den = np.maximum(tol * den, max(floor, 1e-300))
     R = np.abs(M) / den
     np.fill_diagonal(R, 0.0)
     return float(R.max()) if R.size else 0.0
@@ -38,8 +43,10 @@ def relative_offdiag(M, tol):
 
 def jacobi_eigh(H, Psi0=None, tol=1e-13, max_sweeps=30, rule="relative"):
     """Returns (lam, Psi, sweeps). Psi0 = None is the cold start Psi0 = I.
-    rule 'relative': continue while some |m_jl| > max(tol sqrt(|m_jj m_ll|), 4 u ||M||_F) (the
-    rule the CUDA path uses); rule 'frobenius': continue while ||offdiag(M)||_F > tol ||M||_F."""
+    rule 'relative': continue while some |m_jl| > max(tol sqrt(|m_jj m_ll|), 4 u ||M||_F);
+    rule 'metric': continue while some |m_jl| > max(tol |m_jj m_ll| / min_i |m_ii|, 4 u ||M||_F)
+    (the coupling's first-order effect on G^-1 below tol relative); rule 'frobenius': continue
+    while ||offdiag(M)||_F > tol ||M||_F."""
     H = np.asarray(H, dtype=np.float64)
     d = H.shape[0]
     Psi = np.eye(d) if Psi0 is None else np.array(Psi0, dtype=np.float64)
@@ -49,7 +56,7 @@ def jacobi_eigh(H, Psi0=None, tol=1e-13, max_sweeps=30, rule="relative"):
     def unconverged(M):
         if rule == "frobenius":
             return offdiag_norm(M) > tol * np.linalg.norm(M)
-        return relative_offdiag(M, tol) > 1.0
+        return relative_offdiag(M, tol, rule) > 1.0
 
     while unconverged(M) and sweeps < max_sweeps:
         for j in range(d - 1):

@@ -13,12 +13,16 @@
 // batch sizes used); accesses are 64-byte row segments, and loads bypass L1 (ld.global.cg) so that
 // writes by other CTAs of the cluster are seen after each barrier.
 //
-// Stopping rule (relative per pair, with a rounding floor): sweeps continue while some
-// |m_jl| > max(zeta sqrt(|m_jj m_ll|), 4 u ||M||_F) (checked before each sweep, so an unchanged
-// basis costs 0 sweeps), up to max_sweeps; hitting the limit marks the chain RMHMC_CHAIN_NOTCONV.
-// A Frobenius rule ||offdiag||_F <= zeta ||M||_F would leave couplings of ~zeta ||H|| between the
-// small eigenpairs, which dominate G^-1; the floor stops the rule from chasing rounding noise
-// (rotations against entries of size ||M|| leave couplings of ~u ||M|| behind).
+// Stopping rule (per pair, with a rounding floor; rmhmc_jacobi_rule): sweeps continue while some
+// pair j != l has |m_jl| > max(zeta * den(j, l), 4 u ||M||_F), den = |m_jj m_ll| / min_i |m_ii|
+// (METRIC: the first-order error that coupling puts into G^-1, W1, W2 and log|G| stays below zeta
+// relative) or den = sqrt(|m_jj m_ll|) (RELATIVE: every eigenpair resolved). The test runs before
+// each sweep, so an unchanged basis costs 0 sweeps; hitting max_sweeps marks the chain
+// RMHMC_CHAIN_NOTCONV. A Frobenius rule ||offdiag||_F <= zeta ||M||_F would leave couplings of
+// ~zeta ||H|| between the small eigenpairs, which dominate G^-1; the floor stops the rule from
+// chasing rounding noise (rotations against entries of size ||M|| leave ~u ||M|| behind). In the
+// dual GP model K^-1 puts ~N eigenvalues of H in a near-degenerate cluster near 1/(c jitter),
+// which every change of q re-mixes: RELATIVE needs 6-10 sweeps per update there, METRIC 2-3.
 // Each 2 x 2 rotation is the symmetric Schur decomposition (Golub and Van Loan, Matrix
 // Computations, Sec. 8.5).
 #include <cooperative_groups.h>
@@ -69,7 +73,17 @@ __device__ __forceinline__ void schur2(double app, double aqq, double apq, doubl
 
 // Inner exact solve of one 16 x 16 sub-problem by a single warp: A <- V^T A V diagonal. Returns
 // false when the block already met the tolerance (then V = I exactly and A is unchanged).
-__device__ bool inner_solve(double* A, double* V, double* cs, double tol2, double floor2) {
+// Stopping test for one pair: m_jl^2 > max(tol2 * den(j, l), floor2) with den = |m_jj m_ll| (RELATIVE)
+// or (m_jj m_ll)^2 / dmin^2 (METRIC); returns the ratio (> 1 means unconverged).
+__device__ __forceinline__ double pair_ratio(double v, double djj, double dll, double tol2,
+                                             double floor2, int rule, double dmin2) {
+  const double p = fabs(djj * dll);
+  const double den = rule == RMHMC_JACOBI_METRIC ? p * p / dmin2 : p;
+  return v * v / fmax(tol2 * den, fmax(floor2, 1e-300));
+}
+
+__device__ bool inner_solve(double* A, double* V, double* cs, double tol2, double floor2, int rule,
+                            double dmin2) {
   const int lane = threadIdx.x & 31;
   bool rotated = false;
   for (int e = lane; e < SB * SB; e += 32) V[(e / SB) * SBP + e % SB] = (e / SB == e % SB) ? 1.0 : 0.0;
@@ -80,7 +94,7 @@ __device__ bool inner_solve(double* A, double* V, double* cs, double tol2, doubl
       const int i = e / SB, j = e % SB;
       const double v = A[i * SBP + j];
       if (i != j && v != 0.0)
-        crit = fmax(crit, v * v / fmax(tol2 * fabs(A[i * SBP + i] * A[j * SBP + j]), fmax(floor2, 1e-300)));
+        crit = fmax(crit, pair_ratio(v, A[i * SBP + i], A[j * SBP + j], tol2, floor2, rule, dmin2));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) crit = fmax(crit, __shfl_xor_sync(0xffffffffu, crit, o));
@@ -183,7 +197,8 @@ __device__ __forceinline__ void load_v(double* dst, const double* src) {
 }
 
 __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, double* __restrict__ Pb,
-                                                   double* __restrict__ lamb, int dp, double tol,
+                                                   double* __restrict__ lamb, int dp, int d, int rule,
+                                                   double tol,
                                                    int max_sweeps, int* __restrict__ status,
                                                    int* __restrict__ sweeps_out,
                                                    int* __restrict__ sweeps_acc,
@@ -220,26 +235,37 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
   int sweeps = 0;
   bool converged = false;
   for (;;) {
-    // ---- convergence test. Pass 1: ||M||_F^2. Pass 2: max over j != l of
-    //      m_jl^2 / max(zeta^2 |m_jj m_ll|, floor^2), floor = 4 u ||M||_F (rounding level)
-    double tot = 0.0;
+    // ---- convergence test. Pass 1: ||M||_F^2 and min_i<d |m_ii|. Pass 2: the worst pair ratio
+    //      (pair_ratio) under the chosen rule, with floor = 4 u ||M||_F (rounding level).
+    double tot = 0.0, dmin = 1e308;
     for (long long e = (long long)rank * blockDim.x + tid; e < (long long)dp * dp;
          e += (long long)C * blockDim.x) {
       const double v = __ldcg(M + e);
       tot = fma(v, v, tot);
+      const int i = (int)(e / dp);
+      if (i < d && (long long)i * dp + i == e) dmin = fmin(dmin, fabs(v));
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    if (lane == 0) red[0][warp] = tot;
+    for (int o = 16; o > 0; o >>= 1) {
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      dmin = fmin(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+    }
+    if (lane == 0) { red[0][warp] = tot; red[1][warp] = dmin; }
     __syncthreads();
     if (tid == 0) {
-      double a = 0.0;
-      for (int w = 0; w < NW; ++w) a += red[0][w];
+      double a = 0.0, b = 1e308;
+      for (int w = 0; w < NW; ++w) { a += red[0][w]; b = fmin(b, red[1][w]); }
       __stcg(slots + (sweeps & 1) * 32 + 2 * rank, a);
+      __stcg(slots + (sweeps & 1) * 32 + 2 * rank + 1, b);
     }
     cluster.sync();
     tot = 0.0;
-    for (int r = 0; r < C; ++r) tot += __ldcg(slots + (sweeps & 1) * 32 + 2 * r);
+    dmin = 1e308;
+    for (int r = 0; r < C; ++r) {
+      tot += __ldcg(slots + (sweeps & 1) * 32 + 2 * r);
+      dmin = fmin(dmin, __ldcg(slots + (sweeps & 1) * 32 + 2 * r + 1));
+    }
+    const double dmin2 = fmax(dmin * dmin, 1e-300);
     const double floor2 = 16.0 * 1.2325951644078310e-32 * tot;  // (4 u)^2 ||M||_F^2, u = 2^-53
     double crit = 0.0, bad = isfinite(tot) ? 0.0 : 1.0;
     for (long long e = (long long)rank * blockDim.x + tid; e < (long long)dp * dp;
@@ -248,8 +274,8 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
       if (j == l) continue;
       const double v = __ldcg(M + e);
       if (v == 0.0) continue;
-      const double den = fabs(__ldcg(M + (long long)j * dp + j) * __ldcg(M + (long long)l * dp + l));
-      const double r = v * v / fmax(tol * tol * den, fmax(floor2, 1e-300));
+      const double r = pair_ratio(v, __ldcg(M + (long long)j * dp + j), __ldcg(M + (long long)l * dp + l),
+                                  tol * tol, floor2, rule, dmin2);
       if (!(r <= 1e308)) bad = 1.0;
       crit = fmax(crit, r);
     }
@@ -289,7 +315,7 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
           X[a * SBP + b] = __ldcg(M + (long long)gidx(I, J, a) * dp + gidx(I, J, b));
         }
         __syncwarp();
-        const bool rot = inner_solve(X, Va, cs[warp], itol2, floor2);
+        const bool rot = inner_solve(X, Va, cs[warp], itol2, floor2, rule, dmin2);
         if (rot) {
           for (int e = lane; e < SB * SB; e += 32) {
             const int a = e / SB, b = e % SB;
@@ -445,17 +471,16 @@ int jacobi_cluster_size(int n_chains) {
 }
 
 void jacobi_f64(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,
-                double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
+                int rule, double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
                 JacobiWork w, int cluster) {
-  (void)d;
   const size_t smem = (size_t)NW * WARP_SMEM * sizeof(double);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  launch_cluster(k_jacobi, n_chains, cluster, smem, s, M, PsiT, lam, dp, tol, max_sweeps, status,
-                 sweeps_out, sweeps_acc, w.V, w.D, w.slots, w.flags);
+  launch_cluster(k_jacobi, n_chains, cluster, smem, s, M, PsiT, lam, dp, d, rule, tol, max_sweeps,
+                 status, sweeps_out, sweeps_acc, w.V, w.D, w.slots, w.flags);
 }
 
 void mgs_rows_f64(cudaStream_t s, double* PsiT, int dp, int d, int n_chains, const int* eig_count,

@@ -89,7 +89,7 @@ struct JacobiWork {
   int* flags;     // n_chains x (nb/2): pair rotated in the current round
 };
 void jacobi_f64(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,
-                double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
+                int rule, double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
                 JacobiWork w, int cluster);
 // Modified Gram-Schmidt on the first d rows of PsiT (dp x dp per chain), for chains whose
 // eig_count is a positive multiple of every (0 = never).

@@ -298,7 +298,7 @@ struct rmhmc_model {
   int N = 0, n = 0, P = 0, d = 0, dp = 0, C = 0;
   int cluster = 1;
   bool has_state = false;
-  int g_kind = 0, max_sweeps = 30, reorth_every = 10, precision = 0;
+  int g_kind = 0, max_sweeps = 30, reorth_every = 10, precision = 0, jacobi_rule = 0;
   double alpha = 1e6, tol = 1e-13;
   uint64_t iter = 0;
   std::vector<void*> allocs;
@@ -431,8 +431,8 @@ void eval_geometry(rmhmc_model* m, bool third) {
   PROF(m, CAT_GEMM, Cf * gemm_flops(df, df, df, true, false))
   gemm_f64(s, false, false, dp, dp, dp, 1.0, m->PsiT, dp, DD, m->Y, dp, DD, 0.0, m->M, dp, DD, C, true, false);
   PROF(m, CAT_JACOBI, 0)
-  jacobi_f64(s, m->M, m->PsiT, m->lam, dp, d, C, m->tol, m->max_sweeps, m->status, m->sweeps_last,
-             m->sweeps_acc, m->jw, m->cluster);
+  jacobi_f64(s, m->M, m->PsiT, m->lam, dp, d, C, m->jacobi_rule, m->tol, m->max_sweeps, m->status,
+             m->sweeps_last, m->sweeps_acc, m->jw, m->cluster);
   PROF(m, CAT_VECTOR, 0)
   k_inc<<<nblk(C), 256, 0, s>>>(m->eig_count, C, m->sweeps_total, m->sweeps_last);
   PROF(m, CAT_VECTOR, 0)
@@ -518,10 +518,13 @@ rmhmc_status check_integ(const rmhmc_model* m, const rmhmc_integrator* in, bool 
   if (in->g_kind != RMHMC_G_COTH && in->g_kind != RMHMC_G_SQRT) return RMHMC_EINVAL;
   if (!(in->alpha > 0.0) || !(in->jacobi_tol > 0.0) || in->max_sweeps < 0 || in->reorth_every < 0)
     return RMHMC_EINVAL;
+  if (in->jacobi_rule != RMHMC_JACOBI_METRIC && in->jacobi_rule != RMHMC_JACOBI_RELATIVE)
+    return RMHMC_EINVAL;
   if (!for_state) {
     if (!m->has_state) return RMHMC_EINVAL;
     if (in->g_kind != m->g_kind || in->alpha != m->alpha || in->jacobi_tol != m->tol ||
-        in->max_sweeps != m->max_sweeps || in->reorth_every != m->reorth_every)
+        in->max_sweeps != m->max_sweeps || in->reorth_every != m->reorth_every ||
+        in->jacobi_rule != m->jacobi_rule)
       return RMHMC_EINVAL;
     if (!(in->eps > 0.0) || in->n_fp < 1) return RMHMC_EINVAL;
   }
@@ -782,6 +785,7 @@ rmhmc_status rmhmc_set_state(rmhmc_model* m, const rmhmc_integrator* integ, cons
   m->max_sweeps = integ->max_sweeps;
   m->reorth_every = integ->reorth_every;
   m->precision = integ->precision;
+  m->jacobi_rule = integ->jacobi_rule;
   cudaStream_t s = m->stream;
   const int C = m->C, dp = m->dp, d = m->d;
   k_restride<<<nblk((long long)C * dp), 256, 0, s>>>(m->q, dp, q_dev, d, d, C);

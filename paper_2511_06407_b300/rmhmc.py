@@ -19,6 +19,7 @@ KINDS = {"se": 0, "linear": 1, "overlap": 2}
 LIKS = {"bernoulli": 0, "gaussian": 1}
 GKINDS = {"coth": 0, "sqrt": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+JACOBI_RULES = {"metric": 0, "relative": 1}
 CHAIN_NOTPD, CHAIN_NOTCONV, CHAIN_NONFINITE = 1, 2, 4
 PROF_NCAT = 8
 
@@ -38,7 +39,7 @@ class ModelDesc(ctypes.Structure):
 class IntegratorC(ctypes.Structure):
     _fields_ = [("eps", c_double), ("n_leapfrog", c_int), ("n_fp", c_int), ("g_kind", c_int),
                 ("alpha", c_double), ("jacobi_tol", c_double), ("max_sweeps", c_int),
-                ("reorth_every", c_int), ("precision", c_int)]
+                ("reorth_every", c_int), ("precision", c_int), ("jacobi_rule", c_int)]
 
 
 @dataclass
@@ -53,11 +54,12 @@ class Integrator:
     max_sweeps: int = 30
     reorth_every: int = 10
     precision: str = "fp64"
+    jacobi_rule: str = "metric"
 
     def c(self):
         return IntegratorC(self.eps, self.n_leapfrog, self.n_fp, GKINDS[self.g_kind], self.alpha,
                            self.jacobi_tol, self.max_sweeps, self.reorth_every,
-                           PRECISIONS[self.precision])
+                           PRECISIONS[self.precision], JACOBI_RULES[self.jacobi_rule])
 
 
 class RmhmcError(RuntimeError):

@@ -65,3 +65,30 @@ def test_jacobi_warm_start_needs_one_to_two_sweeps_cold_grows_with_d():
     _, _, s0 = jacobi_eigh(np.diag([3.0, -1.0, 2.0]))
     assert s0 == 0
     assert offdiag_norm(np.eye(3)) == 0.0
+
+
+def test_metric_rule_needs_fewer_sweeps_on_a_gp_hessian_and_keeps_G_inverse():
+    """On the Hessian of the dual GP model (K^-1 puts ~N eigenvalues in a near-degenerate cluster
+    near 1/(c jitter)), the 'metric' stopping rule stops earlier than 'relative' from a warm start
+    while G^-1 p (soft-abs metric, alpha = 1e6) stays as accurate."""
+    from oracle import model as mdl
+    from oracle.softabs import g_and_gprime
+    from paper_2511_06407_b300 import workloads as wl
+    prob = wl.gp_classification(40, seed=0)
+    m = mdl.from_problem(prob)
+    q0 = wl.random_state(prob, 1, seed=3, f_scale=0.2, u_scale=0.1)[0]
+    _, P0, _ = jacobi_eigh(mdl.hessian(m, q0))
+    q1 = q0 + 1e-3 * np.random.default_rng(1).standard_normal(m.d)
+    H1 = mdl.hessian(m, q1)
+    p = np.random.default_rng(2).standard_normal(m.d)
+    lam_ref, Psi_ref = np.linalg.eigh(H1)
+    g_ref, _ = g_and_gprime(lam_ref)
+    ref = Psi_ref @ ((Psi_ref.T @ p) / g_ref)
+    out = {}
+    for rule in ("relative", "metric"):
+        lam, Psi, sw = jacobi_eigh(H1, Psi0=P0, rule=rule)
+        g, _ = g_and_gprime(lam)
+        v = Psi @ ((Psi.T @ p) / g)
+        out[rule] = (sw, np.linalg.norm(v - ref) / np.linalg.norm(ref))
+    assert out["metric"][0] < out["relative"][0], out
+    assert out["metric"][1] < 1e-8 and out["relative"][1] < 1e-8, out
