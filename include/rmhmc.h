@@ -48,7 +48,8 @@ typedef enum {
   RMHMC_ENONFINITE = 5, /* per chain: a non-finite Hamiltonian or position */
   RMHMC_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
   RMHMC_ENOTIMPL = 7,   /* option not implemented in this build */
-  RMHMC_ENOTPD = 8      /* per chain: a kernel matrix lost positive definiteness (Cholesky) */
+  RMHMC_ENOTPD = 8,     /* per chain: a kernel matrix lost positive definiteness (Cholesky) */
+  RMHMC_ESCRATCH = 9    /* rmhmc_eigh_noalloc: the batch does not fit its fixed workspace */
 } rmhmc_status;
 
 /* per-chain status bits written to status_dev / chain_status_dev (0 = healthy) */
@@ -182,6 +183,28 @@ const char* rmhmc_profile_category(int i);
  * dependent-chain DFMA kernel on every SM for about ms_target milliseconds on cuda_stream and writes
  * the achieved TFLOP/s (2 flops per FMA) to *tflops_host. Synchronises the stream. */
 rmhmc_status rmhmc_fp64_peak(void* cuda_stream, int ms_target, double* tflops_host);
+
+/* Allocation-free eigendecomposition of a batch of symmetric matrices, for callers that cannot
+ * allocate device memory (e.g. code running inside another framework's memory pool or arena, a
+ * plug-in whose host forbids cudaMalloc, or a real-time loop that must not hit the allocator).
+ * The paper has no counterpart: it is this library's cold-start block-Jacobi (the solver inside
+ * rmhmc_set_state) with its workspace in a fixed, file-scope device array of 8 MiB
+ * (1,048,576 doubles) that every GPU loading the library keeps until the process exits.
+ * A_dev (n x d x d, read only) holds symmetric matrices; outputs lam_dev (n x d, eigenvalues in
+ * the solver's order) and/or Q_dev (n x d x d, eigenvectors as columns, A = Q diag(lam) Q^T);
+ * tol and max_sweeps as in rmhmc_integrator (jacobi_tol, max_sweeps; the RELATIVE rule, so every
+ * eigenpair is resolved); sweeps_dev and status_dev
+ * (n ints each, RMHMC_CHAIN_NOTCONV on failure) may be NULL. With dp = d rounded up to a multiple
+ * of 16, the batch must satisfy 2 n dp^2 + n dp + 512 n dp/16 + 64 n + O(n dp/16) <= 1,048,576
+ * doubles (e.g. n = 64 at d = 64, n = 1 at d = 700); larger batches return RMHMC_ESCRATCH
+ * without touching the GPU. No device memory is allocated or freed. The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress), so make that first call before any
+ * stream capture. All calls share the one array and it keeps the previous call's contents (every
+ * value the solver reads is rewritten first); calls that overlap on the GPU, from two streams or
+ * two threads, race on it and must be serialised by the caller. Enqueued on cuda_stream. */
+rmhmc_status rmhmc_eigh_noalloc(void* cuda_stream, int n, int d, const double* A_dev,
+                                double* lam_dev, double* Q_dev, double tol, int max_sweeps,
+                                int* sweeps_dev, int* status_dev);
 
 /* Dimension d of q, and number of chains. */
 int rmhmc_dim(const rmhmc_model* m);

@@ -444,6 +444,37 @@ __global__ void __launch_bounds__(NW * 32) k_mgs(double* __restrict__ Pb, int dp
   }
 }
 
+// ------------------------------------------------------------------ allocation-free variant
+// Workspace of rmhmc_eigh_noalloc: one file-scope device array shared by every call on a device.
+constexpr size_t kNoAllocDoubles = size_t(1) << 20;  // 8 MiB
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+constexpr int kMaxDevices = 64;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// M = A zero-padded to dp x dp, PsiT = I, status = 0 (the workspace keeps the previous call's
+// contents, so everything the solver reads is rewritten here).
+__global__ void k_noalloc_pack(const double* __restrict__ A, int d, int dp, int n, double* __restrict__ M,
+                               double* __restrict__ P, int* __restrict__ status) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * dp * dp) return;
+  const long long c = e / ((long long)dp * dp), r = e % ((long long)dp * dp);
+  const int i = (int)(r / dp), j = (int)(r % dp);
+  M[e] = (i < d && j < d) ? A[c * d * d + (long long)i * d + j] : 0.0;
+  P[e] = (i == j) ? 1.0 : 0.0;
+  if (r == 0) status[c] = 0;
+}
+
+// lam (n x d) from the padded eigenvalues; Q (n x d x d) with the eigenvectors as columns.
+__global__ void k_noalloc_unpack(const double* __restrict__ lamp, const double* __restrict__ P, int d,
+                                 int dp, int n, double* __restrict__ lam, double* __restrict__ Q) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * d * d) return;
+  const long long c = e / ((long long)d * d), r = e % ((long long)d * d);
+  const int i = (int)(r / d), j = (int)(r % d);
+  if (Q) Q[e] = P[c * dp * dp + (long long)j * dp + i];
+  if (lam && i == 0) lam[c * d + j] = lamp[c * dp + j];
+}
+
 template <typename K, typename... Args>
 cudaError_t launch_cluster(K kernel, int n_chains, int C, size_t smem, cudaStream_t s, Args... args) {
   cudaLaunchConfig_t cfg = {};
@@ -462,6 +493,13 @@ cudaError_t launch_cluster(K kernel, int n_chains, int C, size_t smem, cudaStrea
 }
 
 }  // namespace
+
+size_t noalloc_doubles(int n, int dp) {
+  const size_t np = (size_t)dp / BL / 2;
+  const size_t ints = 2 * (size_t)n + (size_t)n * np;  // status, sweeps, flags
+  return 2 * (size_t)n * dp * dp + (size_t)n * dp + 2 * (size_t)n * np * SB * SB + (size_t)n * 64 +
+         (ints + 1) / 2 + 4;
+}
 
 int jacobi_cluster_size(int n_chains) {
   if (n_chains <= 18) return 8;
@@ -490,3 +528,49 @@ void mgs_rows_f64(cudaStream_t s, double* PsiT, int dp, int d, int n_chains, con
 }
 
 }  // namespace rmhmc
+
+// ------------------------------------------------------------------ C ABI: allocation-free eigen
+extern "C" rmhmc_status rmhmc_eigh_noalloc(void* cuda_stream, int n, int d, const double* A_dev,
+                                           double* lam_dev, double* Q_dev, double tol, int max_sweeps,
+                                           int* sweeps_dev, int* status_dev) {
+  using namespace rmhmc;
+  if (n < 1 || d < 1 || !A_dev || (!lam_dev && !Q_dev) || !(tol > 0.0) || max_sweeps < 0)
+    return RMHMC_EINVAL;
+  const int dp = ((d + kJacSB - 1) / kJacSB) * kJacSB;
+  if (noalloc_doubles(n, dp) > kNoAllocDoubles) return RMHMC_ESCRATCH;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RMHMC_ECUDA;
+  if (!g_noalloc_ptr[dev]) {
+    // host code cannot use the symbol itself as a device address: look it up once per device
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RMHMC_ECUDA;
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int np = dp / BL / 2;
+  double* base = g_noalloc_ptr[dev];
+  double* M = base;
+  double* P = M + (size_t)n * dp * dp;
+  double* lamp = P + (size_t)n * dp * dp;
+  double* V = lamp + (size_t)n * dp;
+  double* D = V + (size_t)n * np * SB * SB;
+  double* slots = D + (size_t)n * np * SB * SB;
+  int* status = (int*)(slots + (size_t)n * 64);
+  int* sweeps = status + n;
+  int* flags = sweeps + n;
+  const long long tot = (long long)n * dp * dp;
+  k_noalloc_pack<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A_dev, d, dp, n, M, P, status);
+  const int C = jacobi_cluster_size(n);
+  const size_t smem = (size_t)NW * WARP_SMEM * sizeof(double);
+  if (cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return RMHMC_ECUDA;
+  if (launch_cluster(k_jacobi, n, C, smem, s, M, P, lamp, dp, d, (int)RMHMC_JACOBI_RELATIVE, tol,
+                     max_sweeps, status,
+                     sweeps_dev ? sweeps_dev : sweeps, (int*)nullptr, V, D, slots, flags) != cudaSuccess)
+    return RMHMC_ECUDA;
+  const long long out = (long long)n * d * d;
+  k_noalloc_unpack<<<(unsigned)((out + 255) / 256), 256, 0, s>>>(lamp, P, d, dp, n, lam_dev, Q_dev);
+  if (status_dev && cudaMemcpyAsync(status_dev, status, n * sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return RMHMC_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? RMHMC_OK : RMHMC_ECUDA;
+}

@@ -548,6 +548,7 @@ const char* rmhmc_status_string(rmhmc_status s) {
     case RMHMC_ETIMEOUT: return "bounded device wait gave up";
     case RMHMC_ENOTIMPL: return "not implemented in this build";
     case RMHMC_ENOTPD: return "kernel matrix not positive definite";
+    case RMHMC_ESCRATCH: return "batch exceeds the fixed workspace of rmhmc_eigh_noalloc";
   }
   return "unknown status";
 }

@@ -101,6 +101,9 @@ def lib():
     L.rmhmc_profile_category.restype = c_char_p
     L.rmhmc_fp64_peak.argtypes = [c_void_p, c_int, POINTER(c_double)]
     L.rmhmc_fp64_peak.restype = c_int
+    L.rmhmc_eigh_noalloc.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                     c_double, c_int, c_void_p, c_void_p]
+    L.rmhmc_eigh_noalloc.restype = c_int
     L.rmhmc_version.argtypes = []
     L.rmhmc_status_string.argtypes = [c_int]
     L.rmhmc_status_string.restype = c_char_p
@@ -252,6 +255,20 @@ def fp64_peak_tflops(ms_target=200, stream=None):
     out = c_double()
     _check(lib().rmhmc_fp64_peak(c_void_p(stream.cuda_stream), int(ms_target), ctypes.byref(out)))
     return out.value
+
+
+def eigh_noalloc(A, lam=None, Q=None, tol=1e-13, max_sweeps=30, sweeps=None, status=None,
+                 stream=None):
+    """Batched symmetric eigendecomposition through rmhmc_eigh_noalloc (no device allocation;
+    fixed 8 MiB workspace shared by all calls on a device). A: (n, d, d) CUDA float64."""
+    import torch
+    n, d, _ = A.shape
+    stream = stream or torch.cuda.current_stream()
+    _check(lib().rmhmc_eigh_noalloc(c_void_p(stream.cuda_stream), int(n), int(d),
+                                    _ptr(A, (n, d, d), torch.float64),
+                                    _ptr(lam, (n, d), torch.float64), _ptr(Q, (n, d, d), torch.float64),
+                                    float(tol), int(max_sweeps), _ptr(sweeps, (n,), torch.int32),
+                                    _ptr(status, (n,), torch.int32)))
 
 
 def version():
