@@ -29,6 +29,10 @@ sys.path.insert(0, ROOT)
 from paper_2511_06407_b300 import workloads as wl  # noqa: E402
 
 N_INPUTS, N_CHAINS, EPS, N_FP = 400, 64, 0.005, 6
+# DRAM bytes per k_jacobi launch per chain, from the ncu capture summarised in
+# profiles/k_jacobi_N400_8chains.md (8 chains: 22.27 MB read + 2.18 MB written on average per launch);
+# traffic grows with the number of chains, so a 64-chain launch is scaled by 64 / 8.
+JACOBI_DRAM_BYTES_PER_CHAIN = (22.27e6 + 0.5 * (2.40e6 + 1.95e6)) / 8
 SUBSTEPS_PER_LEAPFROG = 2 * N_FP + 1
 METRIC = "RMHMC leapfrog substeps/s"
 UNIT = "substeps/s"
@@ -167,7 +171,7 @@ def run_b300(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     prob = wl.gp_classification(N_INPUTS, seed=0)
-    C = N_CHAINS
+    C = args.chains
     model = rmhmc.Model(prob, C, stream=stream)
     d = model.d
     integ = rmhmc.Integrator(eps=EPS, n_fp=N_FP, n_leapfrog=1)
@@ -252,29 +256,36 @@ def run_b300(args):
     achieved = (dom_flops / dom_launches) / ((dom_ms / dom_launches) * 1e-3) / 1e12 if dom_launches else 0.0
     gpu_launches = int(sum(v[2] for v in prof.values()))
     # CPU baseline: the oracle on this host's cores, bounded sample
-    cb_value, cb_n, cb_s = oracle_leapfrogs(args.cpu_seconds)
+    cpu_baseline = None
+    if not args.no_cpu_baseline:
+        cb_value, cb_n, cb_s = oracle_leapfrogs(args.cpu_seconds)
+        cpu_baseline = {"value": cb_value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                        "sample": f"{cb_n} oracle leapfrog(s) of one chain of the workload in {cb_s:.1f} s "
+                                  "(numpy/LAPACK FP64, full third-derivative tensor)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N_INPUTS, "d": d, "chains_per_gpu": C,
+        "config": {"workload": WORKLOAD if C == N_CHAINS else WORKLOAD.replace(f"{N_CHAINS} chains", f"{C} chains"),
+                   "N": N_INPUTS, "d": d, "chains_per_gpu": C,
                    "substeps_per_leapfrog": SUBSTEPS_PER_LEAPFROG,
                    "l2": "inputs larger than L2 (per-chain state ~16 MB, 64 chains ~1 GB > 126 MB)",
                    "parallelism": f"replicas x{ws}"},
         "leapfrogs_per_s": total_chains * args.steps / (ms * 1e-3),
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
+                     "traffic": (JACOBI_DRAM_BYTES_PER_CHAIN * C) if dom == "jacobi_f64" else None,
+                     "traffic_note": "bytes per k_jacobi launch, ncu capture at 8 chains scaled to the chain count",
                      "peak_note": "FP64 FMA throughput measured live on this GPU (rmhmc_fp64_peak)"},
         "profile_ms": {k: round(v[0], 3) for k, v in prof.items()},
         "profile_tflops": {k: (v[1] / (v[0] * 1e-3) / 1e12 if v[0] > 0 else 0.0) for k, v in prof.items()},
-        "cpu_baseline": {"value": cb_value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
-                         "sample": f"{cb_n} oracle leapfrog(s) of one chain of the workload in {cb_s:.1f} s "
-                                   "(numpy/LAPACK FP64, full third-derivative tensor)"},
+        "cpu_baseline": cpu_baseline,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(p_host.numel() * 8),
                 "d2h_bytes_per_step": int((q_host.numel() + pout_host.numel() + H_host.numel()) * 8)},
         "gpu_launches": gpu_launches,
         "chain_status_nonzero": int((status != 0).sum()),
+        "valid": bool((status == 0).all()),
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -291,6 +302,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--chains", type=int, default=N_CHAINS,
+                    help="chains per GPU (the workload is 64; smaller values are for profiling)")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
