@@ -99,7 +99,7 @@ typedef struct {
 } rmhmc_model_desc;
 
 /* Integrator and geometry settings. The geometry fields (g_kind, alpha, jacobi_tol, max_sweeps,
- * reorth_every, precision, jacobi_rule) must be the same in every call on a model as in
+ * reorth_every, precision, jacobi_rule, eigen_start) must be the same in every call on a model as in
  * rmhmc_set_state. */
 typedef struct {
   double eps;          /* leapfrog step size (Eq. leapfrog) */
@@ -112,6 +112,8 @@ typedef struct {
   int reorth_every;    /* Gram-Schmidt of Psi every this many eigen-updates (Sec. 2.4); 0 = never */
   int precision;       /* rmhmc_precision; only RMHMC_FP64 in this build */
   int jacobi_rule;     /* rmhmc_jacobi_rule: when M = Psi^T H Psi counts as diagonal */
+  int eigen_start;     /* 0: warm start from the previous Psi (dynamic, Sec. 2.4); 1: cold start
+                          from Psi = I at every eigen-update (the static ablation of Sec. 3.1) */
 } rmhmc_integrator;
 
 typedef struct rmhmc_model rmhmc_model;
@@ -123,6 +125,11 @@ typedef struct rmhmc_model rmhmc_model;
  * Errors: EINVAL (bad sizes/kinds), ENOMEM, ECUDA. */
 rmhmc_status rmhmc_init_model(const rmhmc_model_desc* desc, int n_chains, const double* tau_host,
                               void* cuda_stream, rmhmc_model** out);
+
+/* Device bytes rmhmc_init_model would allocate for desc and n_chains (every buffer, each rounded
+ * to 256 bytes), without allocating: what an admission controller budgets HBM with. The arrays
+ * in desc are not read (only the sizes and kinds). Errors: EINVAL. */
+rmhmc_status rmhmc_plan_bytes(const rmhmc_model_desc* desc, int n_chains, size_t* bytes);
 
 /* Set every chain's position (q_dev: n_chains x d) and momentum (p_dev: n_chains x d, may be
  * NULL = zero) and evaluate the geometry there: U, its gradient, Hessian (Eq. d_Hamiltonian
@@ -145,13 +152,16 @@ rmhmc_status rmhmc_leapfrog(rmhmc_model* m, const rmhmc_integrator* integ, int n
  * leapfrogs, Metropolis-Hastings with r from counter (0, iteration, 1, 0) (accept iff
  * log r < H0 - H1). Iteration numbers continue across calls on the same model. The last n_iter
  * iterations are recorded: q_samples_dev (n_iter x n_chains x d), logp_dev (n_iter x n_chains,
- * log P_tau(q) = -U(q)), accept_dev (n_iter x n_chains ints), sweeps_dev (n_iter x n_chains ints,
+ * log P_tau(q) = -U(q)), loglik_dev (n_iter x n_chains, the untempered log-likelihood
+ * ln P(y | F), the integrand of thermodynamic integration for the model evidence), accept_dev
+ * (n_iter x n_chains ints), sweeps_dev (n_iter x n_chains ints,
  * Jacobi sweeps in that iteration's trajectory), chain_status_dev (n_chains ints, OR of the
  * RMHMC_CHAIN_* bits seen). Any output pointer may be NULL. The host enqueues iteration by
  * iteration; the call returns after enqueueing. Errors: EINVAL, ECUDA. */
 rmhmc_status rmhmc_sample(rmhmc_model* m, const rmhmc_integrator* integ, int n_iter, int n_burn,
-                          uint64_t seed, double* q_samples_dev, double* logp_dev, int* accept_dev,
-                          int* sweeps_dev, int* chain_status_dev);
+                          uint64_t seed, double* q_samples_dev, double* logp_dev,
+                          double* loglik_dev, int* accept_dev, int* sweeps_dev,
+                          int* chain_status_dev);
 
 /* Copy out the geometry at the current state (for checks and diagnostics): U_dev (n_chains),
  * dU_dev (n_chains x d), hess_dev (n_chains x d x d, Hessian of U), lam_dev (n_chains x d,
@@ -165,6 +175,28 @@ rmhmc_status rmhmc_geometry(rmhmc_model* m, double* U_dev, double* dU_dev, doubl
  * of Eq. Hamiltonian), Ginv_p_dev = G^-1 p = dH/dp, H_dev = Eq. Hamiltonian. NULL skips an output. */
 rmhmc_status rmhmc_hamiltonian_grad(rmhmc_model* m, const double* p_dev, double* dHdq_dev,
                                     double* Ginv_p_dev, double* H_dev);
+
+/* ---------------------------------------------------------------- uneven batches (one graph)
+ * A batch advances several models of different sizes (N, kernels, chains) together: the first
+ * rmhmc_batch_leapfrog captures one generalized leapfrog of every model into a single CUDA graph
+ * (each model's kernels on its own stream, forked from and joined back to the batch stream with
+ * events, so models overlap on the GPU) and every call replays it n_steps times with one graph
+ * launch per leapfrog; the graph is re-captured when eps or n_fp change. cuda_stream must be a
+ * created stream (the legacy default stream cannot be captured); every model needs its own
+ * non-default stream (distinct from cuda_stream), a state (rmhmc_set_state) and profiling off.
+ * The models stay usable on their own; rmhmc_batch_free does not free them.
+ * Errors: EINVAL (bad arguments, shared or default streams, no state), ECUDA (capture failed). */
+typedef struct rmhmc_batch rmhmc_batch;
+rmhmc_status rmhmc_batch_create(rmhmc_model* const* models, int n_models, void* cuda_stream,
+                                rmhmc_batch** out);
+rmhmc_status rmhmc_batch_leapfrog(rmhmc_batch* b, const rmhmc_integrator* integ, int n_steps);
+void rmhmc_batch_free(rmhmc_batch* b);
+
+/* Choose the model's Jacobi cluster size (CTAs per chain: 1, 2, 4 or 8) by timing up to three
+ * cold-start sweeps of each candidate on the model's own current Hessian (in scratch buffers; the
+ * state is untouched) and keeping the fastest time per sweep. Synchronises the stream; needs a
+ * state. *cluster_out (may be NULL) receives the choice. */
+rmhmc_status rmhmc_autotune(rmhmc_model* m, int* cluster_out);
 
 /* Kernel-level profile (for measurement; not part of the method). While enabled, every kernel
  * launch of the model is bracketed by CUDA events on the model's stream and counted in one of

@@ -73,13 +73,16 @@ __device__ __forceinline__ void schur2(double app, double aqq, double apq, doubl
 
 // Inner exact solve of one 16 x 16 sub-problem by a single warp: A <- V^T A V diagonal. Returns
 // false when the block already met the tolerance (then V = I exactly and A is unchanged).
-// Stopping test for one pair: m_jl^2 > max(tol2 * den(j, l), floor2) with den = |m_jj m_ll| (RELATIVE)
-// or (m_jj m_ll)^2 / dmin^2 (METRIC); returns the ratio (> 1 means unconverged).
-__device__ __forceinline__ double pair_ratio(double v, double djj, double dll, double tol2,
-                                             double floor2, int rule, double dmin2) {
+// Stopping test for one pair (no FP64 division): true when m_jl^2 > max(tol2 * den, floor2), with
+// den = |m_jj m_ll| (RELATIVE) or (m_jj m_ll)^2 / dmin^2 (METRIC, compared as m_jl^2 dmin^2 against
+// tol2 (m_jj m_ll)^2).
+__device__ __forceinline__ bool pair_unconverged(double v, double djj, double dll, double tol2,
+                                                 double floor2, int rule, double dmin2) {
+  const double v2 = v * v;
+  if (!(v2 > floor2)) return false;
   const double p = fabs(djj * dll);
-  const double den = rule == RMHMC_JACOBI_METRIC ? p * p / dmin2 : p;
-  return v * v / fmax(tol2 * den, fmax(floor2, 1e-300));
+  if (rule == RMHMC_JACOBI_METRIC) return v2 * dmin2 > tol2 * p * p;
+  return v2 > tol2 * p;
 }
 
 __device__ bool inner_solve(double* A, double* V, double* cs, double tol2, double floor2, int rule,
@@ -89,16 +92,15 @@ __device__ bool inner_solve(double* A, double* V, double* cs, double tol2, doubl
   for (int e = lane; e < SB * SB; e += 32) V[(e / SB) * SBP + e % SB] = (e / SB == e % SB) ? 1.0 : 0.0;
   __syncwarp();
   for (int it = 0; it < MAX_INNER; ++it) {
-    double crit = 0.0;
+    bool unconv = false;
     for (int e = lane; e < SB * SB; e += 32) {
       const int i = e / SB, j = e % SB;
       const double v = A[i * SBP + j];
       if (i != j && v != 0.0)
-        crit = fmax(crit, pair_ratio(v, A[i * SBP + i], A[j * SBP + j], tol2, floor2, rule, dmin2));
+        unconv |= pair_unconverged(v, A[i * SBP + i], A[j * SBP + j], tol2, floor2, rule, dmin2) ||
+                  !isfinite(v);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) crit = fmax(crit, __shfl_xor_sync(0xffffffffu, crit, o));
-    if (!(crit > 1.0)) break;
+    if (!__any_sync(0xffffffffu, unconv)) break;
     rotated = true;
     for (int r = 0; r < SB - 1; ++r) {
       if (lane < SB / 2) {
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
       dmin = fmin(dmin, __ldcg(slots + (sweeps & 1) * 32 + 2 * r + 1));
     }
     const double dmin2 = fmax(dmin * dmin, 1e-300);
-    const double floor2 = 16.0 * 1.2325951644078310e-32 * tot;  // (4 u)^2 ||M||_F^2, u = 2^-53
+    const double floor2 = fmax(16.0 * 1.2325951644078310e-32 * tot, 1e-300);  // (4u)^2 ||M||_F^2
     double crit = 0.0, bad = isfinite(tot) ? 0.0 : 1.0;
     for (long long e = (long long)rank * blockDim.x + tid; e < (long long)dp * dp;
          e += (long long)C * blockDim.x) {
@@ -274,10 +276,10 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
       if (j == l) continue;
       const double v = __ldcg(M + e);
       if (v == 0.0) continue;
-      const double r = pair_ratio(v, __ldcg(M + (long long)j * dp + j), __ldcg(M + (long long)l * dp + l),
-                                  tol * tol, floor2, rule, dmin2);
-      if (!(r <= 1e308)) bad = 1.0;
-      crit = fmax(crit, r);
+      if (!isfinite(v)) bad = 1.0;
+      if (pair_unconverged(v, __ldcg(M + (long long)j * dp + j), __ldcg(M + (long long)l * dp + l),
+                           tol * tol, floor2, rule, dmin2))
+        crit = 1.0;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
       bad = fmax(bad, __ldcg(slots + (sweeps & 1) * 32 + 16 + 2 * r + 1));
     }
     if (bad != 0.0) break;
-    if (crit <= 1.0) { converged = true; break; }
+    if (crit == 0.0) { converged = true; break; }
     if (sweeps >= max_sweeps) break;
     const double itol2 = 1e-4 * tol * tol;  // inner problems are solved 100x tighter
 
@@ -330,7 +332,7 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
       // ---- phase 2: apply all rotations to M (P <= Q tiles) and to the rows of Psi^T
       for (int job = gw; job < nMjobs + np * nct; job += nwt) {
         if (job < nMjobs) {
-          int Q = (int)((sqrt(8.0 * job + 1.0) - 1.0) * 0.5);
+          int Q = (int)((sqrtf(8.0f * (float)job + 1.0f) - 1.0f) * 0.5f);  // then exact integer fix-up
           while (Q * (Q + 1) / 2 > job) --Q;
           while ((Q + 1) * (Q + 2) / 2 <= job) ++Q;
           const int Pp = job - Q * (Q + 1) / 2;

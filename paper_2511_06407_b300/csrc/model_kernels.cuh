@@ -73,7 +73,7 @@ __global__ void k_assemble(ModelDev md, const double* __restrict__ q, int dp, do
 // F = sum_k f_k (Sec. 2.5 logistic / Gaussian): l, l', l'', l''' per (chain, sample).
 __global__ void k_lik(ModelDev md, const double* __restrict__ q, int dp, double* __restrict__ fpk,
                       double* __restrict__ l0, double* __restrict__ l1, double* __restrict__ l2,
-                      double* __restrict__ l3) {
+                      double* __restrict__ l3, double* __restrict__ lraw) {
   const int c = blockIdx.y, N = md.N;
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= N) return;
@@ -100,6 +100,7 @@ __global__ void k_lik(ModelDev md, const double* __restrict__ q, int dp, double*
     a3 = 0.0;
   }
   const long long o = (long long)c * N + m;
+  lraw[o] = a0;
   l0[o] = tau * a0;
   l1[o] = tau * a1;
   l2[o] = tau * a2;
@@ -238,24 +239,32 @@ __device__ __forceinline__ double log_prior_u(double a, double b, double u) {
   return a * log(b) - lgamma(a) - a * u - b * exp(-u);
 }
 
-// U = -log P_tau(q) and dU/dq for every chain (one CTA per chain).
+// U = -log P_tau(q), dU/dq and the untempered log-likelihood LL = ln P(y | F) per chain (one CTA
+// per chain).
 __global__ void __launch_bounds__(256) k_udu(ModelDev md, const double* __restrict__ q, int dp,
                                              const double* __restrict__ l0,
                                              const double* __restrict__ l1,
+                                             const double* __restrict__ lraw,
                                              const double* __restrict__ alphab,
                                              const double* __restrict__ stats,
-                                             double* __restrict__ U, double* __restrict__ dU) {
+                                             double* __restrict__ U, double* __restrict__ dU,
+                                             double* __restrict__ LL) {
   const int c = blockIdx.x, N = md.N, n = md.n;
   __shared__ double sh[32];
-  double s = 0.0;
-  for (int m = threadIdx.x; m < N; m += blockDim.x) s += l0[(long long)c * N + m];
+  double s = 0.0, sr = 0.0;
+  for (int m = threadIdx.x; m < N; m += blockDim.x) {
+    s += l0[(long long)c * N + m];
+    sr += lraw[(long long)c * N + m];
+  }
   for (int e = threadIdx.x; e < n * N; e += blockDim.x) {
     const int k = e / N, m = e % N;
     dU[(long long)c * dp + e] = l1[(long long)c * N + m] + alphab[((long long)c * n + k) * N + m];
   }
   for (int e = md.d + threadIdx.x; e < dp; e += blockDim.x) dU[(long long)c * dp + e] = 0.0;
   const double tot = block_sum(s, sh);
+  const double totr = block_sum(sr, sh);
   if (threadIdx.x == 0) {
+    LL[c] = -totr;
     double Uc = tot;
     for (int k = 0; k < n; ++k) {
       const double* st = stats + ((long long)c * n + k) * kStatSlots;

@@ -241,13 +241,16 @@ __global__ void k_inc(int* __restrict__ v, int C, int* __restrict__ tot, const i
   }
 }
 
-__global__ void k_record(const double* __restrict__ q, const double* __restrict__ U, int dp, int d,
-                         int C, double* __restrict__ qs, double* __restrict__ logp) {
+__global__ void k_record(const double* __restrict__ q, const double* __restrict__ U,
+                         const double* __restrict__ LL, int dp, int d, int C,
+                         double* __restrict__ qs, double* __restrict__ logp,
+                         double* __restrict__ loglik) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)C * d) return;
   const int c = (int)(e / d), i = (int)(e % d);
   if (qs) qs[e] = q[(long long)c * dp + i];
   if (logp && i == 0) logp[c] = -U[c];
+  if (loglik && i == 0) loglik[c] = LL[c];
 }
 
 // dst (C x d x d) <- the leading d x d block of src (C x dp x dp)
@@ -298,7 +301,7 @@ struct rmhmc_model {
   int N = 0, n = 0, P = 0, d = 0, dp = 0, C = 0;
   int cluster = 1;
   bool has_state = false;
-  int g_kind = 0, max_sweeps = 30, reorth_every = 10, precision = 0, jacobi_rule = 0;
+  int g_kind = 0, max_sweeps = 30, reorth_every = 10, precision = 0, jacobi_rule = 0, eigen_start = 0;
   double alpha = 1e6, tol = 1e-13;
   uint64_t iter = 0;
   std::vector<void*> allocs;
@@ -308,13 +311,13 @@ struct rmhmc_model {
   double *fpk, *alpha_, *beta, *gamma, *eps2, *eps3, *delta, *fuu11;
   double* stats;
   // per chain N-vectors
-  double *l0, *l1, *l2, *l3;
+  double *l0, *l1, *l2, *l3, *lraw;
   // per chain dp x dp
   double *H, *M, *PsiT, *W, *Y, *PsiT_save;
   // per chain dp-vectors
   double *q, *p, *ph, *q0, *v0, *vk, *t1, *dU, *dHdq, *lam, *g, *gp, *q_save, *z, *vtr, *xin;
   // per chain scalars
-  double *U, *Ham0, *Ham1;
+  double *U, *Ham0, *Ham1, *LL;
   int *status, *sweeps_last, *sweeps_acc, *eig_count, *eig_save, *acc, *sweeps_total;
   JacobiWork jw;
   // kernel-level profile (rmhmc_profile)
@@ -325,6 +328,8 @@ struct rmhmc_model {
   std::vector<Rec> recs;
   double prof_flops[RMHMC_PROF_NCAT] = {};
   long long prof_launch[RMHMC_PROF_NCAT] = {};
+  size_t* plan_bytes = nullptr;  // set only while planning (rmhmc_plan_bytes)
+  double *X_dev = nullptr, *y_dev = nullptr, *uf_dev = nullptr, *tau_dev = nullptr;
 };
 
 namespace {
@@ -362,8 +367,14 @@ inline double gemm_flops(double mm, double nn, double kk, bool sym, bool tri) {
   return sym ? mm * (mm + 1.0) * kk : 2.0 * mm * nn * kk;
 }
 
+// When planning (m->plan_bytes != nullptr) nothing is allocated: the bytes are only counted.
 template <typename T>
 rmhmc_status dalloc(rmhmc_model* m, T** p, size_t count) {
+  if (m->plan_bytes) {
+    *m->plan_bytes += ((count * sizeof(T) + 16 + 255) / 256) * 256;
+    *p = nullptr;
+    return RMHMC_OK;
+  }
   void* ptr = nullptr;
   if (cudaMalloc(&ptr, count * sizeof(T) + 16) != cudaSuccess) return RMHMC_ENOMEM;
   cudaMemsetAsync(ptr, 0, count * sizeof(T) + 16, m->stream);
@@ -387,7 +398,7 @@ void eval_geometry(rmhmc_model* m, bool third) {
   PROF(m, CAT_MODEL, 0)
   dev::k_assemble<<<dim3(nblk(NN), n, C), 256, 0, s>>>(m->md, m->q, dp, m->KL, m->D1);
   PROF(m, CAT_MODEL, 0)
-  dev::k_lik<<<dim3(nblk(N), C), 256, 0, s>>>(m->md, m->q, dp, m->fpk, m->l0, m->l1, m->l2, m->l3);
+  dev::k_lik<<<dim3(nblk(N), C), 256, 0, s>>>(m->md, m->q, dp, m->fpk, m->l0, m->l1, m->l2, m->l3, m->lraw);
   PROF(m, CAT_CHOL, Bf * Nf * Nf * Nf / 3.0)
   cholesky_f64(s, m->KL, N, B, m->stats + ST_LOGDET, kStatSlots, m->status, n);
   PROF(m, CAT_TRINV, Bf * Nf * Nf * Nf / 3.0)
@@ -416,13 +427,18 @@ void eval_geometry(rmhmc_model* m, bool third) {
                                           m->fuu11, m->stats);
   }
   PROF(m, CAT_MODEL, 0)
-  dev::k_udu<<<C, 256, 0, s>>>(m->md, m->q, dp, m->l0, m->l1, m->alpha_, m->stats, m->U, m->dU);
+  dev::k_udu<<<C, 256, 0, s>>>(m->md, m->q, dp, m->l0, m->l1, m->lraw, m->alpha_, m->stats, m->U,
+                               m->dU, m->LL);
   const long long DD = (long long)dp * dp;
   PROF(m, CAT_MODEL, 0)
   dev::k_hessian<<<dim3(nblk(DD), C), 256, 0, s>>>(m->md, m->q, dp, m->Kinv, m->l2, m->alpha_,
                                                    m->gamma, m->stats, m->H);
   // Sec. 2.4: Gram-Schmidt of Psi every reorth_every eigen-updates, then M = Psi^T H Psi
-  if (m->reorth_every > 0) {
+  // (the static ablation restarts every eigen-update from Psi = I instead)
+  if (m->eigen_start == 1) {
+    PROF(m, CAT_VECTOR, 0)
+    k_set_identity<<<nblk((long long)C * DD), 256, 0, s>>>(m->PsiT, dp, C);
+  } else if (m->reorth_every > 0) {
     PROF(m, CAT_MGS, 0)
     mgs_rows_f64(s, m->PsiT, dp, d, C, m->eig_count, m->reorth_every, m->cluster);
   }
@@ -512,6 +528,63 @@ void leapfrog_step(rmhmc_model* m, double eps, int n_fp) {
   k_axpy<<<g, 256, 0, s>>>(m->p, m->ph, m->dHdq, -0.5 * eps, nv);
 }
 
+// Every device buffer of a model, in one place for allocation and for rmhmc_plan_bytes.
+rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
+  const int N = m->N, n = m->n, C = m->C, dp = m->dp;
+  const size_t NN = (size_t)N * N, DD = (size_t)dp * dp;
+  const size_t B = (size_t)C * n;
+  rmhmc_status st = RMHMC_OK;
+#define ALLOC(ptr, cnt) \
+  if (st == RMHMC_OK) st = dalloc(m, &(ptr), (cnt))
+  ALLOC(m->X_dev, (size_t)N * n_cov);
+  ALLOC(m->y_dev, (size_t)N);
+  ALLOC(m->uf_dev, (size_t)2 * n);
+  ALLOC(m->tau_dev, (size_t)C);
+  ALLOC(m->KL, B * NN);
+  ALLOC(m->D1, B * NN);
+  ALLOC(m->Kinv, B * NN);
+  ALLOC(m->S, B * NN);
+  ALLOC(m->Aux, B * NN);
+  ALLOC(m->S2, B * NN);
+  ALLOC(m->fpk, B * N);
+  ALLOC(m->alpha_, B * N);
+  ALLOC(m->beta, B * N);
+  ALLOC(m->gamma, B * N);
+  ALLOC(m->eps2, B * N);
+  ALLOC(m->eps3, B * N);
+  ALLOC(m->delta, B * N);
+  ALLOC(m->fuu11, B * N);
+  ALLOC(m->stats, B * kStatSlots);
+  ALLOC(m->l0, (size_t)C * N);
+  ALLOC(m->l1, (size_t)C * N);
+  ALLOC(m->l2, (size_t)C * N);
+  ALLOC(m->l3, (size_t)C * N);
+  ALLOC(m->lraw, (size_t)C * N);
+  ALLOC(m->H, C * DD);
+  ALLOC(m->M, C * DD);
+  ALLOC(m->PsiT, C * DD);
+  ALLOC(m->W, C * DD);
+  ALLOC(m->Y, C * DD);
+  ALLOC(m->PsiT_save, C * DD);
+  double** vecs[] = {&m->q, &m->p, &m->ph, &m->q0, &m->v0, &m->vk, &m->t1, &m->dU, &m->dHdq,
+                     &m->lam, &m->g, &m->gp, &m->q_save, &m->z, &m->vtr, &m->xin};
+  for (double** v : vecs) ALLOC(*v, (size_t)C * dp);
+  ALLOC(m->U, (size_t)C);
+  ALLOC(m->Ham0, (size_t)C);
+  ALLOC(m->Ham1, (size_t)C);
+  ALLOC(m->LL, (size_t)C);
+  int** ivecs[] = {&m->status, &m->sweeps_last, &m->sweeps_acc, &m->eig_count, &m->eig_save, &m->acc,
+                   &m->sweeps_total};
+  for (int** v : ivecs) ALLOC(*v, (size_t)C);
+  const int np = dp / kJacBlk / 2;
+  ALLOC(m->jw.V, (size_t)C * np * 256);
+  ALLOC(m->jw.D, (size_t)C * np * 256);
+  ALLOC(m->jw.slots, (size_t)C * 64);
+  ALLOC(m->jw.flags, (size_t)C * np);
+#undef ALLOC
+  return st;
+}
+
 rmhmc_status check_integ(const rmhmc_model* m, const rmhmc_integrator* in, bool for_state) {
   if (!in) return RMHMC_EINVAL;
   if (in->precision != RMHMC_FP64) return RMHMC_ENOTIMPL;
@@ -520,11 +593,12 @@ rmhmc_status check_integ(const rmhmc_model* m, const rmhmc_integrator* in, bool 
     return RMHMC_EINVAL;
   if (in->jacobi_rule != RMHMC_JACOBI_METRIC && in->jacobi_rule != RMHMC_JACOBI_RELATIVE)
     return RMHMC_EINVAL;
+  if (in->eigen_start != 0 && in->eigen_start != 1) return RMHMC_EINVAL;
   if (!for_state) {
     if (!m->has_state) return RMHMC_EINVAL;
     if (in->g_kind != m->g_kind || in->alpha != m->alpha || in->jacobi_tol != m->tol ||
         in->max_sweeps != m->max_sweeps || in->reorth_every != m->reorth_every ||
-        in->jacobi_rule != m->jacobi_rule)
+        in->jacobi_rule != m->jacobi_rule || in->eigen_start != m->eigen_start)
       return RMHMC_EINVAL;
     if (!(in->eps > 0.0) || in->n_fp < 1) return RMHMC_EINVAL;
   }
@@ -533,9 +607,156 @@ rmhmc_status check_integ(const rmhmc_model* m, const rmhmc_integrator* in, bool 
 
 }  // namespace
 
+// ------------------------------------------------------------------------- uneven batches
+
+struct rmhmc_batch {
+  std::vector<rmhmc_model*> models;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr, post = nullptr;
+  std::vector<cudaEvent_t> joins, pre;
+  cudaGraphExec_t exec = nullptr;
+  double eps = 0.0;
+  int n_fp = 0;
+};
+
 // ----------------------------------------------------------------------------------- C ABI
 
 extern "C" {
+
+rmhmc_status rmhmc_batch_create(rmhmc_model* const* models, int n_models, void* cuda_stream,
+                                rmhmc_batch** out) {
+  if (!models || n_models < 1 || !out) return RMHMC_EINVAL;
+  *out = nullptr;
+  cudaStream_t bs = (cudaStream_t)cuda_stream;
+  if (bs == nullptr) return RMHMC_EINVAL;  // the legacy default stream cannot be captured
+  for (int i = 0; i < n_models; ++i) {
+    rmhmc_model* m = models[i];
+    if (!m || !m->has_state || m->stream == nullptr || m->stream == bs) return RMHMC_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (models[j] == m || models[j]->stream == m->stream) return RMHMC_EINVAL;
+  }
+  rmhmc_batch* b = new rmhmc_batch();
+  b->models.assign(models, models + n_models);
+  b->stream = bs;
+  b->joins.resize(n_models);
+  b->pre.resize(n_models);
+  bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->post, cudaEventDisableTiming) == cudaSuccess;
+  for (auto& e : b->joins) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+  for (auto& e : b->pre) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    rmhmc_batch_free(b);
+    return RMHMC_ECUDA;
+  }
+  *out = b;
+  return RMHMC_OK;
+}
+
+void rmhmc_batch_free(rmhmc_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->post) cudaEventDestroy(b->post);
+  for (cudaEvent_t e : b->joins)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->pre)
+    if (e) cudaEventDestroy(e);
+  delete b;
+}
+
+rmhmc_status rmhmc_batch_leapfrog(rmhmc_batch* b, const rmhmc_integrator* integ, int n_steps) {
+  if (!b || n_steps < 0) return RMHMC_EINVAL;
+  for (rmhmc_model* m : b->models) {
+    rmhmc_status st = check_integ(m, integ, false);
+    if (st != RMHMC_OK) return st;
+    if (m->prof) return RMHMC_EINVAL;
+  }
+  if (!b->exec || b->eps != integ->eps || b->n_fp != integ->n_fp) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return RMHMC_ECUDA;
+    }
+    cudaEventRecord(b->fork, b->stream);
+    for (size_t i = 0; i < b->models.size(); ++i) {
+      rmhmc_model* m = b->models[i];
+      cudaStreamWaitEvent(m->stream, b->fork, 0);
+      leapfrog_step(m, integ->eps, integ->n_fp);
+      cudaEventRecord(b->joins[i], m->stream);
+      cudaStreamWaitEvent(b->stream, b->joins[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(b->stream, &g) != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return RMHMC_ECUDA;
+    }
+    const cudaError_t e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->exec = nullptr;
+      cudaGetLastError();
+      return RMHMC_ECUDA;
+    }
+    b->eps = integ->eps;
+    b->n_fp = integ->n_fp;
+  }
+  // the replay waits for work already queued on every model's stream, and later calls on a
+  // model's own stream wait for the replay
+  for (size_t i = 0; i < b->models.size(); ++i) {
+    cudaEventRecord(b->pre[i], b->models[i]->stream);
+    cudaStreamWaitEvent(b->stream, b->pre[i], 0);
+  }
+  for (int i = 0; i < n_steps; ++i)
+    if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return RMHMC_ECUDA;
+  cudaEventRecord(b->post, b->stream);
+  for (rmhmc_model* m : b->models) cudaStreamWaitEvent(m->stream, b->post, 0);
+  return check_launch();
+}
+
+rmhmc_status rmhmc_autotune(rmhmc_model* m, int* cluster_out) {
+  if (!m || !m->has_state || m->prof) return RMHMC_EINVAL;
+  cudaStream_t s = m->stream;
+  const int C = m->C, dp = m->dp, d = m->d;
+  const long long DD = (long long)dp * dp;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RMHMC_ECUDA;
+  double best = 1e300;
+  int best_c = m->cluster;
+  const int cands[4] = {1, 2, 4, 8};
+  std::vector<int> sw(C);
+  for (int ci = 0; ci < 4; ++ci) {
+    const int cl = cands[ci];
+    // scratch: W <- H (cold start, Psi = I in Y), eigenvalues in vtr, status in acc, sweeps in eig_save
+    cudaMemcpyAsync(m->W, m->H, C * DD * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    k_set_identity<<<nblk((long long)C * DD), 256, 0, s>>>(m->Y, dp, C);
+    cudaMemsetAsync(m->acc, 0, C * sizeof(int), s);
+    cudaEventRecord(e0, s);
+    jacobi_f64(s, m->W, m->Y, m->vtr, dp, d, C, m->jacobi_rule, m->tol, 3, m->acc, m->eig_save,
+               nullptr, m->jw, cl);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return RMHMC_ECUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaMemcpy(sw.data(), m->eig_save, C * sizeof(int), cudaMemcpyDeviceToHost);
+    double sweeps = 0.0;
+    for (int v : sw) sweeps += v;
+    const double per = ms / (sweeps > 0.0 ? sweeps : 1.0);
+    if (per < best) {
+      best = per;
+      best_c = cl;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  m->cluster = best_c;
+  if (cluster_out) *cluster_out = best_c;
+  return check_launch();
+}
+
 
 const char* rmhmc_status_string(rmhmc_status s) {
   switch (s) {
@@ -644,10 +865,11 @@ void rmhmc_free_model(rmhmc_model* m) {
   delete m;
 }
 
-rmhmc_status rmhmc_init_model(const rmhmc_model_desc* desc, int n_chains, const double* tau_host,
-                              void* cuda_stream, rmhmc_model** out) {
-  if (!desc || !out || n_chains < 1 || n_chains > 65535) return RMHMC_EINVAL;
-  *out = nullptr;
+namespace {
+
+rmhmc_status validate_desc(const rmhmc_model_desc* desc, int n_chains, const double* tau_host) {
+  if (!desc || n_chains < 1 || n_chains > 65535) return RMHMC_EINVAL;
+
   if (desc->N < 1 || desc->N > kMaxN || desc->n_cov < 1 || !desc->X || !desc->y) return RMHMC_EINVAL;
   if (desc->n_kernels < 1 || desc->n_kernels > RMHMC_MAX_KERNELS || !desc->kernels) return RMHMC_EINVAL;
   if (desc->lik != RMHMC_LIK_BERNOULLI_LOGIT && desc->lik != RMHMC_LIK_GAUSSIAN) return RMHMC_EINVAL;
@@ -666,7 +888,11 @@ rmhmc_status rmhmc_init_model(const rmhmc_model_desc* desc, int n_chains, const 
     for (int c = 0; c < n_chains; ++c)
       if (!(tau_host[c] >= 0.0) || tau_host[c] > 1.0) return RMHMC_EINVAL;
 
-  rmhmc_model* m = new rmhmc_model();
+  return RMHMC_OK;
+}
+
+// Sizes and the device-side description (without device pointers) of a model for desc.
+void setup_fields(rmhmc_model* m, const rmhmc_model_desc* desc, int n_chains, void* cuda_stream) {
   cudaGetDevice(&m->device);
   m->stream = (cudaStream_t)cuda_stream;
   m->N = desc->N;
@@ -698,57 +924,37 @@ rmhmc_status rmhmc_init_model(const rmhmc_model_desc* desc, int n_chains, const 
       md.k[k].b[h] = kd.prior_b[h];
     }
   }
+}
+
+}  // namespace
+
+rmhmc_status rmhmc_plan_bytes(const rmhmc_model_desc* desc, int n_chains, size_t* bytes) {
+  if (!bytes) return RMHMC_EINVAL;
+  *bytes = 0;
+  rmhmc_status st = validate_desc(desc, n_chains, nullptr);
+  if (st != RMHMC_OK) return st;
+  rmhmc_model m;
+  setup_fields(&m, desc, n_chains, nullptr);
+  size_t total = 0;
+  m.plan_bytes = &total;
+  st = allocate_model(&m, desc->n_cov);
+  *bytes = total;
+  return st;
+}
+
+rmhmc_status rmhmc_init_model(const rmhmc_model_desc* desc, int n_chains, const double* tau_host,
+                              void* cuda_stream, rmhmc_model** out) {
+  if (!out) return RMHMC_EINVAL;
+  *out = nullptr;
+  rmhmc_status vst = validate_desc(desc, n_chains, tau_host);
+  if (vst != RMHMC_OK) return vst;
+  rmhmc_model* m = new rmhmc_model();
+  setup_fields(m, desc, n_chains, cuda_stream);
+  ModelDev& md = m->md;
   const int N = m->N, n = m->n, C = m->C, dp = m->dp;
   const size_t NN = (size_t)N * N, DD = (size_t)dp * dp;
   const size_t B = (size_t)C * n;
-  rmhmc_status st = RMHMC_OK;
-#define ALLOC(ptr, cnt) \
-  if (st == RMHMC_OK) st = dalloc(m, &(ptr), (cnt))
-  double *X = nullptr, *y = nullptr, *uf = nullptr, *tau = nullptr;
-  ALLOC(X, (size_t)N * desc->n_cov);
-  ALLOC(y, (size_t)N);
-  ALLOC(uf, (size_t)2 * n);
-  ALLOC(tau, (size_t)C);
-  ALLOC(m->KL, B * NN);
-  ALLOC(m->D1, B * NN);
-  ALLOC(m->Kinv, B * NN);
-  ALLOC(m->S, B * NN);
-  ALLOC(m->Aux, B * NN);
-  ALLOC(m->S2, B * NN);
-  ALLOC(m->fpk, B * N);
-  ALLOC(m->alpha_, B * N);
-  ALLOC(m->beta, B * N);
-  ALLOC(m->gamma, B * N);
-  ALLOC(m->eps2, B * N);
-  ALLOC(m->eps3, B * N);
-  ALLOC(m->delta, B * N);
-  ALLOC(m->fuu11, B * N);
-  ALLOC(m->stats, B * kStatSlots);
-  ALLOC(m->l0, (size_t)C * N);
-  ALLOC(m->l1, (size_t)C * N);
-  ALLOC(m->l2, (size_t)C * N);
-  ALLOC(m->l3, (size_t)C * N);
-  ALLOC(m->H, C * DD);
-  ALLOC(m->M, C * DD);
-  ALLOC(m->PsiT, C * DD);
-  ALLOC(m->W, C * DD);
-  ALLOC(m->Y, C * DD);
-  ALLOC(m->PsiT_save, C * DD);
-  double** vecs[] = {&m->q, &m->p, &m->ph, &m->q0, &m->v0, &m->vk, &m->t1, &m->dU, &m->dHdq,
-                     &m->lam, &m->g, &m->gp, &m->q_save, &m->z, &m->vtr, &m->xin};
-  for (double** v : vecs) ALLOC(*v, (size_t)C * dp);
-  ALLOC(m->U, (size_t)C);
-  ALLOC(m->Ham0, (size_t)C);
-  ALLOC(m->Ham1, (size_t)C);
-  int** ivecs[] = {&m->status, &m->sweeps_last, &m->sweeps_acc, &m->eig_count, &m->eig_save, &m->acc,
-                   &m->sweeps_total};
-  for (int** v : ivecs) ALLOC(*v, (size_t)C);
-  const int np = dp / kJacBlk / 2;
-  ALLOC(m->jw.V, (size_t)C * np * 256);
-  ALLOC(m->jw.D, (size_t)C * np * 256);
-  ALLOC(m->jw.slots, (size_t)C * 64);
-  ALLOC(m->jw.flags, (size_t)C * np);
-#undef ALLOC
+  rmhmc_status st = allocate_model(m, desc->n_cov);
   if (st != RMHMC_OK) {
     rmhmc_free_model(m);
     return st;
@@ -757,6 +963,7 @@ rmhmc_status rmhmc_init_model(const rmhmc_model_desc* desc, int n_chains, const 
   if (tau_host) memcpy(tauv.data(), tau_host, C * sizeof(double));
   std::vector<double> ufv(2 * n, 0.0);
   if (!desc->sample_hypers) memcpy(ufv.data(), desc->u_fixed, 2 * n * sizeof(double));
+  double *X = m->X_dev, *y = m->y_dev, *uf = m->uf_dev, *tau = m->tau_dev;
   cudaError_t e = cudaMemcpyAsync(X, desc->X, (size_t)N * desc->n_cov * sizeof(double),
                                   cudaMemcpyHostToDevice, m->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(y, desc->y, N * sizeof(double), cudaMemcpyHostToDevice, m->stream);
@@ -787,6 +994,7 @@ rmhmc_status rmhmc_set_state(rmhmc_model* m, const rmhmc_integrator* integ, cons
   m->reorth_every = integ->reorth_every;
   m->precision = integ->precision;
   m->jacobi_rule = integ->jacobi_rule;
+  m->eigen_start = integ->eigen_start;
   cudaStream_t s = m->stream;
   const int C = m->C, dp = m->dp, d = m->d;
   k_restride<<<nblk((long long)C * dp), 256, 0, s>>>(m->q, dp, q_dev, d, d, C);
@@ -827,8 +1035,9 @@ rmhmc_status rmhmc_leapfrog(rmhmc_model* m, const rmhmc_integrator* integ, int n
 }
 
 rmhmc_status rmhmc_sample(rmhmc_model* m, const rmhmc_integrator* integ, int n_iter, int n_burn,
-                          uint64_t seed, double* q_samples_dev, double* logp_dev, int* accept_dev,
-                          int* sweeps_dev, int* chain_status_dev) {
+                          uint64_t seed, double* q_samples_dev, double* logp_dev,
+                          double* loglik_dev, int* accept_dev, int* sweeps_dev,
+                          int* chain_status_dev) {
   if (!m || n_iter < 0 || n_burn < 0) return RMHMC_EINVAL;
   rmhmc_status st = check_integ(m, integ, false);
   if (st != RMHMC_OK) return st;
@@ -860,10 +1069,11 @@ rmhmc_status rmhmc_sample(rmhmc_model* m, const rmhmc_integrator* integ, int n_i
     k_restore<<<dim3(nblk(DD), C), 256, 0, s>>>(m->acc, m->q, m->q_save, m->PsiT, m->PsiT_save,
                                                 m->eig_count, m->eig_save, dp);
     eval_geometry(m, true);
-    if (rec && (q_samples_dev || logp_dev))
-      k_record<<<nblk((long long)C * d), 256, 0, s>>>(m->q, m->U, dp, d, C,
+    if (rec && (q_samples_dev || logp_dev || loglik_dev))
+      k_record<<<nblk((long long)C * d), 256, 0, s>>>(m->q, m->U, m->LL, dp, d, C,
                                                        q_samples_dev ? q_samples_dev + ro * C * d : nullptr,
-                                                       logp_dev ? logp_dev + ro * C : nullptr);
+                                                       logp_dev ? logp_dev + ro * C : nullptr,
+                                                       loglik_dev ? loglik_dev + ro * C : nullptr);
   }
   return check_launch();
 }

@@ -20,6 +20,7 @@ LIKS = {"bernoulli": 0, "gaussian": 1}
 GKINDS = {"coth": 0, "sqrt": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 JACOBI_RULES = {"metric": 0, "relative": 1}
+EIGEN_STARTS = {"warm": 0, "cold": 1}
 CHAIN_NOTPD, CHAIN_NOTCONV, CHAIN_NONFINITE = 1, 2, 4
 PROF_NCAT = 8
 
@@ -39,7 +40,8 @@ class ModelDesc(ctypes.Structure):
 class IntegratorC(ctypes.Structure):
     _fields_ = [("eps", c_double), ("n_leapfrog", c_int), ("n_fp", c_int), ("g_kind", c_int),
                 ("alpha", c_double), ("jacobi_tol", c_double), ("max_sweeps", c_int),
-                ("reorth_every", c_int), ("precision", c_int), ("jacobi_rule", c_int)]
+                ("reorth_every", c_int), ("precision", c_int), ("jacobi_rule", c_int),
+                ("eigen_start", c_int)]
 
 
 @dataclass
@@ -55,11 +57,13 @@ class Integrator:
     reorth_every: int = 10
     precision: str = "fp64"
     jacobi_rule: str = "metric"
+    eigen_start: str = "warm"
 
     def c(self):
         return IntegratorC(self.eps, self.n_leapfrog, self.n_fp, GKINDS[self.g_kind], self.alpha,
                            self.jacobi_tol, self.max_sweeps, self.reorth_every,
-                           PRECISIONS[self.precision], JACOBI_RULES[self.jacobi_rule])
+                           PRECISIONS[self.precision], JACOBI_RULES[self.jacobi_rule],
+                           EIGEN_STARTS[self.eigen_start])
 
 
 class RmhmcError(RuntimeError):
@@ -83,7 +87,7 @@ def lib():
     L.rmhmc_leapfrog.argtypes = [c_void_p, POINTER(IntegratorC), c_int, c_void_p, c_void_p,
                                  c_void_p, c_void_p, c_void_p]
     L.rmhmc_sample.argtypes = [c_void_p, POINTER(IntegratorC), c_int, c_int, c_uint64, c_void_p,
-                               c_void_p, c_void_p, c_void_p, c_void_p]
+                               c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     L.rmhmc_geometry.argtypes = [c_void_p] + [c_void_p] * 6
     L.rmhmc_hamiltonian_grad.argtypes = [c_void_p] + [c_void_p] * 4
     L.rmhmc_dim.argtypes = [c_void_p]
@@ -104,6 +108,16 @@ def lib():
     L.rmhmc_eigh_noalloc.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                      c_double, c_int, c_void_p, c_void_p]
     L.rmhmc_eigh_noalloc.restype = c_int
+    L.rmhmc_batch_create.argtypes = [POINTER(c_void_p), c_int, c_void_p, POINTER(c_void_p)]
+    L.rmhmc_batch_create.restype = c_int
+    L.rmhmc_batch_leapfrog.argtypes = [c_void_p, POINTER(IntegratorC), c_int]
+    L.rmhmc_batch_leapfrog.restype = c_int
+    L.rmhmc_batch_free.argtypes = [c_void_p]
+    L.rmhmc_batch_free.restype = None
+    L.rmhmc_autotune.argtypes = [c_void_p, POINTER(c_int)]
+    L.rmhmc_autotune.restype = c_int
+    L.rmhmc_plan_bytes.argtypes = [POINTER(ModelDesc), c_int, POINTER(ctypes.c_size_t)]
+    L.rmhmc_plan_bytes.restype = c_int
     L.rmhmc_version.argtypes = []
     L.rmhmc_status_string.argtypes = [c_int]
     L.rmhmc_status_string.restype = c_char_p
@@ -134,32 +148,46 @@ def _ptr(t, shape=None, dtype=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _desc(problem):
+    """(ModelDesc, keep-alive list) for a workload dict."""
+    X = np.ascontiguousarray(problem["X"], dtype=np.float64)
+    y = np.ascontiguousarray(problem["y"], dtype=np.float64)
+    ks = (KernelDesc * len(problem["kernels"]))()
+    for i, k in enumerate(problem["kernels"]):
+        cols = list(k["cols"])
+        ks[i].kind = KINDS[k["kind"]]
+        ks[i].n_cols = len(cols)
+        for j, cidx in enumerate(cols):
+            ks[i].cols[j] = int(cidx)
+        ks[i].jitter = float(k["jitter"])
+        ks[i].prior_a[0], ks[i].prior_a[1] = (float(v) for v in k["prior_a"])
+        ks[i].prior_b[0], ks[i].prior_b[1] = (float(v) for v in k["prior_b"])
+    uf = None
+    if not problem["sample_hypers"]:
+        uf = np.ascontiguousarray(problem["u_fixed"], dtype=np.float64)
+    desc = ModelDesc(X.shape[0], X.shape[1], X.ctypes.data_as(POINTER(c_double)),
+                     y.ctypes.data_as(POINTER(c_double)), LIKS[problem["lik"]],
+                     float(problem["noise_var"]), len(problem["kernels"]), ks,
+                     1 if problem["sample_hypers"] else 0,
+                     uf.ctypes.data_as(POINTER(c_double)) if uf is not None else None)
+    return desc, [X, y, ks, uf]
+
+
+def plan_bytes(problem, n_chains):
+    """Device bytes a Model for this problem and chain count would allocate (rmhmc_plan_bytes)."""
+    desc, keep = _desc(problem)
+    out = ctypes.c_size_t()
+    _check(lib().rmhmc_plan_bytes(ctypes.byref(desc), int(n_chains), ctypes.byref(out)))
+    return out.value
+
+
 class Model:
     """One problem (a workload dict) with n_chains chains on the current CUDA device/stream."""
 
     def __init__(self, problem, n_chains, tau=None, stream=None):
         import torch
         L = lib()
-        X = np.ascontiguousarray(problem["X"], dtype=np.float64)
-        y = np.ascontiguousarray(problem["y"], dtype=np.float64)
-        ks = (KernelDesc * len(problem["kernels"]))()
-        for i, k in enumerate(problem["kernels"]):
-            cols = list(k["cols"])
-            ks[i].kind = KINDS[k["kind"]]
-            ks[i].n_cols = len(cols)
-            for j, cidx in enumerate(cols):
-                ks[i].cols[j] = int(cidx)
-            ks[i].jitter = float(k["jitter"])
-            ks[i].prior_a[0], ks[i].prior_a[1] = (float(v) for v in k["prior_a"])
-            ks[i].prior_b[0], ks[i].prior_b[1] = (float(v) for v in k["prior_b"])
-        uf = None
-        if not problem["sample_hypers"]:
-            uf = np.ascontiguousarray(problem["u_fixed"], dtype=np.float64)
-        desc = ModelDesc(X.shape[0], X.shape[1], X.ctypes.data_as(POINTER(c_double)),
-                         y.ctypes.data_as(POINTER(c_double)), LIKS[problem["lik"]],
-                         float(problem["noise_var"]), len(problem["kernels"]), ks,
-                         1 if problem["sample_hypers"] else 0,
-                         uf.ctypes.data_as(POINTER(c_double)) if uf is not None else None)
+        desc, keep = _desc(problem)
         tau_arr = None
         if tau is not None:
             tau_arr = np.ascontiguousarray(np.broadcast_to(np.asarray(tau, dtype=np.float64), (n_chains,)))
@@ -210,13 +238,14 @@ class Model:
                                     _ptr(status_out, (self.n_chains,), torch.int32)))
 
     def sample(self, n_iter, n_burn, seed, q_samples=None, logp=None, accept=None, sweeps=None,
-               chain_status=None, integ=None):
+               chain_status=None, integ=None, loglik=None):
         import torch
         integ, ic = self._integ(integ)
         C, d = self.n_chains, self.d
         _check(lib().rmhmc_sample(self._h, ctypes.byref(ic), int(n_iter), int(n_burn), int(seed),
                                   _ptr(q_samples, (n_iter, C, d), torch.float64),
                                   _ptr(logp, (n_iter, C), torch.float64),
+                                  _ptr(loglik, (n_iter, C), torch.float64),
                                   _ptr(accept, (n_iter, C), torch.int32),
                                   _ptr(sweeps, (n_iter, C), torch.int32),
                                   _ptr(chain_status, (C,), torch.int32)))
@@ -237,6 +266,12 @@ class Model:
                                             _ptr(Ginv_p, (C, d), f64), _ptr(H, (C,), f64)))
 
 
+    def autotune(self):
+        """Pick this model's Jacobi cluster size by timing (rmhmc_autotune); returns it."""
+        out = c_int()
+        _check(lib().rmhmc_autotune(self._h, ctypes.byref(out)))
+        return out.value
+
     def profile(self, enable=True):
         _check(lib().rmhmc_profile(self._h, 1 if enable else 0))
 
@@ -246,6 +281,35 @@ class Model:
         ms, fl, ln = (c_double * n)(), (c_double * n)(), (ctypes.c_longlong * n)()
         _check(lib().rmhmc_profile_read(self._h, ms, fl, ln))
         return {lib().rmhmc_profile_category(i).decode(): (ms[i], fl[i], int(ln[i])) for i in range(n)}
+
+
+class Batch:
+    """Models of different sizes advanced together by one CUDA graph per leapfrog
+    (rmhmc_batch_*). Each model must have been created with its own torch.cuda.Stream."""
+
+    def __init__(self, models, stream=None):
+        import torch
+        self.models = list(models)
+        self.stream = stream or torch.cuda.Stream()  # a created stream: the default one cannot be captured
+        arr = (c_void_p * len(self.models))(*[m._h for m in self.models])
+        h = c_void_p()
+        _check(lib().rmhmc_batch_create(arr, len(self.models), c_void_p(self.stream.cuda_stream),
+                                        ctypes.byref(h)))
+        self._h = h
+
+    def leapfrog(self, n_steps, integ):
+        _check(lib().rmhmc_batch_leapfrog(self._h, ctypes.byref(integ.c()), int(n_steps)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rmhmc_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fp64_peak_tflops(ms_target=200, stream=None):

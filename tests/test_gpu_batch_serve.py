@@ -1,0 +1,118 @@
+"""Uneven batches in one CUDA graph, the Jacobi autotuner, and the continuous-batching server."""
+import numpy as np
+import pytest
+
+from paper_2511_06407_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rm():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2511_06407_b300 import build, rmhmc
+    build.build()
+    return rmhmc
+
+
+def _uneven_problems():
+    return [(wl.gp_classification(30, seed=1), 3), (wl.propensity(24, seed=2, n_kernels=2), 2),
+            (wl.propensity(41, seed=3, n_kernels=3), 4)]
+
+
+def _make(rm, prob, C, seed, integ):
+    s = torch.cuda.Stream()
+    m = rm.Model(prob, C, stream=s)
+    q = torch.tensor(wl.random_state(prob, C, seed=seed, f_scale=0.2, u_scale=0.1), device="cuda")
+    p = torch.tensor(0.3 * wl.random_momentum(prob, C, seed=seed + 100), device="cuda")
+    with torch.cuda.stream(s):
+        m.set_state(q, p, integ=integ)
+    return m, s
+
+
+def _state(m, s, integ):
+    q = torch.empty(m.n_chains, m.d, dtype=torch.float64, device="cuda")
+    p = torch.empty_like(q)
+    with torch.cuda.stream(s):
+        m.leapfrog(0, q, p, integ=integ)
+    torch.cuda.synchronize()
+    return q.cpu().numpy(), p.cpu().numpy()
+
+
+def test_uneven_batch_graph_equals_individual_leapfrogs(rm):
+    """Three problems of different d (30, 52, 129) advanced by one captured CUDA graph per leapfrog
+    give exactly the states of the same models advanced one by one."""
+    integ = rm.Integrator(eps=0.01, n_fp=4)
+    probs = _uneven_problems()
+    solo = [_make(rm, p, C, 10 + i, integ) for i, (p, C) in enumerate(probs)]
+    group = [_make(rm, p, C, 10 + i, integ) for i, (p, C) in enumerate(probs)]
+    for m, s in solo:
+        with torch.cuda.stream(s):
+            m.leapfrog(3, integ=integ)
+    batch = rm.Batch([m for m, _ in group])
+    batch.leapfrog(2, integ)      # captures the graph, replays twice
+    batch.leapfrog(1, integ)      # replays the captured graph
+    torch.cuda.synchronize()
+    for (ms, ss), (mg, sg) in zip(solo, group):
+        qs, ps = _state(ms, ss, integ)
+        qg, pg = _state(mg, sg, integ)
+        np.testing.assert_array_equal(qs, qg)
+        np.testing.assert_array_equal(ps, pg)
+    batch.close()
+
+
+def test_autotune_picks_a_cluster_and_keeps_the_state(rm, oracle_model):
+    from oracle.geometry import Geometry
+    integ = rm.Integrator(eps=0.01, n_fp=4)
+    prob = wl.gp_classification(40, seed=4)
+    m, s = _make(rm, prob, 4, 7, integ)
+    U0 = torch.empty(4, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(s):
+        m.geometry(U=U0)
+        c = m.autotune()
+        U1 = torch.empty_like(U0)
+        m.geometry(U=U1)
+        dHdq = torch.empty(4, m.d, dtype=torch.float64, device="cuda")
+        P = wl.random_momentum(prob, 4, seed=8)
+        m.hamiltonian_grad(torch.tensor(P, device="cuda"), dHdq=dHdq)
+    torch.cuda.synchronize()
+    assert c in (1, 2, 4, 8)
+    np.testing.assert_array_equal(U0.cpu().numpy(), U1.cpu().numpy())
+    q = wl.random_state(prob, 4, seed=7, f_scale=0.2, u_scale=0.1)
+    ref = Geometry(oracle_model(prob), q[2], 1.0).dHdq(P[2])
+    assert np.linalg.norm(dHdq.cpu().numpy()[2] - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_server_results_are_the_same_alone_and_in_the_mix(rm):
+    from paper_2511_06407_b300.serve import Job, Server
+    integ = rm.Integrator(eps=0.01, n_leapfrog=3, n_fp=4)
+    probs = _uneven_problems()
+    taus = [np.linspace(0.2, 1.0, C) for _, C in probs]
+
+    def jobs(arrivals):
+        return [Job(p, C, n_iter=3, n_burn=1, seed=5 + i, tau=taus[i], integ=integ, arrival=a, job_id=i)
+                for i, ((p, C), a) in enumerate(zip(probs, arrivals))]
+
+    mixed, stats = Server(hbm_budget_bytes=2**30).run(jobs([0.0, 0.0, 0.01]))
+    assert stats["jobs"] == 3 and stats["max_concurrent_jobs"] >= 2
+    assert stats["p50_latency_s"] > 0 and stats["p99_latency_s"] >= stats["p50_latency_s"]
+    for i in range(3):
+        alone, _ = Server(hbm_budget_bytes=2**30).run([jobs([0.0, 0.0, 0.0])[i]])
+        np.testing.assert_array_equal(alone[0].q_samples, mixed[i].q_samples)
+        np.testing.assert_array_equal(alone[0].logp, mixed[i].logp)
+        np.testing.assert_array_equal(alone[0].accept, mixed[i].accept)
+
+
+def test_server_admits_by_hbm_budget(rm):
+    """With a budget that fits one job at a time, jobs run one after another (never two resident)."""
+    from paper_2511_06407_b300.serve import Job, Server
+    integ = rm.Integrator(eps=0.01, n_leapfrog=2, n_fp=3)
+    prob = wl.gp_classification(30, seed=1)
+    need = rm.plan_bytes(prob, 2)
+    js = [Job(prob, 2, n_iter=2, seed=i, integ=integ, arrival=0.0, job_id=i) for i in range(3)]
+    done, stats = Server(hbm_budget_bytes=int(need * 1.5)).run(js)
+    assert stats["max_concurrent_jobs"] == 1 and stats["jobs"] == 3
+    for a, b in zip(done, done[1:]):
+        assert b.admitted >= a.finished - 1e-3
