@@ -2,8 +2,10 @@
 """Benchmark: SoftAbs-RMHMC generalized-leapfrog substeps per second on B300.
 
 Workload (default): GP binary classification, N = 400 inputs x ~ U[-1, 1]^2, SE kernel with log
-amplitude and log lengthscale (d = 402), 64 chains in one batch, plain FP64 path, soft-abs
-alpha = 1e6, eps = 0.1, 6 fixed-point iterations. A step is one generalized leapfrog of every chain:
+amplitude and log lengthscale (d = 402), 64 chains in one batch, soft-abs alpha = 1e6, eps = 0.005,
+6 fixed-point iterations; the mixed-precision form (the headline value) and the plain FP64 path are
+timed one after the other, with the error of one 10-leapfrog trajectory between them. A step is one
+generalized leapfrog of every chain:
 13 substeps per chain (6 implicit-momentum iterations, 6 implicit-position iterations, 1 explicit
 half-step). value = chains x 13 x steps / seconds, whole job over all ranks.
 
@@ -38,6 +40,30 @@ METRIC = "RMHMC leapfrog substeps/s"
 UNIT = "substeps/s"
 WORKLOAD = (f"GP classification N={N_INPUTS} (d={N_INPUTS + 2}), SE kernel, {N_CHAINS} chains batched, "
             f"plain FP64, alpha=1e6, eps={EPS}, n_fp={N_FP}")
+
+
+MIXED_NOTE = ("mixed precision: Jacobi rotations and the d x d products Psi^T H Psi, Psi C Psi^T in "
+              "double-float (FP32 pairs, ~48-bit); Cholesky, K^-1 algebra, log|G|, H in FP64")
+
+
+def aux_precision(args):
+    """Precision of the auxiliary workloads: mixed unless --precision fp64."""
+    return "fp64" if args.precision == "fp64" else "mixed"
+
+
+def dtype_of(prec):
+    return "f64" if prec == "fp64" else "f64 + f32x2 (double-float)"
+
+
+def arm_config(C, ws, head):
+    """The workload description both arms print (the GPU arm and the oracle reference arm)."""
+    workload = WORKLOAD if C == N_CHAINS else WORKLOAD.replace(f"{N_CHAINS} chains", f"{C} chains")
+    workload = workload.replace("plain FP64", "plain FP64" if head == "fp64" else "mixed precision")
+    return {"workload": workload, "N": N_INPUTS, "d": N_INPUTS + 2, "chains_per_gpu": C,
+            "precision": "plain FP64" if head == "fp64" else MIXED_NOTE,
+            "substeps_per_leapfrog": SUBSTEPS_PER_LEAPFROG,
+            "l2": "inputs larger than L2 (per-chain state ~16 MB, 64 chains ~1 GB > 126 MB)",
+            "parallelism": f"replicas x{ws}"}
 
 
 def dist_env():
@@ -147,13 +173,89 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": N_INPUTS, "d": N_INPUTS + 2, "chains": N_CHAINS},
+            "config": arm_config(args.chains, args.gpus, "mixed" if args.precision == "both" else args.precision),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "one chain of the workload, one leapfrog per step (numpy/LAPACK FP64, "
                                        "full third-derivative tensor)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _time_leapfrogs(model, integ, steps, stream, local, ws, dev):
+    """K timed leapfrogs of every chain (device-resident state), CUDA events on the model's stream,
+    clocks sampled meanwhile; returns (ms, profile, clocks), ms the max over ranks."""
+    import torch
+    import torch.distributed as dist
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    model.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        model.leapfrog(1, integ=integ)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = model.profile_read()
+    model.profile(False)
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item()), prof, clk
+
+
+def _roofline(rmhmc, prof, C):
+    """Roofline of the dominant kernel category (ALU bound; peaks measured live on this GPU)."""
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_flops, dom_launches = prof[dom]
+    if dom in ("jacobi_df", "gemm_df"):
+        # a double-float multiply-add (Dot2 step) is 12 FP32 instructions issuing at the FFMA
+        # rate, so its ALU ceiling is the measured FP32 rate / 12 (in FP64-equivalent flops)
+        fp32 = rmhmc.fp32_peak_tflops(300)
+        peak = fp32 / 12.0
+        peak_note = (f"double-float ceiling = measured FP32 FMA rate {fp32:.1f} TFLOP/s (rmhmc_fp32_peak) / 12 "
+                     "FP32 instructions per double-float multiply-add")
+    else:
+        peak = rmhmc.fp64_peak_tflops(300)
+        peak_note = "FP64 FMA throughput measured live on this GPU (rmhmc_fp64_peak)"
+    achieved = (dom_flops / dom_launches) / ((dom_ms / dom_launches) * 1e-3) / 1e12 if dom_launches else 0.0
+    out = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": achieved / peak if peak else None, "traffic": None, "peak_note": peak_note}
+    if dom.startswith("jacobi"):
+        out["achieved_note"] = ("executed 16x16x16 rotation-tile products x 8192 flops; skipped identity tiles "
+                                "and the 16x16 inner solves not counted")
+    if dom == "jacobi_f64":
+        out["traffic"] = JACOBI_DRAM_BYTES_PER_CHAIN * C
+        out["traffic_note"] = "bytes per k_jacobi launch, ncu capture at 8 chains scaled to the chain count"
+    return out
+
+
+def _trajectory_error(rmhmc, prob, q0, p0):
+    """One 10-leapfrog trajectory of the same chains from the same (q, p) in both precisions:
+    max over chains of ||x_mixed - x_fp64|| / ||x_fp64|| for x = q and p."""
+    import torch
+    out = {}
+    for prec in ("fp64", "mixed"):
+        integ = rmhmc.Integrator(eps=EPS, n_fp=N_FP, n_leapfrog=1, precision=prec)
+        m = rmhmc.Model(prob, q0.shape[0])
+        m.set_state(q0, p0, integ=integ)
+        m.leapfrog(10, integ=integ)
+        q, p = torch.empty_like(q0), torch.empty_like(q0)
+        m.leapfrog(0, q, p, integ=integ)
+        torch.cuda.synchronize()
+        out[prec] = (q.cpu().numpy(), p.cpu().numpy())
+        m.close()
+    rel = {}
+    for k, name in enumerate(("q", "p")):
+        a, b = out["fp64"][k], out["mixed"][k]
+        rel[name] = float(np.max(np.linalg.norm(b - a, axis=1) / np.linalg.norm(a, axis=1)))
+    return {"chains": int(q0.shape[0]), "leapfrogs": 10, "max_rel_q": rel["q"], "max_rel_p": rel["p"]}
 
 
 def run_b300(args):
@@ -172,52 +274,35 @@ def run_b300(args):
     stream = torch.cuda.current_stream()
     prob = wl.gp_classification(N_INPUTS, seed=0)
     C = args.chains
-    model = rmhmc.Model(prob, C, stream=stream)
-    d = model.d
-    integ = rmhmc.Integrator(eps=EPS, n_fp=N_FP, n_leapfrog=1)
-    q0 = torch.zeros(C, d, dtype=torch.float64, device=dev)
-    model.set_state(q0, integ=integ)
-    qo = torch.empty(C, d, dtype=torch.float64, device=dev)
-    po = torch.empty_like(qo)
-    Ho = torch.empty(C, dtype=torch.float64, device=dev)
-    st = torch.empty(C, dtype=torch.int32, device=dev)
-
-    # ---- warm-up: one Algorithm 1 iteration (momenta p ~ N(0, G) drawn by the library, one
-    # leapfrog, Metropolis-Hastings), then plain leapfrogs
-    model.sample(1, 0, 1234 + rank, integ=integ)
-    if args.warmup > 1:
-        model.leapfrog(args.warmup - 1, integ=integ)
-    model.leapfrog(0, qo, po, integ=integ)
-    p0 = po.clone()
-    torch.cuda.synchronize()
-    # ---- timed region: device-resident inputs
-    clocks = ClockSampler(local)
-    clocks.start()
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    model.profile(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        model.leapfrog(1, integ=integ)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    prof = model.profile_read()
-    model.profile(False)
-    if ws > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    precisions = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
+    runs = {}
+    for prec in precisions:
+        model = rmhmc.Model(prob, C, stream=stream)
+        d = model.d
+        integ = rmhmc.Integrator(eps=EPS, n_fp=N_FP, n_leapfrog=1, precision=prec)
+        model.set_state(torch.zeros(C, d, dtype=torch.float64, device=dev), integ=integ)
+        # warm-up: one Algorithm 1 iteration (momenta p ~ N(0, G) drawn by the library, one
+        # leapfrog, Metropolis-Hastings), then plain leapfrogs
+        model.sample(1, 0, 1234 + rank, integ=integ)
+        if args.warmup > 1:
+            model.leapfrog(args.warmup - 1, integ=integ)
+        qo = torch.empty(C, d, dtype=torch.float64, device=dev)
+        po = torch.empty_like(qo)
+        model.leapfrog(0, qo, po, integ=integ)
+        torch.cuda.synchronize()
+        ms, prof, clk = _time_leapfrogs(model, integ, args.steps, stream, local, ws, dev)
+        runs[prec] = {"model": model, "integ": integ, "ms": ms, "prof": prof, "clk": clk, "q": qo, "p": po}
+    head = precisions[0]
+    model, integ, d = runs[head]["model"], runs[head]["integ"], runs[head]["model"].d
+    ms = runs[head]["ms"]
 
     # ---- end to end: per step, momenta uploaded from pinned host memory, one leapfrog through the
     # C ABI, position / momentum / Hamiltonian read back into pinned host memory
-    p_host = p0.cpu().pin_memory()
-    p_dev = torch.empty_like(p0)
+    qo, po = torch.empty(C, d, dtype=torch.float64, device=dev), torch.empty(C, d, dtype=torch.float64, device=dev)
+    Ho = torch.empty(C, dtype=torch.float64, device=dev)
+    st = torch.empty(C, dtype=torch.int32, device=dev)
+    p_host = runs[head]["p"].cpu().pin_memory()
+    p_dev = torch.empty_like(runs[head]["p"])
     q_host = torch.empty(C, d, dtype=torch.float64).pin_memory()
     pout_host = torch.empty_like(q_host).pin_memory()
     H_host = torch.empty(C, dtype=torch.float64).pin_memory()
@@ -239,6 +324,10 @@ def run_b300(args):
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_s = float(te.item())
     status = st.cpu().numpy()
+    for prec in precisions:
+        x = torch.empty(C, dtype=torch.int32, device=dev)
+        runs[prec]["model"].leapfrog(0, status_out=x, integ=runs[prec]["integ"])
+        runs[prec]["status"] = x.cpu().numpy()
 
     if rank != 0:
         if ws > 1:
@@ -249,12 +338,12 @@ def run_b300(args):
     total_chains = C * ws
     value = total_chains * SUBSTEPS_PER_LEAPFROG * args.steps / (ms * 1e-3)
     e2e_value = total_chains * SUBSTEPS_PER_LEAPFROG * e_steps / e2e_s
-    # roofline of the dominant kernel category (FP64 ALU bound), peak measured live on this GPU
-    dom = max(prof, key=lambda k: prof[k][0])
-    dom_ms, dom_flops, dom_launches = prof[dom]
-    peak = rmhmc.fp64_peak_tflops(300)
-    achieved = (dom_flops / dom_launches) / ((dom_ms / dom_launches) * 1e-3) / 1e12 if dom_launches else 0.0
-    gpu_launches = int(sum(v[2] for v in prof.values()))
+    roof = _roofline(rmhmc, runs[head]["prof"], C)
+    gpu_launches = int(sum(v[2] for v in runs[head]["prof"].values()))
+    traj = None
+    if args.precision == "both":
+        k = min(4, C)
+        traj = _trajectory_error(rmhmc, prob, runs["fp64"]["q"][:k].clone(), runs["fp64"]["p"][:k].clone())
     # CPU baseline: the oracle on this host's cores, bounded sample
     cpu_baseline = None
     if not args.no_cpu_baseline:
@@ -262,36 +351,224 @@ def run_b300(args):
         cpu_baseline = {"value": cb_value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
                         "sample": f"{cb_n} oracle leapfrog(s) of one chain of the workload in {cb_s:.1f} s "
                                   "(numpy/LAPACK FP64, full third-derivative tensor)"}
+    def prof_summary(prof):
+        return ({k: round(v[0], 3) for k, v in prof.items() if v[2]},
+                {k: (v[1] / (v[0] * 1e-3) / 1e12 if v[0] > 0 else 0.0) for k, v in prof.items() if v[2]})
+
+    pms, ptf = prof_summary(runs[head]["prof"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if C == N_CHAINS else WORKLOAD.replace(f"{N_CHAINS} chains", f"{C} chains"),
-                   "N": N_INPUTS, "d": d, "chains_per_gpu": C,
-                   "substeps_per_leapfrog": SUBSTEPS_PER_LEAPFROG,
-                   "l2": "inputs larger than L2 (per-chain state ~16 MB, 64 chains ~1 GB > 126 MB)",
-                   "parallelism": f"replicas x{ws}"},
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head == "fp64" else "f64 + f32x2 (double-float)",
+        "data": "synthetic",
+        "config": arm_config(C, ws, head),
         "leapfrogs_per_s": total_chains * args.steps / (ms * 1e-3),
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
-                     "traffic": (JACOBI_DRAM_BYTES_PER_CHAIN * C) if dom == "jacobi_f64" else None,
-                     "traffic_note": "bytes per k_jacobi launch, ncu capture at 8 chains scaled to the chain count",
-                     "peak_note": "FP64 FMA throughput measured live on this GPU (rmhmc_fp64_peak)"},
-        "profile_ms": {k: round(v[0], 3) for k, v in prof.items()},
-        "profile_tflops": {k: (v[1] / (v[0] * 1e-3) / 1e12 if v[0] > 0 else 0.0) for k, v in prof.items()},
+        "roofline": roof,
+        "profile_ms": pms, "profile_tflops": ptf,
         "cpu_baseline": cpu_baseline,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(p_host.numel() * 8),
                 "d2h_bytes_per_step": int((q_host.numel() + pout_host.numel() + H_host.numel()) * 8)},
         "gpu_launches": gpu_launches,
-        "chain_status_nonzero": int((status != 0).sum()),
-        "valid": bool((status == 0).all()),
-        "clocks": clk,
+        "chain_status_nonzero": int((status != 0).sum() + (runs[head]["status"] != 0).sum()),
+        "valid": bool((status == 0).all() and (runs[head]["status"] == 0).all()),
+        "clocks": runs[head]["clk"],
     }
+    if "fp64" in runs and head != "fp64":
+        r = runs["fp64"]
+        f_ms, f_tf = prof_summary(r["prof"])
+        f_value = total_chains * SUBSTEPS_PER_LEAPFROG * args.steps / (r["ms"] * 1e-3)
+        line["fp64"] = {"value": f_value, "ms_per_step": r["ms"] / args.steps, "roofline": _roofline(rmhmc, r["prof"], C),
+                        "profile_ms": f_ms, "profile_tflops": f_tf,
+                        "chain_status_nonzero": int((r["status"] != 0).sum()), "clocks": r["clk"]}
+        line["speedup_vs_fp64"] = value / f_value
+        line["trajectory_error_vs_fp64"] = traj
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+    return 0
+
+
+def _clock_and_time(fn, local):
+    import torch
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fn()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return el, clocks.stop()
+
+
+def run_propensity(args):
+    """Additive 3-kernel propensity model, N = 500 (d = 1506), 32 chains."""
+    import torch
+    from paper_2511_06407_b300 import build, rmhmc
+    build.build()
+    prob = wl.propensity(500, seed=0, n_kernels=3)
+    C = 32
+    model = rmhmc.Model(prob, C)
+    prec = aux_precision(args)
+    integ = rmhmc.Integrator(eps=args.eps or 0.005, n_fp=N_FP, n_leapfrog=1, precision=prec)
+    model.set_state(torch.zeros(C, model.d, dtype=torch.float64, device="cuda"), integ=integ)
+    model.sample(1, 0, 99, integ=integ)
+    model.leapfrog(max(args.warmup - 1, 0), integ=integ)
+    st = torch.empty(C, dtype=torch.int32, device="cuda")
+    model.profile(True)
+    el, clk = _clock_and_time(lambda: model.leapfrog(args.steps, status_out=st, integ=integ), 0)
+    prof = model.profile_read()
+    status = st.cpu().numpy()
+    value = C * SUBSTEPS_PER_LEAPFROG * args.steps / el
+    print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+                      "dtype": dtype_of(prec), "data": "synthetic",
+                      "config": {"workload": "propensity model N=500, SE+linear+overlap (d=1506), 32 chains, "
+                                             f"{prec}, eps={integ.eps}", "d": model.d, "chains": C},
+                      "profile_ms": {k: round(v[0], 1) for k, v in prof.items()},
+                      "profile_tflops": {k: (v[1] / (v[0] * 1e-3) / 1e12 if v[0] > 0 else 0.0) for k, v in prof.items()},
+                      "chain_status_nonzero": int((status != 0).sum()), "clocks": clk}), flush=True)
+    return 0
+
+
+def run_ess(args):
+    """Effective samples per second of Algorithm 1 on the GP-classification problem (L = 10,
+    n_fp = 6), plain FP64 and mixed precision, independent seeds, plus the matched-error check:
+    posterior means and variances of (log P, u, mean f) of the mixed run within 3 Monte-Carlo
+    standard errors of the FP64 run's."""
+    import torch
+    from paper_2511_06407_b300 import build, rmhmc
+    from paper_2511_06407_b300 import diagnostics as dg
+    build.build()
+    N, C = args.ess_n, args.chains
+    prob = wl.gp_classification(N, seed=0)
+    eps = args.eps or 0.01
+    names = ["log P", "log c", "log l", "mean f"]
+    runs = {}
+    for k, prec in enumerate(("fp64", "mixed")):
+        integ = rmhmc.Integrator(eps=eps, n_leapfrog=10, n_fp=N_FP, precision=prec)
+        model = rmhmc.Model(prob, C)
+        d = model.d
+        model.set_state(torch.zeros(C, d, dtype=torch.float64, device="cuda"), integ=integ)
+        cs = torch.zeros(C, dtype=torch.int32, device="cuda")
+        seed = 11 + 1000 * k
+        model.sample(0, args.burn, seed, chain_status=cs, integ=integ)
+        qs = torch.empty(args.iters, C, d, dtype=torch.float64, device="cuda")
+        lp = torch.empty(args.iters, C, dtype=torch.float64, device="cuda")
+        acc = torch.empty(args.iters, C, dtype=torch.int32, device="cuda")
+        cs2 = torch.zeros(C, dtype=torch.int32, device="cuda")
+        el, clk = _clock_and_time(lambda: model.sample(args.iters, 0, seed, qs, lp, acc, chain_status=cs2,
+                                                       integ=integ), 0)
+        Q, LP = qs.cpu().numpy(), lp.cpu().numpy()
+        draws = np.concatenate([LP[:, :, None], Q[:, :, -2:], Q[:, :, :N].mean(axis=2, keepdims=True)], axis=2)
+        summ = dg.summary(draws, names)
+        x = draws.transpose(1, 0, 2)  # chains x iterations x quantities
+        mean = x.reshape(-1, 4).mean(axis=0)
+        var = x.reshape(-1, 4).var(axis=0)
+        se_mean = np.array([dg.mcse_mean(x[:, :, j]) for j in range(4)])
+        se_var = np.array([dg.mcse_mean((x[:, :, j] - mean[j]) ** 2) for j in range(4)])
+        runs[prec] = {"seconds": el, "min_ess": summ["min_ess"], "ess_per_s": summ["min_ess"] / el,
+                      "max_rhat": summ["max_rhat"], "acceptance": float(acc.cpu().numpy().mean()),
+                      "substeps_per_s": C * args.iters * 10 * SUBSTEPS_PER_LEAPFROG / el,
+                      "chain_status_nonzero": int(((cs | cs2).cpu().numpy() != 0).sum()),
+                      "ess": {r["name"]: round(min(r["ess_bulk"], r["ess_tail"]), 1) for r in summ["rows"]},
+                      "mean": mean, "var": var, "se_mean": se_mean, "se_var": se_var, "clocks": clk}
+        model.close()
+    a, b = runs["fp64"], runs["mixed"]
+    z_mean = np.abs(a["mean"] - b["mean"]) / np.sqrt(a["se_mean"] ** 2 + b["se_mean"] ** 2)
+    z_var = np.abs(a["var"] - b["var"]) / np.sqrt(a["se_var"] ** 2 + b["se_var"] ** 2)
+    matched = bool((z_mean <= 3).all() and (z_var <= 3).all())
+    for r in runs.values():
+        for key in ("mean", "var", "se_mean", "se_var"):
+            r[key] = [round(float(v), 6) for v in r[key]]
+    print(json.dumps({"metric": "effective samples/s (min over log P, u, mean f; bulk and tail ESS)",
+                      "value": b["ess_per_s"], "unit": "ESS/s", "n_gpus": 1, "higher_is_better": True,
+                      "dtype": "f64; Jacobi rotations f32x2 (double-float)", "data": "synthetic",
+                      "config": {"workload": f"GP classification N={N} (d={N + 2}), {C} chains, eps={eps}, L=10, "
+                                             f"n_fp=6, {args.burn} burn-in + {args.iters} kept iterations",
+                                 "quantities": names},
+                      "fp64": runs["fp64"], "mixed": runs["mixed"],
+                      "speedup_ess_per_s": b["ess_per_s"] / a["ess_per_s"] if a["ess_per_s"] > 0 else None,
+                      "matched_error": {"z_mean": [round(float(v), 2) for v in z_mean],
+                                        "z_var": [round(float(v), 2) for v in z_var], "within_3_se": matched}}),
+          flush=True)
+    return 0
+
+
+def run_uneven(args):
+    """Problems of uneven size (N ~ U{32..256}, 1-3 kernels, 8 chains each) advanced together by
+    one CUDA graph per leapfrog, each with its autotuned Jacobi cluster size."""
+    import torch
+    from paper_2511_06407_b300 import build, rmhmc
+    build.build()
+    probs = wl.uneven_batch(args.problems, seed=0, n_min=32, n_max=256)
+    C = 8
+    prec = aux_precision(args)
+    integ = rmhmc.Integrator(eps=args.eps or 0.005, n_fp=N_FP, n_leapfrog=1, precision=prec)
+    models, clusters = [], []
+    for i, prob in enumerate(probs):
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            m = rmhmc.Model(prob, C, stream=s)
+            m.set_state(torch.zeros(C, m.d, dtype=torch.float64, device="cuda"), integ=integ)
+            clusters.append(m.autotune())
+            m.sample(1, 0, 7 + i, integ=integ)
+        models.append(m)
+    torch.cuda.synchronize()
+    batch = rmhmc.Batch(models)
+    batch.leapfrog(max(args.warmup - 1, 1), integ)
+    el, clk = _clock_and_time(lambda: batch.leapfrog(args.steps, integ), 0)
+    st = []
+    for m in models:
+        x = torch.empty(C, dtype=torch.int32, device="cuda")
+        with torch.cuda.stream(m.stream):
+            m.leapfrog(0, status_out=x, integ=integ)
+        st.append(x)
+    torch.cuda.synchronize()
+    bad = int(sum((x.cpu().numpy() != 0).sum() for x in st))
+    chains = C * len(models)
+    ds = [m.d for m in models]
+    print(json.dumps({"metric": METRIC, "value": chains * SUBSTEPS_PER_LEAPFROG * args.steps / el, "unit": UNIT,
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "dtype": dtype_of(prec),
+                      "data": "synthetic",
+                      "config": {"workload": f"uneven batch: {len(models)} problems, N~U{{32..256}}, 1-3 kernels, "
+                                             f"8 chains each, one CUDA graph per leapfrog, eps={integ.eps}",
+                                 "d_min": min(ds), "d_max": max(ds), "chains": chains,
+                                 "jacobi_clusters": clusters},
+                      "chain_status_nonzero": bad, "clocks": clk}), flush=True)
+    batch.close()
+    return 0
+
+
+def run_serve(args):
+    """A Poisson trace of sampling jobs served with continuous batching (scaled-down form of the
+    served-stream configuration: N ~ U{50..200}, 1-3 kernels, 8 inverse temperatures x 2 chains,
+    2 burn-in + 6 recorded iterations of 4 leapfrogs)."""
+    from paper_2511_06407_b300 import build, rmhmc
+    from paper_2511_06407_b300.bme import power_schedule
+    from paper_2511_06407_b300.serve import Job, Server, poisson_trace
+    build.build()
+    probs = wl.uneven_batch(args.jobs, seed=100, n_min=50, n_max=200)
+    prec = aux_precision(args)
+    integ = rmhmc.Integrator(eps=args.eps or 0.005, n_fp=N_FP, n_leapfrog=4, precision=prec)
+    taus = np.repeat(power_schedule(8), 2)
+    arrivals = poisson_trace(probs, args.rate, seed=1)
+    jobs = [Job(p, 16, n_iter=6, n_burn=2, seed=i, tau=taus, integ=integ, arrival=a, job_id=i)
+            for i, (p, a) in enumerate(zip(probs, arrivals))]
+    done, stats = Server(hbm_budget_bytes=int(args.hbm_gb * 2**30)).run(jobs)
+    bad = int(sum((j.chain_status != 0).sum() for j in done))
+    print(json.dumps({"metric": "served RMHMC substeps/s; job latency p50/p99", "value": stats["substeps_per_s"],
+                      "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": dtype_of(prec), "data": "synthetic",
+                      "p50_latency_s": stats["p50_latency_s"], "p99_latency_s": stats["p99_latency_s"],
+                      "makespan_s": stats["makespan_s"], "jobs": stats["jobs"],
+                      "max_concurrent_jobs": stats["max_concurrent_jobs"],
+                      "config": {"workload": f"Poisson trace, {args.jobs} jobs at {args.rate}/s, N~U{{50..200}}, "
+                                             "1-3 kernels, 8 temperatures x 2 chains, 2+6 iterations x 4 leapfrogs, "
+                                             f"HBM budget {args.hbm_gb} GiB", "eps": integ.eps},
+                      "chain_status_nonzero": bad}), flush=True)
     return 0
 
 
@@ -305,9 +582,30 @@ def main():
     ap.add_argument("--chains", type=int, default=N_CHAINS,
                     help="chains per GPU (the workload is 64; smaller values are for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    ap.add_argument("--workload", default="gp400", choices=["gp400", "propensity", "uneven", "serve", "ess"],
+                    help="gp400 is the benchmark; the others are extra measurements")
+    ap.add_argument("--eps", type=float, default=None)
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"],
+                    help="both (default): the mixed form is the headline, timed beside the plain FP64 path "
+                         "on the same workload, with the trajectory error between them")
+    ap.add_argument("--problems", type=int, default=16)
+    ap.add_argument("--ess-n", type=int, default=100, help="inputs N of the ESS workload")
+    ap.add_argument("--iters", type=int, default=200, help="kept iterations of the ESS workload")
+    ap.add_argument("--burn", type=int, default=100, help="burn-in iterations of the ESS workload")
+    ap.add_argument("--jobs", type=int, default=24)
+    ap.add_argument("--rate", type=float, default=2.0)
+    ap.add_argument("--hbm-gb", type=float, default=64.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "propensity":
+        return run_propensity(args)
+    if args.workload == "uneven":
+        return run_uneven(args)
+    if args.workload == "ess":
+        return run_ess(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_b300(args)
 
 

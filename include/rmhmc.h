@@ -110,7 +110,9 @@ typedef struct {
   double jacobi_tol;   /* zeta, the tolerance of Sec. 2.4 (see jacobi_rule for how it is applied) */
   int max_sweeps;      /* Jacobi sweep limit per eigen-update */
   int reorth_every;    /* Gram-Schmidt of Psi every this many eigen-updates (Sec. 2.4); 0 = never */
-  int precision;       /* rmhmc_precision; only RMHMC_FP64 in this build */
+  int precision;       /* rmhmc_precision: FP64, or MIXED = the Jacobi rotations and the d x d
+                          products M = Psi^T H Psi and W = Psi C Psi^T in double-float (FP32 pairs,
+                          ~48-bit significand); Cholesky, K^-1 algebra, H and log|G| stay FP64 */
   int jacobi_rule;     /* rmhmc_jacobi_rule: when M = Psi^T H Psi counts as diagonal */
   int eigen_start;     /* 0: warm start from the previous Psi (dynamic, Sec. 2.4); 1: cold start
                           from Psi = I at every eigen-update (the static ablation of Sec. 3.1) */
@@ -202,10 +204,11 @@ rmhmc_status rmhmc_autotune(rmhmc_model* m, int* cluster_out);
  * launch of the model is bracketed by CUDA events on the model's stream and counted in one of
  * RMHMC_PROF_NCAT categories (names from rmhmc_profile_category), with the algorithmic FLOPs of
  * the work it must do (GEMM 2mnk on the unpadded sizes, halved for symmetric outputs; Cholesky
- * and triangular inverse N^3/3; Jacobi 8 d^3 per sweep actually performed). rmhmc_profile(m, 1)
+ * and triangular inverse N^3/3; Jacobi 2 * 16^3 per 16 x 16 x 16 rotation-tile product executed,
+ * tiles skipped because both rotations were the identity not counted). rmhmc_profile(m, 1)
  * resets and starts, rmhmc_profile(m, 0) stops. rmhmc_profile_read synchronises the stream and
  * writes per-category milliseconds, FLOPs and launch counts (host arrays of RMHMC_PROF_NCAT). */
-#define RMHMC_PROF_NCAT 8
+#define RMHMC_PROF_NCAT 10
 rmhmc_status rmhmc_profile(rmhmc_model* m, int enable);
 rmhmc_status rmhmc_profile_read(rmhmc_model* m, double* ms_host, double* flops_host,
                                 long long* launches_host);
@@ -215,6 +218,8 @@ const char* rmhmc_profile_category(int i);
  * dependent-chain DFMA kernel on every SM for about ms_target milliseconds on cuda_stream and writes
  * the achieved TFLOP/s (2 flops per FMA) to *tflops_host. Synchronises the stream. */
 rmhmc_status rmhmc_fp64_peak(void* cuda_stream, int ms_target, double* tflops_host);
+/* The same for FP32 FFMA (the denominator of the double-float Jacobi of RMHMC_MIXED). */
+rmhmc_status rmhmc_fp32_peak(void* cuda_stream, int ms_target, double* tflops_host);
 
 /* Allocation-free eigendecomposition of a batch of symmetric matrices, for callers that cannot
  * allocate device memory (e.g. code running inside another framework's memory pool or arena, a

@@ -28,6 +28,7 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include "df.cuh"
 #include "internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -206,7 +207,8 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
                                                    int* __restrict__ sweeps_acc,
                                                    double* __restrict__ Vb, double* __restrict__ Db,
                                                    double* __restrict__ slotsb,
-                                                   int* __restrict__ flagsb) {
+                                                   int* __restrict__ flagsb,
+                                                   unsigned long long* __restrict__ tiles) {
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
@@ -236,6 +238,7 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
   const int nMjobs = np * (np + 1) / 2, nct = dp / SB;
   int sweeps = 0;
   bool converged = false;
+  unsigned int ntile = 0;  // 16 x 16 x 16 tile products this warp executed
   for (;;) {
     // ---- convergence test. Pass 1: ||M||_F^2 and min_i<d |m_ii|. Pass 2: the worst pair ratio
     //      (pair_ratio) under the chosen rule, with floor = 4 u ||M||_F (rounding level).
@@ -356,6 +359,7 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
             if (fQ) load_v(Vq, V + (long long)Q * SB * SB);
             __syncwarp();
             tile_transform(X, fP ? Va : nullptr, fQ ? Vq : nullptr, Tt, X);
+            ntile += (fP ? 1u : 0u) + (fQ ? 1u : 0u);
             const int t = lane >> 1, u0 = (lane & 1) * 8;
 #pragma unroll
             for (int j = 0; j < 8; ++j)
@@ -378,6 +382,7 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
           load_v(Va, V + (long long)Pp * SB * SB);
           __syncwarp();
           tile_transform(X, Va, nullptr, Tt, X);
+          ++ntile;
           const int t = lane >> 1, u0 = (lane & 1) * 8;
 #pragma unroll
           for (int j = 0; j < 8; ++j)
@@ -391,6 +396,282 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
   }
   for (int i = rank * blockDim.x + tid; i < dp; i += C * blockDim.x)
     lamb[(long long)chain * dp + i] = __ldcg(M + (long long)i * dp + i);
+  if (tiles && lane == 0 && ntile) atomicAdd(tiles + chain, (unsigned long long)ntile);
+  if (rank == 0 && tid == 0) {
+    sweeps_out[chain] = sweeps;
+    if (sweeps_acc) sweeps_acc[chain] += sweeps;
+    if (!converged) atomicOr(&status[chain], RMHMC_CHAIN_NOTCONV);
+  }
+}
+
+// ------------------------------------------------------------------ double-float variant
+// Mixed precision: the rotations of phase 2 are applied in double-float arithmetic (df.cuh). M and
+// Psi^T are held as FP32 pairs in scratch for the whole kernel; the 16 x 16 inner solves (phase 1),
+// the stopping test and the conversions stay in FP64.
+// Y = Vp^T X Vq on 16 x 16 double-float tiles in shared memory (null Vp / Vq = identity).
+__device__ __forceinline__ void tile_transform_df(const float2* X, const float2* Vp, const float2* Vq,
+                                                  float2* T, float2* Y) {
+  const int lane = threadIdx.x & 31;
+  const int t = lane >> 1, u0 = (lane & 1) * 8;
+  const float2* src = X;
+  if (Vq) {
+    float sh[8], cl[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { sh[j] = 0.f; cl[j] = 0.f; }
+#pragma unroll 4
+    for (int v = 0; v < SB; ++v) {
+      const float2 x = X[t * SBP + v];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) dot2_step(sh[j], cl[j], x, Vq[v * SBP + u0 + j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) T[t * SBP + u0 + j] = df_renorm(sh[j], cl[j]);
+    __syncwarp();
+    src = T;
+  }
+  float2 out[8];
+  if (Vp) {
+    float sh[8], cl[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { sh[j] = 0.f; cl[j] = 0.f; }
+#pragma unroll 4
+    for (int v = 0; v < SB; ++v) {
+      const float2 p = Vp[v * SBP + t];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) dot2_step(sh[j], cl[j], p, src[v * SBP + u0 + j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) out[j] = df_renorm(sh[j], cl[j]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) out[j] = src[t * SBP + u0 + j];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) Y[t * SBP + u0 + j] = out[j];
+  __syncwarp();
+}
+
+__device__ __forceinline__ float2 ldcg2(const float2* p) { return __ldcg(p); }
+
+__device__ __forceinline__ void load_v_df(float2* dst, const float2* src) {
+  const int lane = threadIdx.x & 31;
+  for (int e = lane; e < SB * SB; e += 32) dst[(e / SB) * SBP + e % SB] = ldcg2(src + e);
+}
+
+// Same algorithm and stopping rule as k_jacobi (the rounding floor uses the double-float unit
+// 2^-48); M and Psi^T (double, dp x dp per chain) are converted into the pair buffers Mw, Pw
+// (float2, same layout) at entry and back at exit.
+__global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, double* __restrict__ Pb,
+                                                      double* __restrict__ lamb, int dp, int d, int rule,
+                                                      double tol, int max_sweeps,
+                                                      int* __restrict__ status,
+                                                      int* __restrict__ sweeps_out,
+                                                      int* __restrict__ sweeps_acc,
+                                                      double* __restrict__ Vb, double* __restrict__ Db,
+                                                      double* __restrict__ slotsb,
+                                                      int* __restrict__ flagsb,
+                                                      unsigned long long* __restrict__ tiles,
+                                                      float2* __restrict__ Mwb, float2* __restrict__ Pwb) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int chain = blockIdx.x / C;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nb = dp / BL, np = nb / 2;
+  if (status[chain] != 0) {
+    if (rank == 0 && tid == 0) sweeps_out[chain] = 0;
+    return;  // uniform for the whole cluster
+  }
+  const long long DD = (long long)dp * dp;
+  double* M = Mb + (long long)chain * DD;
+  double* P = Pb + (long long)chain * DD;
+  float2* Mw = Mwb + (long long)chain * DD;
+  float2* Pw = Pwb + (long long)chain * DD;
+  float2* V = (float2*)(Vb + (long long)chain * np * SB * SB);
+  float2* D = (float2*)(Db + (long long)chain * np * SB * SB);
+  double* slots = slotsb + (long long)chain * 64;
+  int* flags = flagsb + (long long)chain * np;
+  extern __shared__ double smem[];
+  double* ws = smem + warp * WARP_SMEM;
+  double* Xd = ws;                    // phase 1 (FP64)
+  double* Vd = ws + 2 * SB * SBP;
+  float2* X = (float2*)ws;            // phase 2 (pairs), same bytes
+  float2* Tt = (float2*)(ws + SB * SBP);
+  float2* Va = (float2*)(ws + 2 * SB * SBP);
+  float2* Vq = (float2*)(ws + 3 * SB * SBP);
+  __shared__ double red[2][NW];
+  __shared__ double cs[NW][SB];
+
+  for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
+    __stcg(Mw + e, df_split(__ldcg(M + e)));
+    __stcg(Pw + e, df_split(__ldcg(P + e)));
+  }
+  cluster.sync();
+
+  const int gw = rank * NW + warp, nwt = C * NW;
+  const int nMjobs = np * (np + 1) / 2, nct = dp / SB;
+  int sweeps = 0;
+  bool converged = false;
+  unsigned int ntile = 0;  // 16 x 16 x 16 tile products this warp executed
+  for (;;) {
+    double tot = 0.0, dmin = 1e308;
+    for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
+      const double v = df_join(ldcg2(Mw + e));
+      tot = fma(v, v, tot);
+      const int i = (int)(e / dp);
+      if (i < d && (long long)i * dp + i == e) dmin = fmin(dmin, fabs(v));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      dmin = fmin(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+    }
+    if (lane == 0) { red[0][warp] = tot; red[1][warp] = dmin; }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 1e308;
+      for (int w = 0; w < NW; ++w) { a += red[0][w]; b = fmin(b, red[1][w]); }
+      __stcg(slots + (sweeps & 1) * 32 + 2 * rank, a);
+      __stcg(slots + (sweeps & 1) * 32 + 2 * rank + 1, b);
+    }
+    cluster.sync();
+    tot = 0.0;
+    dmin = 1e308;
+    for (int r = 0; r < C; ++r) {
+      tot += __ldcg(slots + (sweeps & 1) * 32 + 2 * r);
+      dmin = fmin(dmin, __ldcg(slots + (sweeps & 1) * 32 + 2 * r + 1));
+    }
+    const double dmin2 = fmax(dmin * dmin, 1e-300);
+    const double floor2 = fmax(16.0 * 1.2621774483536189e-29 * tot, 1e-300);  // (4 * 2^-48)^2 ||M||^2
+    double crit = 0.0, bad = isfinite(tot) ? 0.0 : 1.0;
+    for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
+      const int j = (int)(e / dp), l = (int)(e % dp);
+      if (j == l) continue;
+      const double v = df_join(ldcg2(Mw + e));
+      if (v == 0.0) continue;
+      if (!isfinite(v)) bad = 1.0;
+      if (pair_unconverged(v, df_join(ldcg2(Mw + (long long)j * dp + j)),
+                           df_join(ldcg2(Mw + (long long)l * dp + l)), tol * tol, floor2, rule, dmin2))
+        crit = 1.0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      crit = fmax(crit, __shfl_xor_sync(0xffffffffu, crit, o));
+      bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, o));
+    }
+    __syncthreads();
+    if (lane == 0) { red[0][warp] = crit; red[1][warp] = bad; }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < NW; ++w) { a = fmax(a, red[0][w]); b = fmax(b, red[1][w]); }
+      __stcg(slots + (sweeps & 1) * 32 + 16 + 2 * rank, a);
+      __stcg(slots + (sweeps & 1) * 32 + 16 + 2 * rank + 1, b);
+    }
+    cluster.sync();
+    crit = 0.0;
+    bad = 0.0;
+    for (int r = 0; r < C; ++r) {
+      crit = fmax(crit, __ldcg(slots + (sweeps & 1) * 32 + 16 + 2 * r));
+      bad = fmax(bad, __ldcg(slots + (sweeps & 1) * 32 + 16 + 2 * r + 1));
+    }
+    if (bad != 0.0) break;
+    if (crit == 0.0) { converged = true; break; }
+    if (sweeps >= max_sweeps) break;
+    const double itol2 = 1e-4 * tol * tol;
+
+    for (int r = 0; r < nb - 1; ++r) {
+      // ---- phase 1 (FP64): exact 16 x 16 solves, one warp per block pair
+      for (int p = gw; p < np; p += nwt) {
+        int I, J;
+        circle_pair(r, p, nb, I, J);
+        for (int e = lane; e < SB * SB; e += 32) {
+          const int a = e / SB, b = e % SB;
+          Xd[a * SBP + b] = df_join(ldcg2(Mw + (long long)gidx(I, J, a) * dp + gidx(I, J, b)));
+        }
+        __syncwarp();
+        const bool rot = inner_solve(Xd, Vd, cs[warp], itol2, floor2, rule, dmin2);
+        if (rot) {
+          for (int e = lane; e < SB * SB; e += 32) {
+            const int a = e / SB, b = e % SB;
+            __stcg(V + (long long)p * SB * SB + e, df_split(Vd[a * SBP + b]));
+            __stcg(D + (long long)p * SB * SB + e, df_split(Xd[a * SBP + b]));
+          }
+        }
+        if (lane == 0) __stcg(flags + p, rot ? 1 : 0);
+        __syncwarp();
+      }
+      cluster.sync();
+      // ---- phase 2 (double-float): apply all rotations to M and to the rows of Psi^T
+      for (int job = gw; job < nMjobs + np * nct; job += nwt) {
+        if (job < nMjobs) {
+          int Q = (int)((sqrtf(8.0f * (float)job + 1.0f) - 1.0f) * 0.5f);
+          while (Q * (Q + 1) / 2 > job) --Q;
+          while ((Q + 1) * (Q + 2) / 2 <= job) ++Q;
+          const int Pp = job - Q * (Q + 1) / 2;
+          const int fP = __ldcg(flags + Pp), fQ = __ldcg(flags + Q);
+          if (!fP && !fQ) continue;
+          int I1, J1, I2, J2;
+          circle_pair(r, Pp, nb, I1, J1);
+          circle_pair(r, Q, nb, I2, J2);
+          if (Pp == Q) {
+            for (int e = lane; e < SB * SB; e += 32) {
+              const int a = e / SB, b = e % SB;
+              __stcg(Mw + (long long)gidx(I1, J1, a) * dp + gidx(I1, J1, b),
+                     ldcg2(D + (long long)Pp * SB * SB + e));
+            }
+          } else {
+            for (int e = lane; e < SB * SB; e += 32) {
+              const int a = e / SB, b = e % SB;
+              X[a * SBP + b] = ldcg2(Mw + (long long)gidx(I1, J1, a) * dp + gidx(I2, J2, b));
+            }
+            if (fP) load_v_df(Va, V + (long long)Pp * SB * SB);
+            if (fQ) load_v_df(Vq, V + (long long)Q * SB * SB);
+            __syncwarp();
+            tile_transform_df(X, fP ? Va : nullptr, fQ ? Vq : nullptr, Tt, X);
+            ntile += (fP ? 1u : 0u) + (fQ ? 1u : 0u);
+            const int t = lane >> 1, u0 = (lane & 1) * 8;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              __stcg(Mw + (long long)gidx(I1, J1, t) * dp + gidx(I2, J2, u0 + j), X[t * SBP + u0 + j]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              __stcg(Mw + (long long)gidx(I2, J2, t) * dp + gidx(I1, J1, u0 + j), X[(u0 + j) * SBP + t]);
+          }
+          __syncwarp();
+        } else {
+          const int pj = job - nMjobs;
+          const int Pp = pj / nct, ct = pj % nct;
+          if (!__ldcg(flags + Pp)) continue;
+          int I1, J1;
+          circle_pair(r, Pp, nb, I1, J1);
+          for (int e = lane; e < SB * SB; e += 32) {
+            const int a = e / SB, b = e % SB;
+            X[a * SBP + b] = ldcg2(Pw + (long long)gidx(I1, J1, a) * dp + ct * SB + b);
+          }
+          load_v_df(Va, V + (long long)Pp * SB * SB);
+          __syncwarp();
+          tile_transform_df(X, Va, nullptr, Tt, X);
+          ++ntile;
+          const int t = lane >> 1, u0 = (lane & 1) * 8;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            __stcg(Pw + (long long)gidx(I1, J1, t) * dp + ct * SB + u0 + j, X[t * SBP + u0 + j]);
+          __syncwarp();
+        }
+      }
+      cluster.sync();
+    }
+    ++sweeps;
+  }
+  for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
+    __stcg(M + e, df_join(ldcg2(Mw + e)));
+    __stcg(P + e, df_join(ldcg2(Pw + e)));
+  }
+  for (int i = rank * blockDim.x + tid; i < dp; i += C * blockDim.x)
+    lamb[(long long)chain * dp + i] = df_join(ldcg2(Mw + (long long)i * dp + i));
+  if (tiles && lane == 0 && ntile) atomicAdd(tiles + chain, (unsigned long long)ntile);
   if (rank == 0 && tid == 0) {
     sweeps_out[chain] = sweeps;
     if (sweeps_acc) sweeps_acc[chain] += sweeps;
@@ -520,7 +801,22 @@ void jacobi_f64(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, in
     attr_set = true;
   }
   launch_cluster(k_jacobi, n_chains, cluster, smem, s, M, PsiT, lam, dp, d, rule, tol, max_sweeps,
-                 status, sweeps_out, sweeps_acc, w.V, w.D, w.slots, w.flags);
+                 status, sweeps_out, sweeps_acc, w.V, w.D, w.slots, w.flags, w.tiles);
+}
+
+void jacobi_df(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,
+               int rule, double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
+               JacobiWork w, int cluster, double* pair_scratch_M, double* pair_scratch_P) {
+  const size_t smem = (size_t)NW * WARP_SMEM * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_jacobi_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  launch_cluster(k_jacobi_df, n_chains, cluster, smem, s, M, PsiT, lam, dp, d, rule, tol, max_sweeps,
+                 status, sweeps_out, sweeps_acc, w.V, w.D, w.slots, w.flags, w.tiles,
+                 (float2*)pair_scratch_M,
+                 (float2*)pair_scratch_P);
 }
 
 void mgs_rows_f64(cudaStream_t s, double* PsiT, int dp, int d, int n_chains, const int* eig_count,
@@ -568,7 +864,8 @@ extern "C" rmhmc_status rmhmc_eigh_noalloc(void* cuda_stream, int n, int d, cons
     return RMHMC_ECUDA;
   if (launch_cluster(k_jacobi, n, C, smem, s, M, P, lamp, dp, d, (int)RMHMC_JACOBI_RELATIVE, tol,
                      max_sweeps, status,
-                     sweeps_dev ? sweeps_dev : sweeps, (int*)nullptr, V, D, slots, flags) != cudaSuccess)
+                     sweeps_dev ? sweeps_dev : sweeps, (int*)nullptr, V, D, slots, flags,
+                     (unsigned long long*)nullptr) != cudaSuccess)
     return RMHMC_ECUDA;
   const long long out = (long long)n * d * d;
   k_noalloc_unpack<<<(unsigned)((out + 255) / 256), 256, 0, s>>>(lamp, P, d, dp, n, lam_dev, Q_dev);

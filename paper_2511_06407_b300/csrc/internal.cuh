@@ -64,6 +64,10 @@ struct GeomDev {
 void gemm_f64(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
               int lda, long long sA, const double* B, int ldb, long long sB, double beta, double* C,
               int ldc, long long sC, int batch, bool sym, bool tri);
+// The same product in double-float arithmetic (FP32 pairs, Dot2 accumulation; no tri form).
+void gemm_df(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
+             int lda, long long sA, const double* B, int ldb, long long sB, double beta, double* C,
+             int ldc, long long sC, int batch, bool sym);
 // In-place lower Cholesky of batch N x N matrices (row-major, ld = N); writes log|K| to
 // logdet[b * logdet_stride] and sets status bit RMHMC_CHAIN_NOTPD in status[b / per_chain].
 void cholesky_f64(cudaStream_t s, double* A, int N, int batch, double* logdet, int logdet_stride,
@@ -87,10 +91,16 @@ struct JacobiWork {
   double* D;      // n_chains x (nb/2) x 256
   double* slots;  // n_chains x 64
   int* flags;     // n_chains x (nb/2): pair rotated in the current round
+  unsigned long long* tiles;  // n_chains: += 16 x 16 x 16 tile products executed (null = not counted)
 };
 void jacobi_f64(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,
                 int rule, double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
                 JacobiWork w, int cluster);
+// The same eigen-update with the phase-2 rotations in double-float (FP32 pair) arithmetic;
+// pair_scratch_M / pair_scratch_P are n_chains x dp x dp doubles of scratch (used as float2).
+void jacobi_df(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,
+               int rule, double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
+               JacobiWork w, int cluster, double* pair_scratch_M, double* pair_scratch_P);
 // Modified Gram-Schmidt on the first d rows of PsiT (dp x dp per chain), for chains whose
 // eig_count is a positive multiple of every (0 = never).
 void mgs_rows_f64(cudaStream_t s, double* PsiT, int dp, int d, int n_chains, const int* eig_count,

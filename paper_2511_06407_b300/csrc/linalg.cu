@@ -4,6 +4,7 @@
 // rather than chasing memory bandwidth.
 #include <math.h>
 
+#include "df.cuh"
 #include "internal.cuh"
 
 namespace rmhmc {
@@ -352,6 +353,106 @@ __global__ void __launch_bounds__(256) k_cholsolve(const double* __restrict__ Lb
 }
 
 }  // namespace
+
+namespace {
+
+// The same tiling in double-float arithmetic (df.cuh) for the mixed-precision form: FP64 operands
+// are split into FP32 pairs as they are staged in shared memory, every output accumulates a Dot2
+// sum (hi word + compensation word), and the result is rounded back to FP64. Thread (ty, tx) owns
+// rows ty + 16 i and columns tx + 16 j of the 64 x 64 tile, as in k_gemm.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(GT, 2) k_gemm_df(int m, int n, int k, double alpha,
+                                                const double* __restrict__ A, int lda, long long sA,
+                                                const double* __restrict__ B, int ldb, long long sB,
+                                                double beta, double* __restrict__ C, int ldc,
+                                                long long sC, int sym) {
+  const int tm = blockIdx.y, tn = blockIdx.x, b = blockIdx.z;
+  if (sym && tn > tm) return;
+  A += b * sA;
+  B += b * sB;
+  C += b * sC;
+  __shared__ float2 As[BK][BM + 1];
+  __shared__ float2 Bs[BK][BN + 1];
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int row0 = tm * BM, col0 = tn * BN;
+  float sh[4][4], cl[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { sh[i][j] = 0.f; cl[i][j] = 0.f; }
+  for (int k0 = 0; k0 < k; k0 += BK) {
+#pragma unroll
+    for (int e = tid; e < BM * BK; e += GT) {
+      int mm, kk;
+      if (TA) { kk = e / BM; mm = e % BM; } else { mm = e / BK; kk = e % BK; }
+      const int gr = row0 + mm, gk = k0 + kk;
+      double v = 0.0;
+      if (gr < m && gk < k) v = TA ? A[(long long)gk * lda + gr] : A[(long long)gr * lda + gk];
+      As[kk][mm] = df_split(v);
+    }
+#pragma unroll
+    for (int e = tid; e < BN * BK; e += GT) {
+      int kk, nn;
+      if (TB) { nn = e / BK; kk = e % BK; } else { kk = e / BN; nn = e % BN; }
+      const int gk = k0 + kk, gc = col0 + nn;
+      double v = 0.0;
+      if (gk < k && gc < n) v = TB ? B[(long long)gc * ldb + gk] : B[(long long)gk * ldb + gc];
+      Bs[kk][nn] = df_split(v);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      float2 a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dot2_step(sh[i][j], cl[i][j], a[i], bb[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = row0 + ty + 16 * i;
+    if (r >= m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = col0 + tx + 16 * j;
+      if (c >= n) continue;
+      const double acc = df_join(df_renorm(sh[i][j], cl[i][j]));
+      if (sym) {
+        if (tm == tn && c > r) continue;
+        const double v = alpha * acc;
+        C[(long long)r * ldc + c] = v;
+        if (c != r) C[(long long)c * ldc + r] = v;
+      } else {
+        const long long o = (long long)r * ldc + c;
+        C[o] = alpha * acc + (beta != 0.0 ? beta * C[o] : 0.0);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+void gemm_df(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
+             int lda, long long sA, const double* B, int ldb, long long sB, double beta, double* C,
+             int ldc, long long sC, int batch, bool sym) {
+  if (m <= 0 || n <= 0 || batch <= 0) return;
+  dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, batch);
+  if (!ta && !tb)
+    k_gemm_df<false, false><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
+  else if (!ta && tb)
+    k_gemm_df<false, true><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
+  else if (ta && !tb)
+    k_gemm_df<true, false><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
+  else
+    k_gemm_df<true, true><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
+}
+
 
 void cholsolve_f64(cudaStream_t s, const double* L, const double* f, double* t, double* a, int N,
                    int batch) {

@@ -274,9 +274,10 @@ __global__ void k_scale_rows(double* __restrict__ Y, const double* __restrict__ 
 
 // Eight independent FMA chains per thread: enough instruction-level parallelism to keep the FP64
 // pipe busy; the result is kept live through a data-dependent store that never happens.
-__global__ void k_dfma_peak(double* __restrict__ sink, int iters, double b, double c) {
-  double a0 = threadIdx.x * 1e-3, a1 = a0 + 1.0, a2 = a0 + 2.0, a3 = a0 + 3.0;
-  double a4 = a0 + 4.0, a5 = a0 + 5.0, a6 = a0 + 6.0, a7 = a0 + 7.0;
+template <typename T>
+__global__ void k_fma_peak(T* __restrict__ sink, int iters, T b, T c) {
+  T a0 = (T)(threadIdx.x * 1e-3), a1 = a0 + (T)1, a2 = a0 + (T)2, a3 = a0 + (T)3;
+  T a4 = a0 + (T)4, a5 = a0 + (T)5, a6 = a0 + (T)6, a7 = a0 + (T)7;
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -284,11 +285,44 @@ __global__ void k_dfma_peak(double* __restrict__ sink, int iters, double b, doub
       a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
     }
   }
-  const double s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
-  if (s == 12345.678) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+  const T s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (s == (T)12345.678) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+template <typename T>
+rmhmc_status fma_peak(void* cuda_stream, int ms_target, double* tflops_host) {
+  if (!tflops_host || ms_target < 1) return RMHMC_EINVAL;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 4, threads = 256;
+  T* sink = nullptr;
+  if (cudaMalloc(&sink, (size_t)blocks * threads * sizeof(T)) != cudaSuccess) return RMHMC_ENOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int iters = 64;
+  float ms = 0.f;
+  k_fma_peak<T><<<blocks, threads, 0, s>>>(sink, 8, (T)0.9999, (T)1e-7);
+  for (int rep = 0; rep < 12; ++rep) {
+    cudaEventRecord(e0, s);
+    k_fma_peak<T><<<blocks, threads, 0, s>>>(sink, iters, (T)0.9999, (T)1e-7);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms >= 0.5f * ms_target || !(ms > 1e-3f)) break;
+    iters = (int)fmin(1e7, iters * fmin(100.0, fmax(2.0, 0.8 * ms_target / ms)));
+  }
+  const double flops = 2.0 * blocks * threads * (double)iters * 16.0 * 8.0;
+  *tflops_host = ms > 1e-3f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  return cudaGetLastError() == cudaSuccess ? RMHMC_OK : RMHMC_ECUDA;
+}
 
 }  // namespace
 
@@ -334,9 +368,12 @@ struct rmhmc_model {
 
 namespace {
 
-enum Cat { CAT_GEMM = 0, CAT_JACOBI, CAT_CHOL, CAT_TRINV, CAT_MODEL, CAT_CONTRACT, CAT_VECTOR, CAT_MGS };
+enum Cat {
+  CAT_GEMM = 0, CAT_JACOBI, CAT_CHOL, CAT_TRINV, CAT_MODEL, CAT_CONTRACT, CAT_VECTOR, CAT_MGS, CAT_JACOBI_DF,
+  CAT_GEMM_DF
+};
 const char* kCatNames[RMHMC_PROF_NCAT] = {"gemm_f64", "jacobi_f64", "cholesky_f64", "trinv_f64",
-                                          "model", "contract", "vector", "mgs_f64"};
+                                          "model", "contract", "vector", "mgs_f64", "jacobi_df", "gemm_df"};
 
 // Brackets one launch site with CUDA events on the model's stream while profiling is enabled.
 struct ProfScope {
@@ -366,6 +403,10 @@ inline double gemm_flops(double mm, double nn, double kk, bool sym, bool tri) {
   if (tri) return mm * mm * mm / 3.0;
   return sym ? mm * (mm + 1.0) * kk : 2.0 * mm * nn * kk;
 }
+
+// The dp x dp products of the eigen-update (M = Psi^T H Psi) and of W = Psi C Psi^T, batched over
+// the chains: FP64, or double-float in the mixed form.
+void gemm_dd(rmhmc_model* m, bool ta, bool tb, const double* A, const double* B, double* out, bool sym);
 
 // When planning (m->plan_bytes != nullptr) nothing is allocated: the bytes are only counted.
 template <typename T>
@@ -442,17 +483,35 @@ void eval_geometry(rmhmc_model* m, bool third) {
     PROF(m, CAT_MGS, 0)
     mgs_rows_f64(s, m->PsiT, dp, d, C, m->eig_count, m->reorth_every, m->cluster);
   }
-  PROF(m, CAT_GEMM, Cf * gemm_flops(df, df, df, false, false))
-  gemm_f64(s, false, true, dp, dp, dp, 1.0, m->H, dp, DD, m->PsiT, dp, DD, 0.0, m->Y, dp, DD, C, false, false);
-  PROF(m, CAT_GEMM, Cf * gemm_flops(df, df, df, true, false))
-  gemm_f64(s, false, false, dp, dp, dp, 1.0, m->PsiT, dp, DD, m->Y, dp, DD, 0.0, m->M, dp, DD, C, true, false);
-  PROF(m, CAT_JACOBI, 0)
-  jacobi_f64(s, m->M, m->PsiT, m->lam, dp, d, C, m->jacobi_rule, m->tol, m->max_sweeps, m->status,
-             m->sweeps_last, m->sweeps_acc, m->jw, m->cluster);
+  gemm_dd(m, false, true, m->H, m->PsiT, m->Y, false);
+  gemm_dd(m, false, false, m->PsiT, m->Y, m->M, true);
+  if (m->precision == RMHMC_MIXED) {
+    // rotations in double-float pairs; W and Y serve as the pair buffers (free during the update)
+    PROF(m, CAT_JACOBI_DF, 0)
+    jacobi_df(s, m->M, m->PsiT, m->lam, dp, d, C, m->jacobi_rule, m->tol, m->max_sweeps, m->status,
+              m->sweeps_last, m->sweeps_acc, m->jw, m->cluster, m->W, m->Y);
+  } else {
+    PROF(m, CAT_JACOBI, 0)
+    jacobi_f64(s, m->M, m->PsiT, m->lam, dp, d, C, m->jacobi_rule, m->tol, m->max_sweeps, m->status,
+               m->sweeps_last, m->sweeps_acc, m->jw, m->cluster);
+  }
   PROF(m, CAT_VECTOR, 0)
   k_inc<<<nblk(C), 256, 0, s>>>(m->eig_count, C, m->sweeps_total, m->sweeps_last);
   PROF(m, CAT_VECTOR, 0)
   k_softabs<<<nblk((long long)C * dp), 256, 0, s>>>(m->lam, m->g, m->gp, dp, d, C, m->alpha, m->g_kind);
+}
+
+void gemm_dd(rmhmc_model* m, bool ta, bool tb, const double* A, const double* B, double* out, bool sym) {
+  const int dp = m->dp;
+  const long long DD = (long long)dp * dp;
+  const double df = m->d, fl = m->C * gemm_flops(df, df, df, sym, false);
+  if (m->precision == RMHMC_MIXED) {
+    PROF(m, CAT_GEMM_DF, fl)
+    gemm_df(m->stream, ta, tb, dp, dp, dp, 1.0, A, dp, DD, B, dp, DD, 0.0, out, dp, DD, m->C, sym);
+  } else {
+    PROF(m, CAT_GEMM, fl)
+    gemm_f64(m->stream, ta, tb, dp, dp, dp, 1.0, A, dp, DD, B, dp, DD, 0.0, out, dp, DD, m->C, sym, false);
+  }
 }
 
 // out = G^-1 x = Psi diag(1/g) Psi^T x
@@ -480,10 +539,8 @@ void grad_h(rmhmc_model* m, const double* x, double* out) {
   PROF(m, CAT_VECTOR, 0)
   k_build_c<<<dim3(nblk(DD), C), 256, 0, s>>>(m->t1, m->lam, m->g, m->gp, m->M, dp, m->d, m->alpha, m->g_kind);
   // W = Psi C Psi^T = PsiT^T (C PsiT)
-  PROF(m, CAT_GEMM, Cf * gemm_flops(df, df, df, false, false))
-  gemm_f64(s, false, false, dp, dp, dp, 1.0, m->M, dp, DD, m->PsiT, dp, DD, 0.0, m->Y, dp, DD, C, false, false);
-  PROF(m, CAT_GEMM, Cf * gemm_flops(df, df, df, true, false))
-  gemm_f64(s, true, false, dp, dp, dp, 1.0, m->PsiT, dp, DD, m->Y, dp, DD, 0.0, m->W, dp, DD, C, true, false);
+  gemm_dd(m, false, false, m->M, m->PsiT, m->Y, false);
+  gemm_dd(m, true, false, m->PsiT, m->Y, m->W, true);
   PROF(m, CAT_CONTRACT, 0)
   dev::k_contract<<<C * n, 256, 2 * N * sizeof(double), s>>>(m->md, m->q, dp, m->W, m->Kinv, m->Aux,
                                                              m->l3, m->alpha_, m->gamma, m->fuu11,
@@ -581,13 +638,14 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
   ALLOC(m->jw.D, (size_t)C * np * 256);
   ALLOC(m->jw.slots, (size_t)C * 64);
   ALLOC(m->jw.flags, (size_t)C * np);
+  ALLOC(m->jw.tiles, (size_t)C);
 #undef ALLOC
   return st;
 }
 
 rmhmc_status check_integ(const rmhmc_model* m, const rmhmc_integrator* in, bool for_state) {
   if (!in) return RMHMC_EINVAL;
-  if (in->precision != RMHMC_FP64) return RMHMC_ENOTIMPL;
+  if (in->precision != RMHMC_FP64 && in->precision != RMHMC_MIXED) return RMHMC_EINVAL;
   if (in->g_kind != RMHMC_G_COTH && in->g_kind != RMHMC_G_SQRT) return RMHMC_EINVAL;
   if (!(in->alpha > 0.0) || !(in->jacobi_tol > 0.0) || in->max_sweeps < 0 || in->reorth_every < 0)
     return RMHMC_EINVAL;
@@ -597,6 +655,7 @@ rmhmc_status check_integ(const rmhmc_model* m, const rmhmc_integrator* in, bool 
   if (!for_state) {
     if (!m->has_state) return RMHMC_EINVAL;
     if (in->g_kind != m->g_kind || in->alpha != m->alpha || in->jacobi_tol != m->tol ||
+        in->precision != m->precision ||
         in->max_sweeps != m->max_sweeps || in->reorth_every != m->reorth_every ||
         in->jacobi_rule != m->jacobi_rule || in->eigen_start != m->eigen_start)
       return RMHMC_EINVAL;
@@ -735,8 +794,10 @@ rmhmc_status rmhmc_autotune(rmhmc_model* m, int* cluster_out) {
     k_set_identity<<<nblk((long long)C * DD), 256, 0, s>>>(m->Y, dp, C);
     cudaMemsetAsync(m->acc, 0, C * sizeof(int), s);
     cudaEventRecord(e0, s);
+    JacobiWork w = m->jw;
+    w.tiles = nullptr;  // trial runs stay out of the profile
     jacobi_f64(s, m->W, m->Y, m->vtr, dp, d, C, m->jacobi_rule, m->tol, 3, m->acc, m->eig_save,
-               nullptr, m->jw, cl);
+               nullptr, w, cl);
     cudaEventRecord(e1, s);
     if (cudaEventSynchronize(e1) != cudaSuccess) return RMHMC_ECUDA;
     float ms = 0.f;
@@ -776,36 +837,13 @@ const char* rmhmc_status_string(rmhmc_status s) {
 
 const char* rmhmc_version(void) { return "rmhmc sm_103a fp64"; }
 
+
 rmhmc_status rmhmc_fp64_peak(void* cuda_stream, int ms_target, double* tflops_host) {
-  if (!tflops_host || ms_target < 1) return RMHMC_EINVAL;
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int blocks = sms * 4, threads = 256;
-  double* sink = nullptr;
-  if (cudaMalloc(&sink, (size_t)blocks * threads * sizeof(double)) != cudaSuccess) return RMHMC_ENOMEM;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  int iters = 64;
-  float ms = 0.f;
-  k_dfma_peak<<<blocks, threads, 0, s>>>(sink, 8, 0.9999, 1e-7);
-  for (int rep = 0; rep < 12; ++rep) {
-    cudaEventRecord(e0, s);
-    k_dfma_peak<<<blocks, threads, 0, s>>>(sink, iters, 0.9999, 1e-7);
-    cudaEventRecord(e1, s);
-    cudaEventSynchronize(e1);
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms >= 0.5f * ms_target || !(ms > 1e-3f)) break;
-    iters = (int)fmin(1e7, iters * fmin(100.0, fmax(2.0, 0.8 * ms_target / ms)));
-  }
-  const double flops = 2.0 * blocks * threads * (double)iters * 16.0 * 8.0;
-  *tflops_host = ms > 1e-3f ? flops / (ms * 1e-3) / 1e12 : 0.0;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaFree(sink);
-  return cudaGetLastError() == cudaSuccess ? RMHMC_OK : RMHMC_ECUDA;
+  return fma_peak<double>(cuda_stream, ms_target, tflops_host);
+}
+
+rmhmc_status rmhmc_fp32_peak(void* cuda_stream, int ms_target, double* tflops_host) {
+  return fma_peak<float>(cuda_stream, ms_target, tflops_host);
 }
 
 const char* rmhmc_profile_category(int i) {
@@ -827,6 +865,7 @@ rmhmc_status rmhmc_profile(rmhmc_model* m, int enable) {
       m->prof_launch[i] = 0;
     }
     cudaMemsetAsync(m->sweeps_total, 0, m->C * sizeof(int), m->stream);
+    cudaMemsetAsync(m->jw.tiles, 0, m->C * sizeof(unsigned long long), m->stream);
   }
   m->prof = enable != 0;
   return RMHMC_OK;
@@ -841,14 +880,18 @@ rmhmc_status rmhmc_profile_read(rmhmc_model* m, double* ms_host, double* flops_h
     float t = 0.f;
     if (cudaEventElapsedTime(&t, m->ev[r.a], m->ev[r.b]) == cudaSuccess) ms[r.cat] += t;
   }
-  std::vector<int> sw(m->C);
-  cudaMemcpy(sw.data(), m->sweeps_total, m->C * sizeof(int), cudaMemcpyDeviceToHost);
-  double sweeps = 0.0;
-  for (int v : sw) sweeps += v;
-  const double d = m->d;
+  // Jacobi work = the 16 x 16 x 16 rotation tile products the kernel executed (2 * 16^3 flops
+  // each); tiles skipped because both rotations were the identity are not counted
+  std::vector<unsigned long long> tl(m->C);
+  cudaMemcpy(tl.data(), m->jw.tiles, m->C * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  double tiles = 0.0;
+  for (unsigned long long v : tl) tiles += (double)v;
   for (int i = 0; i < RMHMC_PROF_NCAT; ++i) {
     if (ms_host) ms_host[i] = ms[i];
-    if (flops_host) flops_host[i] = (i == CAT_JACOBI) ? sweeps * 8.0 * d * d * d : m->prof_flops[i];
+    if (flops_host)
+      flops_host[i] = (i == CAT_JACOBI || i == CAT_JACOBI_DF)
+                          ? (m->prof_launch[i] ? tiles * 8192.0 : 0.0)
+                          : m->prof_flops[i];
     if (launches_host) launches_host[i] = m->prof_launch[i];
   }
   return RMHMC_OK;

@@ -22,7 +22,7 @@ PRECISIONS = {"fp64": 0, "mixed": 1}
 JACOBI_RULES = {"metric": 0, "relative": 1}
 EIGEN_STARTS = {"warm": 0, "cold": 1}
 CHAIN_NOTPD, CHAIN_NOTCONV, CHAIN_NONFINITE = 1, 2, 4
-PROF_NCAT = 8
+PROF_NCAT = 10
 
 
 class KernelDesc(ctypes.Structure):
@@ -105,6 +105,8 @@ def lib():
     L.rmhmc_profile_category.restype = c_char_p
     L.rmhmc_fp64_peak.argtypes = [c_void_p, c_int, POINTER(c_double)]
     L.rmhmc_fp64_peak.restype = c_int
+    L.rmhmc_fp32_peak.argtypes = [c_void_p, c_int, POINTER(c_double)]
+    L.rmhmc_fp32_peak.restype = c_int
     L.rmhmc_eigh_noalloc.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                      c_double, c_int, c_void_p, c_void_p]
     L.rmhmc_eigh_noalloc.restype = c_int
@@ -318,6 +320,15 @@ def fp64_peak_tflops(ms_target=200, stream=None):
     stream = stream or torch.cuda.current_stream()
     out = c_double()
     _check(lib().rmhmc_fp64_peak(c_void_p(stream.cuda_stream), int(ms_target), ctypes.byref(out)))
+    return out.value
+
+
+def fp32_peak_tflops(ms_target=200, stream=None):
+    """Measured FP32 FMA throughput of the current GPU (TFLOP/s)."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    out = c_double()
+    _check(lib().rmhmc_fp32_peak(c_void_p(stream.cuda_stream), int(ms_target), ctypes.byref(out)))
     return out.value
 
 
