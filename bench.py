@@ -31,10 +31,10 @@ sys.path.insert(0, ROOT)
 from paper_2511_06407_b300 import workloads as wl  # noqa: E402
 
 N_INPUTS, N_CHAINS, EPS, N_FP = 400, 64, 0.005, 6
-# DRAM bytes per k_jacobi launch per chain, from the ncu capture summarised in
-# profiles/k_jacobi_N400_8chains.md (8 chains: 22.27 MB read + 2.18 MB written on average per launch);
-# traffic grows with the number of chains, so a 64-chain launch is scaled by 64 / 8.
-JACOBI_DRAM_BYTES_PER_CHAIN = (22.27e6 + 0.5 * (2.40e6 + 1.95e6)) / 8
+# DRAM bytes per launch per chain of the Jacobi kernels, from the ncu captures summarised under
+# profiles/ (8 chains; traffic grows with the number of chains, so a 64-chain launch is scaled by
+# 64 / 8). Empty until the current kernels are captured.
+JACOBI_DRAM_BYTES_PER_CHAIN = {}
 SUBSTEPS_PER_LEAPFROG = 2 * N_FP + 1
 METRIC = "RMHMC leapfrog substeps/s"
 UNIT = "substeps/s"
@@ -228,11 +228,12 @@ def _roofline(rmhmc, prof, C):
     out = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
            "frac": achieved / peak if peak else None, "traffic": None, "peak_note": peak_note}
     if dom.startswith("jacobi"):
-        out["achieved_note"] = ("executed 16x16x16 rotation-tile products x 8192 flops; skipped identity tiles "
-                                "and the 16x16 inner solves not counted")
-    if dom == "jacobi_f64":
-        out["traffic"] = JACOBI_DRAM_BYTES_PER_CHAIN * C
-        out["traffic_note"] = "bytes per k_jacobi launch, ncu capture at 8 chains scaled to the chain count"
+        out["achieved_note"] = ("executed work: 16x16x16 rotation-tile products x 8192 flops (skipped identity "
+                                "tiles not counted) + inner rotation rounds x 1952 flops; rotation angles, "
+                                "stopping tests and conversions not counted")
+    if dom in JACOBI_DRAM_BYTES_PER_CHAIN:
+        out["traffic"] = JACOBI_DRAM_BYTES_PER_CHAIN[dom] * C
+        out["traffic_note"] = "bytes per launch, ncu capture at 8 chains scaled to the chain count"
     return out
 
 
@@ -497,6 +498,47 @@ def run_ess(args):
     return 0
 
 
+def run_solin(args):
+    """The primal (reduced-rank) model of the paper's own experiments (Sec. 2.5): simulated
+    logistic data, N = 500, D Gaussian kernels x M = 30 sinusoidal features (d = 30 D + 4), g =
+    sqrt(1 + lambda^2), eps = 0.001, n_fp = 6; both precisions, one after the other."""
+    import torch
+    from paper_2511_06407_b300 import build, rmhmc
+    build.build()
+    D = args.solin_d
+    prob = wl.solin_logistic(D, N=500, seed=0)
+    C = args.chains
+    out = {}
+    for prec in ("mixed", "fp64"):
+        model = rmhmc.Model(prob, C)
+        integ = rmhmc.Integrator(eps=args.eps or 0.001, n_fp=N_FP, n_leapfrog=1, g_kind="sqrt", alpha=1.0,
+                                 precision=prec)
+        model.set_state(torch.zeros(C, model.d, dtype=torch.float64, device="cuda"), integ=integ)
+        model.sample(1, 0, 5, integ=integ)
+        model.leapfrog(max(args.warmup - 1, 0), integ=integ)
+        st = torch.empty(C, dtype=torch.int32, device="cuda")
+        model.profile(True)
+        el, clk = _clock_and_time(lambda: model.leapfrog(args.steps, status_out=st, integ=integ), 0)
+        prof = model.profile_read()
+        out[prec] = {"value": C * SUBSTEPS_PER_LEAPFROG * args.steps / el,
+                     "leapfrogs_per_s_per_chain": args.steps / el, "ms_per_step": 1e3 * el / args.steps,
+                     "profile_ms": {k: round(v[0], 1) for k, v in prof.items() if v[2]},
+                     "roofline": _roofline(rmhmc, prof, C),
+                     "chain_status_nonzero": int((st.cpu().numpy() != 0).sum()), "clocks": clk}
+        d = model.d
+        model.close()
+    head = out[aux_precision(args)]
+    print(json.dumps({"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+                      "dtype": dtype_of(aux_precision(args)), "data": "synthetic",
+                      "config": {"workload": f"primal reduced-rank model (Sec. 2.5): simulated logistic data N=500, "
+                                             f"D={D} Gaussian kernels x 30 features (d={d}), {C} chains, "
+                                             f"g=sqrt(1+l^2), eps={args.eps or 0.001}", "d": d, "chains": C},
+                      "mixed": out["mixed"], "fp64": out["fp64"],
+                      "speedup_vs_fp64": out["mixed"]["value"] / out["fp64"]["value"]}), flush=True)
+    return 0
+
+
 def run_uneven(args):
     """Problems of uneven size (N ~ U{32..256}, 1-3 kernels, 8 chains each) advanced together by
     one CUDA graph per leapfrog, each with its autotuned Jacobi cluster size."""
@@ -582,7 +624,7 @@ def main():
     ap.add_argument("--chains", type=int, default=N_CHAINS,
                     help="chains per GPU (the workload is 64; smaller values are for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
-    ap.add_argument("--workload", default="gp400", choices=["gp400", "propensity", "uneven", "serve", "ess"],
+    ap.add_argument("--workload", default="gp400", choices=["gp400", "propensity", "uneven", "serve", "ess", "solin"],
                     help="gp400 is the benchmark; the others are extra measurements")
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"],
@@ -590,6 +632,7 @@ def main():
                          "on the same workload, with the trajectory error between them")
     ap.add_argument("--problems", type=int, default=16)
     ap.add_argument("--ess-n", type=int, default=100, help="inputs N of the ESS workload")
+    ap.add_argument("--solin-d", type=int, default=16, help="Gaussian kernels D of the solin workload (d = 30 D + 4)")
     ap.add_argument("--iters", type=int, default=200, help="kept iterations of the ESS workload")
     ap.add_argument("--burn", type=int, default=100, help="burn-in iterations of the ESS workload")
     ap.add_argument("--jobs", type=int, default=24)
@@ -604,6 +647,8 @@ def main():
         return run_uneven(args)
     if args.workload == "ess":
         return run_ess(args)
+    if args.workload == "solin":
+        return run_solin(args)
     if args.workload == "serve":
         return run_serve(args)
     return run_b300(args)

@@ -133,6 +133,40 @@ rmhmc_status rmhmc_init_model(const rmhmc_model_desc* desc, int n_chains, const 
  * in desc are not read (only the sizes and kinds). Errors: EINVAL. */
 rmhmc_status rmhmc_plan_bytes(const rmhmc_model_desc* desc, int n_chains, size_t* bytes);
 
+/* The primal (reduced-rank) model of the paper's experiments (Sec. 2.1 Eq. Solin_representation,
+ * the reduced-rank appendix, Sec. 2.5): every covariate column of Xg has a one-dimensional
+ * Gaussian kernel represented by M sinusoidal features phi_m(x) = sin(pi m (x + L) / (2L))
+ * (m = 1..M) with coefficients a_km ~ N(0, c_g V_m(s_g)), V_m(s) = sqrt(pi s)
+ * exp(-pi^2 m^2 s / (16 L^2)) (the spectral density of exp(-r^2/s) at pi m / (2L)); every column
+ * of Xl has a linear kernel, a_l ~ N(0, c_l); a bias b ~ N(0, bias_var); one shared (c_g, s_g) for
+ * the Gaussian kernels and one c_l for the linear ones, each ~ InvGamma(prior_a, prior_b) and
+ * sampled as u = log(theta). F_i = sum_km a_km phi_m(Xg_ik) + sum_l a_l Xl_il + b, and the
+ * likelihood is lik on (F_i, y_i) tempered by tau. Coordinates q = (a_km (k-major, m fastest),
+ * a_l, b, u_cg, u_sg, u_cl): d = M n_gauss + n_linear + 4 (= 30 D + 4 for Sec. 2.5).
+ * Host arrays are read during rmhmc_init_primal only. */
+typedef struct {
+  int N;                        /* number of samples, >= 1 */
+  int n_gauss;                  /* columns of Xg (Gaussian kernels), >= 0 */
+  int n_linear;                 /* columns of Xl (linear kernels), >= 0 */
+  const double* Xg;             /* host, N x n_gauss (NULL if n_gauss == 0) */
+  const double* Xl;             /* host, N x n_linear (NULL if n_linear == 0) */
+  const double* y;              /* host, N (0/1 for Bernoulli) */
+  int lik;                      /* rmhmc_lik */
+  double noise_var;             /* Gaussian likelihood variance */
+  int M;                        /* features per Gaussian kernel, >= 1 */
+  double L;                     /* half-width of the feature domain [-L, L], > 0 */
+  double bias_var;              /* Sigma, the prior variance of b, > 0 */
+  double prior_a[3];            /* InvGamma shapes for (c_g, s_g, c_l) */
+  double prior_b[3];            /* InvGamma scales for (c_g, s_g, c_l) */
+} rmhmc_primal_desc;
+
+/* As rmhmc_init_model, for the primal model; the returned model works with every other call of
+ * this header. Errors: EINVAL (bad sizes, d > 4096, N > 2^20), ENOMEM, ECUDA. */
+rmhmc_status rmhmc_init_primal(const rmhmc_primal_desc* desc, int n_chains, const double* tau_host,
+                               void* cuda_stream, rmhmc_model** out);
+/* As rmhmc_plan_bytes, for the primal model. */
+rmhmc_status rmhmc_plan_bytes_primal(const rmhmc_primal_desc* desc, int n_chains, size_t* bytes);
+
 /* Set every chain's position (q_dev: n_chains x d) and momentum (p_dev: n_chains x d, may be
  * NULL = zero) and evaluate the geometry there: U, its gradient, Hessian (Eq. d_Hamiltonian
  * derivatives), a cold-start Jacobi eigendecomposition from Psi = I (Sec. 2.4), and the
@@ -205,7 +239,8 @@ rmhmc_status rmhmc_autotune(rmhmc_model* m, int* cluster_out);
  * RMHMC_PROF_NCAT categories (names from rmhmc_profile_category), with the algorithmic FLOPs of
  * the work it must do (GEMM 2mnk on the unpadded sizes, halved for symmetric outputs; Cholesky
  * and triangular inverse N^3/3; Jacobi 2 * 16^3 per 16 x 16 x 16 rotation-tile product executed,
- * tiles skipped because both rotations were the identity not counted). rmhmc_profile(m, 1)
+ * tiles skipped because both rotations were the identity not counted, plus 1952 per round of 8
+ * rotations applied inside a 16 x 16 sub-problem). rmhmc_profile(m, 1)
  * resets and starts, rmhmc_profile(m, 0) stops. rmhmc_profile_read synchronises the stream and
  * writes per-category milliseconds, FLOPs and launch counts (host arrays of RMHMC_PROF_NCAT). */
 #define RMHMC_PROF_NCAT 10

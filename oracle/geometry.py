@@ -14,12 +14,32 @@ metric terms with swapped signs; differentiating Eq. Hamiltonian gives):
 with dH_i = d/dq_i of the Hessian taken from the full third-derivative tensor.
 dH/dp = G^-1 p. Momentum refresh p ~ N(0, G): p = Psi diag(sqrt g) Psi^T z (the symmetric root).
 """
+from contextlib import contextmanager
+
 import numpy as np
+import scipy.linalg as sla
 
 from . import model as mdl
+from . import primal
 from .softabs import G_COTH, divided_differences, g_and_gprime
 
 LOG2PI = np.log(2.0 * np.pi)
+
+_EIG = {"driver": "evd"}
+
+
+@contextmanager
+def eigen_driver(name):
+    """Take the eigendecomposition of H with LAPACK's divide and conquer ('evd', numpy's eigh, the
+    default) or its QR iteration ('ev'). Both are backward stable; their difference measures how
+    far rounding inside any eigensolver moves the basis-free results (used to calibrate parity
+    tolerances, as inverse_method does for K^-1)."""
+    old = _EIG["driver"]
+    _EIG["driver"] = name
+    try:
+        yield
+    finally:
+        _EIG["driver"] = old
 
 
 class Geometry:
@@ -32,13 +52,17 @@ class Geometry:
         self.tau = tau
         self.alpha = alpha
         self.gkind = gkind
-        self.U = mdl.potential(model, q, tau)
-        self.dU = mdl.gradient(model, q, tau)
-        self.H = mdl.hessian(model, q, tau)
-        self.lam, self.Psi = np.linalg.eigh(self.H)
+        ops = primal if isinstance(model, primal.PrimalModel) else mdl  # primal or dual GP model
+        self.U = ops.potential(model, q, tau)
+        self.dU = ops.gradient(model, q, tau)
+        self.H = ops.hessian(model, q, tau)
+        if _EIG["driver"] == "evd":
+            self.lam, self.Psi = np.linalg.eigh(self.H)
+        else:
+            self.lam, self.Psi = sla.eigh(self.H, driver=_EIG["driver"], check_finite=False)
         self.g, self.gp = g_and_gprime(self.lam, alpha, gkind)
         self.T = divided_differences(self.lam, alpha, gkind)
-        self.third = mdl.ThirdDerivatives(model, q, tau).tensor() if with_third else None
+        self.third = ops.ThirdDerivatives(model, q, tau).tensor() if with_third else None
 
     # --- metric --------------------------------------------------------------------------
     def G(self):

@@ -57,19 +57,50 @@ __device__ __forceinline__ void circle_pair(int r, int p, int nb, int& I, int& J
 
 __device__ __forceinline__ int gidx(int I, int J, int t) { return t < BL ? I * BL + t : J * BL + (t - BL); }
 
-// Symmetric Schur rotation zeroing A_ab: returns (c, s) with J = [[c, s], [-s, c]] on (a, b).
-__device__ __forceinline__ void schur2(double app, double aqq, double apq, double& c, double& s) {
+// Symmetric Schur rotation zeroing A_ab: (c, s, t = s / c) with J = [[c, s], [-s, c]] on (a, b).
+// The tangent t is the root of smaller magnitude of A_ab t^2 + (A_bb - A_aa) t - A_ab = 0
+// (t = sign(theta) / (|theta| + sqrt(1 + theta^2)), theta = (A_bb - A_aa) / (2 A_ab)). B300's FP64
+// division and square root cost tens of FP64-pipe slots each, so t is first taken in FP32 and then
+// refined by one Newton step on that quadratic in FP64 (the FP32 reciprocal of the derivative is
+// enough for a step of relative size 1e-7): the result is accurate to ~1e-14, so setting the
+// rotated pair to zero commits an error of ~1e-14 |A_ab|. c = (1 + t^2)^-1/2 comes from the FP32
+// reciprocal square root refined by two FP64 Newton steps, s = t c, so the rotation is orthogonal
+// to FP64 rounding. Where theta is out of FP32 range the FP64 formulas are used.
+__device__ __forceinline__ void schur2(double app, double aqq, double apq, double& c, double& s,
+                                       double& t) {
   if (fabs(apq) < 1e-300) {
     c = 1.0;
     s = 0.0;
+    t = 0.0;
     return;
   }
-  const double theta = (aqq - app) / (2.0 * apq);
-  double t;
-  if (fabs(theta) > 1e150) t = 0.5 / theta;
-  else t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
-  c = 1.0 / sqrt(1.0 + t * t);
-  s = t * c;
+  const double num = aqq - app, den = 2.0 * apq;
+  const double an = fabs(num), ad = fabs(den);
+  t = 0.0;
+  bool fast = ad > 1e-30 && ad < 1e30 && an < 1e30;
+  if (fast) {
+    const float th = __fdividef((float)num, (float)den);
+    const float ath = fabsf(th);
+    const float tf = ath > 1e15f ? 0.5f / th : copysignf(1.0f, th) / (ath + sqrtf(fmaf(th, th, 1.0f)));
+    fast = tf != 0.0f && isfinite(tf);
+    if (fast) {
+      t = (double)tf;
+      const double f = fma(fma(apq, t, num), t, -apq);   // A_ab t^2 + (A_bb - A_aa) t - A_ab
+      const double fp = fma(2.0 * apq, t, num);          // its derivative
+      t -= f * (double)__frcp_rn((float)fp);
+    }
+  }
+  if (!fast) {
+    const double theta = num / den;
+    if (fabs(theta) > 1e150) t = 0.5 / theta;
+    else t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
+  }
+  const double x = fma(t, t, 1.0);
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  c = y;
+  s = t * y;
 }
 
 // Inner exact solve of one 16 x 16 sub-problem by a single warp: A <- V^T A V diagonal. Returns
@@ -86,8 +117,23 @@ __device__ __forceinline__ bool pair_unconverged(double v, double djj, double dl
   return v2 > tol2 * p;
 }
 
+// Floor for a coupling between diagonal entries x and y: 1e-13 max(|x|, |y|) (about 450 units of
+// FP64 rounding of the larger entry), never above the caller's floor2. A coupling below it moves
+// G^-1 by at most ~1e-13 / min(|x|, |y|) relative.
+__device__ __forceinline__ double local_floor2(double x, double y, double floor2) {
+  return fmin(floor2, fmax(1e-26 * fmax(x * x, y * y), 1e-300));
+}
+
+// The floor of the stopping tests: the caller's floor ~4u ||M||_F under METRIC (the sampler's
+// rule: a residual coupling's effect on G^-1 is what matters, and the floor keeps the sweep count
+// low); the pair-local floor under RELATIVE, whose purpose is every eigenpair resolved, the small
+// ones included.
+__device__ __forceinline__ double stop_floor2(double x, double y, double floor2, int rule) {
+  return rule == RMHMC_JACOBI_RELATIVE ? local_floor2(x, y, floor2) : floor2;
+}
+
 __device__ bool inner_solve(double* A, double* V, double* cs, double tol2, double floor2, int rule,
-                            double dmin2) {
+                            double dmin2, unsigned int& nround) {
   const int lane = threadIdx.x & 31;
   bool rotated = false;
   for (int e = lane; e < SB * SB; e += 32) V[(e / SB) * SBP + e % SB] = (e / SB == e % SB) ? 1.0 : 0.0;
@@ -97,54 +143,83 @@ __device__ bool inner_solve(double* A, double* V, double* cs, double tol2, doubl
     for (int e = lane; e < SB * SB; e += 32) {
       const int i = e / SB, j = e % SB;
       const double v = A[i * SBP + j];
-      if (i != j && v != 0.0)
-        unconv |= pair_unconverged(v, A[i * SBP + i], A[j * SBP + j], tol2, floor2, rule, dmin2) ||
+      if (i != j && v != 0.0) {
+        const double aii = A[i * SBP + i], ajj = A[j * SBP + j];
+        unconv |= pair_unconverged(v, aii, ajj, tol2, stop_floor2(aii, ajj, floor2, rule), rule, dmin2) ||
                   !isfinite(v);
+      }
     }
     if (!__any_sync(0xffffffffu, unconv)) break;
     rotated = true;
     for (int r = 0; r < SB - 1; ++r) {
+      // the pairs of this round above the tolerance are rotated, the others left alone; a round
+      // with none to rotate is skipped (warp-uniform). Within a sweep that runs, a pair is rotated
+      // unless it is at the tolerance or at the level of its own diagonal entries (local_floor2),
+      // so the small eigenpairs that dominate G^-1 are resolved to their relative accuracy, not to
+      // the caller's floor ~4u ||M||_F (which decides only whether another sweep runs)
+      bool need = false;
       if (lane < SB / 2) {
         int a, b;
         circle_pair(r, lane, SB, a, b);
-        double c, s;
-        schur2(A[a * SBP + a], A[b * SBP + b], A[a * SBP + b], c, s);
-        cs[2 * lane] = c;
-        cs[2 * lane + 1] = s;
+        const double app = A[a * SBP + a], aqq = A[b * SBP + b], apq = A[a * SBP + b];
+        need = !isfinite(apq) || pair_unconverged(apq, app, aqq, tol2, local_floor2(app, aqq, floor2), rule, dmin2);
+        double c = 1.0, sn = 0.0, t = 0.0;
+        if (need) schur2(app, aqq, apq, c, sn, t);
+        cs[3 * lane] = c;
+        cs[3 * lane + 1] = sn;
+        cs[3 * lane + 2] = t;
       }
+      if (!__any_sync(0xffffffffu, need)) continue;
+      ++nround;
       __syncwarp();
-      // rows: A <- J^T A
+      // A <- J^T A J by 2 x 2 blocks, each written once with its mirror: lane l < 28 owns the
+      // off-diagonal block of pairs (P, Q), P < Q; lanes 28..31 own two diagonal blocks each, whose
+      // update is A_aa - t A_ab, A_bb + t A_ab and a zero coupling (the Schur rotation's identities)
+      if (lane < 28) {
+        int P = 0, rem = lane;
+        while (rem >= SB / 2 - 1 - P) {
+          rem -= SB / 2 - 1 - P;
+          ++P;
+        }
+        const int Q = P + 1 + rem;
+        int a, b, e, f;
+        circle_pair(r, P, SB, a, b);
+        circle_pair(r, Q, SB, e, f);
+        const double cp = cs[3 * P], sp = cs[3 * P + 1], cq = cs[3 * Q], sq = cs[3 * Q + 1];
+        const double x00 = A[a * SBP + e], x01 = A[a * SBP + f], x10 = A[b * SBP + e], x11 = A[b * SBP + f];
+        const double y00 = cp * x00 - sp * x10, y01 = cp * x01 - sp * x11;
+        const double y10 = sp * x00 + cp * x10, y11 = sp * x01 + cp * x11;
+        const double z00 = cq * y00 - sq * y01, z01 = sq * y00 + cq * y01;
+        const double z10 = cq * y10 - sq * y11, z11 = sq * y10 + cq * y11;
+        A[a * SBP + e] = z00;
+        A[e * SBP + a] = z00;
+        A[a * SBP + f] = z01;
+        A[f * SBP + a] = z01;
+        A[b * SBP + e] = z10;
+        A[e * SBP + b] = z10;
+        A[b * SBP + f] = z11;
+        A[f * SBP + b] = z11;
+      } else {
+        for (int P = 2 * (lane - 28); P < 2 * (lane - 28) + 2; ++P) {
+          if (cs[3 * P + 1] == 0.0) continue;
+          int a, b;
+          circle_pair(r, P, SB, a, b);
+          const double t = cs[3 * P + 2], apq = A[a * SBP + b];
+          A[a * SBP + a] -= t * apq;
+          A[b * SBP + b] += t * apq;
+          A[a * SBP + b] = 0.0;
+          A[b * SBP + a] = 0.0;
+        }
+      }
+      // V <- V J
       for (int task = lane; task < (SB / 2) * SB; task += 32) {
         const int pr = task / SB, u = task % SB;
         int a, b;
         circle_pair(r, pr, SB, a, b);
-        const double c = cs[2 * pr], s = cs[2 * pr + 1];
-        const double xa = A[a * SBP + u], xb = A[b * SBP + u];
-        A[a * SBP + u] = c * xa - s * xb;
-        A[b * SBP + u] = s * xa + c * xb;
-      }
-      __syncwarp();
-      // columns: A <- A J, and V <- V J
-      for (int task = lane; task < (SB / 2) * SB; task += 32) {
-        const int pr = task / SB, t = task % SB;
-        int a, b;
-        circle_pair(r, pr, SB, a, b);
-        const double c = cs[2 * pr], s = cs[2 * pr + 1];
-        const double xa = A[t * SBP + a], xb = A[t * SBP + b];
-        A[t * SBP + a] = c * xa - s * xb;
-        A[t * SBP + b] = s * xa + c * xb;
-        const double va = V[t * SBP + a], vb = V[t * SBP + b];
-        V[t * SBP + a] = c * va - s * vb;
-        V[t * SBP + b] = s * va + c * vb;
-      }
-      __syncwarp();
-      if (lane < SB / 2) {
-        int a, b;
-        circle_pair(r, lane, SB, a, b);
-        if (cs[2 * lane + 1] != 0.0) {
-          A[a * SBP + b] = 0.0;
-          A[b * SBP + a] = 0.0;
-        }
+        const double c = cs[3 * pr], s = cs[3 * pr + 1];
+        const double va = V[u * SBP + a], vb = V[u * SBP + b];
+        V[u * SBP + a] = c * va - s * vb;
+        V[u * SBP + b] = s * va + c * vb;
       }
       __syncwarp();
     }
@@ -232,13 +307,14 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
   double* Va = ws + 2 * SB * SBP;
   double* Vq = ws + 3 * SB * SBP;
   __shared__ double red[2][NW];
-  __shared__ double cs[NW][SB];
+  __shared__ double cs[NW][3 * SB / 2];  // (c, s, t) of the 8 rotations of a round, per warp
 
   const int gw = rank * NW + warp, nwt = C * NW;
   const int nMjobs = np * (np + 1) / 2, nct = dp / SB;
   int sweeps = 0;
   bool converged = false;
-  unsigned int ntile = 0;  // 16 x 16 x 16 tile products this warp executed
+  unsigned int ntile = 0;   // 16 x 16 x 16 tile products this warp executed (phase 2)
+  unsigned int nround = 0;  // rounds of 8 rotations this warp applied to a 16 x 16 block (phase 1)
   for (;;) {
     // ---- convergence test. Pass 1: ||M||_F^2 and min_i<d |m_ii|. Pass 2: the worst pair ratio
     //      (pair_ratio) under the chosen rule, with floor = 4 u ||M||_F (rounding level).
@@ -280,8 +356,8 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
       const double v = __ldcg(M + e);
       if (v == 0.0) continue;
       if (!isfinite(v)) bad = 1.0;
-      if (pair_unconverged(v, __ldcg(M + (long long)j * dp + j), __ldcg(M + (long long)l * dp + l),
-                           tol * tol, floor2, rule, dmin2))
+      const double djj = __ldcg(M + (long long)j * dp + j), dll = __ldcg(M + (long long)l * dp + l);
+      if (pair_unconverged(v, djj, dll, tol * tol, stop_floor2(djj, dll, floor2, rule), rule, dmin2))
         crit = 1.0;
     }
 #pragma unroll
@@ -320,7 +396,7 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
           X[a * SBP + b] = __ldcg(M + (long long)gidx(I, J, a) * dp + gidx(I, J, b));
         }
         __syncwarp();
-        const bool rot = inner_solve(X, Va, cs[warp], itol2, floor2, rule, dmin2);
+        const bool rot = inner_solve(X, Va, cs[warp], itol2, floor2, rule, dmin2, nround);
         if (rot) {
           for (int e = lane; e < SB * SB; e += 32) {
             const int a = e / SB, b = e % SB;
@@ -396,7 +472,10 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
   }
   for (int i = rank * blockDim.x + tid; i < dp; i += C * blockDim.x)
     lamb[(long long)chain * dp + i] = __ldcg(M + (long long)i * dp + i);
-  if (tiles && lane == 0 && ntile) atomicAdd(tiles + chain, (unsigned long long)ntile);
+  if (tiles && lane == 0) {
+    if (ntile) atomicAdd(tiles + 2 * chain, (unsigned long long)ntile);
+    if (nround) atomicAdd(tiles + 2 * chain + 1, (unsigned long long)nround);
+  }
   if (rank == 0 && tid == 0) {
     sweeps_out[chain] = sweeps;
     if (sweeps_acc) sweeps_acc[chain] += sweeps;
@@ -501,7 +580,7 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
   float2* Va = (float2*)(ws + 2 * SB * SBP);
   float2* Vq = (float2*)(ws + 3 * SB * SBP);
   __shared__ double red[2][NW];
-  __shared__ double cs[NW][SB];
+  __shared__ double cs[NW][3 * SB / 2];  // (c, s, t) of the 8 rotations of a round, per warp
 
   for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
     __stcg(Mw + e, df_split(__ldcg(M + e)));
@@ -513,7 +592,8 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
   const int nMjobs = np * (np + 1) / 2, nct = dp / SB;
   int sweeps = 0;
   bool converged = false;
-  unsigned int ntile = 0;  // 16 x 16 x 16 tile products this warp executed
+  unsigned int ntile = 0;   // 16 x 16 x 16 tile products this warp executed (phase 2)
+  unsigned int nround = 0;  // rounds of 8 rotations this warp applied to a 16 x 16 block (phase 1)
   for (;;) {
     double tot = 0.0, dmin = 1e308;
     for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
@@ -551,8 +631,8 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
       const double v = df_join(ldcg2(Mw + e));
       if (v == 0.0) continue;
       if (!isfinite(v)) bad = 1.0;
-      if (pair_unconverged(v, df_join(ldcg2(Mw + (long long)j * dp + j)),
-                           df_join(ldcg2(Mw + (long long)l * dp + l)), tol * tol, floor2, rule, dmin2))
+      const double djj = df_join(ldcg2(Mw + (long long)j * dp + j)), dll = df_join(ldcg2(Mw + (long long)l * dp + l));
+      if (pair_unconverged(v, djj, dll, tol * tol, stop_floor2(djj, dll, floor2, rule), rule, dmin2))
         crit = 1.0;
     }
 #pragma unroll
@@ -591,7 +671,7 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
           Xd[a * SBP + b] = df_join(ldcg2(Mw + (long long)gidx(I, J, a) * dp + gidx(I, J, b)));
         }
         __syncwarp();
-        const bool rot = inner_solve(Xd, Vd, cs[warp], itol2, floor2, rule, dmin2);
+        const bool rot = inner_solve(Xd, Vd, cs[warp], itol2, floor2, rule, dmin2, nround);
         if (rot) {
           for (int e = lane; e < SB * SB; e += 32) {
             const int a = e / SB, b = e % SB;
@@ -671,7 +751,10 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
   }
   for (int i = rank * blockDim.x + tid; i < dp; i += C * blockDim.x)
     lamb[(long long)chain * dp + i] = df_join(ldcg2(Mw + (long long)i * dp + i));
-  if (tiles && lane == 0 && ntile) atomicAdd(tiles + chain, (unsigned long long)ntile);
+  if (tiles && lane == 0) {
+    if (ntile) atomicAdd(tiles + 2 * chain, (unsigned long long)ntile);
+    if (nround) atomicAdd(tiles + 2 * chain + 1, (unsigned long long)nround);
+  }
   if (rank == 0 && tid == 0) {
     sweeps_out[chain] = sweeps;
     if (sweeps_acc) sweeps_acc[chain] += sweeps;

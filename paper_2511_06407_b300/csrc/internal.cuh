@@ -51,6 +51,19 @@ struct ModelDev {
   KernelDev k[RMHMC_MAX_KERNELS];
 };
 
+// The primal (reduced-rank) model: M sinusoidal features per Gaussian-kernel column of Xg, one
+// coefficient per linear-kernel column of Xl, a bias; P = M Dg + Dl + 1 coefficients, then
+// (u_cg, u_sg, u_cl); d = P + 3.
+struct PrimalDev {
+  int N, Dg, Dl, M, P, d, dp, lik, n_chains;
+  double noise_var, L, bias_var;
+  double a[3], b[3];
+  const double* Xg;   // N x Dg
+  const double* Xl;   // N x Dl
+  const double* y;    // N
+  const double* tau;  // n_chains
+};
+
 struct GeomDev {
   int g_kind;
   double alpha;
@@ -91,7 +104,8 @@ struct JacobiWork {
   double* D;      // n_chains x (nb/2) x 256
   double* slots;  // n_chains x 64
   int* flags;     // n_chains x (nb/2): pair rotated in the current round
-  unsigned long long* tiles;  // n_chains: += 16 x 16 x 16 tile products executed (null = not counted)
+  unsigned long long* tiles;  // n_chains x 2: += 16 x 16 x 16 tile products executed (phase 2) and
+                              // rotation rounds applied to 16 x 16 blocks (phase 1); null = not counted
 };
 void jacobi_f64(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,
                 int rule, double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,

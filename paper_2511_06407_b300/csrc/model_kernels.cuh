@@ -71,6 +71,24 @@ __global__ void k_assemble(ModelDev md, const double* __restrict__ q, int dp, do
 
 // Latent blocks f_k packed contiguously per (chain, kernel), and tau-scaled likelihood maps of
 // F = sum_k f_k (Sec. 2.5 logistic / Gaussian): l, l', l'', l''' per (chain, sample).
+// Negative log likelihood l of one sample and its first three derivatives in F (untempered):
+// Bernoulli-logit (y in {0,1}): l = softplus(F) - y F; Gaussian: l = (y - F)^2 / (2v) + log(2 pi v)/2.
+__device__ __forceinline__ void lik_point(int lik, double y, double F, double v, double& a0, double& a1,
+                                          double& a2, double& a3) {
+  if (lik == RMHMC_LIK_BERNOULLI_LOGIT) {
+    const double s = 1.0 / (1.0 + exp(-F));
+    a0 = fmax(F, 0.0) + log1p(exp(-fabs(F))) - y * F;
+    a1 = s - y;
+    a2 = s * (1.0 - s);
+    a3 = a2 * (1.0 - 2.0 * s);
+  } else {
+    a0 = (y - F) * (y - F) / (2.0 * v) + 0.5 * log(2.0 * M_PI * v);
+    a1 = (F - y) / v;
+    a2 = 1.0 / v;
+    a3 = 0.0;
+  }
+}
+
 __global__ void k_lik(ModelDev md, const double* __restrict__ q, int dp, double* __restrict__ fpk,
                       double* __restrict__ l0, double* __restrict__ l1, double* __restrict__ l2,
                       double* __restrict__ l3, double* __restrict__ lraw) {
@@ -84,21 +102,9 @@ __global__ void k_lik(ModelDev md, const double* __restrict__ q, int dp, double*
     fpk[((long long)c * md.n + k) * N + m] = f;
     F += f;
   }
-  const double tau = md.tau[c], y = md.y[m];
+  const double tau = md.tau[c];
   double a0, a1, a2, a3;
-  if (md.lik == RMHMC_LIK_BERNOULLI_LOGIT) {
-    const double s = 1.0 / (1.0 + exp(-F));
-    a0 = fmax(F, 0.0) + log1p(exp(-fabs(F))) - y * F;
-    a1 = s - y;
-    a2 = s * (1.0 - s);
-    a3 = a2 * (1.0 - 2.0 * s);
-  } else {
-    const double v = md.noise_var;
-    a0 = (y - F) * (y - F) / (2.0 * v) + 0.5 * log(2.0 * M_PI * v);
-    a1 = (F - y) / v;
-    a2 = 1.0 / v;
-    a3 = 0.0;
-  }
+  lik_point(md.lik, md.y[m], F, md.noise_var, a0, a1, a2, a3);
   const long long o = (long long)c * N + m;
   lraw[o] = a0;
   l0[o] = tau * a0;
@@ -145,7 +151,6 @@ __global__ void __launch_bounds__(256) k_stats(ModelDev md, const double* __rest
   const double* D1 = D1b + mo;
   const double* S = Sb + mo;
   const double* al = alphab + vo;
-  const double* f = fpk + vo;
   double* beta = betab + vo;
   double* gam = gammab + vo;
   double* eps2 = eps2b + vo;

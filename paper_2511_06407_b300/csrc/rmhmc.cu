@@ -14,6 +14,7 @@
 
 #include "internal.cuh"
 #include "model_kernels.cuh"
+#include "primal.cuh"
 
 using namespace rmhmc;
 
@@ -364,6 +365,15 @@ struct rmhmc_model {
   long long prof_launch[RMHMC_PROF_NCAT] = {};
   size_t* plan_bytes = nullptr;  // set only while planning (rmhmc_plan_bytes)
   double *X_dev = nullptr, *y_dev = nullptr, *uf_dev = nullptr, *tau_dev = nullptr;
+  // the primal (reduced-rank) model: kind == 1
+  int kind = 0;
+  PrimalDev pd{};
+  double *Phi = nullptr;   // N x P features (shared by the chains)
+  double *Z = nullptr;     // C x N x P: diag(l'') Phi, then Phi W[:P, :P]
+  double *Fv = nullptr;    // C x N latent values F = Phi w
+  double *rvec = nullptr;  // C x N: l''' o rowsum((Phi W) o Phi)
+  double *ustat = nullptr; // C x 9: hyperparameter block of the Hessian
+  double *Xg_dev = nullptr, *Xl_dev = nullptr;
 };
 
 namespace {
@@ -428,14 +438,14 @@ rmhmc_status check_launch() {
   return cudaGetLastError() == cudaSuccess ? RMHMC_OK : RMHMC_ECUDA;
 }
 
-// --- geometry at the current q: U, dU, Hessian, warm-started eigendecomposition, g(lambda);
-//     with `third`, also the third-derivative operator (A1, S^2 and the F-phase statistics).
-void eval_geometry(rmhmc_model* m, bool third) {
+// The dual model layer: kernel matrices, Cholesky, K^-1 algebra, likelihood maps, U, dU and the
+// Hessian; with `third`, also the third-derivative operator (A1, S^2 and the F-phase statistics).
+void dual_model_layer(rmhmc_model* m, bool third) {
   cudaStream_t s = m->stream;
-  const int N = m->N, n = m->n, C = m->C, dp = m->dp, d = m->d;
+  const int N = m->N, n = m->n, C = m->C, dp = m->dp;
   const long long NN = (long long)N * N;
   const int B = C * n;
-  const double Nf = N, df = d, Bf = B, Cf = C;
+  const double Nf = N, Bf = B;
   PROF(m, CAT_MODEL, 0)
   dev::k_assemble<<<dim3(nblk(NN), n, C), 256, 0, s>>>(m->md, m->q, dp, m->KL, m->D1);
   PROF(m, CAT_MODEL, 0)
@@ -474,6 +484,40 @@ void eval_geometry(rmhmc_model* m, bool third) {
   PROF(m, CAT_MODEL, 0)
   dev::k_hessian<<<dim3(nblk(DD), C), 256, 0, s>>>(m->md, m->q, dp, m->Kinv, m->l2, m->alpha_,
                                                    m->gamma, m->stats, m->H);
+}
+
+// The primal model layer: F = Phi w, likelihood maps, U and dU (Phi^T l' + prior), the Hessian
+// (Phi^T diag(l'') Phi + prior). The third-derivative operator needs only l''' (kept in l3).
+void primal_model_layer(rmhmc_model* m) {
+  cudaStream_t s = m->stream;
+  const int N = m->N, C = m->C, dp = m->dp, P = m->pd.P;
+  const long long NP = (long long)N * P, DD = (long long)dp * dp;
+  const double Nf = N, Pf = P, Cf = C;
+  PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf)
+  gemm_f64(s, false, true, C, N, P, 1.0, m->q, dp, 0, m->Phi, P, 0, 0.0, m->Fv, N, 0, 1, false, false);
+  PROF(m, CAT_MODEL, 0)
+  dev::k_lik_primal<<<dim3(nblk(N), C), 256, 0, s>>>(m->pd, m->Fv, m->l0, m->l1, m->l2, m->l3, m->lraw);
+  PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf)
+  gemm_f64(s, false, false, C, P, N, 1.0, m->l1, N, 0, m->Phi, P, 0, 0.0, m->dU, dp, 0, 1, false, false);
+  PROF(m, CAT_MODEL, 0)
+  dev::k_primal_udu<<<C, 256, 0, s>>>(m->pd, m->q, dp, m->l0, m->lraw, m->U, m->dU, m->LL, m->ustat);
+  PROF(m, CAT_MODEL, 0)
+  dev::k_rowscale<<<dim3(nblk(NP), C), 256, 0, s>>>(m->pd, m->l2, m->Phi, m->Z);
+  PROF(m, CAT_GEMM, Cf * gemm_flops(Pf, Pf, Nf, true, false))
+  gemm_f64(s, true, false, P, P, N, 1.0, m->Phi, P, 0, m->Z, P, NP, 0.0, m->H, dp, DD, C, true, false);
+  PROF(m, CAT_MODEL, 0)
+  dev::k_primal_hess<<<dim3(nblk(DD), C), 256, 0, s>>>(m->pd, m->q, dp, m->ustat, m->H);
+}
+
+// --- geometry at the current q: U, dU, Hessian, warm-started eigendecomposition, g(lambda);
+//     with `third`, also the third-derivative operator (the dual model's A1, S^2 and F-phase
+//     statistics; the primal model needs no more than l''').
+void eval_geometry(rmhmc_model* m, bool third) {
+  cudaStream_t s = m->stream;
+  const int C = m->C, dp = m->dp, d = m->d;
+  const long long DD = (long long)dp * dp;
+  if (m->kind == 1) primal_model_layer(m);
+  else dual_model_layer(m, third);
   // Sec. 2.4: Gram-Schmidt of Psi every reorth_every eigen-updates, then M = Psi^T H Psi
   // (the static ablation restarts every eigen-update from Psi = I instead)
   if (m->eigen_start == 1) {
@@ -541,10 +585,25 @@ void grad_h(rmhmc_model* m, const double* x, double* out) {
   // W = Psi C Psi^T = PsiT^T (C PsiT)
   gemm_dd(m, false, false, m->M, m->PsiT, m->Y, false);
   gemm_dd(m, true, false, m->PsiT, m->Y, m->W, true);
-  PROF(m, CAT_CONTRACT, 0)
-  dev::k_contract<<<C * n, 256, 2 * N * sizeof(double), s>>>(m->md, m->q, dp, m->W, m->Kinv, m->Aux,
-                                                             m->l3, m->alpha_, m->gamma, m->fuu11,
-                                                             m->stats, m->vtr);
+  if (m->kind == 1) {
+    // Sec. 2.3 ordering: v = Phi^T [l''' o rowsum((Phi W) o Phi)] + the prior parts
+    const int P = m->pd.P;
+    const long long NP = (long long)N * P;
+    const double Nf = N, Pf = P;
+    PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf * Pf)
+    gemm_f64(s, false, false, N, P, P, 1.0, m->Phi, P, 0, m->W, dp, DD, 0.0, m->Z, P, NP, C, false, false);
+    PROF(m, CAT_CONTRACT, 2.0 * Cf * Nf * Pf)
+    dev::k_primal_rowdot<<<dim3((N + 7) / 8, C), 256, 0, s>>>(m->pd, m->Z, m->Phi, m->l3, m->rvec);
+    PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf)
+    gemm_f64(s, false, false, C, P, N, 1.0, m->rvec, N, 0, m->Phi, P, 0, 0.0, m->vtr, dp, 0, 1, false, false);
+    PROF(m, CAT_CONTRACT, 0)
+    dev::k_primal_contract<<<C, 256, 0, s>>>(m->pd, m->q, dp, m->W, m->vtr);
+  } else {
+    PROF(m, CAT_CONTRACT, 0)
+    dev::k_contract<<<C * n, 256, 2 * N * sizeof(double), s>>>(m->md, m->q, dp, m->W, m->Kinv, m->Aux,
+                                                               m->l3, m->alpha_, m->gamma, m->fuu11,
+                                                               m->stats, m->vtr);
+  }
   PROF(m, CAT_VECTOR, 0)
   k_axpy<<<nblk((long long)C * dp), 256, 0, s>>>(out, m->dU, m->vtr, 0.5, (long long)C * dp);
 }
@@ -593,25 +652,36 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
   rmhmc_status st = RMHMC_OK;
 #define ALLOC(ptr, cnt) \
   if (st == RMHMC_OK) st = dalloc(m, &(ptr), (cnt))
-  ALLOC(m->X_dev, (size_t)N * n_cov);
   ALLOC(m->y_dev, (size_t)N);
-  ALLOC(m->uf_dev, (size_t)2 * n);
   ALLOC(m->tau_dev, (size_t)C);
-  ALLOC(m->KL, B * NN);
-  ALLOC(m->D1, B * NN);
-  ALLOC(m->Kinv, B * NN);
-  ALLOC(m->S, B * NN);
-  ALLOC(m->Aux, B * NN);
-  ALLOC(m->S2, B * NN);
-  ALLOC(m->fpk, B * N);
-  ALLOC(m->alpha_, B * N);
-  ALLOC(m->beta, B * N);
-  ALLOC(m->gamma, B * N);
-  ALLOC(m->eps2, B * N);
-  ALLOC(m->eps3, B * N);
-  ALLOC(m->delta, B * N);
-  ALLOC(m->fuu11, B * N);
-  ALLOC(m->stats, B * kStatSlots);
+  if (m->kind == 1) {
+    const size_t P = (size_t)m->pd.P;
+    if (m->pd.Dg) ALLOC(m->Xg_dev, (size_t)N * m->pd.Dg);
+    if (m->pd.Dl) ALLOC(m->Xl_dev, (size_t)N * m->pd.Dl);
+    ALLOC(m->Phi, (size_t)N * P);
+    ALLOC(m->Z, (size_t)C * N * P);
+    ALLOC(m->Fv, (size_t)C * N);
+    ALLOC(m->rvec, (size_t)C * N);
+    ALLOC(m->ustat, (size_t)C * 9);
+  } else {
+    ALLOC(m->X_dev, (size_t)N * n_cov);
+    ALLOC(m->uf_dev, (size_t)2 * n);
+    ALLOC(m->KL, B * NN);
+    ALLOC(m->D1, B * NN);
+    ALLOC(m->Kinv, B * NN);
+    ALLOC(m->S, B * NN);
+    ALLOC(m->Aux, B * NN);
+    ALLOC(m->S2, B * NN);
+    ALLOC(m->fpk, B * N);
+    ALLOC(m->alpha_, B * N);
+    ALLOC(m->beta, B * N);
+    ALLOC(m->gamma, B * N);
+    ALLOC(m->eps2, B * N);
+    ALLOC(m->eps3, B * N);
+    ALLOC(m->delta, B * N);
+    ALLOC(m->fuu11, B * N);
+    ALLOC(m->stats, B * kStatSlots);
+  }
   ALLOC(m->l0, (size_t)C * N);
   ALLOC(m->l1, (size_t)C * N);
   ALLOC(m->l2, (size_t)C * N);
@@ -638,7 +708,7 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
   ALLOC(m->jw.D, (size_t)C * np * 256);
   ALLOC(m->jw.slots, (size_t)C * 64);
   ALLOC(m->jw.flags, (size_t)C * np);
-  ALLOC(m->jw.tiles, (size_t)C);
+  ALLOC(m->jw.tiles, (size_t)2 * C);
 #undef ALLOC
   return st;
 }
@@ -865,7 +935,7 @@ rmhmc_status rmhmc_profile(rmhmc_model* m, int enable) {
       m->prof_launch[i] = 0;
     }
     cudaMemsetAsync(m->sweeps_total, 0, m->C * sizeof(int), m->stream);
-    cudaMemsetAsync(m->jw.tiles, 0, m->C * sizeof(unsigned long long), m->stream);
+    cudaMemsetAsync(m->jw.tiles, 0, 2 * m->C * sizeof(unsigned long long), m->stream);
   }
   m->prof = enable != 0;
   return RMHMC_OK;
@@ -880,17 +950,23 @@ rmhmc_status rmhmc_profile_read(rmhmc_model* m, double* ms_host, double* flops_h
     float t = 0.f;
     if (cudaEventElapsedTime(&t, m->ev[r.a], m->ev[r.b]) == cudaSuccess) ms[r.cat] += t;
   }
-  // Jacobi work = the 16 x 16 x 16 rotation tile products the kernel executed (2 * 16^3 flops
-  // each); tiles skipped because both rotations were the identity are not counted
-  std::vector<unsigned long long> tl(m->C);
-  cudaMemcpy(tl.data(), m->jw.tiles, m->C * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
-  double tiles = 0.0;
-  for (unsigned long long v : tl) tiles += (double)v;
+  // Jacobi work = the 16 x 16 x 16 rotation tile products of phase 2 (2 * 16^3 flops each; tiles
+  // skipped because both rotations were the identity are not counted) + the rotation rounds of
+  // phase 1 (8 rotations applied to a 16 x 16 block by 2 x 2 blocks, 28 off-diagonal and 8
+  // diagonal, and to its accumulated rotation: 976 FP64 multiply / FMA instructions, counted as
+  // 2 flops each like the DFMA peak)
+  std::vector<unsigned long long> tl(2 * m->C);
+  cudaMemcpy(tl.data(), m->jw.tiles, 2 * m->C * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  double tiles = 0.0, rounds = 0.0;
+  for (int c = 0; c < m->C; ++c) {
+    tiles += (double)tl[2 * c];
+    rounds += (double)tl[2 * c + 1];
+  }
   for (int i = 0; i < RMHMC_PROF_NCAT; ++i) {
     if (ms_host) ms_host[i] = ms[i];
     if (flops_host)
       flops_host[i] = (i == CAT_JACOBI || i == CAT_JACOBI_DF)
-                          ? (m->prof_launch[i] ? tiles * 8192.0 : 0.0)
+                          ? (m->prof_launch[i] ? tiles * 8192.0 + rounds * 1952.0 : 0.0)
                           : m->prof_flops[i];
     if (launches_host) launches_host[i] = m->prof_launch[i];
   }
@@ -994,9 +1070,7 @@ rmhmc_status rmhmc_init_model(const rmhmc_model_desc* desc, int n_chains, const 
   rmhmc_model* m = new rmhmc_model();
   setup_fields(m, desc, n_chains, cuda_stream);
   ModelDev& md = m->md;
-  const int N = m->N, n = m->n, C = m->C, dp = m->dp;
-  const size_t NN = (size_t)N * N, DD = (size_t)dp * dp;
-  const size_t B = (size_t)C * n;
+  const int N = m->N, n = m->n, C = m->C;
   rmhmc_status st = allocate_model(m, desc->n_cov);
   if (st != RMHMC_OK) {
     rmhmc_free_model(m);
@@ -1021,6 +1095,117 @@ rmhmc_status rmhmc_init_model(const rmhmc_model_desc* desc, int n_chains, const 
   md.y = y;
   md.u_fixed = uf;
   md.tau = tau;
+  *out = m;
+  return RMHMC_OK;
+}
+
+namespace {
+
+rmhmc_status validate_primal(const rmhmc_primal_desc* desc, int n_chains, const double* tau_host) {
+  if (!desc || n_chains < 1 || n_chains > 65535) return RMHMC_EINVAL;
+  if (desc->N < 1 || desc->N > (1 << 20) || !desc->y) return RMHMC_EINVAL;
+  if (desc->n_gauss < 0 || desc->n_linear < 0 || desc->n_gauss + desc->n_linear < 1) return RMHMC_EINVAL;
+  if ((desc->n_gauss > 0 && !desc->Xg) || (desc->n_linear > 0 && !desc->Xl)) return RMHMC_EINVAL;
+  if (desc->n_gauss > 0 && (desc->M < 1 || !(desc->L > 0.0))) return RMHMC_EINVAL;
+  const long long d = (long long)(desc->n_gauss > 0 ? desc->M : 0) * desc->n_gauss + desc->n_linear + 4;
+  if (d > 4096) return RMHMC_EINVAL;
+  if (desc->lik != RMHMC_LIK_BERNOULLI_LOGIT && desc->lik != RMHMC_LIK_GAUSSIAN) return RMHMC_EINVAL;
+  if (desc->lik == RMHMC_LIK_GAUSSIAN && !(desc->noise_var > 0.0)) return RMHMC_EINVAL;
+  if (!(desc->bias_var > 0.0)) return RMHMC_EINVAL;
+  for (int j = 0; j < 3; ++j)
+    if (!(desc->prior_a[j] > 0.0) || !(desc->prior_b[j] > 0.0)) return RMHMC_EINVAL;
+  if (tau_host)
+    for (int c = 0; c < n_chains; ++c)
+      if (!(tau_host[c] >= 0.0) || tau_host[c] > 1.0) return RMHMC_EINVAL;
+  return RMHMC_OK;
+}
+
+void setup_primal(rmhmc_model* m, const rmhmc_primal_desc* desc, int n_chains, void* cuda_stream) {
+  cudaGetDevice(&m->device);
+  m->stream = (cudaStream_t)cuda_stream;
+  m->kind = 1;
+  PrimalDev& pd = m->pd;
+  pd.N = desc->N;
+  pd.Dg = desc->n_gauss;
+  pd.Dl = desc->n_linear;
+  pd.M = desc->n_gauss > 0 ? desc->M : 0;
+  pd.P = pd.M * pd.Dg + pd.Dl + 1;
+  pd.d = pd.P + 3;
+  pd.dp = ((pd.d + kJacSB - 1) / kJacSB) * kJacSB;
+  pd.lik = desc->lik;
+  pd.n_chains = n_chains;
+  pd.noise_var = desc->noise_var;
+  pd.L = desc->L;
+  pd.bias_var = desc->bias_var;
+  for (int j = 0; j < 3; ++j) {
+    pd.a[j] = desc->prior_a[j];
+    pd.b[j] = desc->prior_b[j];
+  }
+  m->N = pd.N;
+  m->n = 1;
+  m->P = 3;
+  m->d = pd.d;
+  m->dp = pd.dp;
+  m->C = n_chains;
+  m->cluster = jacobi_cluster_size(n_chains);
+}
+
+}  // namespace
+
+rmhmc_status rmhmc_plan_bytes_primal(const rmhmc_primal_desc* desc, int n_chains, size_t* bytes) {
+  if (!bytes) return RMHMC_EINVAL;
+  *bytes = 0;
+  rmhmc_status st = validate_primal(desc, n_chains, nullptr);
+  if (st != RMHMC_OK) return st;
+  rmhmc_model m;
+  setup_primal(&m, desc, n_chains, nullptr);
+  size_t total = 0;
+  m.plan_bytes = &total;
+  st = allocate_model(&m, 0);
+  *bytes = total;
+  return st;
+}
+
+rmhmc_status rmhmc_init_primal(const rmhmc_primal_desc* desc, int n_chains, const double* tau_host,
+                               void* cuda_stream, rmhmc_model** out) {
+  if (!out) return RMHMC_EINVAL;
+  *out = nullptr;
+  rmhmc_status vst = validate_primal(desc, n_chains, tau_host);
+  if (vst != RMHMC_OK) return vst;
+  rmhmc_model* m = new rmhmc_model();
+  setup_primal(m, desc, n_chains, cuda_stream);
+  rmhmc_status st = allocate_model(m, 0);
+  if (st != RMHMC_OK) {
+    rmhmc_free_model(m);
+    return st;
+  }
+  PrimalDev& pd = m->pd;
+  const int N = pd.N, C = m->C;
+  std::vector<double> tauv(C, 1.0);
+  if (tau_host) memcpy(tauv.data(), tau_host, C * sizeof(double));
+  cudaError_t e = cudaMemcpyAsync(m->y_dev, desc->y, N * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess && pd.Dg)
+    e = cudaMemcpyAsync(m->Xg_dev, desc->Xg, (size_t)N * pd.Dg * sizeof(double), cudaMemcpyHostToDevice,
+                        m->stream);
+  if (e == cudaSuccess && pd.Dl)
+    e = cudaMemcpyAsync(m->Xl_dev, desc->Xl, (size_t)N * pd.Dl * sizeof(double), cudaMemcpyHostToDevice,
+                        m->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->tau_dev, tauv.data(), C * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+  pd.Xg = m->Xg_dev;
+  pd.Xl = m->Xl_dev;
+  pd.y = m->y_dev;
+  pd.tau = m->tau_dev;
+  if (e == cudaSuccess) {
+    const long long NP = (long long)N * pd.P;
+    dev::k_phi<<<nblk(NP), 256, 0, m->stream>>>(pd, m->Phi);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) {
+    rmhmc_free_model(m);
+    return RMHMC_ECUDA;
+  }
   *out = m;
   return RMHMC_OK;
 }

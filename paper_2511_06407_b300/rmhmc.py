@@ -37,6 +37,13 @@ class ModelDesc(ctypes.Structure):
                 ("u_fixed", POINTER(c_double))]
 
 
+class PrimalDesc(ctypes.Structure):
+    _fields_ = [("N", c_int), ("n_gauss", c_int), ("n_linear", c_int), ("Xg", POINTER(c_double)),
+                ("Xl", POINTER(c_double)), ("y", POINTER(c_double)), ("lik", c_int),
+                ("noise_var", c_double), ("M", c_int), ("L", c_double), ("bias_var", c_double),
+                ("prior_a", c_double * 3), ("prior_b", c_double * 3)]
+
+
 class IntegratorC(ctypes.Structure):
     _fields_ = [("eps", c_double), ("n_leapfrog", c_int), ("n_fp", c_int), ("g_kind", c_int),
                 ("alpha", c_double), ("jacobi_tol", c_double), ("max_sweeps", c_int),
@@ -120,6 +127,11 @@ def lib():
     L.rmhmc_autotune.restype = c_int
     L.rmhmc_plan_bytes.argtypes = [POINTER(ModelDesc), c_int, POINTER(ctypes.c_size_t)]
     L.rmhmc_plan_bytes.restype = c_int
+    L.rmhmc_init_primal.argtypes = [POINTER(PrimalDesc), c_int, POINTER(c_double), c_void_p,
+                                    POINTER(c_void_p)]
+    L.rmhmc_init_primal.restype = c_int
+    L.rmhmc_plan_bytes_primal.argtypes = [POINTER(PrimalDesc), c_int, POINTER(ctypes.c_size_t)]
+    L.rmhmc_plan_bytes_primal.restype = c_int
     L.rmhmc_version.argtypes = []
     L.rmhmc_status_string.argtypes = [c_int]
     L.rmhmc_status_string.restype = c_char_p
@@ -175,11 +187,35 @@ def _desc(problem):
     return desc, [X, y, ks, uf]
 
 
+def _primal_desc(problem):
+    """(PrimalDesc, keep-alive list) for a primal-model workload dict."""
+    y = np.ascontiguousarray(problem["y"], dtype=np.float64)
+    N = y.shape[0]
+    Xg = np.ascontiguousarray(problem["Xg"], dtype=np.float64).reshape(N, -1)
+    Xl = np.ascontiguousarray(problem["Xl"], dtype=np.float64).reshape(N, -1)
+    desc = PrimalDesc(N, Xg.shape[1], Xl.shape[1],
+                      Xg.ctypes.data_as(POINTER(c_double)) if Xg.shape[1] else None,
+                      Xl.ctypes.data_as(POINTER(c_double)) if Xl.shape[1] else None,
+                      y.ctypes.data_as(POINTER(c_double)), LIKS[problem["lik"]], float(problem["noise_var"]),
+                      int(problem["M"]), float(problem["L"]), float(problem["bias_var"]),
+                      (c_double * 3)(*[float(v) for v in problem["prior_a"]]),
+                      (c_double * 3)(*[float(v) for v in problem["prior_b"]]))
+    return desc, [y, Xg, Xl]
+
+
+def is_primal(problem):
+    return problem.get("model") == "primal"
+
+
 def plan_bytes(problem, n_chains):
     """Device bytes a Model for this problem and chain count would allocate (rmhmc_plan_bytes)."""
-    desc, keep = _desc(problem)
     out = ctypes.c_size_t()
-    _check(lib().rmhmc_plan_bytes(ctypes.byref(desc), int(n_chains), ctypes.byref(out)))
+    if is_primal(problem):
+        desc, keep = _primal_desc(problem)
+        _check(lib().rmhmc_plan_bytes_primal(ctypes.byref(desc), int(n_chains), ctypes.byref(out)))
+    else:
+        desc, keep = _desc(problem)
+        _check(lib().rmhmc_plan_bytes(ctypes.byref(desc), int(n_chains), ctypes.byref(out)))
     return out.value
 
 
@@ -189,7 +225,8 @@ class Model:
     def __init__(self, problem, n_chains, tau=None, stream=None):
         import torch
         L = lib()
-        desc, keep = _desc(problem)
+        primal = is_primal(problem)
+        desc, keep = _primal_desc(problem) if primal else _desc(problem)
         tau_arr = None
         if tau is not None:
             tau_arr = np.ascontiguousarray(np.broadcast_to(np.asarray(tau, dtype=np.float64), (n_chains,)))
@@ -197,9 +234,10 @@ class Model:
             stream = torch.cuda.current_stream()
         self.stream = stream
         handle = c_void_p()
-        _check(L.rmhmc_init_model(ctypes.byref(desc), int(n_chains),
-                                  tau_arr.ctypes.data_as(POINTER(c_double)) if tau_arr is not None else None,
-                                  c_void_p(stream.cuda_stream), ctypes.byref(handle)))
+        init = L.rmhmc_init_primal if primal else L.rmhmc_init_model
+        _check(init(ctypes.byref(desc), int(n_chains),
+                    tau_arr.ctypes.data_as(POINTER(c_double)) if tau_arr is not None else None,
+                    c_void_p(stream.cuda_stream), ctypes.byref(handle)))
         self._h = handle
         self.d = L.rmhmc_dim(self._h)
         self.n_chains = L.rmhmc_n_chains(self._h)

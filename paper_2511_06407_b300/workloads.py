@@ -104,6 +104,30 @@ def propensity(N, seed=0, n_kernels=3):
             "kernels": kernels[:n_kernels], "sample_hypers": True, "u_fixed": None, "f_true": F}
 
 
+def solin_logistic(D, N=500, seed=0, M=30, L=8.0, sd=1.5, bias=-0.5, n_linear=0):
+    """The simulated logistic-regression data of Sec. 2.5 for the primal (reduced-rank) model:
+    X ~ N(0, 1)^{N x D}; the true log-odds f*(x) = sum_k sum_{m=4..16} a*_km sin(pi m (x_k + L)/(2L))
+    + b*, a*_km ~ N(0, c*/m), b* = -0.5, c* set so that the empirical SD of f* is 1.5; labels
+    y ~ Bernoulli(sigmoid(f*)) coded {0, 1}. (The true function is drawn from the paper's own
+    sinusoidal data-generating recipe; the model's features are evaluated separately by the
+    sampler.) Optional linear covariates ~ N(0, 1) enter the truth with unit weights."""
+    rng = np.random.default_rng(seed)
+    Xg = rng.standard_normal((N, D))
+    Xl = rng.standard_normal((N, n_linear))
+    m = np.arange(1, M + 1)
+    a = rng.standard_normal((D, M)) / np.sqrt(m)[None, :]
+    a[:, (m < 4) | (m > 16)] = 0.0
+    f0 = np.zeros(N)
+    for k in range(D):
+        f0 += np.sin(np.pi * m[None, :] * (Xg[:, k:k + 1] + L) / (2.0 * L)) @ a[k]
+    f0 += Xl.sum(axis=1)
+    f = f0 * (sd / f0.std()) + bias
+    y = _bernoulli(rng, f)
+    return {"model": "primal", "Xg": Xg, "Xl": Xl, "y": y, "M": M, "L": L, "lik": "bernoulli",
+            "noise_var": 1.0, "bias_var": 1.0, "prior_a": (2.0, 2.0, 2.0), "prior_b": (2.0, 2.0, 2.0),
+            "f_true": f}
+
+
 def uneven_batch(n_problems=128, seed=0, n_min=32, n_max=512):
     """Problems of uneven dimension: N ~ U{n_min..n_max}, 1-3 kernels (SE, linear, overlap in that
     order) on the propensity covariates; problem i uses seed + i."""
@@ -117,13 +141,19 @@ def uneven_batch(n_problems=128, seed=0, n_min=32, n_max=512):
 
 
 def dims(problem):
+    """(N, number of latent blocks or coefficients, d)."""
+    if problem.get("model") == "primal":
+        N = problem["Xg"].shape[0]
+        P = problem["M"] * problem["Xg"].shape[1] + problem["Xl"].shape[1] + 1
+        return N, P, P + 3
     N = problem["X"].shape[0]
     n = len(problem["kernels"])
     return N, n, n * N + (2 * n if problem["sample_hypers"] else 0)
 
 
 def initial_state(problem, n_chains):
-    """f = 0 and u = 0 (amplitude = lengthscale = 1) for every chain, as an (n_chains, d) array."""
+    """f = 0 (a = 0, b = 0 for the primal model) and u = 0 (every hyperparameter 1) for every chain,
+    as an (n_chains, d) array."""
     _, _, d = dims(problem)
     return np.zeros((n_chains, d))
 
@@ -134,6 +164,9 @@ def random_state(problem, n_chains, seed, f_scale=0.5, u_scale=0.3):
     _, _, d = dims(problem)
     q = f_scale * rng.standard_normal((n_chains, d))
     N, n, _ = dims(problem)
+    if problem.get("model") == "primal":
+        q[:, d - 3:] = u_scale * rng.standard_normal((n_chains, 3))
+        return q
     if problem["sample_hypers"]:
         q[:, n * N:] = u_scale * rng.standard_normal((n_chains, 2 * n))
     return q

@@ -15,7 +15,10 @@ def pytest_configure(config):
 
 
 def to_oracle_model(problem):
-    """Workload dict -> oracle GPModel."""
+    """Workload dict -> oracle model (GPModel, or PrimalModel for the reduced-rank model)."""
+    if problem.get("model") == "primal":
+        from oracle.primal import from_problem as primal_from_problem
+        return primal_from_problem(problem)
     from oracle.model import from_problem
     return from_problem(problem)
 
@@ -38,3 +41,13 @@ def potential_rounding_bound(m, q):
         a = np.abs(st.alpha)
         b += 0.5 * a @ K @ a + 0.5 * np.sum(np.abs(st.Kinv) * K)
     return 2.0 ** -53 * b
+
+
+def eigen_backward_bound(H, G, Ginv_p, sweeps, unit=2.0 ** -53):
+    """First-order change of G^-1 p under a symmetric perturbation E of H with
+    ||E|| <= 4u ||H||_2 per Jacobi sweep (the normwise backward error the rotations of Sec. 2.4
+    commit): g(H + E) - g(H) = Psi (T o Psi^T E Psi) Psi^T (Daleckii-Krein) with |T_jl| <= 1 for
+    both soft-abs maps, so G^-1 p moves by at most ||G^-1||_2 * 4u sweeps ||H||_2 * ||G^-1 p||."""
+    ev = np.linalg.eigvalsh(G)
+    h2 = float(np.abs(np.linalg.eigvalsh(H)).max())
+    return (1.0 / ev.min()) * 4.0 * unit * max(int(sweeps), 1) * h2 * float(np.linalg.norm(Ginv_p))

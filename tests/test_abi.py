@@ -63,7 +63,7 @@ def test_binding_structs_match_header_layout(tmp_path):
     import subprocess
     from paper_2511_06407_b300 import rmhmc
     structs = {"rmhmc_kernel_desc": rmhmc.KernelDesc, "rmhmc_model_desc": rmhmc.ModelDesc,
-               "rmhmc_integrator": rmhmc.IntegratorC}
+               "rmhmc_integrator": rmhmc.IntegratorC, "rmhmc_primal_desc": rmhmc.PrimalDesc}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rmhmc.h"', "int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -91,3 +91,18 @@ def test_invalid_descriptions_are_rejected_without_a_gpu():
     desc.N = 0
     assert L.rmhmc_init_model(ctypes.byref(desc), 1, None, None, ctypes.byref(out)) == 1
     assert L.rmhmc_init_model(None, 1, None, None, ctypes.byref(out)) == 1
+    # the primal model: no covariates, then too many features (d > 4096), then a bad prior
+    pd = rmhmc.PrimalDesc()
+    pd.N = 10
+    assert L.rmhmc_init_primal(ctypes.byref(pd), 1, None, None, ctypes.byref(out)) == 1
+    y = (ctypes.c_double * 10)()
+    xg = (ctypes.c_double * 10)()
+    pd.y, pd.Xg, pd.n_gauss, pd.M, pd.L, pd.bias_var = y, xg, 1, 5000, 8.0, 1.0
+    pd.prior_a[:] = [2.0, 2.0, 2.0]
+    pd.prior_b[:] = [2.0, 2.0, 2.0]
+    size = ctypes.c_size_t()
+    assert L.rmhmc_plan_bytes_primal(ctypes.byref(pd), 1, ctypes.byref(size)) == 1
+    pd.M = 30
+    assert L.rmhmc_plan_bytes_primal(ctypes.byref(pd), 2, ctypes.byref(size)) == 0 and size.value > 0
+    pd.prior_b[1] = 0.0
+    assert L.rmhmc_plan_bytes_primal(ctypes.byref(pd), 2, ctypes.byref(size)) == 1
