@@ -31,10 +31,12 @@ sys.path.insert(0, ROOT)
 from paper_2511_06407_b300 import workloads as wl  # noqa: E402
 
 N_INPUTS, N_CHAINS, EPS, N_FP = 400, 64, 0.005, 6
-# DRAM bytes per launch per chain of the Jacobi kernels, from the ncu captures summarised under
-# profiles/ (8 chains; traffic grows with the number of chains, so a 64-chain launch is scaled by
-# 64 / 8). Empty until the current kernels are captured.
-JACOBI_DRAM_BYTES_PER_CHAIN = {}
+# DRAM bytes per launch per chain of the Jacobi kernels, from the ncu captures summarised in
+# profiles/k_jacobi_N400_8chains.md and profiles/k_jacobi_df_N400_8chains.md (8 chains, mean of the
+# two captured launches; traffic grows with the number of chains, so a 64-chain launch is scaled
+# by 64 / 8).
+JACOBI_DRAM_BYTES_PER_CHAIN = {"jacobi_f64": (22.252e6 + 0.5 * (1.828e6 + 1.670e6)) / 8,
+                               "jacobi_df": (22.269e6 + 0.5 * (1.636e6 + 1.591e6)) / 8}
 SUBSTEPS_PER_LEAPFROG = 2 * N_FP + 1
 METRIC = "RMHMC leapfrog substeps/s"
 UNIT = "substeps/s"

@@ -229,8 +229,9 @@ rmhmc_status rmhmc_batch_leapfrog(rmhmc_batch* b, const rmhmc_integrator* integ,
 void rmhmc_batch_free(rmhmc_batch* b);
 
 /* Choose the model's Jacobi cluster size (CTAs per chain: 1, 2, 4 or 8) by timing up to three
- * cold-start sweeps of each candidate on the model's own current Hessian (in scratch buffers; the
- * state is untouched) and keeping the fastest time per sweep. Synchronises the stream; needs a
+ * cold-start sweeps of each candidate, with the Jacobi kernel of the model's precision, on the
+ * model's own current Hessian (in scratch buffers; the state is untouched) and keeping the fastest
+ * time per sweep. Without it a model uses the largest cluster that keeps two CTAs per SM. Synchronises the stream; needs a
  * state. *cluster_out (may be NULL) receives the choice. */
 rmhmc_status rmhmc_autotune(rmhmc_model* m, int* cluster_out);
 

@@ -867,10 +867,18 @@ size_t noalloc_doubles(int n, int dp) {
          (ints + 1) / 2 + 4;
 }
 
+// CTAs per chain: the largest of 8, 4, 2, 1 that keeps n_chains x cluster within two CTAs per SM
+// (a CTA holds 256 threads x 128 registers, half of an SM's register file), so that every SM runs
+// two CTAs (16 warps) and the barrier and latency stalls of one hide behind the other.
 int jacobi_cluster_size(int n_chains) {
-  if (n_chains <= 18) return 8;
-  if (n_chains <= 37) return 4;
-  if (n_chains <= 74) return 2;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
+  }
+  for (int c = 8; c > 1; c >>= 1)
+    if ((long long)n_chains * c <= 2LL * sms) return c;
   return 1;
 }
 

@@ -866,8 +866,14 @@ rmhmc_status rmhmc_autotune(rmhmc_model* m, int* cluster_out) {
     cudaEventRecord(e0, s);
     JacobiWork w = m->jw;
     w.tiles = nullptr;  // trial runs stay out of the profile
-    jacobi_f64(s, m->W, m->Y, m->vtr, dp, d, C, m->jacobi_rule, m->tol, 3, m->acc, m->eig_save,
-               nullptr, w, cl);
+    if (m->precision == RMHMC_MIXED)
+      // the double-float kernel's pair buffers: M (scratch between eigen-updates: the C matrix of
+      // the next gradient is built there) and PsiT_save (used only inside rmhmc_sample)
+      jacobi_df(s, m->W, m->Y, m->vtr, dp, d, C, m->jacobi_rule, m->tol, 3, m->acc, m->eig_save, nullptr, w,
+                cl, m->M, m->PsiT_save);
+    else
+      jacobi_f64(s, m->W, m->Y, m->vtr, dp, d, C, m->jacobi_rule, m->tol, 3, m->acc, m->eig_save,
+                 nullptr, w, cl);
     cudaEventRecord(e1, s);
     if (cudaEventSynchronize(e1) != cudaSuccess) return RMHMC_ECUDA;
     float ms = 0.f;
