@@ -43,6 +43,7 @@ constexpr int BL = kJacBlk;      // 8
 constexpr int SBP = SB + 1;
 constexpr int MAX_INNER = 8;
 constexpr int WARP_SMEM = 4 * SB * SBP;  // doubles per warp
+constexpr int kMaxPairs = 256;           // dp <= 16 * kMaxPairs = 4096
 
 __device__ __forceinline__ void circle_pair(int r, int p, int nb, int& I, int& J) {
   const int m1 = nb - 1;
@@ -290,6 +291,13 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
   const int chain = blockIdx.x / C;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nb = dp / BL, np = nb / 2;
+  if (np > kMaxPairs) {  // larger than any model or batch the library accepts
+    if (rank == 0 && tid == 0) {
+      atomicOr(&status[chain], RMHMC_CHAIN_NOTCONV);
+      sweeps_out[chain] = 0;
+    }
+    return;  // uniform for the whole cluster
+  }
   if (status[chain] != 0) {
     if (rank == 0 && tid == 0) sweeps_out[chain] = 0;
     return;  // uniform for the whole cluster
@@ -308,9 +316,13 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
   double* Vq = ws + 3 * SB * SBP;
   __shared__ double red[2][NW];
   __shared__ double cs[NW][3 * SB / 2];  // (c, s, t) of the 8 rotations of a round, per warp
+  __shared__ unsigned char sflag[kMaxPairs];  // pair rotated in this round
+  __shared__ short sact[kMaxPairs];           // the rotated pairs, in order
+  __shared__ int scum[kMaxPairs];             // cumulative active M tiles per column
+  __shared__ int snact;
 
   const int gw = rank * NW + warp, nwt = C * NW;
-  const int nMjobs = np * (np + 1) / 2, nct = dp / SB;
+  const int nct = dp / SB;
   int sweeps = 0;
   bool converged = false;
   unsigned int ntile = 0;   // 16 x 16 x 16 tile products this warp executed (phase 2)
@@ -408,23 +420,54 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
         __syncwarp();
       }
       cluster.sync();
+      // ---- the pairs rotated in phase 1, in order (every CTA of the cluster builds the same list)
+      // and, per column Q of M's tiles, the cumulative count of active tiles (P <= Q with P or Q
+      // rotated): column Q holds Q + 1 of them if Q rotated, else as many as rotated pairs P < Q
+      if (warp == 0) {
+        int base = 0, run = 0;
+        for (int p0 = 0; p0 < np; p0 += 32) {
+          const int p = p0 + lane;
+          const bool f = p < np && __ldcg(flags + p) != 0;
+          const unsigned bal = __ballot_sync(0xffffffffu, f);
+          const int before = base + __popc(bal & ((1u << lane) - 1u));  // rotated pairs < p
+          if (p < np) sflag[p] = f ? 1 : 0;
+          if (f) sact[before] = (short)p;
+          int c = p < np ? (f ? p + 1 : before) : 0;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {  // inclusive warp scan
+            const int v = __shfl_up_sync(0xffffffffu, c, o);
+            if (lane >= o) c += v;
+          }
+          if (p < np) scum[p] = run + c;
+          run += __shfl_sync(0xffffffffu, c, 31);
+          base += __popc(bal);
+        }
+        if (lane == 0) snact = base;
+      }
+      __syncthreads();
       // ---- phase 2: apply all rotations to M (P <= Q tiles) and to the rows of Psi^T
-      for (int job = gw; job < nMjobs + np * nct; job += nwt) {
-        if (job < nMjobs) {
-          int Q = (int)((sqrtf(8.0f * (float)job + 1.0f) - 1.0f) * 0.5f);  // then exact integer fix-up
-          while (Q * (Q + 1) / 2 > job) --Q;
-          while ((Q + 1) * (Q + 2) / 2 <= job) ++Q;
-          const int Pp = job - Q * (Q + 1) / 2;
-          const int fP = __ldcg(flags + Pp), fQ = __ldcg(flags + Q);
-          if (!fP && !fQ) continue;  // both rotations are exactly I: the tile is unchanged
+      //      over the active jobs only, dealt round-robin to the cluster's warps: the M tiles
+      //      (P <= Q) of which P or Q rotated, then the Psi^T row tiles of the rotated pairs
+      const int k = scum[np - 1];  // active M tiles
+      for (int i = gw; i < k; i += nwt) {
+        {
+          int lo = 0, hi = np - 1;  // the column: smallest Q with scum[Q] > i
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (scum[mid] > i) hi = mid;
+            else lo = mid + 1;
+          }
+          const int Q = lo, o = i - (Q > 0 ? scum[Q - 1] : 0);
+          const int fQ = sflag[Q];
+          const int Pp = fQ ? o : sact[o];
+          const int fP = sflag[Pp];
           int I1, J1, I2, J2;
           circle_pair(r, Pp, nb, I1, J1);
           circle_pair(r, Q, nb, I2, J2);
           if (Pp == Q) {
             for (int e = lane; e < SB * SB; e += 32) {
               const int a = e / SB, b = e % SB;
-              __stcg(M + (long long)gidx(I1, J1, a) * dp + gidx(I1, J1, b),
-                     __ldcg(D + (long long)Pp * SB * SB + e));
+              __stcg(M + (long long)gidx(I1, J1, a) * dp + gidx(I1, J1, b), __ldcg(D + (long long)Pp * SB * SB + e));
             }
           } else {
             for (int e = lane; e < SB * SB; e += 32) {
@@ -445,26 +488,26 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
               __stcg(M + (long long)gidx(I2, J2, t) * dp + gidx(I1, J1, u0 + j), X[(u0 + j) * SBP + t]);
           }
           __syncwarp();
-        } else {
-          const int pj = job - nMjobs;
-          const int Pp = pj / nct, ct = pj % nct;
-          if (!__ldcg(flags + Pp)) continue;
-          int I1, J1;
-          circle_pair(r, Pp, nb, I1, J1);
-          for (int e = lane; e < SB * SB; e += 32) {
-            const int a = e / SB, b = e % SB;
-            X[a * SBP + b] = __ldcg(P + (long long)gidx(I1, J1, a) * dp + ct * SB + b);
-          }
-          load_v(Va, V + (long long)Pp * SB * SB);
-          __syncwarp();
-          tile_transform(X, Va, nullptr, Tt, X);
-          ++ntile;
-          const int t = lane >> 1, u0 = (lane & 1) * 8;
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            __stcg(P + (long long)gidx(I1, J1, t) * dp + ct * SB + u0 + j, X[t * SBP + u0 + j]);
-          __syncwarp();
         }
+      }
+      const int nPsi = snact * nct;
+      for (int j = ((gw - k) % nwt + nwt) % nwt; j < nPsi; j += nwt) {
+        const int Pp = sact[j / nct], ct = j % nct;
+        int I1, J1;
+        circle_pair(r, Pp, nb, I1, J1);
+        for (int e = lane; e < SB * SB; e += 32) {
+          const int a = e / SB, b = e % SB;
+          X[a * SBP + b] = __ldcg(P + (long long)gidx(I1, J1, a) * dp + ct * SB + b);
+        }
+        load_v(Va, V + (long long)Pp * SB * SB);
+        __syncwarp();
+        tile_transform(X, Va, nullptr, Tt, X);
+        ++ntile;
+        const int t = lane >> 1, u0 = (lane & 1) * 8;
+#pragma unroll
+        for (int j2 = 0; j2 < 8; ++j2)
+          __stcg(P + (long long)gidx(I1, J1, t) * dp + ct * SB + u0 + j2, X[t * SBP + u0 + j2]);
+        __syncwarp();
       }
       cluster.sync();
     }
@@ -558,6 +601,13 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
   const int chain = blockIdx.x / C;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nb = dp / BL, np = nb / 2;
+  if (np > kMaxPairs) {  // larger than any model or batch the library accepts
+    if (rank == 0 && tid == 0) {
+      atomicOr(&status[chain], RMHMC_CHAIN_NOTCONV);
+      sweeps_out[chain] = 0;
+    }
+    return;  // uniform for the whole cluster
+  }
   if (status[chain] != 0) {
     if (rank == 0 && tid == 0) sweeps_out[chain] = 0;
     return;  // uniform for the whole cluster
@@ -581,6 +631,10 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
   float2* Vq = (float2*)(ws + 3 * SB * SBP);
   __shared__ double red[2][NW];
   __shared__ double cs[NW][3 * SB / 2];  // (c, s, t) of the 8 rotations of a round, per warp
+  __shared__ unsigned char sflag[kMaxPairs];  // pair rotated in this round
+  __shared__ short sact[kMaxPairs];           // the rotated pairs, in order
+  __shared__ int scum[kMaxPairs];             // cumulative active M tiles per column
+  __shared__ int snact;
 
   for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
     __stcg(Mw + e, df_split(__ldcg(M + e)));
@@ -589,7 +643,7 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
   cluster.sync();
 
   const int gw = rank * NW + warp, nwt = C * NW;
-  const int nMjobs = np * (np + 1) / 2, nct = dp / SB;
+  const int nct = dp / SB;
   int sweeps = 0;
   bool converged = false;
   unsigned int ntile = 0;   // 16 x 16 x 16 tile products this warp executed (phase 2)
@@ -683,23 +737,54 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
         __syncwarp();
       }
       cluster.sync();
+      // ---- the pairs rotated in phase 1, in order (every CTA of the cluster builds the same list)
+      // and, per column Q of M's tiles, the cumulative count of active tiles (P <= Q with P or Q
+      // rotated): column Q holds Q + 1 of them if Q rotated, else as many as rotated pairs P < Q
+      if (warp == 0) {
+        int base = 0, run = 0;
+        for (int p0 = 0; p0 < np; p0 += 32) {
+          const int p = p0 + lane;
+          const bool f = p < np && __ldcg(flags + p) != 0;
+          const unsigned bal = __ballot_sync(0xffffffffu, f);
+          const int before = base + __popc(bal & ((1u << lane) - 1u));  // rotated pairs < p
+          if (p < np) sflag[p] = f ? 1 : 0;
+          if (f) sact[before] = (short)p;
+          int c = p < np ? (f ? p + 1 : before) : 0;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {  // inclusive warp scan
+            const int v = __shfl_up_sync(0xffffffffu, c, o);
+            if (lane >= o) c += v;
+          }
+          if (p < np) scum[p] = run + c;
+          run += __shfl_sync(0xffffffffu, c, 31);
+          base += __popc(bal);
+        }
+        if (lane == 0) snact = base;
+      }
+      __syncthreads();
       // ---- phase 2 (double-float): apply all rotations to M and to the rows of Psi^T
-      for (int job = gw; job < nMjobs + np * nct; job += nwt) {
-        if (job < nMjobs) {
-          int Q = (int)((sqrtf(8.0f * (float)job + 1.0f) - 1.0f) * 0.5f);
-          while (Q * (Q + 1) / 2 > job) --Q;
-          while ((Q + 1) * (Q + 2) / 2 <= job) ++Q;
-          const int Pp = job - Q * (Q + 1) / 2;
-          const int fP = __ldcg(flags + Pp), fQ = __ldcg(flags + Q);
-          if (!fP && !fQ) continue;
+      //      over the active jobs only, dealt round-robin to the cluster's warps: the M tiles
+      //      (P <= Q) of which P or Q rotated, then the Psi^T row tiles of the rotated pairs
+      const int k = scum[np - 1];  // active M tiles
+      for (int i = gw; i < k; i += nwt) {
+        {
+          int lo = 0, hi = np - 1;  // the column: smallest Q with scum[Q] > i
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (scum[mid] > i) hi = mid;
+            else lo = mid + 1;
+          }
+          const int Q = lo, o = i - (Q > 0 ? scum[Q - 1] : 0);
+          const int fQ = sflag[Q];
+          const int Pp = fQ ? o : sact[o];
+          const int fP = sflag[Pp];
           int I1, J1, I2, J2;
           circle_pair(r, Pp, nb, I1, J1);
           circle_pair(r, Q, nb, I2, J2);
           if (Pp == Q) {
             for (int e = lane; e < SB * SB; e += 32) {
               const int a = e / SB, b = e % SB;
-              __stcg(Mw + (long long)gidx(I1, J1, a) * dp + gidx(I1, J1, b),
-                     ldcg2(D + (long long)Pp * SB * SB + e));
+              __stcg(Mw + (long long)gidx(I1, J1, a) * dp + gidx(I1, J1, b), ldcg2(D + (long long)Pp * SB * SB + e));
             }
           } else {
             for (int e = lane; e < SB * SB; e += 32) {
@@ -720,26 +805,26 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
               __stcg(Mw + (long long)gidx(I2, J2, t) * dp + gidx(I1, J1, u0 + j), X[(u0 + j) * SBP + t]);
           }
           __syncwarp();
-        } else {
-          const int pj = job - nMjobs;
-          const int Pp = pj / nct, ct = pj % nct;
-          if (!__ldcg(flags + Pp)) continue;
-          int I1, J1;
-          circle_pair(r, Pp, nb, I1, J1);
-          for (int e = lane; e < SB * SB; e += 32) {
-            const int a = e / SB, b = e % SB;
-            X[a * SBP + b] = ldcg2(Pw + (long long)gidx(I1, J1, a) * dp + ct * SB + b);
-          }
-          load_v_df(Va, V + (long long)Pp * SB * SB);
-          __syncwarp();
-          tile_transform_df(X, Va, nullptr, Tt, X);
-          ++ntile;
-          const int t = lane >> 1, u0 = (lane & 1) * 8;
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            __stcg(Pw + (long long)gidx(I1, J1, t) * dp + ct * SB + u0 + j, X[t * SBP + u0 + j]);
-          __syncwarp();
         }
+      }
+      const int nPsi = snact * nct;
+      for (int j = ((gw - k) % nwt + nwt) % nwt; j < nPsi; j += nwt) {
+        const int Pp = sact[j / nct], ct = j % nct;
+        int I1, J1;
+        circle_pair(r, Pp, nb, I1, J1);
+        for (int e = lane; e < SB * SB; e += 32) {
+          const int a = e / SB, b = e % SB;
+          X[a * SBP + b] = ldcg2(Pw + (long long)gidx(I1, J1, a) * dp + ct * SB + b);
+        }
+        load_v_df(Va, V + (long long)Pp * SB * SB);
+        __syncwarp();
+        tile_transform_df(X, Va, nullptr, Tt, X);
+        ++ntile;
+        const int t = lane >> 1, u0 = (lane & 1) * 8;
+#pragma unroll
+        for (int j2 = 0; j2 < 8; ++j2)
+          __stcg(Pw + (long long)gidx(I1, J1, t) * dp + ct * SB + u0 + j2, X[t * SBP + u0 + j2]);
+        __syncwarp();
       }
       cluster.sync();
     }
