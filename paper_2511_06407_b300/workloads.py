@@ -128,6 +128,35 @@ def solin_logistic(D, N=500, seed=0, M=30, L=8.0, sd=1.5, bias=-0.5, n_linear=0)
             "f_true": f}
 
 
+def _sinusoid_draw(rng, X, M, L, sd):
+    """sum_k sum_{m=4..16} a_km sin(pi m (x_k + L) / (2L)), a_km ~ N(0, c/m), scaled to SD sd (the
+    data recipe of Sec. 2.5)."""
+    m = np.arange(1, M + 1)
+    a = rng.standard_normal((X.shape[1], M)) / np.sqrt(m)[None, :]
+    a[:, (m < 4) | (m > 16)] = 0.0
+    f = np.zeros(X.shape[0])
+    for k in range(X.shape[1]):
+        f += np.sin(np.pi * m[None, :] * (X[:, k:k + 1] + L) / (2.0 * L)) @ a[k]
+    return f * (sd / f.std())
+
+
+def meanvar_regression(D, N=500, seed=0, M=30, L=8.0, delta=0.05, n_linear=0):
+    """Example 1 of Sec. 2.1 (covariate-dependent mean and variance, J = 2) on synthetic data in
+    the layout of Sec. 2.6 (the NMES records are not available): X ~ N(0, 1)^{N x D}, true mean
+    f1* (SD 1) and log-variance f2* (SD 0.7, mean log 0.3) drawn with the recipe of Sec. 2.5,
+    y = f1* + sqrt(delta + exp f2*) eps, eps ~ N(0, 1). Optional linear covariates ~ N(0, 1) add
+    to both functions with unit and 0.3 weights."""
+    rng = np.random.default_rng(seed)
+    Xg = rng.standard_normal((N, D))
+    Xl = rng.standard_normal((N, n_linear))
+    f1 = _sinusoid_draw(rng, Xg, M, L, 1.0) + Xl.sum(axis=1)
+    f2 = _sinusoid_draw(rng, Xg, M, L, 0.7) + np.log(0.3) + 0.3 * Xl.sum(axis=1)
+    y = f1 + np.sqrt(delta + np.exp(f2)) * rng.standard_normal(N)
+    return {"model": "primal", "J": 2, "delta": delta, "Xg": Xg, "Xl": Xl, "y": y, "M": M, "L": L,
+            "lik": "meanvar", "noise_var": 1.0, "bias_var": 1.0, "prior_a": (2.0, 2.0, 2.0),
+            "prior_b": (2.0, 2.0, 2.0), "f_true": np.stack([f1, f2])}
+
+
 def uneven_batch(n_problems=128, seed=0, n_min=32, n_max=512):
     """Problems of uneven dimension: N ~ U{n_min..n_max}, 1-3 kernels (SE, linear, overlap in that
     order) on the propensity covariates; problem i uses seed + i."""
@@ -145,7 +174,7 @@ def dims(problem):
     if problem.get("model") == "primal":
         N = problem["Xg"].shape[0]
         P = problem["M"] * problem["Xg"].shape[1] + problem["Xl"].shape[1] + 1
-        return N, P, P + 3
+        return N, P, problem.get("J", 1) * P + 3
     N = problem["X"].shape[0]
     n = len(problem["kernels"])
     return N, n, n * N + (2 * n if problem["sample_hypers"] else 0)
