@@ -57,7 +57,11 @@ typedef enum {
 #define RMHMC_CHAIN_NOTCONV 2
 #define RMHMC_CHAIN_NONFINITE 4
 
-typedef enum { RMHMC_LIK_BERNOULLI_LOGIT = 0, RMHMC_LIK_GAUSSIAN = 1 } rmhmc_lik;
+typedef enum {
+  RMHMC_LIK_BERNOULLI_LOGIT = 0,
+  RMHMC_LIK_GAUSSIAN = 1,
+  RMHMC_LIK_MEANVAR = 2  /* primal model with J = 2 only: y ~ N(F_1, delta + exp F_2) (Example 1) */
+} rmhmc_lik;
 typedef enum { RMHMC_K_SE = 0, RMHMC_K_LINEAR = 1, RMHMC_K_OVERLAP = 2 } rmhmc_kernel_kind;
 typedef enum { RMHMC_G_COTH = 0, RMHMC_G_SQRT = 1 } rmhmc_gkind;
 typedef enum { RMHMC_FP64 = 0, RMHMC_MIXED = 1 } rmhmc_precision;
@@ -142,7 +146,10 @@ rmhmc_status rmhmc_plan_bytes(const rmhmc_model_desc* desc, int n_chains, size_t
  * the Gaussian kernels and one c_l for the linear ones, each ~ InvGamma(prior_a, prior_b) and
  * sampled as u = log(theta). F_i = sum_km a_km phi_m(Xg_ik) + sum_l a_l Xl_il + b, and the
  * likelihood is lik on (F_i, y_i) tempered by tau. Coordinates q = (a_km (k-major, m fastest),
- * a_l, b, u_cg, u_sg, u_cl): d = M n_gauss + n_linear + 4 (= 30 D + 4 for Sec. 2.5).
+ * a_l, b, u_cg, u_sg, u_cl): d = M n_gauss + n_linear + 4 (= 30 D + 4 for Sec. 2.5). With J = 2
+ * (Example 1 of Sec. 2.1, the covariate-dependent mean and variance of Sec. 2.6) there are two
+ * functions F_1, F_2 on the same features with y_i ~ N(F_1i, delta + exp F_2i): q = (coefficients
+ * of F_1, coefficients of F_2, u_cg, u_sg, u_cl), d = 2 P + 3 with P = M n_gauss + n_linear + 1.
  * Host arrays are read during rmhmc_init_primal only. */
 typedef struct {
   int N;                        /* number of samples, >= 1 */
@@ -158,6 +165,10 @@ typedef struct {
   double bias_var;              /* Sigma, the prior variance of b, > 0 */
   double prior_a[3];            /* InvGamma shapes for (c_g, s_g, c_l) */
   double prior_b[3];            /* InvGamma scales for (c_g, s_g, c_l) */
+  int J;                        /* latent functions: 1, or 2 for the mean/variance model (lik must
+                                   then be RMHMC_LIK_MEANVAR); each has its own coefficients on the
+                                   same features, all share (c_g, s_g, c_l) */
+  double delta;                 /* J = 2: the fixed variance floor, >= 0 */
 } rmhmc_primal_desc;
 
 /* As rmhmc_init_model, for the primal model; the returned model works with every other call of

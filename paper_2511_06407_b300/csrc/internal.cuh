@@ -52,11 +52,12 @@ struct ModelDev {
 };
 
 // The primal (reduced-rank) model: M sinusoidal features per Gaussian-kernel column of Xg, one
-// coefficient per linear-kernel column of Xl, a bias; P = M Dg + Dl + 1 coefficients, then
-// (u_cg, u_sg, u_cl); d = P + 3.
+// coefficient per linear-kernel column of Xl, a bias; P = M Dg + Dl + 1 coefficients per latent
+// function, J functions, then (u_cg, u_sg, u_cl); d = J P + 3.
 struct PrimalDev {
   int N, Dg, Dl, M, P, d, dp, lik, n_chains;
-  double noise_var, L, bias_var;
+  int J, JP;  // latent functions (1 or 2) and J P, the offset of (u_cg, u_sg, u_cl) in q
+  double noise_var, L, bias_var, delta;
   double a[3], b[3];
   const double* Xg;   // N x Dg
   const double* Xl;   // N x Dl

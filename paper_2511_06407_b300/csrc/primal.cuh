@@ -2,7 +2,9 @@
 // likelihood maps, U / dU / Hessian assembly and the third-derivative contraction. Included once,
 // by rmhmc.cu, after model_kernels.cuh.
 //
-// Model (Sec. 2.1 Eq. Solin_representation; the reduced-rank appendix; Sec. 2.5):
+// Model (Sec. 2.1 Eq. Solin_representation; the reduced-rank appendix; Sec. 2.5, 2.6). With J = 2
+// (Example 1) two functions F_1, F_2 share the features and the hyperparameters, and
+// y_i ~ N(F_1i, delta + exp F_2i); coefficient i of q belongs to function i / P, position i % P.
 //   F_i = sum_km a_km phi_m(Xg_ik) + sum_l a_l Xl_il + b,  phi_m(x) = sin(pi m (x + L) / (2L))
 //   a_km ~ N(0, c_g V_m(s_g)), V_m(s) = sqrt(pi s) exp(-kappa_m s), kappa_m = pi^2 m^2 / (16 L^2)
 //   a_l ~ N(0, c_l), b ~ N(0, Sigma), c_g, s_g, c_l ~ InvGamma, sampled as u = log(theta).
@@ -85,6 +87,45 @@ __global__ void k_lik_primal(PrimalDev pd, const double* __restrict__ F, double*
   l3[o] = tau * a3;
 }
 
+// Mean/variance likelihood (J = 2): F is (2, C, N); writes l (tempered) and the untempered l, and
+// in ld (9, C, N) the tempered derivatives l_1, l_2, l_11, l_12, l_22, l_111, l_112, l_122, l_222 of
+// l = z / 2 + log(2 pi v) / 2 with r = y - F_1, w = e^{F_2}, v = delta + w, rho = w / v,
+// z = r^2 / v: l_1 = -r / v, l_2 = rho (1 - z) / 2, l_11 = 1 / v, l_12 = r rho / v,
+// l_22 = rho A / 2 with A = (1 - rho)(1 - z) + z rho, l_111 = 0, l_112 = -rho / v,
+// l_122 = r rho (1 - 2 rho) / v, l_222 = [rho (1 - rho) A + rho A'] / 2 with
+// A' = -rho (1 - rho) + z rho + 2 z rho (1 - 2 rho) (d rho / dF_2 = rho (1 - rho), dz / dF_2 = -z rho).
+__global__ void k_lik_meanvar(PrimalDev pd, const double* __restrict__ F, double* __restrict__ l0,
+                              double* __restrict__ lraw, double* __restrict__ ld) {
+  const int c = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= pd.N) return;
+  const long long CN = (long long)pd.n_chains * pd.N, o = (long long)c * pd.N + i;
+  const double r = pd.y[i] - F[o], w = exp(F[CN + o]);
+  const double v = pd.delta + w, rho = w / v, z = r * r / v;
+  const double A = (1.0 - rho) * (1.0 - z) + z * rho;
+  const double dA = -rho * (1.0 - rho) + z * rho + 2.0 * z * rho * (1.0 - 2.0 * rho);
+  const double tau = pd.tau[c];
+  const double a0 = 0.5 * z + 0.5 * log(2.0 * M_PI * v);
+  lraw[o] = a0;
+  l0[o] = tau * a0;
+  const double der[9] = {-r / v, 0.5 * rho * (1.0 - z), 1.0 / v, r * rho / v, 0.5 * rho * A, 0.0, -rho / v,
+                         r * rho * (1.0 - 2.0 * rho) / v, 0.5 * (rho * (1.0 - rho) * A + rho * dA)};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) ld[k * CN + o] = tau * der[k];
+}
+
+// r_j = sum_{k, l} l_jkl s_kl for the mean/variance model, s_kl = rowsum((Phi W_kl) o Phi) given
+// for (k, l) = (0, 0), (0, 1), (1, 1) in s (3, C, N) (s_10 = s_01): r (2, C, N).
+__global__ void k_mv_combine(PrimalDev pd, const double* __restrict__ s, const double* __restrict__ ld,
+                             double* __restrict__ r) {
+  const long long CN = (long long)pd.n_chains * pd.N;
+  const long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= CN) return;
+  const double s00 = s[o], s01 = s[CN + o], s11 = s[2 * CN + o];
+  const double t111 = ld[5 * CN + o], t112 = ld[6 * CN + o], t122 = ld[7 * CN + o], t222 = ld[8 * CN + o];
+  r[o] = t111 * s00 + 2.0 * t112 * s01 + t122 * s11;
+  r[CN + o] = t112 * s00 + 2.0 * t122 * s01 + t222 * s11;
+}
+
 // Z_c = diag(l''_c) Phi (C x N x P).
 __global__ void k_rowscale(PrimalDev pd, const double* __restrict__ l2, const double* __restrict__ Phi,
                            double* __restrict__ Z) {
@@ -106,8 +147,8 @@ __global__ void k_primal_udu(PrimalDev pd, const double* __restrict__ q, int dp,
   const int c = blockIdx.x;
   const double* qc = q + (long long)c * dp;
   double* g = dU + (long long)c * dp;
-  const int P = pd.P, MG = pd.M * pd.Dg;
-  const double u_cg = qc[P], u_sg = qc[P + 1], u_cl = qc[P + 2];
+  const int P = pd.P, JP = pd.JP, MG = pd.M * pd.Dg;
+  const double u_cg = qc[JP], u_sg = qc[JP + 1], u_cl = qc[JP + 2];
   const double el = exp(-u_cl);
   double sl0 = 0.0, slraw = 0.0;
   for (int i = threadIdx.x; i < pd.N; i += blockDim.x) {
@@ -115,10 +156,11 @@ __global__ void k_primal_udu(PrimalDev pd, const double* __restrict__ q, int dp,
     slraw += lraw[(long long)c * pd.N + i];
   }
   double pv = 0.0, gcg = 0.0, gsg = 0.0, gcl = 0.0, hcc = 0.0, hcs = 0.0, hss = 0.0, hll = 0.0;
-  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+  for (int i = threadIdx.x; i < JP; i += blockDim.x) {
     const double a = qc[i];
-    if (i < MG) {
-      const HDerivs r = h_derivs(pd, i % pd.M + 1, u_cg, u_sg);
+    const int li = i % P;  // position within its function's coefficients
+    if (li < MG) {
+      const HDerivs r = h_derivs(pd, li % pd.M + 1, u_cg, u_sg);
       const double Eh = 0.5 * a * a * r.eh - 0.5, Ehh = 0.5 * a * a * r.eh;
       pv += 0.5 * a * a * r.eh - 0.5 * r.h;
       g[i] += a * r.eh;
@@ -127,7 +169,7 @@ __global__ void k_primal_udu(PrimalDev pd, const double* __restrict__ q, int dp,
       hcc += Ehh * r.h1[0] * r.h1[0];
       hcs += Ehh * r.h1[0] * r.h1[1];
       hss += Ehh * r.h1[1] * r.h1[1] + Eh * r.hss;
-    } else if (i < MG + pd.Dl) {
+    } else if (li < MG + pd.Dl) {
       pv += 0.5 * a * a * el + 0.5 * u_cl;
       g[i] += a * el;
       gcl += -0.5 * a * a * el + 0.5;
@@ -152,11 +194,11 @@ __global__ void k_primal_udu(PrimalDev pd, const double* __restrict__ q, int dp,
     const double u[3] = {u_cg, u_sg, u_cl};
     double hv, hg[3], h2[3], h3[3];
     hyper_terms(pd, u, hv, hg, h2, h3);
-    U[c] = sl0 + pv + 0.5 * P * LOG2PI + hv;
+    U[c] = sl0 + pv + 0.5 * JP * LOG2PI + hv;
     LL[c] = -slraw;
-    g[P] = gcg + hg[0];
-    g[P + 1] = gsg + hg[1];
-    g[P + 2] = gcl + hg[2];
+    g[JP] = gcg + hg[0];
+    g[JP + 1] = gsg + hg[1];
+    g[JP + 2] = gcl + hg[2];
     double* us = ustat + (long long)c * 9;
     us[0] = hcc + h2[0];
     us[1] = us[3] = hcs;
@@ -177,13 +219,14 @@ __global__ void k_primal_hess(PrimalDev pd, const double* __restrict__ q, int dp
   if (e >= DD) return;
   const int i = (int)(e / dp), j = (int)(e % dp);
   const double* qc = q + (long long)c * dp;
-  const int P = pd.P, MG = pd.M * pd.Dg;
+  const int P = pd.P, JP = pd.JP, MG = pd.M * pd.Dg;
   double* Hc = H + c * DD;
-  if (i < P && j < P) {
+  if (i < JP && j < JP) {
     if (i == j) {
+      const int li = i % P;
       double v;
-      if (i < MG) v = h_derivs(pd, i % pd.M + 1, qc[P], qc[P + 1]).eh;
-      else if (i < MG + pd.Dl) v = exp(-qc[P + 2]);
+      if (li < MG) v = h_derivs(pd, li % pd.M + 1, qc[JP], qc[JP + 1]).eh;
+      else if (li < MG + pd.Dl) v = exp(-qc[JP + 2]);
       else v = 1.0 / pd.bias_var;
       Hc[e] += v;
     }
@@ -192,21 +235,23 @@ __global__ void k_primal_hess(PrimalDev pd, const double* __restrict__ q, int dp
   double v = 0.0;
   if (i < pd.d && j < pd.d) {
     const int r = min(i, j), s = max(i, j);
-    if (r < P) {
-      if (r < MG && s <= P + 1) {
-        const HDerivs hd = h_derivs(pd, r % pd.M + 1, qc[P], qc[P + 1]);
-        v = qc[r] * hd.eh * hd.h1[s - P];
-      } else if (r >= MG && r < MG + pd.Dl && s == P + 2) {
-        v = -qc[r] * exp(-qc[P + 2]);
+    if (r < JP) {
+      const int lr = r % P;
+      if (lr < MG && s <= JP + 1) {
+        const HDerivs hd = h_derivs(pd, lr % pd.M + 1, qc[JP], qc[JP + 1]);
+        v = qc[r] * hd.eh * hd.h1[s - JP];
+      } else if (lr >= MG && lr < MG + pd.Dl && s == JP + 2) {
+        v = -qc[r] * exp(-qc[JP + 2]);
       }
     } else {
-      v = ustat[(long long)c * 9 + (r - P) * 3 + (s - P)];
+      v = ustat[(long long)c * 9 + (r - JP) * 3 + (s - JP)];
     }
   }
   Hc[e] = v;
 }
 
-// r_c,i = tau l'''_c,i sum_j Y_c,ij Phi_ij (one warp per row; Y = Phi W[:P, :P]).
+// r_c,i = m_c,i sum_j Y_c,ij Phi_ij (one warp per row; Y = Phi W_block) with m = tau l''' for
+// J = 1, or m = 1 (l3 null) for the mean/variance model, whose r are combined afterwards.
 __global__ void k_primal_rowdot(PrimalDev pd, const double* __restrict__ Y, const double* __restrict__ Phi,
                                 const double* __restrict__ l3, double* __restrict__ r) {
   const int c = blockIdx.y;
@@ -219,7 +264,7 @@ __global__ void k_primal_rowdot(PrimalDev pd, const double* __restrict__ Y, cons
   for (int j = lane; j < pd.P; j += 32) s = fma(y[j], ph[j], s);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) r[(long long)c * pd.N + i] = l3[(long long)c * pd.N + i] * s;
+  if (lane == 0) r[(long long)c * pd.N + i] = l3 ? l3[(long long)c * pd.N + i] * s : s;
 }
 
 // The prior parts of v_i = tr(W dH_i): on entry v[c, :P] holds the likelihood part; adds the
@@ -236,20 +281,21 @@ __global__ void k_primal_contract(PrimalDev pd, const double* __restrict__ q, in
   const double* qc = q + (long long)c * dp;
   const double* Wc = W + c * DD;
   double* vc = v + (long long)c * dp;
-  const int P = pd.P, MG = pd.M * pd.Dg;
-  const double u_cg = qc[P], u_sg = qc[P + 1], u_cl = qc[P + 2];
+  const int P = pd.P, JP = pd.JP, MG = pd.M * pd.Dg;
+  const double u_cg = qc[JP], u_sg = qc[JP + 1], u_cl = qc[JP + 2];
   const double el = exp(-u_cl);
   // W on the hyperparameters
-  const double Wu[2][2] = {{Wc[(long long)P * dp + P], Wc[(long long)P * dp + P + 1]},
-                           {Wc[(long long)(P + 1) * dp + P], Wc[(long long)(P + 1) * dp + P + 1]}};
-  const double Wll = Wc[(long long)(P + 2) * dp + P + 2];
+  const double Wu[2][2] = {{Wc[(long long)JP * dp + JP], Wc[(long long)JP * dp + JP + 1]},
+                           {Wc[(long long)(JP + 1) * dp + JP], Wc[(long long)(JP + 1) * dp + JP + 1]}};
+  const double Wll = Wc[(long long)(JP + 2) * dp + JP + 2];
   double vcg = 0.0, vsg = 0.0, vcl = 0.0;
-  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+  for (int i = threadIdx.x; i < JP; i += blockDim.x) {
     const double a = qc[i];
     const double Waa = Wc[(long long)i * dp + i];
-    if (i < MG) {
-      const HDerivs r = h_derivs(pd, i % pd.M + 1, u_cg, u_sg);
-      const double Wau[2] = {Wc[(long long)i * dp + P], Wc[(long long)i * dp + P + 1]};
+    const int li = i % P;
+    if (li < MG) {
+      const HDerivs r = h_derivs(pd, li % pd.M + 1, u_cg, u_sg);
+      const double Wau[2] = {Wc[(long long)i * dp + JP], Wc[(long long)i * dp + JP + 1]};
       const double Eh = 0.5 * a * a * r.eh - 0.5, Ehh = 0.5 * a * a * r.eh, Ehhh = Ehh;
       double hjk[2][2] = {{0.0, 0.0}, {0.0, r.hss}};
       double va = 0.0, vu[2] = {0.0, 0.0};
@@ -279,8 +325,8 @@ __global__ void k_primal_contract(PrimalDev pd, const double* __restrict__ q, in
       vc[i] += va;
       vcg += vu[0];
       vsg += vu[1];
-    } else if (i < MG + pd.Dl) {
-      const double Wau = Wc[(long long)i * dp + P + 2];
+    } else if (li < MG + pd.Dl) {
+      const double Wau = Wc[(long long)i * dp + JP + 2];
       vc[i] += -2.0 * el * Wau + a * el * Wll;
       vcl += -el * Waa + 2.0 * a * el * Wau - 0.5 * a * a * el * Wll;
     }
@@ -293,9 +339,9 @@ __global__ void k_primal_contract(PrimalDev pd, const double* __restrict__ q, in
     const double u[3] = {u_cg, u_sg, u_cl};
     double hv, hg[3], h2[3], h3[3];
     hyper_terms(pd, u, hv, hg, h2, h3);
-    vc[P] = vcg + h3[0] * Wu[0][0];
-    vc[P + 1] = vsg + h3[1] * Wu[1][1];
-    vc[P + 2] = vcl + h3[2] * Wll;
+    vc[JP] = vcg + h3[0] * Wu[0][0];
+    vc[JP + 1] = vsg + h3[1] * Wu[1][1];
+    vc[JP + 2] = vcl + h3[2] * Wll;
   }
 }
 

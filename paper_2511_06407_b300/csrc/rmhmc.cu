@@ -374,6 +374,7 @@ struct rmhmc_model {
   double *rvec = nullptr;  // C x N: l''' o rowsum((Phi W) o Phi)
   double *ustat = nullptr; // C x 9: hyperparameter block of the Hessian
   double *Xg_dev = nullptr, *Xl_dev = nullptr;
+  double *ld = nullptr;    // J = 2: (9, C, N) likelihood derivatives
 };
 
 namespace {
@@ -490,21 +491,44 @@ void dual_model_layer(rmhmc_model* m, bool third) {
 // (Phi^T diag(l'') Phi + prior). The third-derivative operator needs only l''' (kept in l3).
 void primal_model_layer(rmhmc_model* m) {
   cudaStream_t s = m->stream;
-  const int N = m->N, C = m->C, dp = m->dp, P = m->pd.P;
-  const long long NP = (long long)N * P, DD = (long long)dp * dp;
+  const int N = m->N, C = m->C, dp = m->dp, P = m->pd.P, J = m->pd.J;
+  const long long NP = (long long)N * P, DD = (long long)dp * dp, CN = (long long)C * N;
   const double Nf = N, Pf = P, Cf = C;
-  PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf)
-  gemm_f64(s, false, true, C, N, P, 1.0, m->q, dp, 0, m->Phi, P, 0, 0.0, m->Fv, N, 0, 1, false, false);
-  PROF(m, CAT_MODEL, 0)
-  dev::k_lik_primal<<<dim3(nblk(N), C), 256, 0, s>>>(m->pd, m->Fv, m->l0, m->l1, m->l2, m->l3, m->lraw);
-  PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf)
-  gemm_f64(s, false, false, C, P, N, 1.0, m->l1, N, 0, m->Phi, P, 0, 0.0, m->dU, dp, 0, 1, false, false);
+  for (int j = 0; j < J; ++j) {
+    PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf)
+    gemm_f64(s, false, true, C, N, P, 1.0, m->q + j * P, dp, 0, m->Phi, P, 0, 0.0, m->Fv + j * CN, N, 0, 1,
+             false, false);
+  }
+  if (J == 1) {
+    PROF(m, CAT_MODEL, 0)
+    dev::k_lik_primal<<<dim3(nblk(N), C), 256, 0, s>>>(m->pd, m->Fv, m->l0, m->l1, m->l2, m->l3, m->lraw);
+  } else {
+    PROF(m, CAT_MODEL, 0)
+    dev::k_lik_meanvar<<<dim3(nblk(N), C), 256, 0, s>>>(m->pd, m->Fv, m->l0, m->lraw, m->ld);
+  }
+  for (int j = 0; j < J; ++j) {
+    const double* lj = J == 1 ? m->l1 : m->ld + j * CN;
+    PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf)
+    gemm_f64(s, false, false, C, P, N, 1.0, lj, N, 0, m->Phi, P, 0, 0.0, m->dU + j * P, dp, 0, 1, false, false);
+  }
   PROF(m, CAT_MODEL, 0)
   dev::k_primal_udu<<<C, 256, 0, s>>>(m->pd, m->q, dp, m->l0, m->lraw, m->U, m->dU, m->LL, m->ustat);
-  PROF(m, CAT_MODEL, 0)
-  dev::k_rowscale<<<dim3(nblk(NP), C), 256, 0, s>>>(m->pd, m->l2, m->Phi, m->Z);
-  PROF(m, CAT_GEMM, Cf * gemm_flops(Pf, Pf, Nf, true, false))
-  gemm_f64(s, true, false, P, P, N, 1.0, m->Phi, P, 0, m->Z, P, NP, 0.0, m->H, dp, DD, C, true, false);
+  // the likelihood blocks Phi^T diag(l_jk) Phi of the Hessian ((j, k) and its mirror (k, j))
+  for (int j = 0; j < J; ++j) {
+    for (int k = j; k < J; ++k) {
+      const double* ljk = J == 1 ? m->l2 : m->ld + (2 + j + k) * CN;
+      PROF(m, CAT_MODEL, 0)
+      dev::k_rowscale<<<dim3(nblk(NP), C), 256, 0, s>>>(m->pd, ljk, m->Phi, m->Z);
+      PROF(m, CAT_GEMM, Cf * gemm_flops(Pf, Pf, Nf, true, false))
+      gemm_f64(s, true, false, P, P, N, 1.0, m->Phi, P, 0, m->Z, P, NP, 0.0, m->H + (long long)j * P * dp + k * P,
+               dp, DD, C, true, false);
+      if (k != j) {
+        PROF(m, CAT_GEMM, Cf * gemm_flops(Pf, Pf, Nf, true, false))
+        gemm_f64(s, true, false, P, P, N, 1.0, m->Phi, P, 0, m->Z, P, NP, 0.0,
+                 m->H + (long long)k * P * dp + j * P, dp, DD, C, true, false);
+      }
+    }
+  }
   PROF(m, CAT_MODEL, 0)
   dev::k_primal_hess<<<dim3(nblk(DD), C), 256, 0, s>>>(m->pd, m->q, dp, m->ustat, m->H);
 }
@@ -586,16 +610,29 @@ void grad_h(rmhmc_model* m, const double* x, double* out) {
   gemm_dd(m, false, false, m->M, m->PsiT, m->Y, false);
   gemm_dd(m, true, false, m->PsiT, m->Y, m->W, true);
   if (m->kind == 1) {
-    // Sec. 2.3 ordering: v = Phi^T [l''' o rowsum((Phi W) o Phi)] + the prior parts
-    const int P = m->pd.P;
-    const long long NP = (long long)N * P;
+    // Sec. 2.3 ordering: v_j = Phi^T [sum_kl l_jkl o rowsum((Phi W_kl) o Phi)] + the prior parts
+    const int P = m->pd.P, J = m->pd.J;
+    const long long NP = (long long)N * P, CN = (long long)C * N;
     const double Nf = N, Pf = P;
-    PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf * Pf)
-    gemm_f64(s, false, false, N, P, P, 1.0, m->Phi, P, 0, m->W, dp, DD, 0.0, m->Z, P, NP, C, false, false);
-    PROF(m, CAT_CONTRACT, 2.0 * Cf * Nf * Pf)
-    dev::k_primal_rowdot<<<dim3((N + 7) / 8, C), 256, 0, s>>>(m->pd, m->Z, m->Phi, m->l3, m->rvec);
-    PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf)
-    gemm_f64(s, false, false, C, P, N, 1.0, m->rvec, N, 0, m->Phi, P, 0, 0.0, m->vtr, dp, 0, 1, false, false);
+    for (int j = 0; j < J; ++j) {
+      for (int k = j; k < J; ++k) {
+        PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf * Pf)
+        gemm_f64(s, false, false, N, P, P, 1.0, m->Phi, P, 0, m->W + (long long)j * P * dp + k * P, dp, DD, 0.0,
+                 m->Z, P, NP, C, false, false);
+        PROF(m, CAT_CONTRACT, 2.0 * Cf * Nf * Pf)
+        dev::k_primal_rowdot<<<dim3((N + 7) / 8, C), 256, 0, s>>>(m->pd, m->Z, m->Phi, J == 1 ? m->l3 : nullptr,
+                                                                   m->rvec + (j + k) * CN);
+      }
+    }
+    if (J == 2) {
+      PROF(m, CAT_CONTRACT, 0)
+      dev::k_mv_combine<<<nblk(CN), 256, 0, s>>>(m->pd, m->rvec, m->ld, m->rvec + 3 * CN);
+    }
+    for (int j = 0; j < J; ++j) {
+      PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf)
+      gemm_f64(s, false, false, C, P, N, 1.0, m->rvec + (J == 1 ? 0 : (3 + j) * CN), N, 0, m->Phi, P, 0, 0.0,
+               m->vtr + j * P, dp, 0, 1, false, false);
+    }
     PROF(m, CAT_CONTRACT, 0)
     dev::k_primal_contract<<<C, 256, 0, s>>>(m->pd, m->q, dp, m->W, m->vtr);
   } else {
@@ -658,11 +695,13 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
     const size_t P = (size_t)m->pd.P;
     if (m->pd.Dg) ALLOC(m->Xg_dev, (size_t)N * m->pd.Dg);
     if (m->pd.Dl) ALLOC(m->Xl_dev, (size_t)N * m->pd.Dl);
+    const size_t J = (size_t)m->pd.J;
     ALLOC(m->Phi, (size_t)N * P);
     ALLOC(m->Z, (size_t)C * N * P);
-    ALLOC(m->Fv, (size_t)C * N);
-    ALLOC(m->rvec, (size_t)C * N);
+    ALLOC(m->Fv, J * C * N);
+    ALLOC(m->rvec, (J == 1 ? 1 : 5) * (size_t)C * N);  // J = 2: s_00, s_01, s_11, r_0, r_1
     ALLOC(m->ustat, (size_t)C * 9);
+    if (J == 2) ALLOC(m->ld, (size_t)9 * C * N);
   } else {
     ALLOC(m->X_dev, (size_t)N * n_cov);
     ALLOC(m->uf_dev, (size_t)2 * n);
@@ -1113,9 +1152,13 @@ rmhmc_status validate_primal(const rmhmc_primal_desc* desc, int n_chains, const 
   if (desc->n_gauss < 0 || desc->n_linear < 0 || desc->n_gauss + desc->n_linear < 1) return RMHMC_EINVAL;
   if ((desc->n_gauss > 0 && !desc->Xg) || (desc->n_linear > 0 && !desc->Xl)) return RMHMC_EINVAL;
   if (desc->n_gauss > 0 && (desc->M < 1 || !(desc->L > 0.0))) return RMHMC_EINVAL;
-  const long long d = (long long)(desc->n_gauss > 0 ? desc->M : 0) * desc->n_gauss + desc->n_linear + 4;
+  if (desc->J != 1 && desc->J != 2) return RMHMC_EINVAL;
+  const long long d =
+      desc->J * ((long long)(desc->n_gauss > 0 ? desc->M : 0) * desc->n_gauss + desc->n_linear + 1) + 3;
   if (d > 4096) return RMHMC_EINVAL;
-  if (desc->lik != RMHMC_LIK_BERNOULLI_LOGIT && desc->lik != RMHMC_LIK_GAUSSIAN) return RMHMC_EINVAL;
+  if (desc->J == 1 && desc->lik != RMHMC_LIK_BERNOULLI_LOGIT && desc->lik != RMHMC_LIK_GAUSSIAN)
+    return RMHMC_EINVAL;
+  if (desc->J == 2 && (desc->lik != RMHMC_LIK_MEANVAR || !(desc->delta >= 0.0))) return RMHMC_EINVAL;
   if (desc->lik == RMHMC_LIK_GAUSSIAN && !(desc->noise_var > 0.0)) return RMHMC_EINVAL;
   if (!(desc->bias_var > 0.0)) return RMHMC_EINVAL;
   for (int j = 0; j < 3; ++j)
@@ -1136,7 +1179,10 @@ void setup_primal(rmhmc_model* m, const rmhmc_primal_desc* desc, int n_chains, v
   pd.Dl = desc->n_linear;
   pd.M = desc->n_gauss > 0 ? desc->M : 0;
   pd.P = pd.M * pd.Dg + pd.Dl + 1;
-  pd.d = pd.P + 3;
+  pd.J = desc->J;
+  pd.JP = pd.J * pd.P;
+  pd.d = pd.JP + 3;
+  pd.delta = desc->delta;
   pd.dp = ((pd.d + kJacSB - 1) / kJacSB) * kJacSB;
   pd.lik = desc->lik;
   pd.n_chains = n_chains;

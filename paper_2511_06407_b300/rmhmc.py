@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "librmhmc.so")
 
 MAX_COLS = 16
 KINDS = {"se": 0, "linear": 1, "overlap": 2}
-LIKS = {"bernoulli": 0, "gaussian": 1}
+LIKS = {"bernoulli": 0, "gaussian": 1, "meanvar": 2}
 GKINDS = {"coth": 0, "sqrt": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 JACOBI_RULES = {"metric": 0, "relative": 1}
@@ -41,7 +41,7 @@ class PrimalDesc(ctypes.Structure):
     _fields_ = [("N", c_int), ("n_gauss", c_int), ("n_linear", c_int), ("Xg", POINTER(c_double)),
                 ("Xl", POINTER(c_double)), ("y", POINTER(c_double)), ("lik", c_int),
                 ("noise_var", c_double), ("M", c_int), ("L", c_double), ("bias_var", c_double),
-                ("prior_a", c_double * 3), ("prior_b", c_double * 3)]
+                ("prior_a", c_double * 3), ("prior_b", c_double * 3), ("J", c_int), ("delta", c_double)]
 
 
 class IntegratorC(ctypes.Structure):
@@ -199,7 +199,8 @@ def _primal_desc(problem):
                       y.ctypes.data_as(POINTER(c_double)), LIKS[problem["lik"]], float(problem["noise_var"]),
                       int(problem["M"]), float(problem["L"]), float(problem["bias_var"]),
                       (c_double * 3)(*[float(v) for v in problem["prior_a"]]),
-                      (c_double * 3)(*[float(v) for v in problem["prior_b"]]))
+                      (c_double * 3)(*[float(v) for v in problem["prior_b"]]),
+                      int(problem.get("J", 1)), float(problem.get("delta", 0.0)))
     return desc, [y, Xg, Xl]
 
 

@@ -97,12 +97,16 @@ def test_invalid_descriptions_are_rejected_without_a_gpu():
     assert L.rmhmc_init_primal(ctypes.byref(pd), 1, None, None, ctypes.byref(out)) == 1
     y = (ctypes.c_double * 10)()
     xg = (ctypes.c_double * 10)()
-    pd.y, pd.Xg, pd.n_gauss, pd.M, pd.L, pd.bias_var = y, xg, 1, 5000, 8.0, 1.0
+    pd.y, pd.Xg, pd.n_gauss, pd.M, pd.L, pd.bias_var, pd.J = y, xg, 1, 5000, 8.0, 1.0, 1
     pd.prior_a[:] = [2.0, 2.0, 2.0]
     pd.prior_b[:] = [2.0, 2.0, 2.0]
     size = ctypes.c_size_t()
     assert L.rmhmc_plan_bytes_primal(ctypes.byref(pd), 1, ctypes.byref(size)) == 1
     pd.M = 30
     assert L.rmhmc_plan_bytes_primal(ctypes.byref(pd), 2, ctypes.byref(size)) == 0 and size.value > 0
+    pd.J = 2  # the mean/variance model needs its own likelihood
+    assert L.rmhmc_plan_bytes_primal(ctypes.byref(pd), 2, ctypes.byref(size)) == 1
+    pd.lik, pd.delta = 2, 0.05
+    assert L.rmhmc_plan_bytes_primal(ctypes.byref(pd), 2, ctypes.byref(size)) == 0
     pd.prior_b[1] = 0.0
     assert L.rmhmc_plan_bytes_primal(ctypes.byref(pd), 2, ctypes.byref(size)) == 1

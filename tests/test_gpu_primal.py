@@ -177,3 +177,48 @@ def test_primal_mixed_precision(rm, oracle_model):
         geo = Geometry(m, Q[c], 1.0, 1.0, "sqrt")
         fails += _compare("primal/mixed", got, c, geo, P[c], ("U", "dU", "H", "dHdq", "Ginv_p", "Ham"), base)
     assert not fails, fails
+
+
+@pytest.mark.parametrize("gkind,alpha", [("sqrt", 1.0), ("coth", 1e6)])
+def test_meanvar_geometry_and_gradient_parity(rm, oracle_model, gkind, alpha):
+    """The mean/variance model (Example 1, J = 2: y ~ N(F_1, delta + exp F_2), both functions on
+    the same features, shared hyperparameters): every geometric quantity."""
+    prob = wl.meanvar_regression(2, N=60, seed=4, M=8, n_linear=1)
+    C = 3
+    Q = wl.random_state(prob, C, seed=14, f_scale=0.3, u_scale=0.2)
+    Q[0] = 0.0
+    P = wl.random_momentum(prob, C, seed=15)
+    tau = [1.0, 0.5, 0.2]
+    got = _geometry(rm, prob, Q, P, tau, rm.Integrator(g_kind=gkind, alpha=alpha, jacobi_rule="relative"))
+    m = oracle_model(prob)
+    assert m.J == 2 and got["U"].shape == (C,)
+    fails = []
+    for c in range(C):
+        geo = Geometry(m, Q[c], tau[c], alpha, gkind)
+        fails += _compare(f"meanvar/{gkind}", got, c, geo, P[c], tuple(BASE), BASE)
+    assert not fails, fails
+
+
+def test_meanvar_sampler_decisions(rm, oracle_model):
+    """Algorithm 1 on the J = 2 model (D = 1, N = 80, M = 12, d = 29) from all-zero coefficients
+    and theta = 1 (eps = 0.05, L = 10, g = sqrt(1 + l^2)): the first proposal diverges and is
+    rejected, the next five are accepted, as in the oracle, along the same chain."""
+    prob = wl.meanvar_regression(1, N=80, seed=1, M=12)
+    m = oracle_model(prob)
+    n_iter, eps = 6, 0.05
+    ref = sample(m, np.zeros(m.d), n_iter, 0, seed=0, chain=0, eps=eps, n_leapfrog=10, n_fp=6,
+                 alpha=1.0, gkind="sqrt")
+    integ = rm.Integrator(eps=eps, n_leapfrog=10, n_fp=6, g_kind="sqrt", alpha=1.0)
+    model = rm.Model(prob, 1)
+    model.set_state(torch.zeros(1, m.d, dtype=torch.float64, device="cuda"), integ=integ)
+    f64 = dict(dtype=torch.float64, device="cuda")
+    qs, lp = torch.empty(n_iter, 1, m.d, **f64), torch.empty(n_iter, 1, **f64)
+    acc = torch.empty(n_iter, 1, dtype=torch.int32, device="cuda")
+    model.sample(n_iter, 0, 0, qs, lp, acc, integ=integ)
+    torch.cuda.synchronize()
+    print("accept oracle", ref["accept"], "gpu", acc.cpu().numpy()[:, 0])
+    np.testing.assert_array_equal(acc.cpu().numpy()[:, 0].astype(bool), ref["accept"])
+    assert ref["accept"].any() and not ref["accept"].all()
+    q = qs.cpu().numpy()[:, 0]
+    for i in range(n_iter):
+        assert np.linalg.norm(q[i] - ref["q"][i]) <= 1e-8 * max(np.linalg.norm(ref["q"][i]), 1.0), i
