@@ -437,21 +437,36 @@ def run_propensity(args):
 
 
 def run_ess(args):
-    """Effective samples per second of Algorithm 1 on the GP-classification problem (L = 10,
-    n_fp = 6), plain FP64 and mixed precision, independent seeds, plus the matched-error check:
-    posterior means and variances of (log P, u, mean f) of the mixed run within 3 Monte-Carlo
-    standard errors of the FP64 run's."""
+    """Effective samples per second of Algorithm 1 (L = 10, n_fp = 6), plain FP64 and mixed
+    precision, independent seeds, plus the matched-error check: posterior means and variances of
+    (log P, hyperparameters, mean F) of the mixed run within 3 Monte-Carlo standard errors of the
+    FP64 run's. --ess-model dual: the GP-classification problem (N = --ess-n, SoftAbs coth);
+    primal (default): the simulated data of Sec. 2.5 with D = --ess-d Gaussian kernels
+    (d = 30 D + 4, g = sqrt(1 + l^2)), the paper's own experimental model."""
     import torch
     from paper_2511_06407_b300 import build, rmhmc
     from paper_2511_06407_b300 import diagnostics as dg
     build.build()
-    N, C = args.ess_n, args.chains
-    prob = wl.gp_classification(N, seed=0)
-    eps = args.eps or 0.01
-    names = ["log P", "log c", "log l", "mean f"]
+    C = args.chains
+    if args.ess_model == "dual":
+        N = args.ess_n
+        prob = wl.gp_classification(N, seed=0)
+        eps = args.eps or 0.01
+        geom = {}
+        names = ["log P", "log c", "log l", "mean f"]
+        label = f"GP classification N={N} (d={N + 2})"
+        hyper = slice(-2, None)
+    else:
+        N = 500
+        prob = wl.solin_logistic(args.ess_d, N=N, seed=0)
+        eps = args.eps or 0.05
+        geom = dict(g_kind="sqrt", alpha=1.0)
+        names = ["log P", "log c_g", "log s_g", "b"]
+        label = f"primal model of Sec. 2.5, D={args.ess_d} (d={wl.dims(prob)[2]}), N=500, g=sqrt(1+l^2)"
+        hyper = slice(-3, -1)
     runs = {}
     for k, prec in enumerate(("fp64", "mixed")):
-        integ = rmhmc.Integrator(eps=eps, n_leapfrog=10, n_fp=N_FP, precision=prec)
+        integ = rmhmc.Integrator(eps=eps, n_leapfrog=10, n_fp=N_FP, precision=prec, **geom)
         model = rmhmc.Model(prob, C)
         d = model.d
         model.set_state(torch.zeros(C, d, dtype=torch.float64, device="cuda"), integ=integ)
@@ -465,7 +480,9 @@ def run_ess(args):
         el, clk = _clock_and_time(lambda: model.sample(args.iters, 0, seed, qs, lp, acc, chain_status=cs2,
                                                        integ=integ), 0)
         Q, LP = qs.cpu().numpy(), lp.cpu().numpy()
-        draws = np.concatenate([LP[:, :, None], Q[:, :, -2:], Q[:, :, :N].mean(axis=2, keepdims=True)], axis=2)
+        # the fourth quantity: the mean latent value (dual) or the bias b (primal)
+        last = Q[:, :, :N].mean(axis=2, keepdims=True) if args.ess_model == "dual" else Q[:, :, -4:-3]
+        draws = np.concatenate([LP[:, :, None], Q[:, :, hyper], last], axis=2)
         summ = dg.summary(draws, names)
         x = draws.transpose(1, 0, 2)  # chains x iterations x quantities
         mean = x.reshape(-1, 4).mean(axis=0)
@@ -476,6 +493,9 @@ def run_ess(args):
                       "max_rhat": summ["max_rhat"], "acceptance": float(acc.cpu().numpy().mean()),
                       "substeps_per_s": C * args.iters * 10 * SUBSTEPS_PER_LEAPFROG / el,
                       "chain_status_nonzero": int(((cs | cs2).cpu().numpy() != 0).sum()),
+                      "chain_status_bits": {name: int((((cs | cs2).cpu().numpy() & bit) != 0).sum())
+                                            for name, bit in (("not_pd", 1), ("jacobi_not_converged", 2),
+                                                              ("non_finite", 4))},
                       "ess": {r["name"]: round(min(r["ess_bulk"], r["ess_tail"]), 1) for r in summ["rows"]},
                       "mean": mean, "var": var, "se_mean": se_mean, "se_var": se_var, "clocks": clk}
         model.close()
@@ -486,10 +506,10 @@ def run_ess(args):
     for r in runs.values():
         for key in ("mean", "var", "se_mean", "se_var"):
             r[key] = [round(float(v), 6) for v in r[key]]
-    print(json.dumps({"metric": "effective samples/s (min over log P, u, mean f; bulk and tail ESS)",
+    print(json.dumps({"metric": "effective samples/s (min over log P, hyperparameters and a mean coordinate; bulk and tail ESS)",
                       "value": b["ess_per_s"], "unit": "ESS/s", "n_gpus": 1, "higher_is_better": True,
                       "dtype": "f64; Jacobi rotations f32x2 (double-float)", "data": "synthetic",
-                      "config": {"workload": f"GP classification N={N} (d={N + 2}), {C} chains, eps={eps}, L=10, "
+                      "config": {"workload": f"{label}, {C} chains, eps={eps}, L=10, "
                                              f"n_fp=6, {args.burn} burn-in + {args.iters} kept iterations",
                                  "quantities": names},
                       "fp64": runs["fp64"], "mixed": runs["mixed"],
@@ -633,7 +653,9 @@ def main():
                     help="both (default): the mixed form is the headline, timed beside the plain FP64 path "
                          "on the same workload, with the trajectory error between them")
     ap.add_argument("--problems", type=int, default=16)
-    ap.add_argument("--ess-n", type=int, default=100, help="inputs N of the ESS workload")
+    ap.add_argument("--ess-n", type=int, default=100, help="inputs N of the dual ESS workload")
+    ap.add_argument("--ess-model", default="primal", choices=["primal", "dual"])
+    ap.add_argument("--ess-d", type=int, default=4, help="Gaussian kernels D of the primal ESS workload")
     ap.add_argument("--solin-d", type=int, default=16, help="Gaussian kernels D of the solin workload (d = 30 D + 4)")
     ap.add_argument("--iters", type=int, default=200, help="kept iterations of the ESS workload")
     ap.add_argument("--burn", type=int, default=100, help="burn-in iterations of the ESS workload")

@@ -950,7 +950,7 @@ const char* rmhmc_status_string(rmhmc_status s) {
   return "unknown status";
 }
 
-const char* rmhmc_version(void) { return "rmhmc sm_103a fp64"; }
+const char* rmhmc_version(void) { return "rmhmc sm_103a fp64 + f32x2"; }
 
 
 rmhmc_status rmhmc_fp64_peak(void* cuda_stream, int ms_target, double* tflops_host) {
