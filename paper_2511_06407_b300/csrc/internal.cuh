@@ -78,10 +78,13 @@ struct GeomDev {
 void gemm_f64(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
               int lda, long long sA, const double* B, int ldb, long long sB, double beta, double* C,
               int ldc, long long sC, int batch, bool sym, bool tri);
-// The same product in double-float arithmetic (FP32 pairs, Dot2 accumulation; no tri form).
+// The same product in double-float arithmetic (FP32 pairs, Dot2 accumulation; no tri form). With
+// a_pairs / b_pairs the operand already holds (hi, lo) pairs (to_pairs) in its double-sized slots.
 void gemm_df(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
              int lda, long long sA, const double* B, int ldb, long long sB, double beta, double* C,
-             int ldc, long long sC, int batch, bool sym);
+             int ldc, long long sC, int batch, bool sym, bool a_pairs = false, bool b_pairs = false);
+// Split n doubles into (hi, lo) FP32 pairs, written into the same-sized buffer `pairs`.
+void to_pairs(cudaStream_t s, const double* x, double* pairs, long long n);
 // In-place lower Cholesky of batch N x N matrices (row-major, ld = N); writes log|K| to
 // logdet[b * logdet_stride] and sets status bit RMHMC_CHAIN_NOTPD in status[b / per_chain].
 void cholesky_f64(cudaStream_t s, double* A, int N, int batch, double* logdet, int logdet_stride,

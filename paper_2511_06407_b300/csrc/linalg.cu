@@ -360,7 +360,7 @@ namespace {
 // are split into FP32 pairs as they are staged in shared memory, every output accumulates a Dot2
 // sum (hi word + compensation word), and the result is rounded back to FP64. Thread (ty, tx) owns
 // rows ty + 16 i and columns tx + 16 j of the 64 x 64 tile, as in k_gemm.
-template <bool TA, bool TB>
+template <bool TA, bool TB, bool AP, bool BP>
 __global__ void __launch_bounds__(GT, 2) k_gemm_df(int m, int n, int k, double alpha,
                                                 const double* __restrict__ A, int lda, long long sA,
                                                 const double* __restrict__ B, int ldb, long long sB,
@@ -386,18 +386,18 @@ __global__ void __launch_bounds__(GT, 2) k_gemm_df(int m, int n, int k, double a
       int mm, kk;
       if (TA) { kk = e / BM; mm = e % BM; } else { mm = e / BK; kk = e % BK; }
       const int gr = row0 + mm, gk = k0 + kk;
-      double v = 0.0;
-      if (gr < m && gk < k) v = TA ? A[(long long)gk * lda + gr] : A[(long long)gr * lda + gk];
-      As[kk][mm] = df_split(v);
+      const long long o = TA ? (long long)gk * lda + gr : (long long)gr * lda + gk;
+      if (AP) As[kk][mm] = (gr < m && gk < k) ? reinterpret_cast<const float2*>(A)[o] : make_float2(0.f, 0.f);
+      else As[kk][mm] = df_split((gr < m && gk < k) ? A[o] : 0.0);
     }
 #pragma unroll
     for (int e = tid; e < BN * BK; e += GT) {
       int kk, nn;
       if (TB) { nn = e / BK; kk = e % BK; } else { kk = e / BN; nn = e % BN; }
       const int gk = k0 + kk, gc = col0 + nn;
-      double v = 0.0;
-      if (gk < k && gc < n) v = TB ? B[(long long)gc * ldb + gk] : B[(long long)gk * ldb + gc];
-      Bs[kk][nn] = df_split(v);
+      const long long o = TB ? (long long)gc * ldb + gk : (long long)gk * ldb + gc;
+      if (BP) Bs[kk][nn] = (gk < k && gc < n) ? reinterpret_cast<const float2*>(B)[o] : make_float2(0.f, 0.f);
+      else Bs[kk][nn] = df_split((gk < k && gc < n) ? B[o] : 0.0);
     }
     __syncthreads();
 #pragma unroll 4
@@ -438,21 +438,48 @@ __global__ void __launch_bounds__(GT, 2) k_gemm_df(int m, int n, int k, double a
 
 }  // namespace
 
-void gemm_df(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
-             int lda, long long sA, const double* B, int ldb, long long sB, double beta, double* C,
-             int ldc, long long sC, int batch, bool sym) {
-  if (m <= 0 || n <= 0 || batch <= 0) return;
-  dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, batch);
+namespace {
+template <bool AP, bool BP>
+void gemm_df_launch(cudaStream_t s, bool ta, bool tb, dim3 grid, int m, int n, int k, double alpha,
+                    const double* A, int lda, long long sA, const double* B, int ldb, long long sB,
+                    double beta, double* C, int ldc, long long sC, bool sym) {
   if (!ta && !tb)
-    k_gemm_df<false, false><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
+    k_gemm_df<false, false, AP, BP><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
   else if (!ta && tb)
-    k_gemm_df<false, true><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
+    k_gemm_df<false, true, AP, BP><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
   else if (ta && !tb)
-    k_gemm_df<true, false><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
+    k_gemm_df<true, false, AP, BP><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
   else
-    k_gemm_df<true, true><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
+    k_gemm_df<true, true, AP, BP><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
 }
 
+// x (double) -> (hi, lo) pairs, element for element (the pair buffer has the double layout).
+__global__ void k_to_pairs(const double* __restrict__ x, float2* __restrict__ y, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    y[e] = df_split(x[e]);
+}
+}  // namespace
+
+void gemm_df(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
+             int lda, long long sA, const double* B, int ldb, long long sB, double beta, double* C,
+             int ldc, long long sC, int batch, bool sym, bool a_pairs, bool b_pairs) {
+  if (m <= 0 || n <= 0 || batch <= 0) return;
+  dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, batch);
+  if (a_pairs && b_pairs)
+    gemm_df_launch<true, true>(s, ta, tb, grid, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
+  else if (a_pairs)
+    gemm_df_launch<true, false>(s, ta, tb, grid, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
+  else if (b_pairs)
+    gemm_df_launch<false, true>(s, ta, tb, grid, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
+  else
+    gemm_df_launch<false, false>(s, ta, tb, grid, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
+}
+
+void to_pairs(cudaStream_t s, const double* x, double* pairs, long long n) {
+  if (n <= 0) return;
+  const long long blocks = (n + 255) / 256;
+  k_to_pairs<<<(unsigned)(blocks < 148 * 16 ? blocks : 148 * 16), 256, 0, s>>>(x, reinterpret_cast<float2*>(pairs), n);
+}
 
 void cholsolve_f64(cudaStream_t s, const double* L, const double* f, double* t, double* a, int N,
                    int batch) {

@@ -375,6 +375,10 @@ struct rmhmc_model {
   double *ustat = nullptr; // C x 9: hyperparameter block of the Hessian
   double *Xg_dev = nullptr, *Xl_dev = nullptr;
   double *ld = nullptr;    // J = 2: (9, C, N) likelihood derivatives
+  // the mixed form's double-float GEMM operands, split once into (hi, lo) pairs: Psi^T (refreshed
+  // whenever Psi^T has changed since) and one scratch operand
+  double *pPsi = nullptr, *pA = nullptr;
+  bool psi_pairs_ok = false;
 };
 
 namespace {
@@ -540,6 +544,7 @@ void eval_geometry(rmhmc_model* m, bool third) {
   cudaStream_t s = m->stream;
   const int C = m->C, dp = m->dp, d = m->d;
   const long long DD = (long long)dp * dp;
+  m->psi_pairs_ok = false;  // Gram-Schmidt or the cold start may change Psi^T below
   if (m->kind == 1) primal_model_layer(m);
   else dual_model_layer(m, third);
   // Sec. 2.4: Gram-Schmidt of Psi every reorth_every eigen-updates, then M = Psi^T H Psi
@@ -563,6 +568,7 @@ void eval_geometry(rmhmc_model* m, bool third) {
     jacobi_f64(s, m->M, m->PsiT, m->lam, dp, d, C, m->jacobi_rule, m->tol, m->max_sweeps, m->status,
                m->sweeps_last, m->sweeps_acc, m->jw, m->cluster);
   }
+  m->psi_pairs_ok = false;  // the eigen-update rotated Psi^T
   PROF(m, CAT_VECTOR, 0)
   k_inc<<<nblk(C), 256, 0, s>>>(m->eig_count, C, m->sweeps_total, m->sweeps_last);
   PROF(m, CAT_VECTOR, 0)
@@ -571,11 +577,28 @@ void eval_geometry(rmhmc_model* m, bool third) {
 
 void gemm_dd(rmhmc_model* m, bool ta, bool tb, const double* A, const double* B, double* out, bool sym) {
   const int dp = m->dp;
-  const long long DD = (long long)dp * dp;
+  const long long DD = (long long)dp * dp, n = m->C * DD;
   const double df = m->d, fl = m->C * gemm_flops(df, df, df, sym, false);
   if (m->precision == RMHMC_MIXED) {
+    // every one of these products has Psi^T as one operand: its pairs are reused until Psi^T
+    // changes, the other operand is split into scratch (one pass instead of one per tile load)
+    const double* Ap = m->pA;
+    const double* Bp = m->pA;
+    if (A == m->PsiT || B == m->PsiT) {
+      if (!m->psi_pairs_ok) {
+        PROF(m, CAT_GEMM_DF, 0)
+        to_pairs(m->stream, m->PsiT, m->pPsi, n);
+        m->psi_pairs_ok = true;
+      }
+      if (A == m->PsiT) Ap = m->pPsi;
+      if (B == m->PsiT) Bp = m->pPsi;
+    }
+    if (A != m->PsiT || B != m->PsiT) {
+      PROF(m, CAT_GEMM_DF, 0)
+      to_pairs(m->stream, A != m->PsiT ? A : B, m->pA, n);
+    }
     PROF(m, CAT_GEMM_DF, fl)
-    gemm_df(m->stream, ta, tb, dp, dp, dp, 1.0, A, dp, DD, B, dp, DD, 0.0, out, dp, DD, m->C, sym);
+    gemm_df(m->stream, ta, tb, dp, dp, dp, 1.0, Ap, dp, DD, Bp, dp, DD, 0.0, out, dp, DD, m->C, sym, true, true);
   } else {
     PROF(m, CAT_GEMM, fl)
     gemm_f64(m->stream, ta, tb, dp, dp, dp, 1.0, A, dp, DD, B, dp, DD, 0.0, out, dp, DD, m->C, sym, false);
@@ -732,6 +755,8 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
   ALLOC(m->W, C * DD);
   ALLOC(m->Y, C * DD);
   ALLOC(m->PsiT_save, C * DD);
+  ALLOC(m->pPsi, C * DD);
+  ALLOC(m->pA, C * DD);
   double** vecs[] = {&m->q, &m->p, &m->ph, &m->q0, &m->v0, &m->vk, &m->t1, &m->dU, &m->dHdq,
                      &m->lam, &m->g, &m->gp, &m->q_save, &m->z, &m->vtr, &m->xin};
   for (double** v : vecs) ALLOC(*v, (size_t)C * dp);
