@@ -80,9 +80,12 @@ __global__ void __launch_bounds__(GT) k_gemm(int m, int n, int k, double alpha,
       const int c = col0 + tx + 16 * j;
       if (c >= n) continue;
       if (sym) {
+        // the lower element (r >= c) is read and written here, its mirror only written: C must
+        // be symmetric on entry when beta != 0 (every lower element belongs to one CTA)
         if (tm == tn && c > r) continue;
-        const double v = alpha * acc[i][j];
-        C[(long long)r * ldc + c] = v;
+        const long long o = (long long)r * ldc + c;
+        const double v = alpha * acc[i][j] + (beta != 0.0 ? beta * C[o] : 0.0);
+        C[o] = v;
         if (c != r) C[(long long)c * ldc + r] = v;
       } else {
         const long long o = (long long)r * ldc + c;
@@ -97,6 +100,72 @@ constexpr int CB = 32;  // Cholesky / triangular-inverse block
 // In-place right-looking blocked Cholesky (lower) of one N x N matrix per CTA; the strict upper
 // triangle is zeroed. A pivot that is not positive marks the chain and is replaced by 1 so that
 // the factor stays finite.
+// One panel step of the blocked right-looking Cholesky, one CTA per matrix: factor the kb x kb
+// diagonal block at (k0, k0) in shared memory, solve the panel below it (L21 = A21 L11^-T, a row
+// per thread) and add the block's share of log|A|. The trailing update A22 -= L21 L21^T between
+// panel steps is a batched symmetric GEMM over all matrices (so every SM takes part), and the last
+// step zeroes the strict upper triangle. A non-positive pivot is replaced by 1 and flags the chain.
+__global__ void __launch_bounds__(256) k_chol_panel(double* __restrict__ Ab, int N, int k0,
+                                                   double* __restrict__ logdet, int lds,
+                                                   int* __restrict__ status, int per_chain) {
+  const int b = blockIdx.x;
+  double* A = Ab + (long long)b * N * N;
+  __shared__ double Dk[CB][CB + 1];
+  __shared__ int bad;
+  __shared__ double ldacc;
+  const int tid = threadIdx.x;
+  const int kb = min(CB, N - k0);
+  if (tid == 0) { bad = 0; ldacc = 0.0; }
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e % kb;
+    Dk[i][j] = A[(long long)(k0 + i) * N + k0 + j];
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (tid == 0) {
+      double piv = Dk[j][j];
+      if (!(piv > 0.0) || !isfinite(piv)) { bad = 1; piv = 1.0; }
+      const double r = sqrt(piv);
+      Dk[j][j] = r;
+      ldacc += log(r);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < kb; i += blockDim.x) Dk[i][j] /= Dk[j][j];
+    __syncthreads();
+    const int rem = kb - j - 1;
+    for (int e = tid; e < rem * rem; e += blockDim.x) {
+      const int i = j + 1 + e / rem, l = j + 1 + e % rem;
+      if (l <= i) Dk[i][l] -= Dk[i][j] * Dk[l][j];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e % kb;
+    A[(long long)(k0 + i) * N + k0 + j] = (j <= i) ? Dk[i][j] : 0.0;
+  }
+  for (int i = k0 + kb + tid; i < N; i += blockDim.x) {
+    double x[CB];
+    for (int j = 0; j < kb; ++j) {
+      double v = A[(long long)i * N + k0 + j];
+      for (int p = 0; p < j; ++p) v -= x[p] * Dk[j][p];
+      x[j] = v / Dk[j][j];
+    }
+    for (int j = 0; j < kb; ++j) A[(long long)i * N + k0 + j] = x[j];
+  }
+  if (tid == 0) {
+    double* ld = logdet + (long long)b * lds;
+    *ld = (k0 == 0 ? 0.0 : *ld) + 2.0 * ldacc;
+    if (bad) atomicOr(&status[b / per_chain], RMHMC_CHAIN_NOTPD);
+  }
+  if (k0 + kb >= N) {
+    __syncthreads();
+    for (long long e = tid; e < (long long)N * N; e += blockDim.x) {
+      const int i = (int)(e / N), j = (int)(e % N);
+      if (j > i) A[e] = 0.0;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_chol(double* __restrict__ Ab, int N,
                                              double* __restrict__ logdet, int lds,
                                              int* __restrict__ status, int per_chain) {
@@ -505,7 +574,18 @@ void gemm_f64(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alph
 void cholesky_f64(cudaStream_t s, double* A, int N, int batch, double* logdet, int logdet_stride,
                   int* status, int per_chain) {
   if (batch <= 0) return;
-  k_chol<<<batch, 256, 0, s>>>(A, N, logdet, logdet_stride, status, per_chain);
+  if (N <= 2 * CB) {  // small: one CTA per matrix does it all
+    k_chol<<<batch, 256, 0, s>>>(A, N, logdet, logdet_stride, status, per_chain);
+    return;
+  }
+  const long long NN = (long long)N * N;
+  for (int k0 = 0; k0 < N; k0 += CB) {
+    k_chol_panel<<<batch, 256, 0, s>>>(A, N, k0, logdet, logdet_stride, status, per_chain);
+    const int k1 = k0 + CB;
+    if (k1 < N)
+      gemm_f64(s, false, true, N - k1, N - k1, CB, -1.0, A + (long long)k1 * N + k0, N, NN,
+               A + (long long)k1 * N + k0, N, NN, 1.0, A + (long long)k1 * N + k1, N, NN, batch, true, false);
+  }
 }
 
 void trinv_lower_f64(cudaStream_t s, const double* L, double* X, int N, int batch) {
