@@ -35,8 +35,8 @@ N_INPUTS, N_CHAINS, EPS, N_FP = 400, 64, 0.005, 6
 # profiles/k_jacobi_N400_8chains.md and profiles/k_jacobi_df_N400_8chains.md (8 chains, mean of the
 # two captured launches; traffic grows with the number of chains, so a 64-chain launch is scaled
 # by 64 / 8).
-JACOBI_DRAM_BYTES_PER_CHAIN = {"jacobi_f64": (22.252e6 + 0.5 * (1.828e6 + 1.670e6)) / 8,
-                               "jacobi_df": (22.269e6 + 0.5 * (1.636e6 + 1.591e6)) / 8}
+JACOBI_DRAM_BYTES_PER_CHAIN = {"jacobi_f64": (22.318e6 + 1.891e6) / 8,
+                               "jacobi_df": (22.271e6 + 1.729e6) / 8}
 SUBSTEPS_PER_LEAPFROG = 2 * N_FP + 1
 METRIC = "RMHMC leapfrog substeps/s"
 UNIT = "substeps/s"
@@ -217,12 +217,11 @@ def _roofline(rmhmc, prof, C):
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_flops, dom_launches = prof[dom]
     if dom in ("jacobi_df", "gemm_df"):
-        # a double-float multiply-add (Dot2 step) is 12 FP32 instructions issuing at the FFMA
-        # rate, so its ALU ceiling is the measured FP32 rate / 12 (in FP64-equivalent flops)
+        # the double-float multiply-add (Dot2 step: 12 FP32 instructions) measured on this GPU
+        peak = rmhmc.df_peak_tflops(300)
         fp32 = rmhmc.fp32_peak_tflops(300)
-        peak = fp32 / 12.0
-        peak_note = (f"double-float ceiling = measured FP32 FMA rate {fp32:.1f} TFLOP/s (rmhmc_fp32_peak) / 12 "
-                     "FP32 instructions per double-float multiply-add")
+        peak_note = (f"double-float multiply-add throughput measured live (rmhmc_df_peak, Dot2 chains); "
+                     f"for reference the FP32 FMA rate is {fp32:.1f} TFLOP/s, /12 = {fp32 / 12:.2f}")
     else:
         peak = rmhmc.fp64_peak_tflops(300)
         peak_note = "FP64 FMA throughput measured live on this GPU (rmhmc_fp64_peak)"

@@ -265,8 +265,12 @@ const char* rmhmc_profile_category(int i);
  * dependent-chain DFMA kernel on every SM for about ms_target milliseconds on cuda_stream and writes
  * the achieved TFLOP/s (2 flops per FMA) to *tflops_host. Synchronises the stream. */
 rmhmc_status rmhmc_fp64_peak(void* cuda_stream, int ms_target, double* tflops_host);
-/* The same for FP32 FFMA (the denominator of the double-float Jacobi of RMHMC_MIXED). */
+/* The same for FP32 FFMA. */
 rmhmc_status rmhmc_fp32_peak(void* cuda_stream, int ms_target, double* tflops_host);
+/* The same for the double-float multiply-add (the Dot2 step of the RMHMC_MIXED kernels: FP32
+ * two-product and two-sum with a compensation word), 2 flops per step: the denominator of the
+ * double-float Jacobi and GEMMs. */
+rmhmc_status rmhmc_df_peak(void* cuda_stream, int ms_target, double* tflops_host);
 
 /* Allocation-free eigendecomposition of a batch of symmetric matrices, for callers that cannot
  * allocate device memory (e.g. code running inside another framework's memory pool or arena, a

@@ -12,6 +12,7 @@
 
 #include <vector>
 
+#include "df.cuh"
 #include "internal.cuh"
 #include "model_kernels.cuh"
 #include "primal.cuh"
@@ -291,6 +292,63 @@ __global__ void k_fma_peak(T* __restrict__ sink, int iters, T b, T c) {
 }
 
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// Double-float multiply-add throughput probe: eight independent Dot2 accumulations per thread (the
+// inner step of the double-float GEMM and Jacobi tiles), counted as 2 flops per step.
+__global__ void k_df_peak(float* __restrict__ sink, int iters, float2 b) {
+  float s[8], c[8];
+  float2 a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    s[i] = 0.f;
+    c[i] = 0.f;
+    a[i] = make_float2(1.0f + threadIdx.x * 1e-3f + i, 1e-9f * i);
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) dot2_step(s[i], c[i], a[i], b);
+    }
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) t += s[i] + c[i];
+  if (t == 12345.678f) sink[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
+rmhmc_status df_peak(void* cuda_stream, int ms_target, double* tflops_host) {
+  if (!tflops_host || ms_target < 1) return RMHMC_EINVAL;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 4, threads = 256;
+  float* sink = nullptr;
+  if (cudaMalloc(&sink, (size_t)blocks * threads * sizeof(float)) != cudaSuccess) return RMHMC_ENOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const float2 b = make_float2(0.9999f, 1e-8f);
+  int iters = 16;
+  float ms = 0.f;
+  k_df_peak<<<blocks, threads, 0, s>>>(sink, 4, b);
+  for (int rep = 0; rep < 12; ++rep) {
+    cudaEventRecord(e0, s);
+    k_df_peak<<<blocks, threads, 0, s>>>(sink, iters, b);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms >= 0.5f * ms_target || !(ms > 1e-3f)) break;
+    iters = (int)fmin(1e7, iters * fmin(100.0, fmax(2.0, 0.8 * ms_target / ms)));
+  }
+  const double flops = 2.0 * blocks * threads * (double)iters * 16.0 * 8.0;
+  *tflops_host = ms > 1e-3f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  return cudaGetLastError() == cudaSuccess ? RMHMC_OK : RMHMC_ECUDA;
+}
 
 template <typename T>
 rmhmc_status fma_peak(void* cuda_stream, int ms_target, double* tflops_host) {
@@ -984,6 +1042,10 @@ rmhmc_status rmhmc_fp64_peak(void* cuda_stream, int ms_target, double* tflops_ho
 
 rmhmc_status rmhmc_fp32_peak(void* cuda_stream, int ms_target, double* tflops_host) {
   return fma_peak<float>(cuda_stream, ms_target, tflops_host);
+}
+
+rmhmc_status rmhmc_df_peak(void* cuda_stream, int ms_target, double* tflops_host) {
+  return df_peak(cuda_stream, ms_target, tflops_host);
 }
 
 const char* rmhmc_profile_category(int i) {

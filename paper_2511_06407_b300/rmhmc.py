@@ -114,6 +114,8 @@ def lib():
     L.rmhmc_fp64_peak.restype = c_int
     L.rmhmc_fp32_peak.argtypes = [c_void_p, c_int, POINTER(c_double)]
     L.rmhmc_fp32_peak.restype = c_int
+    L.rmhmc_df_peak.argtypes = [c_void_p, c_int, POINTER(c_double)]
+    L.rmhmc_df_peak.restype = c_int
     L.rmhmc_eigh_noalloc.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                      c_double, c_int, c_void_p, c_void_p]
     L.rmhmc_eigh_noalloc.restype = c_int
@@ -368,6 +370,15 @@ def fp32_peak_tflops(ms_target=200, stream=None):
     stream = stream or torch.cuda.current_stream()
     out = c_double()
     _check(lib().rmhmc_fp32_peak(c_void_p(stream.cuda_stream), int(ms_target), ctypes.byref(out)))
+    return out.value
+
+
+def df_peak_tflops(ms_target=200, stream=None):
+    """Measured double-float (Dot2) multiply-add throughput of the current GPU (TFLOP/s, 2 per step)."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    out = c_double()
+    _check(lib().rmhmc_df_peak(c_void_p(stream.cuda_stream), int(ms_target), ctypes.byref(out)))
     return out.value
 
 
