@@ -325,18 +325,29 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
   const int nct = dp / SB;
   int sweeps = 0;
   bool converged = false;
+  double tot0 = 0.0;        // ||M||_F^2 from the first pass
   unsigned int ntile = 0;   // 16 x 16 x 16 tile products this warp executed (phase 2)
   unsigned int nround = 0;  // rounds of 8 rotations this warp applied to a 16 x 16 block (phase 1)
   for (;;) {
     // ---- convergence test. Pass 1: ||M||_F^2 and min_i<d |m_ii|. Pass 2: the worst pair ratio
     //      (pair_ratio) under the chosen rule, with floor = 4 u ||M||_F (rounding level).
+    // ||M||_F is invariant under the rotations: summed over M in the first pass only; later
+    // passes read the diagonal (a non-finite diagonal entry still poisons tot)
     double tot = 0.0, dmin = 1e308;
-    for (long long e = (long long)rank * blockDim.x + tid; e < (long long)dp * dp;
-         e += (long long)C * blockDim.x) {
-      const double v = __ldcg(M + e);
-      tot = fma(v, v, tot);
-      const int i = (int)(e / dp);
-      if (i < d && (long long)i * dp + i == e) dmin = fmin(dmin, fabs(v));
+    if (sweeps == 0) {
+      for (long long e = (long long)rank * blockDim.x + tid; e < (long long)dp * dp;
+           e += (long long)C * blockDim.x) {
+        const double v = __ldcg(M + e);
+        tot = fma(v, v, tot);
+        const int i = (int)(e / dp);
+        if (i < d && (long long)i * dp + i == e) dmin = fmin(dmin, fabs(v));
+      }
+    } else {
+      for (int i = rank * blockDim.x + tid; i < d; i += C * blockDim.x) {
+        const double v = __ldcg(M + (long long)i * dp + i);
+        if (!isfinite(v)) tot = v;
+        dmin = fmin(dmin, fabs(v));
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -358,13 +369,15 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, dou
       tot += __ldcg(slots + (sweeps & 1) * 32 + 2 * r);
       dmin = fmin(dmin, __ldcg(slots + (sweeps & 1) * 32 + 2 * r + 1));
     }
+    if (sweeps == 0) tot0 = tot;
+    else if (isfinite(tot)) tot = tot0;
     const double dmin2 = fmax(dmin * dmin, 1e-300);
     const double floor2 = fmax(16.0 * 1.2325951644078310e-32 * tot, 1e-300);  // (4u)^2 ||M||_F^2
     double crit = 0.0, bad = isfinite(tot) ? 0.0 : 1.0;
     for (long long e = (long long)rank * blockDim.x + tid; e < (long long)dp * dp;
          e += (long long)C * blockDim.x) {
       const int j = (int)(e / dp), l = (int)(e % dp);
-      if (j == l) continue;
+      if (j >= l) continue;  // M is kept symmetric: the upper triangle decides
       const double v = __ldcg(M + e);
       if (v == 0.0) continue;
       if (!isfinite(v)) bad = 1.0;
@@ -646,15 +659,24 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
   const int nct = dp / SB;
   int sweeps = 0;
   bool converged = false;
+  double tot0 = 0.0;        // ||M||_F^2 from the first pass
   unsigned int ntile = 0;   // 16 x 16 x 16 tile products this warp executed (phase 2)
   unsigned int nround = 0;  // rounds of 8 rotations this warp applied to a 16 x 16 block (phase 1)
   for (;;) {
     double tot = 0.0, dmin = 1e308;
-    for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
-      const double v = df_join(ldcg2(Mw + e));
-      tot = fma(v, v, tot);
-      const int i = (int)(e / dp);
-      if (i < d && (long long)i * dp + i == e) dmin = fmin(dmin, fabs(v));
+    if (sweeps == 0) {
+      for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
+        const double v = df_join(ldcg2(Mw + e));
+        tot = fma(v, v, tot);
+        const int i = (int)(e / dp);
+        if (i < d && (long long)i * dp + i == e) dmin = fmin(dmin, fabs(v));
+      }
+    } else {  // ||M||_F is invariant under the rotations (see k_jacobi)
+      for (int i = rank * blockDim.x + tid; i < d; i += C * blockDim.x) {
+        const double v = df_join(ldcg2(Mw + (long long)i * dp + i));
+        if (!isfinite(v)) tot = v;
+        dmin = fmin(dmin, fabs(v));
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -676,12 +698,14 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
       tot += __ldcg(slots + (sweeps & 1) * 32 + 2 * r);
       dmin = fmin(dmin, __ldcg(slots + (sweeps & 1) * 32 + 2 * r + 1));
     }
+    if (sweeps == 0) tot0 = tot;
+    else if (isfinite(tot)) tot = tot0;
     const double dmin2 = fmax(dmin * dmin, 1e-300);
     const double floor2 = fmax(16.0 * 1.2621774483536189e-29 * tot, 1e-300);  // (4 * 2^-48)^2 ||M||^2
     double crit = 0.0, bad = isfinite(tot) ? 0.0 : 1.0;
     for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
       const int j = (int)(e / dp), l = (int)(e % dp);
-      if (j == l) continue;
+      if (j >= l) continue;  // M is kept symmetric: the upper triangle decides
       const double v = df_join(ldcg2(Mw + e));
       if (v == 0.0) continue;
       if (!isfinite(v)) bad = 1.0;
