@@ -56,6 +56,7 @@ typedef enum {
 #define RMHMC_CHAIN_NOTPD 1
 #define RMHMC_CHAIN_NOTCONV 2
 #define RMHMC_CHAIN_NONFINITE 4
+#define RMHMC_CHAIN_TIMEOUT 8   /* a bounded device-side wait gave up (results of that call invalid) */
 
 typedef enum {
   RMHMC_LIK_BERNOULLI_LOGIT = 0,
@@ -293,6 +294,28 @@ rmhmc_status rmhmc_df_peak(void* cuda_stream, int ms_target, double* tflops_host
 rmhmc_status rmhmc_eigh_noalloc(void* cuda_stream, int n, int d, const double* A_dev,
                                 double* lam_dev, double* Q_dev, double tol, int max_sweeps,
                                 int* sweeps_dev, int* status_dev);
+
+/* Batched FP64-accurate GEMM on the tensor cores (tcgen05, bf16 operands, FP32 accumulators in
+ * tensor memory), the contraction engine of the RMHMC_MIXED path (K^-1 algebra, Psi^T H Psi and
+ * Psi C Psi^T of Sec. 2.3-2.4), exposed for direct use and testing:
+ *   C_b = alpha op(A_b) op(B_b) + beta C_b,  b < batch,
+ * row-major; op(A) is m x k (A_dev + b strideA, A^T when ta), op(B) is k x n (B^T when tb), C is
+ * m x n with leading dimension ldc. Method: error-free splitting (Ozaki, Ogita, Oishi and Rump,
+ * Numer. Algorithms 59, 2012): every row of op(A) and column of op(B) is scaled by a power of two
+ * and cut into `slices` bf16 numbers of 7 bits each (the first 8); the slice products whose
+ * weights sum to at most slices + 1 are formed on the tensor cores with exact FP32 group sums (k is
+ * processed 512 at a time), and combined in FP64. Error: about 2^(-7 slices) k max|row of op(A)|
+ * max|column of op(B)| plus FP64 rounding of the result; slices = 9 (63 bits) is at or below
+ * FP64 GEMM rounding, 7 about 2^-49. slices: 6..9. sym (m == n): the product is known to be
+ * symmetric; only its lower triangle is computed and mirrored. A row or column holding a
+ * non-finite value gives NaN in the corresponding row or column of C. Scratch of
+ * about 2 (m + n) k slices bytes (rows padded to 128) is taken with cudaMallocAsync on cuda_stream
+ * and released the same way; ENOMEM if that fails. status_dev (batch ints, may be NULL) receives
+ * RMHMC_CHAIN_TIMEOUT for an entry whose bounded device wait gave up. Enqueued on cuda_stream. */
+rmhmc_status rmhmc_gemm_tc(void* cuda_stream, int ta, int tb, int m, int n, int k, double alpha,
+                           const double* A_dev, int lda, long long strideA, const double* B_dev,
+                           int ldb, long long strideB, double beta, double* C_dev, int ldc,
+                           long long strideC, int batch, int slices, int sym, int* status_dev);
 
 /* Dimension d of q, and number of chains. */
 int rmhmc_dim(const rmhmc_model* m);

@@ -99,6 +99,29 @@ void gemv_f64(cudaStream_t s, bool ta, int rows, int cols, const double* A, int 
               const double* x, long long sx, double* y, long long sy, int batch, double alpha,
               double beta);
 
+// ---------------------------------------------------------------- tensor-core GEMM (tcgemm.cu)
+// FP64-accurate GEMM on tcgen05 by error-free bf16 slicing. An operand is the K-major view of a
+// matrix (R rows, K columns) split into S bf16 slices (6..9) plus one exponent per row, in device
+// memory of tc_operand_bytes(R, K, S, batch) bytes placed by tc_operand.
+// The slices are laid out for one role: A (tiles of 128 rows, b_side = false) or B (64 rows).
+struct TcOperand {
+  uint8_t* dig = nullptr;  // slices, bytes_per_entry per batch entry
+  int* ex = nullptr;       // row exponents, R8 * 8 per batch entry
+  int R = 0, K = 0, S = 0, TR = 0, R8 = 0, KS = 0;
+  long long bytes_per_entry = 0;
+};
+int tc_tile_rows(bool b_side);
+size_t tc_operand_bytes(int R, int K, int S, int batch, bool b_side);
+TcOperand tc_operand(void* mem, int R, int K, int S, int batch, bool b_side);
+// Split the K-major view of X (kmaj: row r is X[r * ld + 0..K), else column r, X[0..K) * ld + r).
+void tc_split(cudaStream_t s, const double* X, int ld, long long sX, bool kmaj, int batch,
+              const TcOperand& op);
+// C_b = alpha A_b B_b^T + beta C_b (A: m x k rows, B: n x k rows, both split with the same S and
+// K); sym: the product is symmetric, written as the mirror of its lower triangle. A bounded wait
+// that gives up sets RMHMC_CHAIN_TIMEOUT in status[b / sdiv] (status may be null).
+void gemm_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, double alpha, double beta,
+             double* C, int ldc, long long sC, int batch, bool sym, int* status, int sdiv);
+
 // ---------------------------------------------------------------- eigen (eigen.cu)
 // Warm-started block-Jacobi on M (dp x dp per chain, symmetric), rotating PsiT's rows alongside;
 // writes lam (dp per chain) and the sweep count; sets RMHMC_CHAIN_NOTCONV on failure. Chains

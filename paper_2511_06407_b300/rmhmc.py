@@ -119,6 +119,11 @@ def lib():
     L.rmhmc_eigh_noalloc.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                      c_double, c_int, c_void_p, c_void_p]
     L.rmhmc_eigh_noalloc.restype = c_int
+    L.rmhmc_gemm_tc.argtypes = [c_void_p, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p,
+                                c_int, ctypes.c_longlong, c_void_p, c_int, ctypes.c_longlong,
+                                c_double, c_void_p, c_int, ctypes.c_longlong, c_int, c_int, c_int,
+                                c_void_p]
+    L.rmhmc_gemm_tc.restype = c_int
     L.rmhmc_batch_create.argtypes = [POINTER(c_void_p), c_int, c_void_p, POINTER(c_void_p)]
     L.rmhmc_batch_create.restype = c_int
     L.rmhmc_batch_leapfrog.argtypes = [c_void_p, POINTER(IntegratorC), c_int]
@@ -394,6 +399,34 @@ def eigh_noalloc(A, lam=None, Q=None, tol=1e-13, max_sweeps=30, sweeps=None, sta
                                     _ptr(lam, (n, d), torch.float64), _ptr(Q, (n, d, d), torch.float64),
                                     float(tol), int(max_sweeps), _ptr(sweeps, (n,), torch.int32),
                                     _ptr(status, (n,), torch.int32)))
+
+
+def gemm_tc(A, B, C=None, ta=False, tb=False, alpha=1.0, beta=0.0, slices=9, sym=False,
+            status=None, stream=None):
+    """C = alpha op(A) op(B) + beta C through rmhmc_gemm_tc (FP64-accurate GEMM on the tensor
+    cores by bf16 slicing). A, B, C: contiguous CUDA float64, (batch, rows, cols) or 2-D; op() is
+    the transpose when ta / tb. Returns C (allocated when None)."""
+    import torch
+    two_d = A.dim() == 2
+    A3 = A.unsqueeze(0) if two_d else A
+    B3 = B.unsqueeze(0) if B.dim() == 2 else B
+    batch = A3.shape[0]
+    m, k = (A3.shape[2], A3.shape[1]) if ta else (A3.shape[1], A3.shape[2])
+    kb, n = (B3.shape[2], B3.shape[1]) if tb else (B3.shape[1], B3.shape[2])
+    if kb != k or B3.shape[0] != batch:
+        raise RmhmcError("gemm_tc: shapes do not conform")
+    if C is None:
+        C = torch.zeros((batch, m, n) if not two_d else (m, n), dtype=torch.float64, device=A.device)
+        beta = 0.0
+    C3 = C.unsqueeze(0) if C.dim() == 2 else C
+    stream = stream or torch.cuda.current_stream()
+    _check(lib().rmhmc_gemm_tc(c_void_p(stream.cuda_stream), int(bool(ta)), int(bool(tb)), m, n, k,
+                               float(alpha), _ptr(A3, None, torch.float64), A3.shape[2],
+                               A3.shape[1] * A3.shape[2], _ptr(B3, None, torch.float64), B3.shape[2],
+                               B3.shape[1] * B3.shape[2], float(beta),
+                               _ptr(C3, (batch, m, n), torch.float64), n, m * n, batch, int(slices),
+                               int(bool(sym)), _ptr(status, (batch,), torch.int32)))
+    return C
 
 
 def version():
