@@ -115,9 +115,11 @@ typedef struct {
   double jacobi_tol;   /* zeta, the tolerance of Sec. 2.4 (see jacobi_rule for how it is applied) */
   int max_sweeps;      /* Jacobi sweep limit per eigen-update */
   int reorth_every;    /* Gram-Schmidt of Psi every this many eigen-updates (Sec. 2.4); 0 = never */
-  int precision;       /* rmhmc_precision: FP64, or MIXED = the Jacobi rotations and the d x d
-                          products M = Psi^T H Psi and W = Psi C Psi^T in double-float (FP32 pairs,
-                          ~48-bit significand); Cholesky, K^-1 algebra, H and log|G| stay FP64 */
+  int precision;       /* rmhmc_precision: FP64, or MIXED = the Jacobi rotations in double-float
+                          (FP32 pairs, ~48-bit significand), and the K^-1 algebra (K^-1 = L^-T L^-1,
+                          K^-1 dK and its products) and the d x d products M = Psi^T H Psi and
+                          W = Psi C Psi^T on the tensor cores (rmhmc_gemm_tc with 9 and 8 slices);
+                          Cholesky, L^-1, H, log|G| and the Hamiltonian stay FP64 */
   int jacobi_rule;     /* rmhmc_jacobi_rule: when M = Psi^T H Psi counts as diagonal */
   int eigen_start;     /* 0: warm start from the previous Psi (dynamic, Sec. 2.4); 1: cold start
                           from Psi = I at every eigen-update (the static ablation of Sec. 3.1) */
@@ -250,13 +252,14 @@ rmhmc_status rmhmc_autotune(rmhmc_model* m, int* cluster_out);
 /* Kernel-level profile (for measurement; not part of the method). While enabled, every kernel
  * launch of the model is bracketed by CUDA events on the model's stream and counted in one of
  * RMHMC_PROF_NCAT categories (names from rmhmc_profile_category), with the algorithmic FLOPs of
- * the work it must do (GEMM 2mnk on the unpadded sizes, halved for symmetric outputs; Cholesky
+ * the work it must do (GEMM 2mnk on the unpadded sizes, halved for symmetric outputs, also for
+ * the tensor-core GEMMs of the mixed form, category "gemm_tc", whose bf16 work is larger; Cholesky
  * and triangular inverse N^3/3; Jacobi 2 * 16^3 per 16 x 16 x 16 rotation-tile product executed,
  * tiles skipped because both rotations were the identity not counted, plus 1952 per round of 8
  * rotations applied inside a 16 x 16 sub-problem). rmhmc_profile(m, 1)
  * resets and starts, rmhmc_profile(m, 0) stops. rmhmc_profile_read synchronises the stream and
  * writes per-category milliseconds, FLOPs and launch counts (host arrays of RMHMC_PROF_NCAT). */
-#define RMHMC_PROF_NCAT 10
+#define RMHMC_PROF_NCAT 11
 rmhmc_status rmhmc_profile(rmhmc_model* m, int enable);
 rmhmc_status rmhmc_profile_read(rmhmc_model* m, double* ms_host, double* flops_host,
                                 long long* launches_host);

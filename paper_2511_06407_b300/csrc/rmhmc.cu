@@ -10,6 +10,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "df.cuh"
@@ -437,16 +438,26 @@ struct rmhmc_model {
   // whenever Psi^T has changed since) and one scratch operand
   double *pPsi = nullptr, *pA = nullptr;
   bool psi_pairs_ok = false;
+  // the mixed form's tensor-core GEMMs: bf16 slices of the current A-side and B-side operands, and
+  // of the two Psi^T views that W = Psi^T^T (C Psi^T) reads (kept until Psi^T changes)
+  uint8_t *tcA = nullptr, *tcB = nullptr, *tcPA = nullptr, *tcPB = nullptr;
+  bool tc_pa_ok = false, tc_pb_ok = false;
 };
 
 namespace {
 
 enum Cat {
   CAT_GEMM = 0, CAT_JACOBI, CAT_CHOL, CAT_TRINV, CAT_MODEL, CAT_CONTRACT, CAT_VECTOR, CAT_MGS, CAT_JACOBI_DF,
-  CAT_GEMM_DF
+  CAT_GEMM_DF, CAT_GEMM_TC
 };
 const char* kCatNames[RMHMC_PROF_NCAT] = {"gemm_f64", "jacobi_f64", "cholesky_f64", "trinv_f64",
-                                          "model", "contract", "vector", "mgs_f64", "jacobi_df", "gemm_df"};
+                                          "model", "contract", "vector", "mgs_f64", "jacobi_df", "gemm_df",
+                                          "gemm_tc"};
+
+// bf16 slices of the mixed form's tensor-core GEMMs: 9 (63 bits, at or below FP64 GEMM rounding)
+// for the K^-1 algebra, whose cond(K) ~ 1e8 amplification needs FP64-level products, and 8 (56 bits)
+// for the d x d products M = Psi^T H Psi and W = Psi C Psi^T
+constexpr int kSlicesK = 9, kSlicesD = 8;
 
 // Brackets one launch site with CUDA events on the model's stream while profiling is enabled.
 struct ProfScope {
@@ -517,19 +528,49 @@ void dual_model_layer(rmhmc_model* m, bool third) {
   cholesky_f64(s, m->KL, N, B, m->stats + ST_LOGDET, kStatSlots, m->status, n);
   PROF(m, CAT_TRINV, Bf * Nf * Nf * Nf / 3.0)
   trinv_lower_f64(s, m->KL, m->Aux, N, B);
+  const bool tc = m->precision == RMHMC_MIXED;
+  const TcOperand ka = tc_operand(m->tcA, N, N, kSlicesK, B, false);
+  const TcOperand kb = tc_operand(m->tcB, N, N, kSlicesK, B, true);
   // K^-1 = L^-T L^-1 (symmetric; the sum runs over k >= max(i, j) only)
-  PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, true, true))
-  gemm_f64(s, true, false, N, N, N, 1.0, m->Aux, N, NN, m->Aux, N, NN, 0.0, m->Kinv, N, NN, B, true, true);
+  if (tc) {  // row i of op(A) and row j of op(B)^T are columns of L^-1
+    PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Aux, N, NN, false, B, ka);
+    PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Aux, N, NN, false, B, kb);
+    PROF(m, CAT_GEMM_TC, Bf * gemm_flops(Nf, Nf, Nf, true, true))
+    gemm_tc(s, ka, kb, 1.0, 0.0, m->Kinv, N, NN, B, true, m->status, n);
+  } else {
+    PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, true, true))
+    gemm_f64(s, true, false, N, N, N, 1.0, m->Aux, N, NN, m->Aux, N, NN, 0.0, m->Kinv, N, NN, B, true, true);
+  }
   // t = L^-1 f (kept in beta for f . alpha = |t|^2) and alpha = L^-T t by substitution
   PROF(m, CAT_VECTOR, 2.0 * Bf * Nf * Nf)
   cholsolve_f64(s, m->KL, m->fpk, m->beta, m->alpha_, N, B);
-  PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, false, false))
-  gemm_f64(s, false, false, N, N, N, 1.0, m->Kinv, N, NN, m->D1, N, NN, 0.0, m->S, N, NN, B, false, false);
-  if (third) {
+  // S = K^-1 D1
+  if (tc) {
+    PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Kinv, N, NN, true, B, ka);
+    PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->D1, N, NN, false, B, kb);
+    PROF(m, CAT_GEMM_TC, Bf * gemm_flops(Nf, Nf, Nf, false, false))
+    gemm_tc(s, ka, kb, 1.0, 0.0, m->S, N, NN, B, false, m->status, n);
+  } else {
+    PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, false, false))
+    gemm_f64(s, false, false, N, N, N, 1.0, m->Kinv, N, NN, m->D1, N, NN, 0.0, m->S, N, NN, B, false, false);
+  }
+  if (third && tc) {
+    // A1 = S K^-1 (K^-1 is exactly symmetric, so its columns are read as rows), then S^2 with the
+    // slices of S's rows reused
+    PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->S, N, NN, true, B, ka);
+    PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Kinv, N, NN, true, B, kb);
+    PROF(m, CAT_GEMM_TC, Bf * gemm_flops(Nf, Nf, Nf, true, false))
+    gemm_tc(s, ka, kb, 1.0, 0.0, m->Aux, N, NN, B, true, m->status, n);
+    PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->S, N, NN, false, B, kb);
+    PROF(m, CAT_GEMM_TC, Bf * gemm_flops(Nf, Nf, Nf, false, false))
+    gemm_tc(s, ka, kb, 1.0, 0.0, m->S2, N, NN, B, false, m->status, n);
+  } else if (third) {
     PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, true, false))
     gemm_f64(s, false, false, N, N, N, 1.0, m->S, N, NN, m->Kinv, N, NN, 0.0, m->Aux, N, NN, B, true, false);
     PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, false, false))
     gemm_f64(s, false, false, N, N, N, 1.0, m->S, N, NN, m->S, N, NN, 0.0, m->S2, N, NN, B, false, false);
+  }
+  if (third) {
     PROF(m, CAT_MODEL, 0)
     dev::k_stats<true><<<B, 256, 0, s>>>(m->md, m->q, dp, m->D1, m->Kinv, m->S, m->Aux, m->S2, m->fpk,
                                          m->alpha_, m->beta, m->gamma, m->eps2, m->eps3, m->delta,
@@ -602,7 +643,7 @@ void eval_geometry(rmhmc_model* m, bool third) {
   cudaStream_t s = m->stream;
   const int C = m->C, dp = m->dp, d = m->d;
   const long long DD = (long long)dp * dp;
-  m->psi_pairs_ok = false;  // Gram-Schmidt or the cold start may change Psi^T below
+  m->psi_pairs_ok = m->tc_pa_ok = m->tc_pb_ok = false;  // Gram-Schmidt or the cold start may change Psi^T
   if (m->kind == 1) primal_model_layer(m);
   else dual_model_layer(m, third);
   // Sec. 2.4: Gram-Schmidt of Psi every reorth_every eigen-updates, then M = Psi^T H Psi
@@ -626,7 +667,7 @@ void eval_geometry(rmhmc_model* m, bool third) {
     jacobi_f64(s, m->M, m->PsiT, m->lam, dp, d, C, m->jacobi_rule, m->tol, m->max_sweeps, m->status,
                m->sweeps_last, m->sweeps_acc, m->jw, m->cluster);
   }
-  m->psi_pairs_ok = false;  // the eigen-update rotated Psi^T
+  m->psi_pairs_ok = m->tc_pa_ok = m->tc_pb_ok = false;  // the eigen-update rotated Psi^T
   PROF(m, CAT_VECTOR, 0)
   k_inc<<<nblk(C), 256, 0, s>>>(m->eig_count, C, m->sweeps_total, m->sweeps_last);
   PROF(m, CAT_VECTOR, 0)
@@ -635,28 +676,24 @@ void eval_geometry(rmhmc_model* m, bool third) {
 
 void gemm_dd(rmhmc_model* m, bool ta, bool tb, const double* A, const double* B, double* out, bool sym) {
   const int dp = m->dp;
-  const long long DD = (long long)dp * dp, n = m->C * DD;
+  const long long DD = (long long)dp * dp;
   const double df = m->d, fl = m->C * gemm_flops(df, df, df, sym, false);
   if (m->precision == RMHMC_MIXED) {
-    // every one of these products has Psi^T as one operand: its pairs are reused until Psi^T
-    // changes, the other operand is split into scratch (one pass instead of one per tile load)
-    const double* Ap = m->pA;
-    const double* Bp = m->pA;
-    if (A == m->PsiT || B == m->PsiT) {
-      if (!m->psi_pairs_ok) {
-        PROF(m, CAT_GEMM_DF, 0)
-        to_pairs(m->stream, m->PsiT, m->pPsi, n);
-        m->psi_pairs_ok = true;
-      }
-      if (A == m->PsiT) Ap = m->pPsi;
-      if (B == m->PsiT) Bp = m->pPsi;
+    // tensor cores: op(A)'s rows and op(B)'s columns cut into bf16 slices; the two column views
+    // of Psi^T (W = Psi^T^T (C Psi^T)) are kept until Psi^T changes
+    const bool pa = A == m->PsiT && ta, pb = B == m->PsiT && !tb;
+    const TcOperand oa = tc_operand(pa ? m->tcPA : m->tcA, dp, dp, kSlicesD, m->C, false);
+    const TcOperand ob = tc_operand(pb ? m->tcPB : m->tcB, dp, dp, kSlicesD, m->C, true);
+    if (!pa || !m->tc_pa_ok) {
+      PROF(m, CAT_GEMM_TC, 0) tc_split(m->stream, A, dp, DD, !ta, m->C, oa);
+      if (pa) m->tc_pa_ok = true;
     }
-    if (A != m->PsiT || B != m->PsiT) {
-      PROF(m, CAT_GEMM_DF, 0)
-      to_pairs(m->stream, A != m->PsiT ? A : B, m->pA, n);
+    if (!pb || !m->tc_pb_ok) {
+      PROF(m, CAT_GEMM_TC, 0) tc_split(m->stream, B, dp, DD, tb, m->C, ob);
+      if (pb) m->tc_pb_ok = true;
     }
-    PROF(m, CAT_GEMM_DF, fl)
-    gemm_df(m->stream, ta, tb, dp, dp, dp, 1.0, Ap, dp, DD, Bp, dp, DD, 0.0, out, dp, DD, m->C, sym, true, true);
+    PROF(m, CAT_GEMM_TC, fl)
+    gemm_tc(m->stream, oa, ob, 1.0, 0.0, out, dp, DD, m->C, sym, m->status, 1);
   } else {
     PROF(m, CAT_GEMM, fl)
     gemm_f64(m->stream, ta, tb, dp, dp, dp, 1.0, A, dp, DD, B, dp, DD, 0.0, out, dp, DD, m->C, sym, false);
@@ -815,6 +852,17 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
   ALLOC(m->PsiT_save, C * DD);
   ALLOC(m->pPsi, C * DD);
   ALLOC(m->pA, C * DD);
+  {  // tensor-core slices: the K^-1 algebra (dual model) and the d x d products share tcA / tcB
+    size_t ba = tc_operand_bytes(dp, dp, kSlicesD, C, false), bb = tc_operand_bytes(dp, dp, kSlicesD, C, true);
+    if (m->kind != 1) {
+      ba = std::max(ba, tc_operand_bytes(N, N, kSlicesK, (int)B, false));
+      bb = std::max(bb, tc_operand_bytes(N, N, kSlicesK, (int)B, true));
+    }
+    ALLOC(m->tcA, ba);
+    ALLOC(m->tcB, bb);
+    ALLOC(m->tcPA, tc_operand_bytes(dp, dp, kSlicesD, C, false));
+    ALLOC(m->tcPB, tc_operand_bytes(dp, dp, kSlicesD, C, true));
+  }
   double** vecs[] = {&m->q, &m->p, &m->ph, &m->q0, &m->v0, &m->vk, &m->t1, &m->dU, &m->dHdq,
                      &m->lam, &m->g, &m->gp, &m->q_save, &m->z, &m->vtr, &m->xin};
   for (double** v : vecs) ALLOC(*v, (size_t)C * dp);
