@@ -44,8 +44,11 @@ WORKLOAD = (f"GP classification N={N_INPUTS} (d={N_INPUTS + 2}), SE kernel, {N_C
             f"plain FP64, alpha=1e6, eps={EPS}, n_fp={N_FP}")
 
 
-MIXED_NOTE = ("mixed precision: Jacobi rotations and the d x d products Psi^T H Psi, Psi C Psi^T in "
-              "double-float (FP32 pairs, ~48-bit); Cholesky, K^-1 algebra, log|G|, H in FP64")
+MIXED_NOTE = ("mixed precision: Jacobi rotations in double-float (FP32 pairs, ~48-bit); the K^-1 algebra "
+              "(K^-1, K^-1 dK and products) and the d x d products Psi^T H Psi, Psi C Psi^T on the tcgen05 "
+              "tensor cores by exact bf16 slicing (9 / 8 slices = 63 / 56 bits, FP32 accumulation in "
+              "TMEM, combined in FP64); Cholesky, L^-1, log|G|, H and the Hamiltonian in FP64")
+DTYPE_MIXED = "f64 + f32x2 (double-float) + bf16 slices on tensor cores (FP64-accurate GEMM)"
 
 
 def aux_precision(args):
@@ -54,7 +57,7 @@ def aux_precision(args):
 
 
 def dtype_of(prec):
-    return "f64" if prec == "fp64" else "f64 + f32x2 (double-float)"
+    return "f64" if prec == "fp64" else DTYPE_MIXED
 
 
 def arm_config(C, ws, head):
@@ -212,11 +215,38 @@ def _time_leapfrogs(model, integ, steps, stream, local, ws, dev):
     return float(t.item()), prof, clk
 
 
+def _measured_bf16_peak():
+    """(sustained, burst) dense bf16 TFLOP/s of the B300s (cuBLAS), from MEASURED_PEAKS.json."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        return float(mp["bf16_tflops_sustained"]), float(mp["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1400.0, 1800.0  # the recipe's fallback figures
+
+
+def _tensor_roofline(prof):
+    """The tensor-core GEMM category against the measured bf16 peak: executed bf16 FLOPs (all slice
+    products of all 128 x 64 tiles) / CUDA-event time, inside the step, so the sustained figure."""
+    if "gemm_tc" not in prof or not prof["gemm_tc"][2]:
+        return None
+    ms, flops, launches = prof["gemm_tc"]
+    sus, burst = _measured_bf16_peak()
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "kernel": "gemm_tc (k_tc_split + k_gemm_tc)", "achieved": achieved, "peak": sus,
+            "unit": "TFLOP/s", "frac": achieved / sus, "traffic": None,
+            "peak_note": f"cuBLAS bf16 measured, sustained ({sus}; burst {burst}), MEASURED_PEAKS.json",
+            "achieved_note": "bf16 tensor FLOPs executed (slice products incl. tile padding); time includes "
+                             "the slicing kernels"}
+
+
 def _roofline(rmhmc, prof, C):
     """Roofline of the dominant kernel category (ALU bound; peaks measured live on this GPU)."""
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_flops, dom_launches = prof[dom]
-    if dom in ("jacobi_df", "gemm_df"):
+    if dom == "gemm_tc":
+        return _tensor_roofline(prof)
+    if dom == "jacobi_df":
         # the double-float multiply-add (Dot2 step: 12 FP32 instructions) measured on this GPU
         peak = rmhmc.df_peak_tflops(300)
         fp32 = rmhmc.fp32_peak_tflops(300)
@@ -362,11 +392,12 @@ def run_b300(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if head == "fp64" else "f64 + f32x2 (double-float)",
+        "dtype": "f64" if head == "fp64" else DTYPE_MIXED,
         "data": "synthetic",
         "config": arm_config(C, ws, head),
         "leapfrogs_per_s": total_chains * args.steps / (ms * 1e-3),
         "roofline": roof,
+        "roofline_tensor_gemm": _tensor_roofline(runs[head]["prof"]),
         "profile_ms": pms, "profile_tflops": ptf,
         "cpu_baseline": cpu_baseline,
         "e2e": {"value": e2e_value, "unit": UNIT,
@@ -507,7 +538,7 @@ def run_ess(args):
             r[key] = [round(float(v), 6) for v in r[key]]
     print(json.dumps({"metric": "effective samples/s (min over log P, hyperparameters and a mean coordinate; bulk and tail ESS)",
                       "value": b["ess_per_s"], "unit": "ESS/s", "n_gpus": 1, "higher_is_better": True,
-                      "dtype": "f64; Jacobi rotations f32x2 (double-float)", "data": "synthetic",
+                      "dtype": "f64; mixed: " + DTYPE_MIXED, "data": "synthetic",
                       "config": {"workload": f"{label}, {C} chains, eps={eps}, L=10, "
                                              f"n_fp=6, {args.burn} burn-in + {args.iters} kept iterations",
                                  "quantities": names},

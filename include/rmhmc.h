@@ -252,14 +252,15 @@ rmhmc_status rmhmc_autotune(rmhmc_model* m, int* cluster_out);
 /* Kernel-level profile (for measurement; not part of the method). While enabled, every kernel
  * launch of the model is bracketed by CUDA events on the model's stream and counted in one of
  * RMHMC_PROF_NCAT categories (names from rmhmc_profile_category), with the algorithmic FLOPs of
- * the work it must do (GEMM 2mnk on the unpadded sizes, halved for symmetric outputs, also for
- * the tensor-core GEMMs of the mixed form, category "gemm_tc", whose bf16 work is larger; Cholesky
+ * the work it must do (GEMM 2mnk on the unpadded sizes, halved for symmetric outputs; for the
+ * tensor-core GEMMs of the mixed form, category "gemm_tc", the bf16 tensor FLOPs executed: every
+ * slice product of every 128 x 64 tile computed, padding included; Cholesky
  * and triangular inverse N^3/3; Jacobi 2 * 16^3 per 16 x 16 x 16 rotation-tile product executed,
  * tiles skipped because both rotations were the identity not counted, plus 1952 per round of 8
  * rotations applied inside a 16 x 16 sub-problem). rmhmc_profile(m, 1)
  * resets and starts, rmhmc_profile(m, 0) stops. rmhmc_profile_read synchronises the stream and
  * writes per-category milliseconds, FLOPs and launch counts (host arrays of RMHMC_PROF_NCAT). */
-#define RMHMC_PROF_NCAT 11
+#define RMHMC_PROF_NCAT 10
 rmhmc_status rmhmc_profile(rmhmc_model* m, int enable);
 rmhmc_status rmhmc_profile_read(rmhmc_model* m, double* ms_host, double* flops_host,
                                 long long* launches_host);

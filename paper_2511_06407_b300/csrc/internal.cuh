@@ -78,13 +78,6 @@ struct GeomDev {
 void gemm_f64(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
               int lda, long long sA, const double* B, int ldb, long long sB, double beta, double* C,
               int ldc, long long sC, int batch, bool sym, bool tri);
-// The same product in double-float arithmetic (FP32 pairs, Dot2 accumulation; no tri form). With
-// a_pairs / b_pairs the operand already holds (hi, lo) pairs (to_pairs) in its double-sized slots.
-void gemm_df(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
-             int lda, long long sA, const double* B, int ldb, long long sB, double beta, double* C,
-             int ldc, long long sC, int batch, bool sym, bool a_pairs = false, bool b_pairs = false);
-// Split n doubles into (hi, lo) FP32 pairs, written into the same-sized buffer `pairs`.
-void to_pairs(cudaStream_t s, const double* x, double* pairs, long long n);
 // In-place lower Cholesky of batch N x N matrices (row-major, ld = N); writes log|K| to
 // logdet[b * logdet_stride] and sets status bit RMHMC_CHAIN_NOTPD in status[b / per_chain].
 void cholesky_f64(cudaStream_t s, double* A, int N, int batch, double* logdet, int logdet_stride,
@@ -109,6 +102,7 @@ struct TcOperand {
   int* ex = nullptr;       // row exponents, R8 * 8 per batch entry
   int R = 0, K = 0, S = 0, TR = 0, R8 = 0, KS = 0;
   long long bytes_per_entry = 0;
+  bool shared = false;  // one entry read by every batch entry of a product (split with batch 1)
 };
 int tc_tile_rows(bool b_side);
 size_t tc_operand_bytes(int R, int K, int S, int batch, bool b_side);
@@ -121,6 +115,8 @@ void tc_split(cudaStream_t s, const double* X, int ld, long long sX, bool kmaj, 
 // that gives up sets RMHMC_CHAIN_TIMEOUT in status[b / sdiv] (status may be null).
 void gemm_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, double alpha, double beta,
              double* C, int ldc, long long sC, int batch, bool sym, int* status, int sdiv);
+// bf16 tensor-core FLOPs gemm_tc executes for these operands (padded tiles, all slice products).
+double gemm_tc_tensor_flops(const TcOperand& A, const TcOperand& B, int batch, bool sym);
 
 // ---------------------------------------------------------------- eigen (eigen.cu)
 // Warm-started block-Jacobi on M (dp x dp per chain, symmetric), rotating PsiT's rows alongside;

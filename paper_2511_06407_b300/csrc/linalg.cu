@@ -4,7 +4,6 @@
 // rather than chasing memory bandwidth.
 #include <math.h>
 
-#include "df.cuh"
 #include "internal.cuh"
 
 namespace rmhmc {
@@ -422,133 +421,6 @@ __global__ void __launch_bounds__(256) k_cholsolve(const double* __restrict__ Lb
 }
 
 }  // namespace
-
-namespace {
-
-// The same tiling in double-float arithmetic (df.cuh) for the mixed-precision form: FP64 operands
-// are split into FP32 pairs as they are staged in shared memory, every output accumulates a Dot2
-// sum (hi word + compensation word), and the result is rounded back to FP64. Thread (ty, tx) owns
-// rows ty + 16 i and columns tx + 16 j of the 64 x 64 tile, as in k_gemm.
-template <bool TA, bool TB, bool AP, bool BP>
-__global__ void __launch_bounds__(GT, 2) k_gemm_df(int m, int n, int k, double alpha,
-                                                const double* __restrict__ A, int lda, long long sA,
-                                                const double* __restrict__ B, int ldb, long long sB,
-                                                double beta, double* __restrict__ C, int ldc,
-                                                long long sC, int sym) {
-  const int tm = blockIdx.y, tn = blockIdx.x, b = blockIdx.z;
-  if (sym && tn > tm) return;
-  A += b * sA;
-  B += b * sB;
-  C += b * sC;
-  __shared__ float2 As[BK][BM + 1];
-  __shared__ float2 Bs[BK][BN + 1];
-  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
-  const int row0 = tm * BM, col0 = tn * BN;
-  float sh[4][4], cl[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) { sh[i][j] = 0.f; cl[i][j] = 0.f; }
-  for (int k0 = 0; k0 < k; k0 += BK) {
-#pragma unroll
-    for (int e = tid; e < BM * BK; e += GT) {
-      int mm, kk;
-      if (TA) { kk = e / BM; mm = e % BM; } else { mm = e / BK; kk = e % BK; }
-      const int gr = row0 + mm, gk = k0 + kk;
-      const long long o = TA ? (long long)gk * lda + gr : (long long)gr * lda + gk;
-      if (AP) As[kk][mm] = (gr < m && gk < k) ? reinterpret_cast<const float2*>(A)[o] : make_float2(0.f, 0.f);
-      else As[kk][mm] = df_split((gr < m && gk < k) ? A[o] : 0.0);
-    }
-#pragma unroll
-    for (int e = tid; e < BN * BK; e += GT) {
-      int kk, nn;
-      if (TB) { nn = e / BK; kk = e % BK; } else { kk = e / BN; nn = e % BN; }
-      const int gk = k0 + kk, gc = col0 + nn;
-      const long long o = TB ? (long long)gc * ldb + gk : (long long)gk * ldb + gc;
-      if (BP) Bs[kk][nn] = (gk < k && gc < n) ? reinterpret_cast<const float2*>(B)[o] : make_float2(0.f, 0.f);
-      else Bs[kk][nn] = df_split((gk < k && gc < n) ? B[o] : 0.0);
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < BK; ++kk) {
-      float2 a[4], bb[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) dot2_step(sh[i][j], cl[i][j], a[i], bb[j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = row0 + ty + 16 * i;
-    if (r >= m) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = col0 + tx + 16 * j;
-      if (c >= n) continue;
-      const double acc = df_join(df_renorm(sh[i][j], cl[i][j]));
-      if (sym) {
-        if (tm == tn && c > r) continue;
-        const double v = alpha * acc;
-        C[(long long)r * ldc + c] = v;
-        if (c != r) C[(long long)c * ldc + r] = v;
-      } else {
-        const long long o = (long long)r * ldc + c;
-        C[o] = alpha * acc + (beta != 0.0 ? beta * C[o] : 0.0);
-      }
-    }
-  }
-}
-
-}  // namespace
-
-namespace {
-template <bool AP, bool BP>
-void gemm_df_launch(cudaStream_t s, bool ta, bool tb, dim3 grid, int m, int n, int k, double alpha,
-                    const double* A, int lda, long long sA, const double* B, int ldb, long long sB,
-                    double beta, double* C, int ldc, long long sC, bool sym) {
-  if (!ta && !tb)
-    k_gemm_df<false, false, AP, BP><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
-  else if (!ta && tb)
-    k_gemm_df<false, true, AP, BP><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
-  else if (ta && !tb)
-    k_gemm_df<true, false, AP, BP><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
-  else
-    k_gemm_df<true, true, AP, BP><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
-}
-
-// x (double) -> (hi, lo) pairs, element for element (the pair buffer has the double layout).
-__global__ void k_to_pairs(const double* __restrict__ x, float2* __restrict__ y, long long n) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    y[e] = df_split(x[e]);
-}
-}  // namespace
-
-void gemm_df(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
-             int lda, long long sA, const double* B, int ldb, long long sB, double beta, double* C,
-             int ldc, long long sC, int batch, bool sym, bool a_pairs, bool b_pairs) {
-  if (m <= 0 || n <= 0 || batch <= 0) return;
-  dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, batch);
-  if (a_pairs && b_pairs)
-    gemm_df_launch<true, true>(s, ta, tb, grid, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
-  else if (a_pairs)
-    gemm_df_launch<true, false>(s, ta, tb, grid, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
-  else if (b_pairs)
-    gemm_df_launch<false, true>(s, ta, tb, grid, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
-  else
-    gemm_df_launch<false, false>(s, ta, tb, grid, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym);
-}
-
-void to_pairs(cudaStream_t s, const double* x, double* pairs, long long n) {
-  if (n <= 0) return;
-  const long long blocks = (n + 255) / 256;
-  k_to_pairs<<<(unsigned)(blocks < 148 * 16 ? blocks : 148 * 16), 256, 0, s>>>(x, reinterpret_cast<float2*>(pairs), n);
-}
 
 void cholsolve_f64(cudaStream_t s, const double* L, const double* f, double* t, double* a, int N,
                    int batch) {

@@ -434,25 +434,24 @@ struct rmhmc_model {
   double *ustat = nullptr; // C x 9: hyperparameter block of the Hessian
   double *Xg_dev = nullptr, *Xl_dev = nullptr;
   double *ld = nullptr;    // J = 2: (9, C, N) likelihood derivatives
-  // the mixed form's double-float GEMM operands, split once into (hi, lo) pairs: Psi^T (refreshed
-  // whenever Psi^T has changed since) and one scratch operand
-  double *pPsi = nullptr, *pA = nullptr;
-  bool psi_pairs_ok = false;
   // the mixed form's tensor-core GEMMs: bf16 slices of the current A-side and B-side operands, and
   // of the two Psi^T views that W = Psi^T^T (C Psi^T) reads (kept until Psi^T changes)
   uint8_t *tcA = nullptr, *tcB = nullptr, *tcPA = nullptr, *tcPB = nullptr;
   bool tc_pa_ok = false, tc_pb_ok = false;
+  // primal model: slices of Phi^T (the Hessian blocks Phi^T diag(l'') Phi) and of Phi (Phi W in the
+  // contraction), split once since Phi is fixed
+  uint8_t *tcPhiT = nullptr, *tcPhi = nullptr;
+  bool tc_phi_ok = false;
 };
 
 namespace {
 
 enum Cat {
   CAT_GEMM = 0, CAT_JACOBI, CAT_CHOL, CAT_TRINV, CAT_MODEL, CAT_CONTRACT, CAT_VECTOR, CAT_MGS, CAT_JACOBI_DF,
-  CAT_GEMM_DF, CAT_GEMM_TC
+  CAT_GEMM_TC
 };
 const char* kCatNames[RMHMC_PROF_NCAT] = {"gemm_f64", "jacobi_f64", "cholesky_f64", "trinv_f64",
-                                          "model", "contract", "vector", "mgs_f64", "jacobi_df", "gemm_df",
-                                          "gemm_tc"};
+                                          "model", "contract", "vector", "mgs_f64", "jacobi_df", "gemm_tc"};
 
 // bf16 slices of the mixed form's tensor-core GEMMs: 9 (63 bits, at or below FP64 GEMM rounding)
 // for the K^-1 algebra, whose cond(K) ~ 1e8 amplification needs FP64-level products, and 8 (56 bits)
@@ -489,7 +488,7 @@ inline double gemm_flops(double mm, double nn, double kk, bool sym, bool tri) {
 }
 
 // The dp x dp products of the eigen-update (M = Psi^T H Psi) and of W = Psi C Psi^T, batched over
-// the chains: FP64, or double-float in the mixed form.
+// the chains: FP64, or on the tensor cores (gemm_tc, bf16 slices) in the mixed form.
 void gemm_dd(rmhmc_model* m, bool ta, bool tb, const double* A, const double* B, double* out, bool sym);
 
 // When planning (m->plan_bytes != nullptr) nothing is allocated: the bytes are only counted.
@@ -535,7 +534,7 @@ void dual_model_layer(rmhmc_model* m, bool third) {
   if (tc) {  // row i of op(A) and row j of op(B)^T are columns of L^-1
     PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Aux, N, NN, false, B, ka);
     PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Aux, N, NN, false, B, kb);
-    PROF(m, CAT_GEMM_TC, Bf * gemm_flops(Nf, Nf, Nf, true, true))
+    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(ka, kb, B, true))
     gemm_tc(s, ka, kb, 1.0, 0.0, m->Kinv, N, NN, B, true, m->status, n);
   } else {
     PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, true, true))
@@ -548,7 +547,7 @@ void dual_model_layer(rmhmc_model* m, bool third) {
   if (tc) {
     PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Kinv, N, NN, true, B, ka);
     PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->D1, N, NN, false, B, kb);
-    PROF(m, CAT_GEMM_TC, Bf * gemm_flops(Nf, Nf, Nf, false, false))
+    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(ka, kb, B, false))
     gemm_tc(s, ka, kb, 1.0, 0.0, m->S, N, NN, B, false, m->status, n);
   } else {
     PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, false, false))
@@ -559,10 +558,10 @@ void dual_model_layer(rmhmc_model* m, bool third) {
     // slices of S's rows reused
     PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->S, N, NN, true, B, ka);
     PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Kinv, N, NN, true, B, kb);
-    PROF(m, CAT_GEMM_TC, Bf * gemm_flops(Nf, Nf, Nf, true, false))
+    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(ka, kb, B, true))
     gemm_tc(s, ka, kb, 1.0, 0.0, m->Aux, N, NN, B, true, m->status, n);
     PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->S, N, NN, false, B, kb);
-    PROF(m, CAT_GEMM_TC, Bf * gemm_flops(Nf, Nf, Nf, false, false))
+    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(ka, kb, B, false))
     gemm_tc(s, ka, kb, 1.0, 0.0, m->S2, N, NN, B, false, m->status, n);
   } else if (third) {
     PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, true, false))
@@ -592,6 +591,24 @@ void dual_model_layer(rmhmc_model* m, bool third) {
 
 // The primal model layer: F = Phi w, likelihood maps, U and dU (Phi^T l' + prior), the Hessian
 // (Phi^T diag(l'') Phi + prior). The third-derivative operator needs only l''' (kept in l3).
+// The primal model's fixed feature matrix, sliced once for the tensor-core GEMMs: op(A) = Phi^T
+// (P rows over the N samples: the Hessian blocks) or Phi (N rows over the P features: Phi W).
+TcOperand phi_operand(rmhmc_model* m, bool transposed) {
+  const int N = m->N, P = m->pd.P;
+  TcOperand op = transposed ? tc_operand(m->tcPhiT, P, N, kSlicesK, 1, false)
+                            : tc_operand(m->tcPhi, N, P, kSlicesK, 1, false);
+  op.shared = true;
+  return op;
+}
+
+void primal_phi_slices(rmhmc_model* m) {
+  if (m->tc_phi_ok) return;
+  const int P = m->pd.P;
+  PROF(m, CAT_GEMM_TC, 0) tc_split(m->stream, m->Phi, P, 0, false, 1, phi_operand(m, true));
+  PROF(m, CAT_GEMM_TC, 0) tc_split(m->stream, m->Phi, P, 0, true, 1, phi_operand(m, false));
+  m->tc_phi_ok = true;
+}
+
 void primal_model_layer(rmhmc_model* m) {
   cudaStream_t s = m->stream;
   const int N = m->N, C = m->C, dp = m->dp, P = m->pd.P, J = m->pd.J;
@@ -617,11 +634,25 @@ void primal_model_layer(rmhmc_model* m) {
   PROF(m, CAT_MODEL, 0)
   dev::k_primal_udu<<<C, 256, 0, s>>>(m->pd, m->q, dp, m->l0, m->lraw, m->U, m->dU, m->LL, m->ustat);
   // the likelihood blocks Phi^T diag(l_jk) Phi of the Hessian ((j, k) and its mirror (k, j))
+  const bool tc = m->precision == RMHMC_MIXED;
+  if (tc) primal_phi_slices(m);
   for (int j = 0; j < J; ++j) {
     for (int k = j; k < J; ++k) {
       const double* ljk = J == 1 ? m->l2 : m->ld + (2 + j + k) * CN;
       PROF(m, CAT_MODEL, 0)
       dev::k_rowscale<<<dim3(nblk(NP), C), 256, 0, s>>>(m->pd, ljk, m->Phi, m->Z);
+      if (tc) {  // op(A) = Phi^T (shared slices), op(B) = Z = diag(l_jk) Phi: its columns
+        const TcOperand pa = phi_operand(m, true);
+        const TcOperand zb = tc_operand(m->tcB, P, N, kSlicesK, C, true);
+        PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Z, P, NP, false, C, zb);
+        PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(pa, zb, C, true) * (k != j ? 2 : 1))
+        {
+          gemm_tc(s, pa, zb, 1.0, 0.0, m->H + (long long)j * P * dp + k * P, dp, DD, C, true, m->status, 1);
+          if (k != j)
+            gemm_tc(s, pa, zb, 1.0, 0.0, m->H + (long long)k * P * dp + j * P, dp, DD, C, true, m->status, 1);
+        }
+        continue;
+      }
       PROF(m, CAT_GEMM, Cf * gemm_flops(Pf, Pf, Nf, true, false))
       gemm_f64(s, true, false, P, P, N, 1.0, m->Phi, P, 0, m->Z, P, NP, 0.0, m->H + (long long)j * P * dp + k * P,
                dp, DD, C, true, false);
@@ -643,7 +674,7 @@ void eval_geometry(rmhmc_model* m, bool third) {
   cudaStream_t s = m->stream;
   const int C = m->C, dp = m->dp, d = m->d;
   const long long DD = (long long)dp * dp;
-  m->psi_pairs_ok = m->tc_pa_ok = m->tc_pb_ok = false;  // Gram-Schmidt or the cold start may change Psi^T
+  m->tc_pa_ok = m->tc_pb_ok = false;  // Gram-Schmidt or the cold start may change Psi^T
   if (m->kind == 1) primal_model_layer(m);
   else dual_model_layer(m, third);
   // Sec. 2.4: Gram-Schmidt of Psi every reorth_every eigen-updates, then M = Psi^T H Psi
@@ -667,7 +698,7 @@ void eval_geometry(rmhmc_model* m, bool third) {
     jacobi_f64(s, m->M, m->PsiT, m->lam, dp, d, C, m->jacobi_rule, m->tol, m->max_sweeps, m->status,
                m->sweeps_last, m->sweeps_acc, m->jw, m->cluster);
   }
-  m->psi_pairs_ok = m->tc_pa_ok = m->tc_pb_ok = false;  // the eigen-update rotated Psi^T
+  m->tc_pa_ok = m->tc_pb_ok = false;  // the eigen-update rotated Psi^T
   PROF(m, CAT_VECTOR, 0)
   k_inc<<<nblk(C), 256, 0, s>>>(m->eig_count, C, m->sweeps_total, m->sweeps_last);
   PROF(m, CAT_VECTOR, 0)
@@ -692,7 +723,7 @@ void gemm_dd(rmhmc_model* m, bool ta, bool tb, const double* A, const double* B,
       PROF(m, CAT_GEMM_TC, 0) tc_split(m->stream, B, dp, DD, tb, m->C, ob);
       if (pb) m->tc_pb_ok = true;
     }
-    PROF(m, CAT_GEMM_TC, fl)
+    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(oa, ob, m->C, sym))
     gemm_tc(m->stream, oa, ob, 1.0, 0.0, out, dp, DD, m->C, sym, m->status, 1);
   } else {
     PROF(m, CAT_GEMM, fl)
@@ -734,9 +765,18 @@ void grad_h(rmhmc_model* m, const double* x, double* out) {
     const double Nf = N, Pf = P;
     for (int j = 0; j < J; ++j) {
       for (int k = j; k < J; ++k) {
-        PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf * Pf)
-        gemm_f64(s, false, false, N, P, P, 1.0, m->Phi, P, 0, m->W + (long long)j * P * dp + k * P, dp, DD, 0.0,
-                 m->Z, P, NP, C, false, false);
+        const double* Wjk = m->W + (long long)j * P * dp + k * P;
+        if (m->precision == RMHMC_MIXED) {  // op(A) = Phi (shared slices), op(B) = W_jk: its columns
+          primal_phi_slices(m);
+          const TcOperand pa = phi_operand(m, false);
+          const TcOperand wb = tc_operand(m->tcB, P, P, kSlicesK, C, true);
+          PROF(m, CAT_GEMM_TC, 0) tc_split(s, Wjk, dp, DD, false, C, wb);
+          PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(pa, wb, C, false))
+          gemm_tc(s, pa, wb, 1.0, 0.0, m->Z, P, NP, C, false, m->status, 1);
+        } else {
+          PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf * Pf)
+          gemm_f64(s, false, false, N, P, P, 1.0, m->Phi, P, 0, Wjk, dp, DD, 0.0, m->Z, P, NP, C, false, false);
+        }
         PROF(m, CAT_CONTRACT, 2.0 * Cf * Nf * Pf)
         dev::k_primal_rowdot<<<dim3((N + 7) / 8, C), 256, 0, s>>>(m->pd, m->Z, m->Phi, J == 1 ? m->l3 : nullptr,
                                                                    m->rvec + (j + k) * CN);
@@ -850,13 +890,17 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
   ALLOC(m->W, C * DD);
   ALLOC(m->Y, C * DD);
   ALLOC(m->PsiT_save, C * DD);
-  ALLOC(m->pPsi, C * DD);
-  ALLOC(m->pA, C * DD);
   {  // tensor-core slices: the K^-1 algebra (dual model) and the d x d products share tcA / tcB
     size_t ba = tc_operand_bytes(dp, dp, kSlicesD, C, false), bb = tc_operand_bytes(dp, dp, kSlicesD, C, true);
     if (m->kind != 1) {
       ba = std::max(ba, tc_operand_bytes(N, N, kSlicesK, (int)B, false));
       bb = std::max(bb, tc_operand_bytes(N, N, kSlicesK, (int)B, true));
+    } else {  // Z = diag(l) Phi and the W blocks as B operands; Phi^T and Phi kept
+      const int P = m->pd.P;
+      bb = std::max(bb, tc_operand_bytes(P, N, kSlicesK, C, true));
+      bb = std::max(bb, tc_operand_bytes(P, P, kSlicesK, C, true));
+      ALLOC(m->tcPhiT, tc_operand_bytes(P, N, kSlicesK, 1, false));
+      ALLOC(m->tcPhi, tc_operand_bytes(N, P, kSlicesK, 1, false));
     }
     ALLOC(m->tcA, ba);
     ALLOC(m->tcB, bb);

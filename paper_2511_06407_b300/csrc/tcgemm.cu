@@ -326,11 +326,13 @@ struct TcArgs {
   const uint8_t* A;  // slices of op(A), rows = output rows
   long long sA;      // bytes per batch entry
   int RA8;           // padded rows / 8
-  const int* eA;     // exponents, RA8 * 8 per batch entry
+  const int* eA;     // exponents, eAs per batch entry (0: one entry shared by all)
+  long long eAs;
   const uint8_t* B;  // slices of op(B)^T, rows = output columns
   long long sB;
   int RB8;
   const int* eB;
+  long long eBs;
   int m, n, KS, ks0, ks1;  // K steps in the split operands, and those of this launch
   double alpha, beta;
   double* C;
@@ -443,13 +445,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
     // the pipeline stages are free now: column exponents, then one 32 x 17 staging tile per warp
     if (threadIdx.x - 64 < TC_N) {
       const int col = n0 + threadIdx.x - 64;
-      sec[threadIdx.x - 64] = col < a.n ? a.eB[(long long)b * a.RB8 * 8 + col] : 0;
+      sec[threadIdx.x - 64] = col < a.n ? a.eB[b * a.eBs + col] : 0;
     }
     asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight epilogue warps only
     double* stg = reinterpret_cast<double*>(smem) + ew * 32 * 17;
     const int r = m0 + q * 32 + lane;
     const bool row_in = r < a.m;
-    const int er = row_in ? a.eA[(long long)b * a.RA8 * 8 + r] : 0;
+    const int er = row_in ? a.eA[b * a.eAs + r] : 0;
     // warp-uniform, since tcgen05.ld is executed by the whole warp
     const bool bad_run = __any_sync(0xffffffffu, !ok || (volatile int&)failed);
     double* Cb = a.C + b * a.sC;
@@ -598,6 +600,15 @@ void tc_split(cudaStream_t s, const double* X, int ld, long long sX, bool kmaj, 
   }
 }
 
+double gemm_tc_tensor_flops(const TcOperand& A, const TcOperand& B, int batch, bool sym) {
+  const int tm = (A.R + TC_M - 1) / TC_M, tn = (B.R + TC_N - 1) / TC_N;
+  long long tiles = 0;  // per batch entry
+  for (int i = 0; i < tm; ++i)
+    for (int j = 0; j < tn; ++j)
+      if (!sym || i * TC_M + TC_M - 1 >= j * TC_N) ++tiles;
+  return (double)tiles * batch * A.KS * (A.S * (A.S + 1) / 2) * 2.0 * TC_M * TC_N * TC_K;
+}
+
 void gemm_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, double alpha, double beta,
              double* C, int ldc, long long sC, int batch, bool sym, int* status, int sdiv) {
   const int m = A.R, n = B.R, KS = A.KS;
@@ -610,13 +621,15 @@ void gemm_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, double alph
   }
   TcArgs a{};
   a.A = A.dig;
-  a.sA = A.bytes_per_entry;
+  a.sA = A.shared ? 0 : A.bytes_per_entry;
   a.RA8 = A.R8;
   a.eA = A.ex;
+  a.eAs = A.shared ? 0 : (long long)A.R8 * 8;
   a.B = B.dig;
-  a.sB = B.bytes_per_entry;
+  a.sB = B.shared ? 0 : B.bytes_per_entry;
   a.RB8 = B.R8;
   a.eB = B.ex;
+  a.eBs = B.shared ? 0 : (long long)B.R8 * 8;
   a.m = m;
   a.n = n;
   a.KS = KS;

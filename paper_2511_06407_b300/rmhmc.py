@@ -22,7 +22,7 @@ PRECISIONS = {"fp64": 0, "mixed": 1}
 JACOBI_RULES = {"metric": 0, "relative": 1}
 EIGEN_STARTS = {"warm": 0, "cold": 1}
 CHAIN_NOTPD, CHAIN_NOTCONV, CHAIN_NONFINITE = 1, 2, 4
-PROF_NCAT = 11
+PROF_NCAT = 10
 
 
 class KernelDesc(ctypes.Structure):
