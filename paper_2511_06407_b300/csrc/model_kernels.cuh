@@ -54,9 +54,9 @@ __device__ __forceinline__ void kern_derivs(const KernelDev& kd, const double* _
   }
 }
 
-// K and D1 = dK/du_1 for every (chain, kernel): grid (tiles, n, C).
+// K and D1, D2, D3 = d^r K / du_1^r for every (chain, kernel): grid (tiles, n, C).
 __global__ void k_assemble(ModelDev md, const double* __restrict__ q, int dp, double* __restrict__ K,
-                           double* __restrict__ D1) {
+                           double* __restrict__ D1, double* __restrict__ D2, double* __restrict__ D3) {
   const int k = blockIdx.y, c = blockIdx.z, N = md.N;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)N * N) return;
@@ -67,6 +67,8 @@ __global__ void k_assemble(ModelDev md, const double* __restrict__ q, int dp, do
   const long long o = ((long long)c * md.n + k) * N * N + e;
   K[o] = D[0];
   D1[o] = D[1];
+  D2[o] = D[2];
+  D3[o] = D[3];
 }
 
 // Latent blocks f_k packed contiguously per (chain, kernel), and tau-scaled likelihood maps of
@@ -127,117 +129,208 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // Per (chain, kernel) vectors and scalars the Hessian (THIRD = false) and the third-derivative
-// operator (THIRD = true) need, with S = K^-1 D1, A1 = S K^-1, S2 = S S (D2, D3 regenerated).
-// On entry `beta` holds t = L^-1 f (used for f . alpha = |t|^2) and is then overwritten:
+// operator (THIRD = true) need, with S = K^-1 D1, A1 = S K^-1, S2 = S S and D1, D2, D3 from
+// k_assemble. On entry `beta` holds t = L^-1 f (used for f . alpha = |t|^2) and is then overwritten:
 //   beta = D1 a, eps2 = D2 a, eps3 = D3 a, gamma = K^-1 beta (= S a), delta = D1 gamma,
 //   fuu11 = K^-1 (2 delta - eps2);  scalars in the Stat slots.
+// Every matrix is symmetric except S and S2, so column sums read rows (coalesced). Each stage runs
+// on a grid (column blocks of 32, chain x kernel): lane = column, the 8 warps split the rows, and
+// the block's part of every scalar goes to part[b][block][slot]; k_stats_reduce adds the parts in a
+// fixed order, so the results do not depend on scheduling.
+constexpr int kStatCols = 32;
+constexpr int kStatMaxBlocks = kMaxN / kStatCols;
+
+__device__ __forceinline__ void stat_part(double v, double* red, double* part_slot) {
+  // sum of v over the CTA (256 threads) into *part_slot; red: 8 doubles of shared memory
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    *part_slot = s;
+  }
+}
+
+// Sum over the 8 warps of a per-(warp, lane) value: the column total, valid in warp 0.
+__device__ __forceinline__ double column_total(double v, double (*col)[kStatCols]) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  col[w][lane] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0)
+    for (int r = 0; r < 8; ++r) s += col[r][lane];
+  __syncthreads();
+  return s;
+}
+
+// Stage 1: beta, eps2, eps3 and the traces <K^-1, D1>, <K^-1, D2>, <K^-1, D3>, <A1, D2>.
 template <bool THIRD>
-__global__ void __launch_bounds__(256) k_stats(ModelDev md, const double* __restrict__ q, int dp,
-                                               const double* __restrict__ D1b,
-                                               const double* __restrict__ Kinvb,
-                                               const double* __restrict__ Sb,
-                                               const double* __restrict__ A1b,
-                                               const double* __restrict__ S2b,
-                                               const double* __restrict__ fpk,
-                                               const double* __restrict__ alphab,
-                                               double* __restrict__ betab, double* __restrict__ gammab,
-                                               double* __restrict__ eps2b, double* __restrict__ eps3b,
-                                               double* __restrict__ deltab,
-                                               double* __restrict__ fuu11b, double* __restrict__ stats) {
-  const int b = blockIdx.x, n = md.n, N = md.N;
-  const int c = b / n, k = b % n;
+__global__ void __launch_bounds__(256) k_stats_cols(int N, const double* __restrict__ D1b,
+                                                    const double* __restrict__ D2b,
+                                                    const double* __restrict__ D3b,
+                                                    const double* __restrict__ Kinvb,
+                                                    const double* __restrict__ A1b,
+                                                    const double* __restrict__ alphab,
+                                                    double* __restrict__ betab, double* __restrict__ eps2b,
+                                                    double* __restrict__ eps3b, double* __restrict__ part) {
+  const int b = blockIdx.y, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kStatCols + lane;
   const long long mo = (long long)b * N * N, vo = (long long)b * N;
-  const double* Kinv = Kinvb + mo;
-  const double* D1 = D1b + mo;
-  const double* S = Sb + mo;
   const double* al = alphab + vo;
-  double* beta = betab + vo;
-  double* gam = gammab + vo;
-  double* eps2 = eps2b + vo;
-  double* eps3 = eps3b + vo;
-  double* del = deltab + vo;
-  double* fuu = fuu11b + vo;
-  double* st = stats + (long long)b * kStatSlots;
-  const double cc = exp(hyper_u(md, q, dp, c, k, 0)), th = exp(hyper_u(md, q, dp, c, k, 1));
-  __shared__ double sh[32];
-  double fa = 0, ab = 0, ae2 = 0, ae3 = 0, trS = 0, trR2 = 0, trR3 = 0, trSR2 = 0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    double bi = 0, e2 = 0, e3 = 0;
-    for (int j = 0; j < N; ++j) {
-      double D[4];
-      kern_derivs(md.k[k], md.X, md.ncov, j, i, cc, th, D);
-      const double aj = al[j];
-      const double kij = Kinv[(long long)j * N + i];
-      bi = fma(D[1], aj, bi);
-      e2 = fma(D[2], aj, e2);
-      trS = fma(kij, D[1], trS);
-      trR2 = fma(kij, D[2], trR2);
+  __shared__ double col[8][kStatCols];
+  __shared__ double red[8];
+  double bi = 0, e2 = 0, e3 = 0, trS = 0, trR2 = 0, trR3 = 0, trSR2 = 0;
+  if (i < N) {
+    for (int j = w; j < N; j += 8) {
+      const long long o = mo + (long long)j * N + i;
+      const double aj = al[j], kij = Kinvb[o], d1 = D1b[o], d2 = D2b[o];
+      bi = fma(d1, aj, bi);
+      e2 = fma(d2, aj, e2);
+      trS = fma(kij, d1, trS);
+      trR2 = fma(kij, d2, trR2);
       if (THIRD) {
-        e3 = fma(D[3], aj, e3);
-        trR3 = fma(kij, D[3], trR3);
-        trSR2 = fma(A1b[mo + (long long)j * N + i], D[2], trSR2);
+        const double d3 = D3b[o];
+        e3 = fma(d3, aj, e3);
+        trR3 = fma(kij, d3, trR3);
+        trSR2 = fma(A1b[o], d2, trSR2);
       }
     }
-    // on entry beta holds t = L^-1 f, so f . alpha = f^T K^-1 f = |t|^2 (a sum of squares)
-    const double ti = beta[i];
-    fa = fma(ti, ti, fa);
-    beta[i] = bi;
-    eps2[i] = e2;
-    if (THIRD) eps3[i] = e3;
-    ab = fma(al[i], bi, ab);
-    ae2 = fma(al[i], e2, ae2);
-    if (THIRD) ae3 = fma(al[i], e3, ae3);
   }
-  __syncthreads();
-  double gb = 0, ge2 = 0, trS2 = 0, trS3 = 0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    double gi = 0, s2 = 0, s3 = 0;
-    for (int j = 0; j < N; ++j) {
-      gi = fma(Kinv[(long long)j * N + i], beta[j], gi);
-      const double sji = S[(long long)j * N + i];
-      s2 = fma(S[(long long)i * N + j], sji, s2);
-      if (THIRD) s3 = fma(S2b[mo + (long long)i * N + j], sji, s3);
+  bi = column_total(bi, col);
+  e2 = column_total(e2, col);
+  if (THIRD) e3 = column_total(e3, col);
+  double fa = 0, ab = 0, ae2 = 0, ae3 = 0;
+  if (w == 0 && i < N) {
+    const double ti = betab[vo + i];  // t = L^-1 f on entry
+    fa = ti * ti;
+    betab[vo + i] = bi;
+    eps2b[vo + i] = e2;
+    if (THIRD) eps3b[vo + i] = e3;
+    ab = al[i] * bi;
+    ae2 = al[i] * e2;
+    ae3 = al[i] * e3;
+  }
+  double* pp = part + ((long long)b * kStatMaxBlocks + blockIdx.x) * ST_COUNT;
+  stat_part(fa, red, pp + ST_FA);
+  stat_part(ab, red, pp + ST_AB);
+  stat_part(ae2, red, pp + ST_AE2);
+  stat_part(trS, red, pp + ST_TRS);
+  stat_part(trR2, red, pp + ST_TRR2);
+  if (THIRD) {
+    stat_part(ae3, red, pp + ST_AE3);
+    stat_part(trR3, red, pp + ST_TRR3);
+    stat_part(trSR2, red, pp + ST_TRSR2);
+  }
+}
+
+// Stage 2: gamma = K^-1 beta, gamma . beta, gamma . eps2, tr(S^2) = sum S_ij S_ji and
+// tr(S^3) = sum (S^2)_ij S_ji; the transposed reads go through a 32 x 33 shared tile.
+template <bool THIRD>
+__global__ void __launch_bounds__(256) k_stats_gamma(int N, const double* __restrict__ Kinvb,
+                                                     const double* __restrict__ Sb,
+                                                     const double* __restrict__ S2b,
+                                                     const double* __restrict__ betab,
+                                                     const double* __restrict__ eps2b,
+                                                     double* __restrict__ gammab, double* __restrict__ part) {
+  const int b = blockIdx.y, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.x * kStatCols, i = i0 + lane;
+  const long long mo = (long long)b * N * N, vo = (long long)b * N;
+  const double* be = betab + vo;
+  __shared__ double col[8][kStatCols];
+  __shared__ double red[8];
+  __shared__ double tS[kStatCols][kStatCols + 1], tS2[kStatCols][kStatCols + 1];
+  double gi = 0, s2 = 0, s3 = 0;
+  for (int j0 = 0; j0 < N; j0 += kStatCols) {
+    // rows i0.. of S (and S2) at columns j0..: tS[ii][jj] = S[i0 + ii][j0 + jj]
+    for (int r = w; r < kStatCols; r += 8) {
+      const int ii = i0 + r, jj = j0 + lane;
+      const bool in = ii < N && jj < N;
+      tS[r][lane] = in ? Sb[mo + (long long)ii * N + jj] : 0.0;
+      if (THIRD) tS2[r][lane] = in ? S2b[mo + (long long)ii * N + jj] : 0.0;
     }
-    gam[i] = gi;
-    gb = fma(gi, beta[i], gb);
-    ge2 = fma(gi, eps2[i], ge2);
-    trS2 += s2;
-    trS3 += s3;
+    __syncthreads();
+    for (int r = w; r < kStatCols; r += 8) {
+      const int j = j0 + r;
+      if (j < N && i < N) {
+        const long long o = mo + (long long)j * N + i;
+        gi = fma(Kinvb[o], be[j], gi);
+        const double sji = Sb[o];
+        s2 = fma(tS[lane][r], sji, s2);
+        if (THIRD) s3 = fma(tS2[lane][r], sji, s3);
+      }
+    }
+    __syncthreads();
   }
+  gi = column_total(gi, col);
+  double gb = 0, ge2 = 0;
+  if (w == 0 && i < N) {
+    gammab[vo + i] = gi;
+    gb = gi * be[i];
+    ge2 = gi * eps2b[vo + i];
+  }
+  double* pp = part + ((long long)b * kStatMaxBlocks + blockIdx.x) * ST_COUNT;
+  stat_part(gb, red, pp + ST_GB);
+  stat_part(ge2, red, pp + ST_GE2);
+  stat_part(s2, red, pp + ST_TRS2);
+  if (THIRD) stat_part(s3, red, pp + ST_TRS3);
+}
+
+// Stage 3 (THIRD): delta = D1 gamma, alpha . delta, gamma . delta.
+__global__ void __launch_bounds__(256) k_stats_delta(int N, const double* __restrict__ D1b,
+                                                     const double* __restrict__ alphab,
+                                                     const double* __restrict__ gammab,
+                                                     double* __restrict__ deltab, double* __restrict__ part) {
+  const int b = blockIdx.y, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kStatCols + lane;
+  const long long mo = (long long)b * N * N, vo = (long long)b * N;
+  __shared__ double col[8][kStatCols];
+  __shared__ double red[8];
+  double di = 0;
+  if (i < N)
+    for (int j = w; j < N; j += 8) di = fma(D1b[mo + (long long)j * N + i], gammab[vo + j], di);
+  di = column_total(di, col);
   double ad = 0, gd = 0;
-  if (THIRD) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-      double di = 0;
-      for (int j = 0; j < N; ++j) di = fma(D1[(long long)j * N + i], gam[j], di);
-      del[i] = di;
-      ad = fma(al[i], di, ad);
-      gd = fma(gam[i], di, gd);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-      double v = 0;
-      for (int j = 0; j < N; ++j) v = fma(Kinv[(long long)j * N + i], 2.0 * del[j] - eps2[j], v);
-      fuu[i] = v;
-    }
+  if (w == 0 && i < N) {
+    deltab[vo + i] = di;
+    ad = alphab[vo + i] * di;
+    gd = gammab[vo + i] * di;
   }
-  double r;
-  r = block_sum(fa, sh);    if (threadIdx.x == 0) st[ST_FA] = r;
-  r = block_sum(ab, sh);    if (threadIdx.x == 0) st[ST_AB] = r;
-  r = block_sum(ae2, sh);   if (threadIdx.x == 0) st[ST_AE2] = r;
-  r = block_sum(gb, sh);    if (threadIdx.x == 0) st[ST_GB] = r;
-  r = block_sum(ge2, sh);   if (threadIdx.x == 0) st[ST_GE2] = r;
-  r = block_sum(trS, sh);   if (threadIdx.x == 0) st[ST_TRS] = r;
-  r = block_sum(trS2, sh);  if (threadIdx.x == 0) st[ST_TRS2] = r;
-  r = block_sum(trR2, sh);  if (threadIdx.x == 0) st[ST_TRR2] = r;
-  if (THIRD) {
-    r = block_sum(ae3, sh);   if (threadIdx.x == 0) st[ST_AE3] = r;
-    r = block_sum(ad, sh);    if (threadIdx.x == 0) st[ST_AD] = r;
-    r = block_sum(gd, sh);    if (threadIdx.x == 0) st[ST_GD] = r;
-    r = block_sum(trS3, sh);  if (threadIdx.x == 0) st[ST_TRS3] = r;
-    r = block_sum(trR3, sh);  if (threadIdx.x == 0) st[ST_TRR3] = r;
-    r = block_sum(trSR2, sh); if (threadIdx.x == 0) st[ST_TRSR2] = r;
-  }
+  double* pp = part + ((long long)b * kStatMaxBlocks + blockIdx.x) * ST_COUNT;
+  stat_part(ad, red, pp + ST_AD);
+  stat_part(gd, red, pp + ST_GD);
+}
+
+// Stage 4 (THIRD): fuu11 = K^-1 (2 delta - eps2).
+__global__ void __launch_bounds__(256) k_stats_fuu(int N, const double* __restrict__ Kinvb,
+                                                   const double* __restrict__ deltab,
+                                                   const double* __restrict__ eps2b,
+                                                   double* __restrict__ fuu11b) {
+  const int b = blockIdx.y, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kStatCols + lane;
+  const long long mo = (long long)b * N * N, vo = (long long)b * N;
+  __shared__ double col[8][kStatCols];
+  double v = 0;
+  if (i < N)
+    for (int j = w; j < N; j += 8)
+      v = fma(Kinvb[mo + (long long)j * N + i], 2.0 * deltab[vo + j] - eps2b[vo + j], v);
+  v = column_total(v, col);
+  if (w == 0 && i < N) fuu11b[vo + i] = v;
+}
+
+// stats[b][slot] = the blocks' parts of the slots the stages wrote, added in block order.
+__global__ void k_stats_reduce(int nblocks, int third, const double* __restrict__ part,
+                               double* __restrict__ stats) {
+  const int b = blockIdx.x, slot = threadIdx.x;
+  if (slot >= ST_COUNT || slot == ST_LOGDET) return;
+  const bool third_slot = slot == ST_AE3 || slot == ST_AD || slot == ST_GD || slot == ST_TRS3 ||
+                          slot == ST_TRR3 || slot == ST_TRSR2;
+  if (third_slot && !third) return;
+  double s = 0.0;
+  for (int k = 0; k < nblocks; ++k) s += part[((long long)b * kStatMaxBlocks + k) * ST_COUNT + slot];
+  stats[(long long)b * kStatSlots + slot] = s;
 }
 
 __device__ __forceinline__ double log_prior_u(double a, double b, double u) {

@@ -400,7 +400,8 @@ struct rmhmc_model {
   uint64_t iter = 0;
   std::vector<void*> allocs;
   // per (chain, kernel) N x N
-  double *KL, *D1, *Kinv, *S, *Aux, *S2;
+  double *KL, *D1, *D2, *D3, *Kinv, *S, *Aux, *S2;
+  double* spart;  // per (chain, kernel): partial sums of the statistics stages
   // per (chain, kernel) N-vectors
   double *fpk, *alpha_, *beta, *gamma, *eps2, *eps3, *delta, *fuu11;
   double* stats;
@@ -520,7 +521,7 @@ void dual_model_layer(rmhmc_model* m, bool third) {
   const int B = C * n;
   const double Nf = N, Bf = B;
   PROF(m, CAT_MODEL, 0)
-  dev::k_assemble<<<dim3(nblk(NN), n, C), 256, 0, s>>>(m->md, m->q, dp, m->KL, m->D1);
+  dev::k_assemble<<<dim3(nblk(NN), n, C), 256, 0, s>>>(m->md, m->q, dp, m->KL, m->D1, m->D2, m->D3);
   PROF(m, CAT_MODEL, 0)
   dev::k_lik<<<dim3(nblk(N), C), 256, 0, s>>>(m->md, m->q, dp, m->fpk, m->l0, m->l1, m->l2, m->l3, m->lraw);
   PROF(m, CAT_CHOL, Bf * Nf * Nf * Nf / 3.0)
@@ -569,17 +570,27 @@ void dual_model_layer(rmhmc_model* m, bool third) {
     PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, false, false))
     gemm_f64(s, false, false, N, N, N, 1.0, m->S, N, NN, m->S, N, NN, 0.0, m->S2, N, NN, B, false, false);
   }
+  const dim3 sg((N + dev::kStatCols - 1) / dev::kStatCols, B);
   if (third) {
     PROF(m, CAT_MODEL, 0)
-    dev::k_stats<true><<<B, 256, 0, s>>>(m->md, m->q, dp, m->D1, m->Kinv, m->S, m->Aux, m->S2, m->fpk,
-                                         m->alpha_, m->beta, m->gamma, m->eps2, m->eps3, m->delta,
-                                         m->fuu11, m->stats);
+    dev::k_stats_cols<true><<<sg, 256, 0, s>>>(N, m->D1, m->D2, m->D3, m->Kinv, m->Aux, m->alpha_, m->beta,
+                                               m->eps2, m->eps3, m->spart);
+    PROF(m, CAT_MODEL, 0)
+    dev::k_stats_gamma<true><<<sg, 256, 0, s>>>(N, m->Kinv, m->S, m->S2, m->beta, m->eps2, m->gamma, m->spart);
+    PROF(m, CAT_MODEL, 0)
+    dev::k_stats_delta<<<sg, 256, 0, s>>>(N, m->D1, m->alpha_, m->gamma, m->delta, m->spart);
+    PROF(m, CAT_MODEL, 0)
+    dev::k_stats_fuu<<<sg, 256, 0, s>>>(N, m->Kinv, m->delta, m->eps2, m->fuu11);
   } else {
     PROF(m, CAT_MODEL, 0)
-    dev::k_stats<false><<<B, 256, 0, s>>>(m->md, m->q, dp, m->D1, m->Kinv, m->S, m->Aux, m->S2, m->fpk,
-                                          m->alpha_, m->beta, m->gamma, m->eps2, m->eps3, m->delta,
-                                          m->fuu11, m->stats);
+    dev::k_stats_cols<false><<<sg, 256, 0, s>>>(N, m->D1, m->D2, m->D3, m->Kinv, m->Aux, m->alpha_, m->beta,
+                                                m->eps2, m->eps3, m->spart);
+    PROF(m, CAT_MODEL, 0)
+    dev::k_stats_gamma<false><<<sg, 256, 0, s>>>(N, m->Kinv, m->S, m->S2, m->beta, m->eps2, m->gamma,
+                                                 m->spart);
   }
+  PROF(m, CAT_MODEL, 0)
+  dev::k_stats_reduce<<<B, 32, 0, s>>>((int)sg.x, third ? 1 : 0, m->spart, m->stats);
   PROF(m, CAT_MODEL, 0)
   dev::k_udu<<<C, 256, 0, s>>>(m->md, m->q, dp, m->l0, m->l1, m->lraw, m->alpha_, m->stats, m->U,
                                m->dU, m->LL);
@@ -865,6 +876,9 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
     ALLOC(m->uf_dev, (size_t)2 * n);
     ALLOC(m->KL, B * NN);
     ALLOC(m->D1, B * NN);
+    ALLOC(m->D2, B * NN);
+    ALLOC(m->D3, B * NN);
+    ALLOC(m->spart, B * dev::kStatMaxBlocks * ST_COUNT);
     ALLOC(m->Kinv, B * NN);
     ALLOC(m->S, B * NN);
     ALLOC(m->Aux, B * NN);
