@@ -87,6 +87,11 @@ void cholsolve_f64(cudaStream_t s, const double* L, const double* f, double* t, 
                    int batch);
 // X = L^-1 (lower triangular) for batch matrices.
 void trinv_lower_f64(cudaStream_t s, const double* L, double* X, int N, int batch);
+// The same, recursively with the off-diagonal blocks X21 = -X22 (L21 X11) on the tensor cores
+// (gemm_tc, 9 slices): tcA / tcB hold the operands' slices (A side and B side, up to N x N), T is
+// batch x N x N doubles of scratch (only (N/2 + 16)^2 per matrix used).
+void trinv_lower_tc(cudaStream_t s, const double* L, double* X, int N, int batch, uint8_t* tcA,
+                    uint8_t* tcB, double* T, int* status, int sdiv);
 // y_b = op(A_b) x_b for batch N x N (ld) matrices; row-major.
 void gemv_f64(cudaStream_t s, bool ta, int rows, int cols, const double* A, int lda, long long sA,
               const double* x, long long sx, double* y, long long sy, int batch, double alpha,

@@ -261,14 +261,15 @@ __global__ void __launch_bounds__(256) k_chol(double* __restrict__ Ab, int N,
   }
 }
 
-// X = L^-1 for lower-triangular L: one CTA per (32-column tile, matrix). Column tile c0 of X is
-// zero above row c0; each 32-row block below is a small GEMM against the rows already solved
-// followed by forward substitution with the diagonal block.
+// X = L^-1 for the lower-triangular diagonal block L[o:o+N, o:o+N] of an ld x ld matrix (o = 0,
+// N = ld: the whole matrix): one CTA per (32-column tile, matrix). Column tile c0 of X is zero above
+// row c0; each 32-row block below is a small GEMM against the rows already solved followed by
+// forward substitution with the diagonal block.
 __global__ void __launch_bounds__(256) k_trinv(const double* __restrict__ Lb,
-                                              double* __restrict__ Xb, int N) {
+                                              double* __restrict__ Xb, int N, int ld, int o) {
   const int ct = blockIdx.x, b = blockIdx.y;
-  const double* L = Lb + (long long)b * N * N;
-  double* X = Xb + (long long)b * N * N;
+  const double* L = Lb + (long long)b * ld * ld + (long long)o * ld + o;
+  double* X = Xb + (long long)b * ld * ld + (long long)o * ld + o;
   const int c0 = ct * CB;
   const int cn = min(CB, N - c0);
   __shared__ double Ls[CB][CB + 1];
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(256) k_trinv(const double* __restrict__ Lb,
   __shared__ double R[CB][CB + 1];
   const int tid = threadIdx.x;
   for (int r = tid; r < c0; r += blockDim.x)
-    for (int j = 0; j < cn; ++j) X[(long long)r * N + c0 + j] = 0.0;
+    for (int j = 0; j < cn; ++j) X[(long long)r * ld + c0 + j] = 0.0;
   for (int r0 = c0; r0 < N; r0 += CB) {
     const int rn = min(CB, N - r0);
     for (int e = tid; e < CB * CB; e += blockDim.x) {
@@ -287,8 +288,8 @@ __global__ void __launch_bounds__(256) k_trinv(const double* __restrict__ Lb,
       __syncthreads();
       for (int e = tid; e < CB * CB; e += blockDim.x) {
         const int i = e / CB, j = e % CB;
-        Ls[i][j] = (i < rn) ? L[(long long)(r0 + i) * N + p0 + j] : 0.0;
-        Xs[i][j] = (j < cn) ? X[(long long)(p0 + i) * N + c0 + j] : 0.0;
+        Ls[i][j] = (i < rn) ? L[(long long)(r0 + i) * ld + p0 + j] : 0.0;
+        Xs[i][j] = (j < cn) ? X[(long long)(p0 + i) * ld + c0 + j] : 0.0;
       }
       __syncthreads();
       for (int e = tid; e < CB * CB; e += blockDim.x) {
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(256) k_trinv(const double* __restrict__ Lb,
     __syncthreads();
     for (int e = tid; e < CB * CB; e += blockDim.x) {
       const int i = e / CB, j = e % CB;
-      Ls[i][j] = (i < rn && j < rn) ? L[(long long)(r0 + i) * N + r0 + j] : (i == j ? 1.0 : 0.0);
+      Ls[i][j] = (i < rn && j < rn) ? L[(long long)(r0 + i) * ld + r0 + j] : (i == j ? 1.0 : 0.0);
     }
     __syncthreads();
     if (tid < CB) {
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(256) k_trinv(const double* __restrict__ Lb,
     __syncthreads();
     for (int e = tid; e < rn * cn; e += blockDim.x) {
       const int i = e / cn, j = e % cn;
-      X[(long long)(r0 + i) * N + c0 + j] = R[i][j];
+      X[(long long)(r0 + i) * ld + c0 + j] = R[i][j];
     }
     __syncthreads();
   }
@@ -463,7 +464,56 @@ void cholesky_f64(cudaStream_t s, double* A, int N, int batch, double* logdet, i
 void trinv_lower_f64(cudaStream_t s, const double* L, double* X, int N, int batch) {
   if (batch <= 0) return;
   dim3 grid((N + CB - 1) / CB, batch);
-  k_trinv<<<grid, 256, 0, s>>>(L, X, N);
+  k_trinv<<<grid, 256, 0, s>>>(L, X, N, N, 0);
+}
+
+// X[i][j] = 0 for j > i (the blocks above the diagonal that the recursion never writes).
+__global__ void k_zero_upper(double* __restrict__ Xb, int N) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)N * N) return;
+  if (e % N > e / N) Xb[(long long)blockIdx.y * N * N + e] = 0.0;
+}
+
+namespace {
+
+// X[o:o+n, o:o+n] = L[o:o+n, o:o+n]^-1: leaves of at most 128 rows by k_trinv, otherwise
+//   X11 = L11^-1, X22 = L22^-1, X21 = -X22 (L21 X11)
+// with the two products on the tensor cores (FP64-accurate, 9 slices). T: batch x (N/2 + 16)^2.
+void trinv_rec(cudaStream_t s, const double* L, double* X, int N, int o, int n, int batch,
+               uint8_t* tcA, uint8_t* tcB, double* T, int* status, int sdiv) {
+  if (n <= 128) {
+    k_trinv<<<dim3((n + CB - 1) / CB, batch), 256, 0, s>>>(L, X, n, N, o);
+    return;
+  }
+  const int n1 = ((n / 2 + 15) / 16) * 16, n2 = n - n1;
+  trinv_rec(s, L, X, N, o, n1, batch, tcA, tcB, T, status, sdiv);
+  trinv_rec(s, L, X, N, o + n1, n2, batch, tcA, tcB, T, status, sdiv);
+  const long long NN = (long long)N * N;
+  const double* L21 = L + (long long)(o + n1) * N + o;
+  const double* X11 = X + (long long)o * N + o;
+  const double* X22 = X + (long long)(o + n1) * N + o + n1;
+  double* X21 = X + (long long)(o + n1) * N + o;
+  constexpr int S = 9;
+  // T = L21 X11 (n2 x n1): rows of L21, columns of X11
+  TcOperand a = tc_operand(tcA, n2, n1, S, batch, false), b = tc_operand(tcB, n1, n1, S, batch, true);
+  tc_split(s, L21, N, NN, true, batch, a);
+  tc_split(s, X11, N, NN, false, batch, b);
+  gemm_tc(s, a, b, 1.0, 0.0, T, n1, (long long)n2 * n1, batch, false, status, sdiv);
+  // X21 = -X22 T (n2 x n1): rows of X22, columns of T
+  a = tc_operand(tcA, n2, n2, S, batch, false);
+  b = tc_operand(tcB, n1, n2, S, batch, true);
+  tc_split(s, X22, N, NN, true, batch, a);
+  tc_split(s, T, n1, (long long)n2 * n1, false, batch, b);
+  gemm_tc(s, a, b, -1.0, 0.0, X21, N, NN, batch, false, status, sdiv);
+}
+
+}  // namespace
+
+void trinv_lower_tc(cudaStream_t s, const double* L, double* X, int N, int batch, uint8_t* tcA,
+                    uint8_t* tcB, double* T, int* status, int sdiv) {
+  if (batch <= 0 || N <= 0) return;
+  k_zero_upper<<<dim3((unsigned)(((long long)N * N + 255) / 256), batch), 256, 0, s>>>(X, N);
+  trinv_rec(s, L, X, N, 0, N, batch, tcA, tcB, T, status, sdiv);
 }
 
 void gemv_f64(cudaStream_t s, bool ta, int rows, int cols, const double* A, int lda, long long sA,

@@ -526,9 +526,11 @@ void dual_model_layer(rmhmc_model* m, bool third) {
   dev::k_lik<<<dim3(nblk(N), C), 256, 0, s>>>(m->md, m->q, dp, m->fpk, m->l0, m->l1, m->l2, m->l3, m->lraw);
   PROF(m, CAT_CHOL, Bf * Nf * Nf * Nf / 3.0)
   cholesky_f64(s, m->KL, N, B, m->stats + ST_LOGDET, kStatSlots, m->status, n);
-  PROF(m, CAT_TRINV, Bf * Nf * Nf * Nf / 3.0)
-  trinv_lower_f64(s, m->KL, m->Aux, N, B);
   const bool tc = m->precision == RMHMC_MIXED;
+  PROF(m, CAT_TRINV, Bf * Nf * Nf * Nf / 3.0) {
+    if (tc) trinv_lower_tc(s, m->KL, m->Aux, N, B, m->tcA, m->tcB, m->S, m->status, n);
+    else trinv_lower_f64(s, m->KL, m->Aux, N, B);
+  }
   const TcOperand ka = tc_operand(m->tcA, N, N, kSlicesK, B, false);
   const TcOperand kb = tc_operand(m->tcB, N, N, kSlicesK, B, true);
   // K^-1 = L^-T L^-1 (symmetric; the sum runs over k >= max(i, j) only)
