@@ -461,6 +461,28 @@ void cholesky_f64(cudaStream_t s, double* A, int N, int batch, double* logdet, i
   }
 }
 
+void cholesky_tc(cudaStream_t s, double* A, int N, int batch, double* logdet, int logdet_stride,
+                 int* status, int per_chain, uint8_t* tcA, uint8_t* tcB) {
+  if (batch <= 0) return;
+  if (N <= 2 * CB) {
+    k_chol<<<batch, 256, 0, s>>>(A, N, logdet, logdet_stride, status, per_chain);
+    return;
+  }
+  const long long NN = (long long)N * N;
+  for (int k0 = 0; k0 < N; k0 += CB) {
+    k_chol_panel<<<batch, 256, 0, s>>>(A, N, k0, logdet, logdet_stride, status, per_chain);
+    const int k1 = k0 + CB;
+    if (k1 < N) {  // A22 -= L21 L21^T, L21 = A[k1:, k0:k1] (rows of L21 on both sides)
+      double* L21 = A + (long long)k1 * N + k0;
+      const TcOperand a = tc_operand(tcA, N - k1, CB, 9, batch, false);
+      const TcOperand b = tc_operand(tcB, N - k1, CB, 9, batch, true);
+      tc_split(s, L21, N, NN, true, batch, a);
+      tc_split(s, L21, N, NN, true, batch, b);
+      gemm_tc(s, a, b, -1.0, 1.0, A + (long long)k1 * N + k1, N, NN, batch, true, status, per_chain);
+    }
+  }
+}
+
 void trinv_lower_f64(cudaStream_t s, const double* L, double* X, int N, int batch) {
   if (batch <= 0) return;
   dim3 grid((N + CB - 1) / CB, batch);

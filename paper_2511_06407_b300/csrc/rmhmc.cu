@@ -451,7 +451,7 @@ enum Cat {
   CAT_GEMM = 0, CAT_JACOBI, CAT_CHOL, CAT_TRINV, CAT_MODEL, CAT_CONTRACT, CAT_VECTOR, CAT_MGS, CAT_JACOBI_DF,
   CAT_GEMM_TC
 };
-const char* kCatNames[RMHMC_PROF_NCAT] = {"gemm_f64", "jacobi_f64", "cholesky_f64", "trinv_f64",
+const char* kCatNames[RMHMC_PROF_NCAT] = {"gemm_f64", "jacobi_f64", "cholesky", "trinv",
                                           "model", "contract", "vector", "mgs_f64", "jacobi_df", "gemm_tc"};
 
 // bf16 slices of the mixed form's tensor-core GEMMs: 9 (63 bits, at or below FP64 GEMM rounding)
@@ -524,9 +524,11 @@ void dual_model_layer(rmhmc_model* m, bool third) {
   dev::k_assemble<<<dim3(nblk(NN), n, C), 256, 0, s>>>(m->md, m->q, dp, m->KL, m->D1, m->D2, m->D3);
   PROF(m, CAT_MODEL, 0)
   dev::k_lik<<<dim3(nblk(N), C), 256, 0, s>>>(m->md, m->q, dp, m->fpk, m->l0, m->l1, m->l2, m->l3, m->lraw);
-  PROF(m, CAT_CHOL, Bf * Nf * Nf * Nf / 3.0)
-  cholesky_f64(s, m->KL, N, B, m->stats + ST_LOGDET, kStatSlots, m->status, n);
   const bool tc = m->precision == RMHMC_MIXED;
+  PROF(m, CAT_CHOL, Bf * Nf * Nf * Nf / 3.0) {
+    if (tc) cholesky_tc(s, m->KL, N, B, m->stats + ST_LOGDET, kStatSlots, m->status, n, m->tcA, m->tcB);
+    else cholesky_f64(s, m->KL, N, B, m->stats + ST_LOGDET, kStatSlots, m->status, n);
+  }
   PROF(m, CAT_TRINV, Bf * Nf * Nf * Nf / 3.0) {
     if (tc) trinv_lower_tc(s, m->KL, m->Aux, N, B, m->tcA, m->tcB, m->S, m->status, n);
     else trinv_lower_f64(s, m->KL, m->Aux, N, B);
