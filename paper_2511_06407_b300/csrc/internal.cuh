@@ -80,12 +80,13 @@ void gemm_f64(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alph
               int ldc, long long sC, int batch, bool sym, bool tri);
 // In-place lower Cholesky of batch N x N matrices (row-major, ld = N); writes log|K| to
 // logdet[b * logdet_stride] and sets status bit RMHMC_CHAIN_NOTPD in status[b / per_chain].
+// rdiag: batch x 32 doubles of scratch (the reciprocal pivots of one panel).
 void cholesky_f64(cudaStream_t s, double* A, int N, int batch, double* logdet, int logdet_stride,
-                  int* status, int per_chain);
+                  int* status, int per_chain, double* rdiag);
 // The same with the trailing updates A22 -= L21 L21^T on the tensor cores (gemm_tc, 9 slices); the
 // panels (diagonal block and L21 by substitution) stay FP64. tcA / tcB: slices of N x 32 operands.
 void cholesky_tc(cudaStream_t s, double* A, int N, int batch, double* logdet, int logdet_stride,
-                 int* status, int per_chain, uint8_t* tcA, uint8_t* tcB);
+                 int* status, int per_chain, uint8_t* tcA, uint8_t* tcB, double* rdiag);
 // t = L^-1 f and a = L^-T t (= K^-1 f) by substitution, per (batch) factor L.
 void cholsolve_f64(cudaStream_t s, const double* L, const double* f, double* t, double* a, int N,
                    int batch);

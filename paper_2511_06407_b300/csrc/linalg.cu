@@ -96,73 +96,90 @@ __global__ void __launch_bounds__(GT) k_gemm(int m, int n, int k, double alpha,
 
 constexpr int CB = 32;  // Cholesky / triangular-inverse block
 
-// In-place right-looking blocked Cholesky (lower) of one N x N matrix per CTA; the strict upper
-// triangle is zeroed. A pivot that is not positive marks the chain and is replaced by 1 so that
-// the factor stays finite.
-// One panel step of the blocked right-looking Cholesky, one CTA per matrix: factor the kb x kb
-// diagonal block at (k0, k0) in shared memory, solve the panel below it (L21 = A21 L11^-T, a row
-// per thread) and add the block's share of log|A|. The trailing update A22 -= L21 L21^T between
-// panel steps is a batched symmetric GEMM over all matrices (so every SM takes part), and the last
-// step zeroes the strict upper triangle. A non-positive pivot is replaced by 1 and flags the chain.
-__global__ void __launch_bounds__(256) k_chol_panel(double* __restrict__ Ab, int N, int k0,
-                                                   double* __restrict__ logdet, int lds,
-                                                   int* __restrict__ status, int per_chain) {
-  const int b = blockIdx.x;
+// In-place right-looking blocked Cholesky (lower) of one N x N matrix per CTA (small N); the strict
+// upper triangle is zeroed. A pivot that is not positive marks the chain and is replaced by 1 so
+// that the factor stays finite. Larger N: panel steps (k_chol_diag + k_chol_rows) with the
+// trailing update A22 -= L21 L21^T between them as a batched symmetric GEMM over all matrices (so
+// every SM takes part).
+// The panel step split for parallelism. k_chol_diag: one warp per matrix factors the kb x kb
+// diagonal block at (k0, k0) (right-looking, lane = row), writes it back with zeros above its
+// diagonal, keeps the reciprocal pivots in rdiag (kb per matrix) and adds its share of log|A|.
+__global__ void __launch_bounds__(32) k_chol_diag(double* __restrict__ Ab, int N, int k0,
+                                                 double* __restrict__ rdiag,
+                                                 double* __restrict__ logdet, int lds,
+                                                 int* __restrict__ status, int per_chain) {
+  const int b = blockIdx.x, lane = threadIdx.x;
   double* A = Ab + (long long)b * N * N;
-  __shared__ double Dk[CB][CB + 1];
-  __shared__ int bad;
-  __shared__ double ldacc;
-  const int tid = threadIdx.x;
   const int kb = min(CB, N - k0);
-  if (tid == 0) { bad = 0; ldacc = 0.0; }
-  for (int e = tid; e < kb * kb; e += blockDim.x) {
-    const int i = e / kb, j = e % kb;
-    Dk[i][j] = A[(long long)(k0 + i) * N + k0 + j];
-  }
-  __syncthreads();
+  __shared__ double Dk[CB][CB + 1];
+  for (int e = lane; e < kb * kb; e += 32) Dk[e / kb][e % kb] = A[(long long)(k0 + e / kb) * N + k0 + e % kb];
+  __syncwarp();
+  __shared__ double sir;
+  bool bad = false;
+  double pm = 1.0;  // product of the pivots' square roots as pm 2^pe (one log at the end)
+  int pe = 0;
   for (int j = 0; j < kb; ++j) {
-    if (tid == 0) {
+    if (lane == 0) {  // pivot arithmetic in one lane (FP64 sqrt and division are costly here)
       double piv = Dk[j][j];
-      if (!(piv > 0.0) || !isfinite(piv)) { bad = 1; piv = 1.0; }
+      if (!(piv > 0.0) || !isfinite(piv)) { bad = true; piv = 1.0; }
       const double r = sqrt(piv);
       Dk[j][j] = r;
-      ldacc += log(r);
+      sir = 1.0 / r;
+      rdiag[(long long)b * CB + j] = sir;
+      int ex;
+      pm = frexp(pm * r, &ex);
+      pe += ex;
     }
-    __syncthreads();
-    for (int i = j + 1 + tid; i < kb; i += blockDim.x) Dk[i][j] /= Dk[j][j];
-    __syncthreads();
-    const int rem = kb - j - 1;
-    for (int e = tid; e < rem * rem; e += blockDim.x) {
-      const int i = j + 1 + e / rem, l = j + 1 + e % rem;
-      if (l <= i) Dk[i][l] -= Dk[i][j] * Dk[l][j];
+    __syncwarp();
+    const double ir = sir;
+    if (lane > j && lane < kb) Dk[lane][j] *= ir;
+    __syncwarp();
+    if (lane > j && lane < kb) {
+      const double lij = Dk[lane][j];
+      for (int l = j + 1; l <= lane; ++l) Dk[lane][l] -= lij * Dk[l][j];
     }
-    __syncthreads();
+    __syncwarp();
   }
-  for (int e = tid; e < kb * kb; e += blockDim.x) {
+  const double ldacc = log(pm) + pe * 0.69314718055994530942;  // log of the product of the roots
+  for (int e = lane; e < kb * kb; e += 32) {
     const int i = e / kb, j = e % kb;
     A[(long long)(k0 + i) * N + k0 + j] = (j <= i) ? Dk[i][j] : 0.0;
   }
-  for (int i = k0 + kb + tid; i < N; i += blockDim.x) {
-    double x[CB];
-    for (int j = 0; j < kb; ++j) {
-      double v = A[(long long)i * N + k0 + j];
-      for (int p = 0; p < j; ++p) v -= x[p] * Dk[j][p];
-      x[j] = v / Dk[j][j];
-    }
-    for (int j = 0; j < kb; ++j) A[(long long)i * N + k0 + j] = x[j];
-  }
-  if (tid == 0) {
-    double* ld = logdet + (long long)b * lds;
-    *ld = (k0 == 0 ? 0.0 : *ld) + 2.0 * ldacc;
+  if (lane == 0) {
+    double* ldp = logdet + (long long)b * lds;
+    *ldp = (k0 == 0 ? 0.0 : *ldp) + 2.0 * ldacc;
     if (bad) atomicOr(&status[b / per_chain], RMHMC_CHAIN_NOTPD);
   }
-  if (k0 + kb >= N) {
-    __syncthreads();
-    for (long long e = tid; e < (long long)N * N; e += blockDim.x) {
-      const int i = (int)(e / N), j = (int)(e % N);
-      if (j > i) A[e] = 0.0;
-    }
+}
+
+// L21 = A21 L11^-T for the rows below the diagonal block: one thread per row, the substitution
+// unrolled over the 32 columns with the row in registers; grid (row blocks of 128, matrices).
+template <int KB>
+__global__ void __launch_bounds__(128) k_chol_rows(double* __restrict__ Ab, int N, int k0,
+                                                  const double* __restrict__ rdiag) {
+  const int b = blockIdx.y;
+  double* A = Ab + (long long)b * N * N;
+  __shared__ double Lk[KB][KB + 1];
+  __shared__ double rd[KB];
+  for (int e = threadIdx.x; e < KB * KB; e += blockDim.x)
+    Lk[e / KB][e % KB] = A[(long long)(k0 + e / KB) * N + k0 + e % KB];
+  if (threadIdx.x < KB) rd[threadIdx.x] = rdiag[(long long)b * CB + threadIdx.x];
+  __syncthreads();
+  const int i = k0 + KB + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double* row = A + (long long)i * N + k0;
+  double x[KB];
+#pragma unroll
+  for (int j = 0; j < KB; ++j) x[j] = row[j];
+#pragma unroll
+  for (int j = 0; j < KB; ++j) {
+    double v = x[j];
+#pragma unroll
+    for (int p = 0; p < j; ++p) v = fma(-x[p], Lk[j][p], v);
+    x[j] = v * rd[j];
   }
+#pragma unroll
+  for (int j = 0; j < KB; ++j) row[j] = x[j];
 }
 
 __global__ void __launch_bounds__(256) k_chol(double* __restrict__ Ab, int N,
@@ -356,9 +373,12 @@ __global__ void k_gemv_t(int rows, int cols, const double* __restrict__ A, int l
   *o = alpha * s + (beta != 0.0 ? beta * *o : 0.0);
 }
 
-// Solve L t = f then L^T a = t for one lower-triangular N x N factor per CTA (blocked substitution:
-// the rows of a 32-row block first subtract the already solved part with warp dot products, then
-// warp 0 finishes the 32 x 32 triangle). Backward stable, unlike multiplying by an explicit inverse.
+// Solve L t = f then L^T a = t for one lower-triangular N x N factor per CTA (blocked substitution,
+// backward stable, unlike multiplying by an explicit inverse). Per 32-row block: the already solved
+// part is subtracted with coalesced dot products over all warps (forward: a warp per row, lanes
+// along the row; backward: lanes along a row segment of L, warps over the rows below, combined in
+// shared memory), then warp 0 finishes the 32 x 32 triangle column by column (lane = row: one
+// shuffle and one FMA per step) with the reciprocal pivots computed once up front.
 __global__ void __launch_bounds__(256) k_cholsolve(const double* __restrict__ Lb,
                                                   const double* __restrict__ fb,
                                                   double* __restrict__ tb, double* __restrict__ ab,
@@ -368,9 +388,13 @@ __global__ void __launch_bounds__(256) k_cholsolve(const double* __restrict__ Lb
   const double* f = fb + (long long)b * N;
   double* t = tb + (long long)b * N;
   double* a = ab + (long long)b * N;
-  extern __shared__ double x[];  // N
+  extern __shared__ double x[];  // N solution, then N reciprocal pivots
+  double* rd = x + N;
   __shared__ double rhs[CB];
+  __shared__ double part[8][CB];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) rd[i] = 1.0 / L[(long long)i * N + i];
+  __syncthreads();
   // forward: L t = f
   for (int r0 = 0; r0 < N; r0 += CB) {
     const int rn = min(CB, N - r0);
@@ -383,13 +407,13 @@ __global__ void __launch_bounds__(256) k_cholsolve(const double* __restrict__ Lb
     }
     __syncthreads();
     if (warp == 0) {
-      for (int i = 0; i < rn; ++i) {
-        double s = (lane < i) ? L[(long long)(r0 + i) * N + r0 + lane] * x[r0 + lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) x[r0 + i] = (rhs[i] - s) / L[(long long)(r0 + i) * N + r0 + i];
-        __syncwarp();
+      double v = lane < rn ? rhs[lane] : 0.0;  // lane = row r0 + lane
+      for (int j = 0; j < rn; ++j) {
+        const double xj = __shfl_sync(0xffffffffu, v * rd[r0 + j], j);
+        if (lane == j) v = xj;
+        else if (lane > j && lane < rn) v = fma(-L[(long long)(r0 + lane) * N + r0 + j], xj, v);
       }
+      if (lane < rn) x[r0 + lane] = v;
     }
     __syncthreads();
   }
@@ -398,23 +422,23 @@ __global__ void __launch_bounds__(256) k_cholsolve(const double* __restrict__ Lb
   // backward: L^T a = t, row blocks from the bottom; (L^T)_{ij} = L_ji
   for (int r1 = N; r1 > 0; r1 -= CB) {
     const int r0 = max(0, r1 - CB), rn = r1 - r0;
-    for (int i = warp; i < rn; i += nw) {
-      double s = 0.0;
-      for (int j = r1 + lane; j < N; j += 32) s = fma(L[(long long)j * N + r0 + i], x[j], s);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) rhs[i] = t[r0 + i] - s;
-    }
+    double s = 0.0;
+    if (lane < rn)
+      for (int j = r1 + warp; j < N; j += nw) s = fma(L[(long long)j * N + r0 + lane], x[j], s);
+    part[warp][lane] = s;
     __syncthreads();
     if (warp == 0) {
-      for (int i = rn - 1; i >= 0; --i) {
-        const int jj = i + 1 + lane;
-        double s = (jj < rn) ? L[(long long)(r0 + jj) * N + r0 + i] * x[r0 + jj] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) x[r0 + i] = (rhs[i] - s) / L[(long long)(r0 + i) * N + r0 + i];
-        __syncwarp();
+      double v = 0.0;
+      if (lane < rn) {
+        v = t[r0 + lane];
+        for (int w = 0; w < nw; ++w) v -= part[w][lane];
       }
+      for (int j = rn - 1; j >= 0; --j) {  // column j of L^T's triangle = row j of L
+        const double xj = __shfl_sync(0xffffffffu, v * rd[r0 + j], j);
+        if (lane == j) v = xj;
+        else if (lane < j) v = fma(-L[(long long)(r0 + j) * N + r0 + lane], xj, v);
+      }
+      if (lane < rn) x[r0 + lane] = v;
     }
     __syncthreads();
   }
@@ -426,7 +450,7 @@ __global__ void __launch_bounds__(256) k_cholsolve(const double* __restrict__ Lb
 void cholsolve_f64(cudaStream_t s, const double* L, const double* f, double* t, double* a, int N,
                    int batch) {
   if (batch <= 0) return;
-  k_cholsolve<<<batch, 256, N * sizeof(double), s>>>(L, f, t, a, N);
+  k_cholsolve<<<batch, 256, 2 * N * sizeof(double), s>>>(L, f, t, a, N);
 }
 
 void gemm_f64(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
@@ -444,8 +468,20 @@ void gemm_f64(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alph
     k_gemm<true, true><<<grid, GT, 0, s>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, sym, tri);
 }
 
+__global__ void k_zero_upper(double* __restrict__ Xb, int N);
+
+// One panel step: the diagonal block, then the rows below it; the last step zeroes the strict
+// upper triangle.
+void chol_panel(cudaStream_t s, double* A, int N, int k0, int batch, double* rdiag, double* logdet,
+                int lds, int* status, int per_chain) {
+  k_chol_diag<<<batch, 32, 0, s>>>(A, N, k0, rdiag, logdet, lds, status, per_chain);
+  const int kb = CB < N - k0 ? CB : N - k0, rows = N - k0 - kb;
+  if (rows > 0) k_chol_rows<CB><<<dim3((rows + 127) / 128, batch), 128, 0, s>>>(A, N, k0, rdiag);
+  else k_zero_upper<<<dim3((unsigned)(((long long)N * N + 255) / 256), batch), 256, 0, s>>>(A, N);
+}
+
 void cholesky_f64(cudaStream_t s, double* A, int N, int batch, double* logdet, int logdet_stride,
-                  int* status, int per_chain) {
+                  int* status, int per_chain, double* rdiag) {
   if (batch <= 0) return;
   if (N <= 2 * CB) {  // small: one CTA per matrix does it all
     k_chol<<<batch, 256, 0, s>>>(A, N, logdet, logdet_stride, status, per_chain);
@@ -453,7 +489,7 @@ void cholesky_f64(cudaStream_t s, double* A, int N, int batch, double* logdet, i
   }
   const long long NN = (long long)N * N;
   for (int k0 = 0; k0 < N; k0 += CB) {
-    k_chol_panel<<<batch, 256, 0, s>>>(A, N, k0, logdet, logdet_stride, status, per_chain);
+    chol_panel(s, A, N, k0, batch, rdiag, logdet, logdet_stride, status, per_chain);
     const int k1 = k0 + CB;
     if (k1 < N)
       gemm_f64(s, false, true, N - k1, N - k1, CB, -1.0, A + (long long)k1 * N + k0, N, NN,
@@ -462,7 +498,7 @@ void cholesky_f64(cudaStream_t s, double* A, int N, int batch, double* logdet, i
 }
 
 void cholesky_tc(cudaStream_t s, double* A, int N, int batch, double* logdet, int logdet_stride,
-                 int* status, int per_chain, uint8_t* tcA, uint8_t* tcB) {
+                 int* status, int per_chain, uint8_t* tcA, uint8_t* tcB, double* rdiag) {
   if (batch <= 0) return;
   if (N <= 2 * CB) {
     k_chol<<<batch, 256, 0, s>>>(A, N, logdet, logdet_stride, status, per_chain);
@@ -470,7 +506,7 @@ void cholesky_tc(cudaStream_t s, double* A, int N, int batch, double* logdet, in
   }
   const long long NN = (long long)N * N;
   for (int k0 = 0; k0 < N; k0 += CB) {
-    k_chol_panel<<<batch, 256, 0, s>>>(A, N, k0, logdet, logdet_stride, status, per_chain);
+    chol_panel(s, A, N, k0, batch, rdiag, logdet, logdet_stride, status, per_chain);
     const int k1 = k0 + CB;
     if (k1 < N) {  // A22 -= L21 L21^T, L21 = A[k1:, k0:k1] (rows of L21 on both sides)
       double* L21 = A + (long long)k1 * N + k0;

@@ -54,21 +54,50 @@ __device__ __forceinline__ void kern_derivs(const KernelDev& kd, const double* _
   }
 }
 
-// K and D1, D2, D3 = d^r K / du_1^r for every (chain, kernel): grid (tiles, n, C).
-__global__ void k_assemble(ModelDev md, const double* __restrict__ q, int dp, double* __restrict__ K,
-                           double* __restrict__ D1, double* __restrict__ D2, double* __restrict__ D3) {
+// K and D1, D2, D3 = d^r K / du_1^r for every (chain, kernel): grid (32 x 32 tiles of the lower
+// triangle, n, C). kern_derivs is exactly symmetric in (i, j), so each tile below the diagonal is
+// evaluated once and written twice (the mirror through a shared-memory transpose, both coalesced).
+__global__ void __launch_bounds__(256) k_assemble(ModelDev md, const double* __restrict__ q, int dp,
+                                                  double* __restrict__ K, double* __restrict__ D1,
+                                                  double* __restrict__ D2, double* __restrict__ D3) {
   const int k = blockIdx.y, c = blockIdx.z, N = md.N;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)N * N) return;
-  const int i = (int)(e / N), j = (int)(e % N);
-  const double cc = exp(hyper_u(md, q, dp, c, k, 0)), th = exp(hyper_u(md, q, dp, c, k, 1));
-  double D[4];
-  kern_derivs(md.k[k], md.X, md.ncov, i, j, cc, th, D);
-  const long long o = ((long long)c * md.n + k) * N * N + e;
-  K[o] = D[0];
-  D1[o] = D[1];
-  D2[o] = D[2];
-  D3[o] = D[3];
+  const int t = blockIdx.x;
+  int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);  // tile (ti, tj), tj <= ti, t = ti (ti + 1) / 2 + tj
+  while (ti * (ti + 1) / 2 > t) --ti;
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  const int tj = t - ti * (ti + 1) / 2;
+  __shared__ double hyp[2];
+  __shared__ double tile[4][32][33];
+  if (threadIdx.x == 0) {
+    hyp[0] = exp(hyper_u(md, q, dp, c, k, 0));
+    hyp[1] = exp(hyper_u(md, q, dp, c, k, 1));
+  }
+  __syncthreads();
+  const double cc = hyp[0], th = hyp[1];
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  const long long base = ((long long)c * md.n + k) * N * N;
+  double* out[4] = {K, D1, D2, D3};
+  for (int r = wy; r < 32; r += 8) {
+    const int i = ti * 32 + r, j = tj * 32 + lane;
+    double D[4] = {0.0, 0.0, 0.0, 0.0};
+    if (i < N && j < N && (ti != tj || j <= i)) {
+      kern_derivs(md.k[k], md.X, md.ncov, i, j, cc, th, D);
+      const long long o = base + (long long)i * N + j;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) out[m][o] = D[m];
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) tile[m][r][lane] = D[m];
+  }
+  __syncthreads();
+  for (int r = wy; r < 32; r += 8) {  // (j, i) = mirror of the tile's (i, j), strictly above the diagonal
+    const int jr = tj * 32 + r, ic = ti * 32 + lane;
+    if (jr < N && ic < N && ic > jr) {
+      const long long o = base + (long long)jr * N + ic;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) out[m][o] = tile[m][lane][r];
+    }
+  }
 }
 
 // Latent blocks f_k packed contiguously per (chain, kernel), and tau-scaled likelihood maps of

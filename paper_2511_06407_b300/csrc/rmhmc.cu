@@ -62,18 +62,6 @@ __device__ __forceinline__ void softabs(double lam, double alpha, int kind, doub
   }
 }
 
-// Divided difference T_jl of Eq. d3_transform; near-equal eigenvalues take g' at the midpoint.
-__device__ __forceinline__ double tdiv(double lj, double ll, double gj, double gl, double alpha,
-                                       int kind) {
-  const double sc = fmax(1.0, fmax(fabs(lj), fabs(ll)));
-  if (fabs(lj - ll) <= 1e-7 * sc) {
-    double g, gp;
-    softabs(0.5 * (lj + ll), alpha, kind, g, gp);
-    return gp;
-  }
-  return (gj - gl) / (lj - ll);
-}
-
 __global__ void k_softabs(const double* __restrict__ lam, double* __restrict__ g,
                           double* __restrict__ gp, int dp, int d, int C, double alpha, int kind) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -85,24 +73,64 @@ __global__ void k_softabs(const double* __restrict__ lam, double* __restrict__ g
   gp[e] = b;
 }
 
-// C = diag(g'/g) - (b b^T) o T on the first d indices (zero elsewhere), b = t / g:
-// Psi C Psi^T = W2 - W1 (Eq. Betancourt_formula).
-__global__ void k_build_c(const double* __restrict__ t, const double* __restrict__ lam,
-                          const double* __restrict__ g, const double* __restrict__ gp,
-                          double* __restrict__ Cm, int dp, int d, double alpha, int kind) {
-  const int c = blockIdx.y;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)dp * dp) return;
-  const int j = (int)(e / dp), l = (int)(e % dp);
-  double v = 0.0;
-  if (j < d && l < d) {
-    const long long o = (long long)c * dp;
-    const double bj = t[o + j] / g[o + j], bl = t[o + l] / g[o + l];
-    const double T = (j == l) ? gp[o + j] : tdiv(lam[o + j], lam[o + l], g[o + j], g[o + l], alpha, kind);
-    v = -bj * bl * T;
-    if (j == l) v += gp[o + j] / g[o + j];
+// 1 / x for |x| in [1e-30, 1e30]: the FP32 reciprocal refined by two Newton steps r <- r (2 - x r)
+// in FP64 (relative error ~1e-7 -> ~1e-14 -> FP64 rounding); a plain division outside that range.
+__device__ __forceinline__ double recip_newton(double x) {
+  const double ax = fabs(x);
+  if (!(ax >= 1e-30 && ax <= 1e30)) return 1.0 / x;
+  double r = (double)__frcp_rn((float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
+// C = diag(g'/g) - (b b^T) o T on the first d indices (zero elsewhere), b = t / g, with T the
+// divided differences of Eq. d3_transform (near-equal eigenvalues take g' at the midpoint):
+// Psi C Psi^T = W2 - W1 (Eq. Betancourt_formula). Grid (32 x 32 tiles, C): the tile's b and g'/g
+// are formed once (64 divisions instead of two per element), and T_jl's division goes through
+// recip_newton.
+__global__ void __launch_bounds__(256) k_build_c(const double* __restrict__ t, const double* __restrict__ lam,
+                                                 const double* __restrict__ g, const double* __restrict__ gp,
+                                                 double* __restrict__ Cm, int dp, int d, double alpha,
+                                                 int kind) {
+  const int c = blockIdx.z, j0 = blockIdx.y * 32, l0 = blockIdx.x * 32;
+  const long long o = (long long)c * dp;
+  __shared__ double sb[2][32], sl[2][32], sg[2][32], sgp[2][32];
+  if (threadIdx.x < 64) {
+    const int side = threadIdx.x >> 5, idx = (side == 0 ? j0 : l0) + (threadIdx.x & 31);
+    const bool in = idx < d;
+    const double gi = in ? g[o + idx] : 1.0;
+    sg[side][threadIdx.x & 31] = gi;
+    sb[side][threadIdx.x & 31] = in ? t[o + idx] / gi : 0.0;
+    sl[side][threadIdx.x & 31] = in ? lam[o + idx] : 0.0;
+    sgp[side][threadIdx.x & 31] = in ? gp[o + idx] : 0.0;
   }
-  Cm[(long long)c * dp * dp + e] = v;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  const int l = l0 + lane;
+  for (int r = wy; r < 32; r += 8) {
+    const int j = j0 + r;
+    if (j >= dp || l >= dp) continue;
+    double v = 0.0;
+    if (j < d && l < d) {
+      double T;
+      if (j == l) {
+        T = sgp[0][r];
+      } else {
+        const double lj = sl[0][r], ll = sl[1][lane];
+        const double sc = fmax(1.0, fmax(fabs(lj), fabs(ll)));
+        if (fabs(lj - ll) <= 1e-7 * sc) {  // near-equal eigenvalues: g' at the midpoint
+          double gm, gpm;
+          softabs(0.5 * (lj + ll), alpha, kind, gm, gpm);
+          T = gpm;
+        } else {
+          T = (sg[0][r] - sg[1][lane]) * recip_newton(lj - ll);
+        }
+      }
+      v = -sb[0][r] * sb[1][lane] * T;
+      if (j == l) v += sgp[0][r] / sg[0][r];
+    }
+    Cm[(long long)c * dp * dp + (long long)j * dp + l] = v;
+  }
 }
 
 // t_i <- t_i * s(g_i) on the first d entries (s = 1/g or sqrt(g)), zero in the padding.
@@ -402,6 +430,7 @@ struct rmhmc_model {
   // per (chain, kernel) N x N
   double *KL, *D1, *D2, *D3, *Kinv, *S, *Aux, *S2;
   double* spart;  // per (chain, kernel): partial sums of the statistics stages
+  double* rdiag;  // per (chain, kernel): the reciprocal pivots of one Cholesky panel (32)
   // per (chain, kernel) N-vectors
   double *fpk, *alpha_, *beta, *gamma, *eps2, *eps3, *delta, *fuu11;
   double* stats;
@@ -520,14 +549,16 @@ void dual_model_layer(rmhmc_model* m, bool third) {
   const long long NN = (long long)N * N;
   const int B = C * n;
   const double Nf = N, Bf = B;
+  const int ntile = (N + 31) / 32;
   PROF(m, CAT_MODEL, 0)
-  dev::k_assemble<<<dim3(nblk(NN), n, C), 256, 0, s>>>(m->md, m->q, dp, m->KL, m->D1, m->D2, m->D3);
+  dev::k_assemble<<<dim3(ntile * (ntile + 1) / 2, n, C), 256, 0, s>>>(m->md, m->q, dp, m->KL, m->D1, m->D2,
+                                                                      m->D3);
   PROF(m, CAT_MODEL, 0)
   dev::k_lik<<<dim3(nblk(N), C), 256, 0, s>>>(m->md, m->q, dp, m->fpk, m->l0, m->l1, m->l2, m->l3, m->lraw);
   const bool tc = m->precision == RMHMC_MIXED;
   PROF(m, CAT_CHOL, Bf * Nf * Nf * Nf / 3.0) {
-    if (tc) cholesky_tc(s, m->KL, N, B, m->stats + ST_LOGDET, kStatSlots, m->status, n, m->tcA, m->tcB);
-    else cholesky_f64(s, m->KL, N, B, m->stats + ST_LOGDET, kStatSlots, m->status, n);
+    if (tc) cholesky_tc(s, m->KL, N, B, m->stats + ST_LOGDET, kStatSlots, m->status, n, m->tcA, m->tcB, m->rdiag);
+    else cholesky_f64(s, m->KL, N, B, m->stats + ST_LOGDET, kStatSlots, m->status, n, m->rdiag);
   }
   PROF(m, CAT_TRINV, Bf * Nf * Nf * Nf / 3.0) {
     if (tc) trinv_lower_tc(s, m->KL, m->Aux, N, B, m->tcA, m->tcB, m->S, m->status, n);
@@ -769,7 +800,8 @@ void grad_h(rmhmc_model* m, const double* x, double* out) {
   PROF(m, CAT_VECTOR, 2.0 * Cf * df * df)
   gemv_f64(s, false, dp, dp, m->PsiT, dp, DD, x, dp, m->t1, dp, C, 1.0, 0.0);
   PROF(m, CAT_VECTOR, 0)
-  k_build_c<<<dim3(nblk(DD), C), 256, 0, s>>>(m->t1, m->lam, m->g, m->gp, m->M, dp, m->d, m->alpha, m->g_kind);
+  k_build_c<<<dim3((dp + 31) / 32, (dp + 31) / 32, C), 256, 0, s>>>(m->t1, m->lam, m->g, m->gp, m->M, dp, m->d,
+                                                                   m->alpha, m->g_kind);
   // W = Psi C Psi^T = PsiT^T (C PsiT)
   gemm_dd(m, false, false, m->M, m->PsiT, m->Y, false);
   gemm_dd(m, true, false, m->PsiT, m->Y, m->W, true);
@@ -883,6 +915,7 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
     ALLOC(m->D2, B * NN);
     ALLOC(m->D3, B * NN);
     ALLOC(m->spart, B * dev::kStatMaxBlocks * ST_COUNT);
+    ALLOC(m->rdiag, B * 32);
     ALLOC(m->Kinv, B * NN);
     ALLOC(m->S, B * NN);
     ALLOC(m->Aux, B * NN);
