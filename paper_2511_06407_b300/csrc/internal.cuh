@@ -119,12 +119,14 @@ size_t tc_operand_bytes(int R, int K, int S, int batch, bool b_side);
 TcOperand tc_operand(void* mem, int R, int K, int S, int batch, bool b_side);
 // Split the K-major view of X (kmaj: row r is X[r * ld + 0..K), else column r, X[0..K) * ld + r).
 void tc_split(cudaStream_t s, const double* X, int ld, long long sX, bool kmaj, int batch,
-              const TcOperand& op);
+              const TcOperand& op, const int* mask = nullptr);
 // C_b = alpha A_b B_b^T + beta C_b (A: m x k rows, B: n x k rows, both split with the same S and
 // K); sym: the product is symmetric, written as the mirror of its lower triangle. A bounded wait
 // that gives up sets RMHMC_CHAIN_TIMEOUT in status[b / sdiv] (status may be null).
+// mask (optional, batch ints): entries with mask[b] == 0 are skipped by the split and the product.
 void gemm_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, double alpha, double beta,
-             double* C, int ldc, long long sC, int batch, bool sym, int* status, int sdiv);
+             double* C, int ldc, long long sC, int batch, bool sym, int* status, int sdiv,
+             const int* mask = nullptr);
 // bf16 tensor-core FLOPs gemm_tc executes for these operands (padded tiles, all slice products).
 double gemm_tc_tensor_flops(const TcOperand& A, const TcOperand& B, int batch, bool sym);
 

@@ -263,6 +263,12 @@ __global__ void k_restore(const int* __restrict__ acc, double* __restrict__ q,
   if (e == 0) eig_count[c] = eig_save[c];
 }
 
+// mask[c] = 1 where eig_count[c] is a positive multiple of every (re-orthonormalisation due)
+__global__ void k_reorth_mask(const int* __restrict__ eig_count, int every, int C, int* __restrict__ mask) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < C) mask[c] = (eig_count[c] > 0 && eig_count[c] % every == 0) ? 1 : 0;
+}
+
 // eig_count += 1 per chain; sweeps_total += sweeps of the eigen-update just done
 __global__ void k_inc(int* __restrict__ v, int C, int* __restrict__ tot, const int* __restrict__ last) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -472,6 +478,7 @@ struct rmhmc_model {
   // contraction), split once since Phi is fixed
   uint8_t *tcPhiT = nullptr, *tcPhi = nullptr;
   bool tc_phi_ok = false;
+  int* tcmask = nullptr;  // per chain: re-orthonormalisation due at this eigen-update
 };
 
 namespace {
@@ -481,7 +488,7 @@ enum Cat {
   CAT_GEMM_TC
 };
 const char* kCatNames[RMHMC_PROF_NCAT] = {"gemm_f64", "jacobi_f64", "cholesky", "trinv",
-                                          "model", "contract", "vector", "mgs_f64", "jacobi_df", "gemm_tc"};
+                                          "model", "contract", "vector", "reorth", "jacobi_df", "gemm_tc"};
 
 // bf16 slices of the mixed form's tensor-core GEMMs: 9 (63 bits, at or below FP64 GEMM rounding)
 // for the K^-1 algebra, whose cond(K) ~ 1e8 amplification needs FP64-level products, and 8 (56 bits)
@@ -728,6 +735,21 @@ void eval_geometry(rmhmc_model* m, bool third) {
   if (m->eigen_start == 1) {
     PROF(m, CAT_VECTOR, 0)
     k_set_identity<<<nblk((long long)C * DD), 256, 0, s>>>(m->PsiT, dp, C);
+  } else if (m->reorth_every > 0 && m->precision == RMHMC_MIXED) {
+    // one Newton-Schulz (polar) step P <- 1.5 P - 0.5 (P P^T) P on the first d rows of Psi^T, on
+    // the tensor cores, for the chains that are due (the others skip every kernel)
+    const int S = kSlicesD;
+    PROF(m, CAT_MGS, 0)
+    k_reorth_mask<<<nblk(C), 256, 0, s>>>(m->eig_count, m->reorth_every, C, m->tcmask);
+    TcOperand pa = tc_operand(m->tcA, d, dp, S, C, false), pb = tc_operand(m->tcB, d, dp, S, C, true);
+    PROF(m, CAT_MGS, 0) tc_split(s, m->PsiT, dp, DD, true, C, pa, m->tcmask);
+    PROF(m, CAT_MGS, 0) tc_split(s, m->PsiT, dp, DD, true, C, pb, m->tcmask);
+    PROF(m, CAT_MGS, 0) gemm_tc(s, pa, pb, 1.0, 0.0, m->Y, dp, DD, C, true, m->status, 1, m->tcmask);
+    pa = tc_operand(m->tcA, d, d, S, C, false);
+    pb = tc_operand(m->tcB, dp, d, S, C, true);
+    PROF(m, CAT_MGS, 0) tc_split(s, m->Y, dp, DD, true, C, pa, m->tcmask);
+    PROF(m, CAT_MGS, 0) tc_split(s, m->PsiT, dp, DD, false, C, pb, m->tcmask);
+    PROF(m, CAT_MGS, 0) gemm_tc(s, pa, pb, -0.5, 1.5, m->PsiT, dp, DD, C, false, m->status, 1, m->tcmask);
   } else if (m->reorth_every > 0) {
     PROF(m, CAT_MGS, 0)
     mgs_rows_f64(s, m->PsiT, dp, d, C, m->eig_count, m->reorth_every, m->cluster);
@@ -966,7 +988,7 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
   ALLOC(m->Ham1, (size_t)C);
   ALLOC(m->LL, (size_t)C);
   int** ivecs[] = {&m->status, &m->sweeps_last, &m->sweeps_acc, &m->eig_count, &m->eig_save, &m->acc,
-                   &m->sweeps_total};
+                   &m->sweeps_total, &m->tcmask};
   for (int** v : ivecs) ALLOC(*v, (size_t)C);
   const int np = dp / kJacBlk / 2;
   ALLOC(m->jw.V, (size_t)C * np * 256);

@@ -191,8 +191,9 @@ __device__ __forceinline__ void scan_abs(double v, unsigned long long& mx, bool&
 // rows R..Rpad-1 get 0. kmaj: one warp per row; otherwise a block covers 32 columns, its 8 warps
 // take every 8th l (coalesced 256-byte rows) and combine through shared memory.
 __global__ void k_tc_exponents(const double* __restrict__ X, int ld, long long sX, int kmaj, int R,
-                               int K, int Rpad, int* __restrict__ ex) {
+                               int K, int Rpad, int* __restrict__ ex, const int* __restrict__ mask) {
   const int b = blockIdx.y;
+  if (mask && !mask[b]) return;  // entry skipped (uniform per CTA)
   X += b * sX;
   ex += (long long)b * Rpad;
   const int lane = threadIdx.x % 32, wy = threadIdx.x / 32;
@@ -260,8 +261,9 @@ __device__ __forceinline__ long long scaled_integer(double x, int sh) {
 template <int S>
 __global__ void k_tc_split(const double* __restrict__ X, int ld, long long sX, int kmaj, int R,
                            int K, int R8, int KS, int TR8, const int* __restrict__ ex,
-                           uint8_t* __restrict__ dig, long long sD) {
+                           uint8_t* __restrict__ dig, long long sD, const int* __restrict__ mask) {
   const int b = blockIdx.y;
+  if (mask && !mask[b]) return;
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= (long long)KS * R8 * 16) return;
   const int ri = (int)(id & 7), kc = (int)((id >> 3) & 1);
@@ -341,6 +343,7 @@ struct TcArgs {
   int sym;
   int* status;  // per-chain status (may be null); entry b reports to status[b / sdiv]
   int sdiv;
+  const int* mask;  // null, or entry b runs only where mask[b] != 0
 };
 
 template <int S>
@@ -351,6 +354,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
   const int tn = blockIdx.x, tm = blockIdx.y, b = blockIdx.z;
   const int m0 = tm * TC_M, n0 = tn * TC_N;
   if (a.sym && m0 + TC_M - 1 < n0) return;  // strictly above the diagonal: mirrored by others
+  if (a.mask && !a.mask[b]) return;          // entry skipped (before any allocation)
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::BAR_OFF);
   const uint32_t full0 = smem_addr(bars), empty0 = smem_addr(bars + NST),
@@ -530,11 +534,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
 
 template <int S>
 void launch_split(cudaStream_t s, const double* X, int ld, long long sX, bool kmaj, int R, int K,
-                  int batch, const TcOperand& op) {
+                  int batch, const TcOperand& op, const int* mask) {
   const long long threads = (long long)op.KS * op.R8 * 16;  // R8 is a multiple of TR8
   dim3 grid((unsigned)((threads + 255) / 256), batch);
   k_tc_split<S><<<grid, 256, 0, s>>>(X, ld, sX, kmaj ? 1 : 0, R, K, op.R8, op.KS, op.TR / 8, op.ex, op.dig,
-                                     op.bytes_per_entry);
+                                     op.bytes_per_entry, mask);
 }
 
 template <int S>
@@ -584,19 +588,19 @@ TcOperand tc_operand(void* mem, int R, int K, int S, int batch, bool b_side) {
 }
 
 void tc_split(cudaStream_t s, const double* X, int ld, long long sX, bool kmaj, int batch,
-              const TcOperand& op) {
+              const TcOperand& op, const int* mask) {
   if (op.R <= 0 || op.K <= 0 || batch <= 0) return;
   const int Rpad = op.R8 * 8;
   if (kmaj)
-    k_tc_exponents<<<dim3((Rpad + 7) / 8, batch), 256, 0, s>>>(X, ld, sX, 1, op.R, op.K, Rpad, op.ex);
+    k_tc_exponents<<<dim3((Rpad + 7) / 8, batch), 256, 0, s>>>(X, ld, sX, 1, op.R, op.K, Rpad, op.ex, mask);
   else
     k_tc_exponents<<<dim3((Rpad + 31) / 32, batch), 256, 0, s>>>(X, ld, sX, 0, op.R, op.K, Rpad,
-                                                                 op.ex);
+                                                                 op.ex, mask);
   switch (op.S) {
-    case 6: launch_split<6>(s, X, ld, sX, kmaj, op.R, op.K, batch, op); break;
-    case 7: launch_split<7>(s, X, ld, sX, kmaj, op.R, op.K, batch, op); break;
-    case 8: launch_split<8>(s, X, ld, sX, kmaj, op.R, op.K, batch, op); break;
-    default: launch_split<9>(s, X, ld, sX, kmaj, op.R, op.K, batch, op); break;
+    case 6: launch_split<6>(s, X, ld, sX, kmaj, op.R, op.K, batch, op, mask); break;
+    case 7: launch_split<7>(s, X, ld, sX, kmaj, op.R, op.K, batch, op, mask); break;
+    case 8: launch_split<8>(s, X, ld, sX, kmaj, op.R, op.K, batch, op, mask); break;
+    default: launch_split<9>(s, X, ld, sX, kmaj, op.R, op.K, batch, op, mask); break;
   }
 }
 
@@ -610,7 +614,8 @@ double gemm_tc_tensor_flops(const TcOperand& A, const TcOperand& B, int batch, b
 }
 
 void gemm_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, double alpha, double beta,
-             double* C, int ldc, long long sC, int batch, bool sym, int* status, int sdiv) {
+             double* C, int ldc, long long sC, int batch, bool sym, int* status, int sdiv,
+             const int* mask) {
   const int m = A.R, n = B.R, KS = A.KS;
   if (m <= 0 || n <= 0 || batch <= 0) return;
   if (A.TR != TC_M || B.TR != TC_N || B.KS != KS || B.S != A.S) return;  // wrong roles: no launch
@@ -640,6 +645,7 @@ void gemm_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, double alph
   a.sym = sym ? 1 : 0;
   a.status = status;
   a.sdiv = sdiv > 0 ? sdiv : 1;
+  a.mask = mask;
   for (int k0 = 0; k0 < KS; k0 += TC_KSTEPS_MAX) {
     a.ks0 = k0;
     a.ks1 = k0 + TC_KSTEPS_MAX < KS ? k0 + TC_KSTEPS_MAX : KS;
