@@ -495,6 +495,13 @@ const char* kCatNames[RMHMC_PROF_NCAT] = {"gemm_f64", "jacobi_f64", "cholesky", 
 // for the d x d products M = Psi^T H Psi and W = Psi C Psi^T
 constexpr int kSlicesK = 9, kSlicesD = 8;
 
+// The mixed form uses the tensor cores for products whose output is at least one 128-row tile
+// each way: below that the slicing launches cost more than the FP64 kernels they replace.
+constexpr int kTcMin = 128;
+inline bool use_tc(const rmhmc_model* m, int rows, int cols) {
+  return m->precision == RMHMC_MIXED && rows >= kTcMin && cols >= kTcMin;
+}
+
 // Brackets one launch site with CUDA events on the model's stream while profiling is enabled.
 struct ProfScope {
   rmhmc_model* m;
@@ -562,7 +569,7 @@ void dual_model_layer(rmhmc_model* m, bool third) {
                                                                       m->D3);
   PROF(m, CAT_MODEL, 0)
   dev::k_lik<<<dim3(nblk(N), C), 256, 0, s>>>(m->md, m->q, dp, m->fpk, m->l0, m->l1, m->l2, m->l3, m->lraw);
-  const bool tc = m->precision == RMHMC_MIXED;
+  const bool tc = use_tc(m, N, N);
   PROF(m, CAT_CHOL, Bf * Nf * Nf * Nf / 3.0) {
     if (tc) cholesky_tc(s, m->KL, N, B, m->stats + ST_LOGDET, kStatSlots, m->status, n, m->tcA, m->tcB, m->rdiag);
     else cholesky_f64(s, m->KL, N, B, m->stats + ST_LOGDET, kStatSlots, m->status, n, m->rdiag);
@@ -687,7 +694,7 @@ void primal_model_layer(rmhmc_model* m) {
   PROF(m, CAT_MODEL, 0)
   dev::k_primal_udu<<<C, 256, 0, s>>>(m->pd, m->q, dp, m->l0, m->lraw, m->U, m->dU, m->LL, m->ustat);
   // the likelihood blocks Phi^T diag(l_jk) Phi of the Hessian ((j, k) and its mirror (k, j))
-  const bool tc = m->precision == RMHMC_MIXED;
+  const bool tc = use_tc(m, P, P);
   if (tc) primal_phi_slices(m);
   for (int j = 0; j < J; ++j) {
     for (int k = j; k < J; ++k) {
@@ -735,7 +742,7 @@ void eval_geometry(rmhmc_model* m, bool third) {
   if (m->eigen_start == 1) {
     PROF(m, CAT_VECTOR, 0)
     k_set_identity<<<nblk((long long)C * DD), 256, 0, s>>>(m->PsiT, dp, C);
-  } else if (m->reorth_every > 0 && m->precision == RMHMC_MIXED) {
+  } else if (m->reorth_every > 0 && use_tc(m, d, d)) {
     // one Newton-Schulz (polar) step P <- 1.5 P - 0.5 (P P^T) P on the first d rows of Psi^T, on
     // the tensor cores, for the chains that are due (the others skip every kernel)
     const int S = kSlicesD;
@@ -777,7 +784,7 @@ void gemm_dd(rmhmc_model* m, bool ta, bool tb, const double* A, const double* B,
   const int dp = m->dp;
   const long long DD = (long long)dp * dp;
   const double df = m->d, fl = m->C * gemm_flops(df, df, df, sym, false);
-  if (m->precision == RMHMC_MIXED) {
+  if (use_tc(m, dp, dp)) {
     // tensor cores: op(A)'s rows and op(B)'s columns cut into bf16 slices; the two column views
     // of Psi^T (W = Psi^T^T (C Psi^T)) are kept until Psi^T changes
     const bool pa = A == m->PsiT && ta, pb = B == m->PsiT && !tb;
@@ -835,7 +842,7 @@ void grad_h(rmhmc_model* m, const double* x, double* out) {
     for (int j = 0; j < J; ++j) {
       for (int k = j; k < J; ++k) {
         const double* Wjk = m->W + (long long)j * P * dp + k * P;
-        if (m->precision == RMHMC_MIXED) {  // op(A) = Phi (shared slices), op(B) = W_jk: its columns
+        if (use_tc(m, N, P)) {  // op(A) = Phi (shared slices), op(B) = W_jk: its columns
           primal_phi_slices(m);
           const TcOperand pa = phi_operand(m, false);
           const TcOperand wb = tc_operand(m->tcB, P, P, kSlicesK, C, true);
