@@ -35,7 +35,7 @@ N_INPUTS, N_CHAINS, EPS, N_FP = 400, 64, 0.005, 6
 # profiles/k_jacobi_N400_8chains.md and profiles/k_jacobi_df_N400_8chains.md (8 chains, mean of the
 # two captured launches; traffic grows with the number of chains, so a 64-chain launch is scaled
 # by 64 / 8).
-JACOBI_DRAM_BYTES_PER_CHAIN = {"jacobi_f64": (22.318e6 + 1.891e6) / 8,
+JACOBI_DRAM_BYTES_PER_CHAIN = {"jacobi_f64": (22.255e6 + 2.149e6) / 8,
                                "jacobi_df": (22.273e6 + 2.176e6) / 8}
 SUBSTEPS_PER_LEAPFROG = 2 * N_FP + 1
 METRIC = "RMHMC leapfrog substeps/s"
