@@ -1205,7 +1205,7 @@ const char* rmhmc_status_string(rmhmc_status s) {
   return "unknown status";
 }
 
-const char* rmhmc_version(void) { return "rmhmc sm_103a fp64 + f32x2"; }
+const char* rmhmc_version(void) { return "rmhmc sm_103a fp64 + f32x2 + tcgen05 bf16 slices"; }
 
 
 rmhmc_status rmhmc_fp64_peak(void* cuda_stream, int ms_target, double* tflops_host) {
