@@ -242,6 +242,61 @@ rmhmc_status rmhmc_batch_create(rmhmc_model* const* models, int n_models, void* 
 rmhmc_status rmhmc_batch_leapfrog(rmhmc_batch* b, const rmhmc_integrator* integ, int n_steps);
 void rmhmc_batch_free(rmhmc_batch* b);
 
+/* Serving (continuous batching of sampling jobs on one GPU). A server owns one scheduler thread
+ * on `device`. rmhmc_server_submit deep-copies a job (its model description, tau and initial state
+ * are host data read during the call) and queues it with its footprint: rmhmc_plan_bytes (or
+ * rmhmc_plan_bytes_primal) plus the server's per-job buffers. The scheduler admits queued jobs in
+ * submission order while the head of the queue fits in what is left of hbm_budget_bytes, gives each
+ * admitted job its own model and non-blocking CUDA stream, sets the state (q0, or zero) and keeps
+ * `depth` one-iteration rmhmc_sample calls in flight per job; jobs of different sizes run
+ * concurrently and their kernels overlap. It notices completion by event queries, releases a
+ * finished job's model and stream at once and returns its bytes to the budget, so new jobs are
+ * admitted while others run. The results are those of one rmhmc_sample(n_iter, n_burn, seed) call
+ * on the job's model (iteration numbers continue across the one-iteration calls), and a job's
+ * results do not depend on what else is running. Outputs go to the caller's device buffers, which
+ * must stay valid until the job is done (state RMHMC_JOB_DONE or RMHMC_JOB_FAILED). Calls are
+ * thread-safe; times are seconds since rmhmc_server_create. */
+typedef struct rmhmc_server rmhmc_server;
+typedef enum {
+  RMHMC_JOB_QUEUED = 0,
+  RMHMC_JOB_RUNNING = 1,
+  RMHMC_JOB_DONE = 2,
+  RMHMC_JOB_FAILED = 3  /* the model could not be created or a call failed: see job_error */
+} rmhmc_job_state;
+typedef struct {
+  const rmhmc_model_desc* model;   /* dual model (host), or NULL */
+  const rmhmc_primal_desc* primal; /* primal model (host), or NULL: exactly one of the two */
+  int n_chains;
+  const double* tau_host;          /* n_chains inverse temperatures, NULL = all 1 */
+  const double* q0_host;           /* n_chains x d initial positions, NULL = zero */
+  rmhmc_integrator integ;
+  int n_iter;                      /* recorded iterations */
+  int n_burn;                      /* burn-in iterations before them */
+  uint64_t seed;
+  double* q_samples_dev;           /* n_iter x n_chains x d, or NULL */
+  double* logp_dev;                /* n_iter x n_chains, or NULL */
+  int* accept_dev;                 /* n_iter x n_chains, or NULL */
+  int* chain_status_dev;           /* n_chains: OR of the RMHMC_CHAIN_* bits of every iteration, or NULL */
+} rmhmc_job_desc;
+/* depth >= 1: iterations in flight per job. Errors: EINVAL. */
+rmhmc_status rmhmc_server_create(int device, size_t hbm_budget_bytes, int depth, rmhmc_server** out);
+/* Queue a job; *job_id receives its id. Errors: EINVAL (bad description, or a footprint larger than
+ * the whole budget). */
+rmhmc_status rmhmc_server_submit(rmhmc_server* s, const rmhmc_job_desc* job, int* job_id);
+/* A job's state (rmhmc_job_state), its error (RMHMC_OK unless FAILED) and, in times_host[3], its
+ * submission, admission and finish times (-1 until they happen); each output may be NULL. */
+rmhmc_status rmhmc_server_poll(rmhmc_server* s, int job_id, int* state, rmhmc_status* job_error,
+                               double* times_host);
+/* Block until the job (job_id >= 0) or every submitted job (job_id = -1) has finished, or until
+ * timeout_s seconds have passed (timeout_s < 0: no limit; then ETIMEOUT). */
+rmhmc_status rmhmc_server_wait(rmhmc_server* s, int job_id, double timeout_s);
+/* The server's clock, running and queued job counts, the most jobs ever resident at once and the
+ * bytes of the budget in use; each output may be NULL. */
+rmhmc_status rmhmc_server_stats(rmhmc_server* s, double* now_s, int* n_active, int* max_active,
+                                int* n_queued, size_t* bytes_in_use);
+/* Finish every submitted job, stop the scheduler and free the server. NULL is a no-op. */
+void rmhmc_server_destroy(rmhmc_server* s);
+
 /* Choose the model's Jacobi cluster size (CTAs per chain: 1, 2, 4 or 8) by timing up to three
  * cold-start sweeps of each candidate, with the Jacobi kernel of the model's precision, on the
  * model's own current Hessian (in scratch buffers; the state is untouched) and keeping the fastest

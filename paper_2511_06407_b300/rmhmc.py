@@ -51,6 +51,13 @@ class IntegratorC(ctypes.Structure):
                 ("eigen_start", c_int)]
 
 
+class JobDesc(ctypes.Structure):
+    _fields_ = [("model", POINTER(ModelDesc)), ("primal", POINTER(PrimalDesc)), ("n_chains", c_int),
+                ("tau_host", POINTER(c_double)), ("q0_host", POINTER(c_double)), ("integ", IntegratorC),
+                ("n_iter", c_int), ("n_burn", c_int), ("seed", ctypes.c_uint64), ("q_samples_dev", c_void_p),
+                ("logp_dev", c_void_p), ("accept_dev", c_void_p), ("chain_status_dev", c_void_p)]
+
+
 @dataclass
 class Integrator:
     """Leapfrog and geometry settings (rmhmc_integrator)."""
@@ -124,6 +131,19 @@ def lib():
                                 c_double, c_void_p, c_int, ctypes.c_longlong, c_int, c_int, c_int,
                                 c_void_p]
     L.rmhmc_gemm_tc.restype = c_int
+    L.rmhmc_server_create.argtypes = [c_int, ctypes.c_size_t, c_int, POINTER(c_void_p)]
+    L.rmhmc_server_create.restype = c_int
+    L.rmhmc_server_submit.argtypes = [c_void_p, POINTER(JobDesc), POINTER(c_int)]
+    L.rmhmc_server_submit.restype = c_int
+    L.rmhmc_server_poll.argtypes = [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_double)]
+    L.rmhmc_server_poll.restype = c_int
+    L.rmhmc_server_wait.argtypes = [c_void_p, c_int, c_double]
+    L.rmhmc_server_wait.restype = c_int
+    L.rmhmc_server_stats.argtypes = [c_void_p, POINTER(c_double), POINTER(c_int), POINTER(c_int),
+                                     POINTER(c_int), POINTER(ctypes.c_size_t)]
+    L.rmhmc_server_stats.restype = c_int
+    L.rmhmc_server_destroy.argtypes = [c_void_p]
+    L.rmhmc_server_destroy.restype = None
     L.rmhmc_batch_create.argtypes = [POINTER(c_void_p), c_int, c_void_p, POINTER(c_void_p)]
     L.rmhmc_batch_create.restype = c_int
     L.rmhmc_batch_leapfrog.argtypes = [c_void_p, POINTER(IntegratorC), c_int]
@@ -427,6 +447,69 @@ def gemm_tc(A, B, C=None, ta=False, tb=False, alpha=1.0, beta=0.0, slices=9, sym
                                _ptr(C3, (batch, m, n), torch.float64), n, m * n, batch, int(slices),
                                int(bool(sym)), _ptr(status, (batch,), torch.int32)))
     return C
+
+
+JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+
+
+class NativeServer:
+    """The library's continuous-batching server (rmhmc_server_*): a native scheduler thread admits
+    jobs by the HBM budget and runs them concurrently, each on its own model and stream."""
+
+    def __init__(self, hbm_budget_bytes, depth=2, device=0):
+        h = c_void_p()
+        _check(lib().rmhmc_server_create(int(device), int(hbm_budget_bytes), int(depth), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, problem, n_chains, integ, n_iter, n_burn=0, seed=0, tau=None, q0=None,
+               q_out=None, logp_out=None, accept_out=None, status_out=None):
+        """Queue a job; the output tensors (CUDA, contiguous) must stay alive until it is done."""
+        if is_primal(problem):
+            desc, keep = _primal_desc(problem)
+            model, primal = None, ctypes.pointer(desc)
+        else:
+            desc, keep = _desc(problem)
+            model, primal = ctypes.pointer(desc), None
+        t = None if tau is None else np.ascontiguousarray(tau, dtype=np.float64)
+        q = None if q0 is None else np.ascontiguousarray(q0, dtype=np.float64)
+        jd = JobDesc(model, primal, int(n_chains),
+                     t.ctypes.data_as(POINTER(c_double)) if t is not None else None,
+                     q.ctypes.data_as(POINTER(c_double)) if q is not None else None,
+                     integ.c(), int(n_iter), int(n_burn), int(seed) & (2 ** 64 - 1),
+                     _ptr(q_out), _ptr(logp_out), _ptr(accept_out), _ptr(status_out))
+        jid = c_int()
+        _check(lib().rmhmc_server_submit(self._h, ctypes.byref(jd), ctypes.byref(jid)))
+        self._keep[jid.value] = (q_out, logp_out, accept_out, status_out)
+        return jid.value
+
+    def poll(self, job_id):
+        """(state name, job error code, (submitted, admitted, finished) seconds)."""
+        st, err, times = c_int(), c_int(), (c_double * 3)()
+        _check(lib().rmhmc_server_poll(self._h, int(job_id), ctypes.byref(st), ctypes.byref(err), times))
+        return JOB_STATES[st.value], err.value, tuple(times)
+
+    def wait(self, job_id=-1, timeout=-1.0):
+        _check(lib().rmhmc_server_wait(self._h, int(job_id), float(timeout)))
+
+    def stats(self):
+        now, na, mx, nq, used = c_double(), c_int(), c_int(), c_int(), ctypes.c_size_t()
+        _check(lib().rmhmc_server_stats(self._h, ctypes.byref(now), ctypes.byref(na), ctypes.byref(mx),
+                                        ctypes.byref(nq), ctypes.byref(used)))
+        return {"now": now.value, "active": na.value, "max_active": mx.value, "queued": nq.value,
+                "bytes_in_use": used.value}
+
+    def close(self):
+        if self._h is not None:
+            lib().rmhmc_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def version():

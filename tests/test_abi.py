@@ -63,7 +63,8 @@ def test_binding_structs_match_header_layout(tmp_path):
     import subprocess
     from paper_2511_06407_b300 import rmhmc
     structs = {"rmhmc_kernel_desc": rmhmc.KernelDesc, "rmhmc_model_desc": rmhmc.ModelDesc,
-               "rmhmc_integrator": rmhmc.IntegratorC, "rmhmc_primal_desc": rmhmc.PrimalDesc}
+               "rmhmc_integrator": rmhmc.IntegratorC, "rmhmc_primal_desc": rmhmc.PrimalDesc,
+               "rmhmc_job_desc": rmhmc.JobDesc}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rmhmc.h"', "int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')

@@ -116,3 +116,45 @@ def test_server_admits_by_hbm_budget(rm):
     assert stats["max_concurrent_jobs"] == 1 and stats["jobs"] == 3
     for a, b in zip(done, done[1:]):
         assert b.admitted >= a.finished - 1e-3
+
+
+def test_native_server_jobs_equal_one_sample_call(rm):
+    """rmhmc_server_*: two jobs submitted together run concurrently, one iteration per call, and
+    each one's samples, log densities, accept flags and chain status equal those of a single
+    rmhmc_sample(n_iter, n_burn, seed) call on a model of its own; the bookkeeping (states, times,
+    budget in use) is consistent, and a job larger than the whole budget is refused."""
+    integ = rm.Integrator(eps=0.01, n_leapfrog=2, n_fp=3)
+    probs = [wl.gp_classification(30, seed=1), wl.gp_classification(45, seed=2)]
+    C, n_iter, n_burn = 3, 3, 1
+    f64 = dict(dtype=torch.float64, device="cuda")
+    i32 = dict(dtype=torch.int32, device="cuda")
+    srv = rm.NativeServer(2**30, depth=2)
+    ids, outs = [], []
+    for i, p in enumerate(probs):
+        d = wl.dims(p)[2]
+        o = (torch.empty(n_iter, C, d, **f64), torch.empty(n_iter, C, **f64), torch.empty(n_iter, C, **i32),
+             torch.zeros(C, **i32))
+        ids.append(srv.submit(p, C, integ, n_iter, n_burn, 11 + i, None, None, *o))
+        outs.append(o)
+    srv.wait()
+    st = srv.stats()
+    assert st["active"] == 0 and st["queued"] == 0 and st["bytes_in_use"] == 0 and st["max_active"] >= 1
+    for jid in ids:
+        state, err, (t_sub, t_adm, t_fin) = srv.poll(jid)
+        assert state == "done" and err == 0 and 0 <= t_sub <= t_adm <= t_fin
+    for i, p in enumerate(probs):
+        m = rm.Model(p, C)
+        d = m.d
+        m.set_state(torch.zeros(C, d, **f64), integ=integ)
+        q, lp = torch.empty(n_iter, C, d, **f64), torch.empty(n_iter, C, **f64)
+        acc, cs = torch.empty(n_iter, C, **i32), torch.zeros(C, **i32)
+        m.sample(n_iter, n_burn, 11 + i, q, lp, acc, chain_status=cs, integ=integ)
+        torch.cuda.synchronize()
+        m.close()
+        for got, want in zip(outs[i], (q, lp, acc, cs)):
+            np.testing.assert_array_equal(got.cpu().numpy(), want.cpu().numpy())
+    srv.close()
+    small = rm.NativeServer(4096)
+    with pytest.raises(rm.RmhmcError):
+        small.submit(probs[0], C, integ, 1, 0, 0)
+    small.close()
