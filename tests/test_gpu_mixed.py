@@ -84,6 +84,8 @@ def _compare(label, got, c, m, q, tau, p, keys):
 
 CASES = [("c0", lambda: wl.gp_classification(50, seed=0), 3, [1.0, 0.5, 0.8]),
          ("propensity3", lambda: wl.propensity(40, seed=1, n_kernels=3), 2, None),
+         # N = 130: every product spans a 128 x 128 tile, so the whole tensor-core path runs
+         ("tc130", lambda: wl.gp_classification(130, seed=4), 2, [1.0, 0.7]),
          ("regression_fixed", lambda: wl.gp_regression(30, seed=3), 2, None)]
 
 
@@ -103,7 +105,7 @@ def test_mixed_geometry_relative_rule(rm, oracle_model, name, make, C, tau):
     assert not fails, fails
 
 
-@pytest.mark.parametrize("name,make,C,tau", CASES[:2], ids=[c[0] for c in CASES[:2]])
+@pytest.mark.parametrize("name,make,C,tau", CASES[:3], ids=[c[0] for c in CASES[:3]])
 def test_mixed_metric_rule_sampler_quantities(rm, oracle_model, name, make, C, tau):
     """The sampler's default METRIC rule: the quantities the Hamiltonian and its gradient use."""
     prob = make()
