@@ -502,6 +502,11 @@ __device__ double uuu(const double* st, int N, int j, int k, int l, double b_e) 
 //                 + W_00 alpha_m + 2 W_01 gamma_m + W_11 fuu11_m,        w_h = W[f_k, u_kh]
 //   i = u_{k,j}:  -<W[f_k, f_k], A_j> + 2 sum_h <w_h, fuu_{j h}> + sum_{h h'} W_{h h'} uuu(j, h, h')
 //   with A_0 = K^-1, A_1 = A1, fuu_00 = alpha, fuu_01 = gamma, fuu_11 = fuu11.
+// Grid (32-column blocks of m, chain x kernel), lane = m, the 8 warps split r (all reads coalesced);
+// the f-coordinates are written here, the block's parts of the hyperparameter sums go to
+// part[b][block][0..6] = (<W[f_k, f_k], K^-1>, <W[f_k, f_k], A1>, w0.alpha, w0.gamma, w1.gamma,
+// w1.fuu11, unused) and k_contract_hyp adds them in a fixed order.
+constexpr int kContractParts = 8;
 __global__ void __launch_bounds__(256) k_contract(ModelDev md, const double* __restrict__ q, int dp,
                                                   const double* __restrict__ Wb,
                                                   const double* __restrict__ Kinvb,
@@ -510,96 +515,93 @@ __global__ void __launch_bounds__(256) k_contract(ModelDev md, const double* __r
                                                   const double* __restrict__ alphab,
                                                   const double* __restrict__ gammab,
                                                   const double* __restrict__ fuu11b,
-                                                  const double* __restrict__ stats,
-                                                  double* __restrict__ vout) {
-  const int b = blockIdx.x, n = md.n, N = md.N, nN = n * N;
+                                                  double* __restrict__ vout, double* __restrict__ part) {
+  const int b = blockIdx.y, n = md.n, N = md.N, nN = n * N;
   const int c = b / n, k = b % n;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = blockIdx.x * kStatCols + lane;
   const double* W = Wb + (long long)c * dp * dp;
   const long long mo = (long long)b * N * N, vo = (long long)b * N;
   const double* Kinv = Kinvb + mo;
   const double* A1 = A1b + mo;
-  const double* al = alphab + vo;
-  const double* ga = gammab + vo;
-  const double* fu = fuu11b + vo;
   double* v = vout + (long long)c * dp;
   const bool hyp = md.sample_hypers != 0;
   extern __shared__ double shm[];
   double* w0 = shm;
   double* w1 = shm + N;
-  __shared__ double sh[32];
+  __shared__ double col[8][kStatCols];
+  __shared__ double red[8];
   const int u0i = nN + 2 * k, u1i = nN + 2 * k + 1;
-  if (hyp) {
+  if (hyp)
     for (int r = threadIdx.x; r < N; r += blockDim.x) {
       w0[r] = W[(long long)(k * N + r) * dp + u0i];
       w1[r] = W[(long long)(k * N + r) * dp + u1i];
     }
-  }
   __syncthreads();
-  double W00 = 0, W01 = 0, W11 = 0;
-  if (hyp) {
-    W00 = W[(long long)u0i * dp + u0i];
-    W01 = W[(long long)u0i * dp + u1i];
-    W11 = W[(long long)u1i * dp + u1i];
-  }
-  double dot00 = 0, dot01 = 0, dot11 = 0, trA0 = 0, trA1 = 0;
-  for (int m = threadIdx.x; m < N; m += blockDim.x) {
+  double k01 = 0.0, t0 = 0.0, t1 = 0.0;  // (K^-1 w0 + A1 w1)_m and column m of <W[f_k, f_k], A_j>
+  if (hyp && m < N)
+    for (int r = w; r < N; r += 8) {
+      const double kr = Kinv[(long long)r * N + m], ar = A1[(long long)r * N + m];
+      const double wr = W[(long long)(k * N + r) * dp + k * N + m];
+      k01 = fma(kr, w0[r], fma(ar, w1[r], k01));
+      t0 = fma(wr, kr, t0);
+      t1 = fma(wr, ar, t1);
+    }
+  k01 = column_total(k01, col);
+  double pa[6] = {0, 0, 0, 0, 0, 0};
+  if (w == 0 && m < N) {
     double diag = 0.0;
     for (int a = 0; a < n; ++a)
       for (int bb = 0; bb < n; ++bb) diag += W[(long long)(a * N + m) * dp + bb * N + m];
     double val = l3[(long long)c * N + m] * diag;
     if (hyp) {
-      double k0 = 0.0, k1 = 0.0;
-      for (int r = 0; r < N; ++r) {
-        k0 = fma(Kinv[(long long)r * N + m], w0[r], k0);
-        k1 = fma(A1[(long long)r * N + m], w1[r], k1);
-      }
-      val += -2.0 * (k0 + k1) + W00 * al[m] + 2.0 * W01 * ga[m] + W11 * fu[m];
-      dot00 = fma(w0[m], al[m], dot00);
-      dot01 = fma(w1[m], ga[m], dot01);
-      dot11 = fma(w1[m], fu[m], dot11);
-      // <W[f_k, f_k], A_j>: column m of the block
-      double t0 = 0.0, t1 = 0.0;
-      for (int r = 0; r < N; ++r) {
-        const double wr = W[(long long)(k * N + r) * dp + k * N + m];
-        t0 = fma(wr, Kinv[(long long)r * N + m], t0);
-        t1 = fma(wr, A1[(long long)r * N + m], t1);
-      }
-      trA0 += t0;
-      trA1 += t1;
+      const double W00 = W[(long long)u0i * dp + u0i], W01 = W[(long long)u0i * dp + u1i],
+                   W11 = W[(long long)u1i * dp + u1i];
+      const double al = alphab[vo + m], ga = gammab[vo + m], fu = fuu11b[vo + m];
+      val += -2.0 * k01 + W00 * al + 2.0 * W01 * ga + W11 * fu;
+      pa[2] = w0[m] * al;
+      pa[3] = w0[m] * ga;
+      pa[4] = w1[m] * ga;
+      pa[5] = w1[m] * fu;
     }
     v[k * N + m] = val;
   }
-  if (!hyp) return;
-  double w0a = 0, w0g = 0, w1a = 0;
-  for (int m = threadIdx.x; m < N; m += blockDim.x) {
-    w0a = fma(w0[m], al[m], w0a);
-    w0g = fma(w0[m], ga[m], w0g);
-    w1a = fma(w1[m], al[m], w1a);
-  }
-  const double s_w0a = block_sum(w0a, sh);
-  const double s_w0g = block_sum(w0g, sh);
-  const double s_w1a = block_sum(w1a, sh);
-  const double s_w1g = block_sum(dot01, sh);
-  const double s_w1f = block_sum(dot11, sh);
-  const double s_trA0 = block_sum(trA0, sh);
-  const double s_trA1 = block_sum(trA1, sh);
-  (void)dot00;
-  if (threadIdx.x == 0) {
-    const double* st = stats + (long long)b * kStatSlots;
-    const KernelDev& kd = md.k[k];
-    const double be0 = kd.b[0] * exp(-hyper_u(md, q, dp, c, k, 0));
-    const double be1 = kd.b[1] * exp(-hyper_u(md, q, dp, c, k, 1));
-    const double Wh[2][2] = {{W00, W01}, {W01, W11}};
-    // <w_h, fuu_{j h}>: fuu_00 = alpha, fuu_01 = fuu_10 = gamma, fuu_11 = fuu11
-    const double wf[2][2] = {{s_w0a, s_w1g}, {s_w0g, s_w1f}};  // [j][h]
-    (void)s_w1a;
-    for (int j = 0; j < 2; ++j) {
-      double val = -(j == 0 ? s_trA0 : s_trA1) + 2.0 * (wf[j][0] + wf[j][1]);
-      const double bej = j == 0 ? be0 : be1;
-      for (int h = 0; h < 2; ++h)
-        for (int h2 = 0; h2 < 2; ++h2) val += Wh[h][h2] * uuu(st, N, j, h, h2, bej);
-      v[nN + 2 * k + j] = val;
-    }
+  if (!hyp) return;  // uniform per CTA
+  pa[0] = t0;
+  pa[1] = t1;
+  double* pp = part + ((long long)b * kStatMaxBlocks + blockIdx.x) * kContractParts;
+  for (int e = 0; e < 6; ++e) stat_part(pa[e], red, pp + e);
+}
+
+// The hyperparameter coordinates of tr(W dH_i) for one (chain, kernel), from the parts of k_contract:
+//   v[u_kj] = -<W[f_k, f_k], A_j> + 2 sum_h <w_h, fuu_{j h}> + sum_{h h'} W_{h h'} uuu(j, h, h').
+__global__ void k_contract_hyp(ModelDev md, const double* __restrict__ q, int dp,
+                               const double* __restrict__ Wb, const double* __restrict__ stats,
+                               const double* __restrict__ part, int nblocks, double* __restrict__ vout) {
+  const int b = blockIdx.x, n = md.n, N = md.N, nN = n * N;
+  const int c = b / n, k = b % n;
+  if (threadIdx.x != 0 || !md.sample_hypers) return;
+  double sm[6] = {0, 0, 0, 0, 0, 0};
+  for (int blk = 0; blk < nblocks; ++blk)
+    for (int e = 0; e < 6; ++e) sm[e] += part[((long long)b * kStatMaxBlocks + blk) * kContractParts + e];
+  const double* W = Wb + (long long)c * dp * dp;
+  const int u0i = nN + 2 * k, u1i = nN + 2 * k + 1;
+  const double W00 = W[(long long)u0i * dp + u0i], W01 = W[(long long)u0i * dp + u1i],
+               W11 = W[(long long)u1i * dp + u1i];
+  const double* st = stats + (long long)b * kStatSlots;
+  const KernelDev& kd = md.k[k];
+  const double be0 = kd.b[0] * exp(-hyper_u(md, q, dp, c, k, 0));
+  const double be1 = kd.b[1] * exp(-hyper_u(md, q, dp, c, k, 1));
+  const double Wh[2][2] = {{W00, W01}, {W01, W11}};
+  // <w_h, fuu_{j h}>: fuu_00 = alpha, fuu_01 = fuu_10 = gamma, fuu_11 = fuu11
+  const double wf[2][2] = {{sm[2], sm[4]}, {sm[3], sm[5]}};  // [j][h]
+  double* v = vout + (long long)c * dp;
+  for (int j = 0; j < 2; ++j) {
+    double val = -sm[j] + 2.0 * (wf[j][0] + wf[j][1]);
+    const double bej = j == 0 ? be0 : be1;
+    for (int h = 0; h < 2; ++h)
+      for (int h2 = 0; h2 < 2; ++h2) val += Wh[h][h2] * uuu(st, N, j, h, h2, bej);
+    v[nN + 2 * k + j] = val;
   }
 }
 

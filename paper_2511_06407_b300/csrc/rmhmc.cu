@@ -437,6 +437,7 @@ struct rmhmc_model {
   double *KL, *D1, *D2, *D3, *Kinv, *S, *Aux, *S2;
   double* spart;  // per (chain, kernel): partial sums of the statistics stages
   double* rdiag;  // per (chain, kernel): the reciprocal pivots of one Cholesky panel (32)
+  double* cpart;  // per (chain, kernel): partial sums of the contraction's hyperparameter terms
   // per (chain, kernel) N-vectors
   double *fpk, *alpha_, *beta, *gamma, *eps2, *eps3, *delta, *fuu11;
   double* stats;
@@ -870,10 +871,12 @@ void grad_h(rmhmc_model* m, const double* x, double* out) {
     PROF(m, CAT_CONTRACT, 0)
     dev::k_primal_contract<<<C, 256, 0, s>>>(m->pd, m->q, dp, m->W, m->vtr);
   } else {
+    const dim3 cg((N + dev::kStatCols - 1) / dev::kStatCols, C * n);
     PROF(m, CAT_CONTRACT, 0)
-    dev::k_contract<<<C * n, 256, 2 * N * sizeof(double), s>>>(m->md, m->q, dp, m->W, m->Kinv, m->Aux,
-                                                               m->l3, m->alpha_, m->gamma, m->fuu11,
-                                                               m->stats, m->vtr);
+    dev::k_contract<<<cg, 256, 2 * N * sizeof(double), s>>>(m->md, m->q, dp, m->W, m->Kinv, m->Aux, m->l3,
+                                                            m->alpha_, m->gamma, m->fuu11, m->vtr, m->cpart);
+    PROF(m, CAT_CONTRACT, 0)
+    dev::k_contract_hyp<<<C * n, 32, 0, s>>>(m->md, m->q, dp, m->W, m->stats, m->cpart, (int)cg.x, m->vtr);
   }
   PROF(m, CAT_VECTOR, 0)
   k_axpy<<<nblk((long long)C * dp), 256, 0, s>>>(out, m->dU, m->vtr, 0.5, (long long)C * dp);
@@ -945,6 +948,7 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
     ALLOC(m->D3, B * NN);
     ALLOC(m->spart, B * dev::kStatMaxBlocks * ST_COUNT);
     ALLOC(m->rdiag, B * 32);
+    ALLOC(m->cpart, B * dev::kStatMaxBlocks * dev::kContractParts);
     ALLOC(m->Kinv, B * NN);
     ALLOC(m->S, B * NN);
     ALLOC(m->Aux, B * NN);
