@@ -292,6 +292,7 @@ __global__ void __launch_bounds__(256) k_trinv(const double* __restrict__ Lb,
   __shared__ double Ls[CB][CB + 1];
   __shared__ double Xs[CB][CB + 1];
   __shared__ double R[CB][CB + 1];
+  __shared__ double rdg[CB];
   const int tid = threadIdx.x;
   for (int r = tid; r < c0; r += blockDim.x)
     for (int j = 0; j < cn; ++j) X[(long long)r * ld + c0 + j] = 0.0;
@@ -323,12 +324,14 @@ __global__ void __launch_bounds__(256) k_trinv(const double* __restrict__ Lb,
       Ls[i][j] = (i < rn && j < rn) ? L[(long long)(r0 + i) * ld + r0 + j] : (i == j ? 1.0 : 0.0);
     }
     __syncthreads();
+    if (tid < CB) rdg[tid] = 1.0 / Ls[tid][tid];  // the block's reciprocal pivots, in parallel
+    __syncthreads();
     if (tid < CB) {
       const int j = tid;
       for (int i = 0; i < rn; ++i) {
         double v = R[i][j];
-        for (int p = 0; p < i; ++p) v -= Ls[i][p] * R[p][j];
-        R[i][j] = v / Ls[i][i];
+        for (int p = 0; p < i; ++p) v = fma(-Ls[i][p], R[p][j], v);
+        R[i][j] = v * rdg[i];
       }
     }
     __syncthreads();
@@ -379,7 +382,7 @@ __global__ void k_gemv_t(int rows, int cols, const double* __restrict__ A, int l
 // along the row; backward: lanes along a row segment of L, warps over the rows below, combined in
 // shared memory), then warp 0 finishes the 32 x 32 triangle column by column (lane = row: one
 // shuffle and one FMA per step) with the reciprocal pivots computed once up front.
-__global__ void __launch_bounds__(256) k_cholsolve(const double* __restrict__ Lb,
+__global__ void __launch_bounds__(1024) k_cholsolve(const double* __restrict__ Lb,
                                                   const double* __restrict__ fb,
                                                   double* __restrict__ tb, double* __restrict__ ab,
                                                   int N) {
@@ -391,7 +394,7 @@ __global__ void __launch_bounds__(256) k_cholsolve(const double* __restrict__ Lb
   extern __shared__ double x[];  // N solution, then N reciprocal pivots
   double* rd = x + N;
   __shared__ double rhs[CB];
-  __shared__ double part[8][CB];
+  __shared__ double part[32][CB];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < N; i += blockDim.x) rd[i] = 1.0 / L[(long long)i * N + i];
   __syncthreads();
@@ -450,7 +453,7 @@ __global__ void __launch_bounds__(256) k_cholsolve(const double* __restrict__ Lb
 void cholsolve_f64(cudaStream_t s, const double* L, const double* f, double* t, double* a, int N,
                    int batch) {
   if (batch <= 0) return;
-  k_cholsolve<<<batch, 256, 2 * N * sizeof(double), s>>>(L, f, t, a, N);
+  k_cholsolve<<<batch, 1024, 2 * N * sizeof(double), s>>>(L, f, t, a, N);
 }
 
 void gemm_f64(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
