@@ -46,7 +46,7 @@ WORKLOAD = (f"GP classification N={N_INPUTS} (d={N_INPUTS + 2}), SE kernel, {N_C
 
 MIXED_NOTE = ("mixed precision: Jacobi rotations in double-float (FP32 pairs, ~48-bit); the K^-1 algebra "
               "(K^-1, K^-1 dK and products) and the d x d products Psi^T H Psi, Psi C Psi^T on the tcgen05 "
-              "tensor cores by exact bf16 slicing (9 / 8 slices = 63 / 56 bits, FP32 accumulation in "
+              "tensor cores by exact bf16 slicing (9 / 7 slices = 63 / 49 bits, FP32 accumulation in "
               "TMEM, combined in FP64); Cholesky, L^-1, log|G|, H and the Hamiltonian in FP64")
 DTYPE_MIXED = "f64 + f32x2 (double-float) + bf16 slices on tensor cores (FP64-accurate GEMM)"
 

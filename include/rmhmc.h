@@ -118,7 +118,7 @@ typedef struct {
   int precision;       /* rmhmc_precision: FP64, or MIXED = the Jacobi rotations in double-float
                           (FP32 pairs, ~48-bit significand), and the K^-1 algebra (K^-1 = L^-T L^-1,
                           K^-1 dK and its products) and the d x d products M = Psi^T H Psi and
-                          W = Psi C Psi^T on the tensor cores (rmhmc_gemm_tc with 9 and 8 slices);
+                          W = Psi C Psi^T on the tensor cores (rmhmc_gemm_tc with 9 and 7 slices);
                           Cholesky, L^-1, H, log|G| and the Hamiltonian stay FP64 */
   int jacobi_rule;     /* rmhmc_jacobi_rule: when M = Psi^T H Psi counts as diagonal */
   int eigen_start;     /* 0: warm start from the previous Psi (dynamic, Sec. 2.4); 1: cold start

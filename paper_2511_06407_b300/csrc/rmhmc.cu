@@ -492,9 +492,10 @@ const char* kCatNames[RMHMC_PROF_NCAT] = {"gemm_f64", "jacobi_f64", "cholesky", 
                                           "model", "contract", "vector", "reorth", "jacobi_df", "gemm_tc"};
 
 // bf16 slices of the mixed form's tensor-core GEMMs: 9 (63 bits, at or below FP64 GEMM rounding)
-// for the K^-1 algebra, whose cond(K) ~ 1e8 amplification needs FP64-level products, and 8 (56 bits)
-// for the d x d products M = Psi^T H Psi and W = Psi C Psi^T
-constexpr int kSlicesK = 9, kSlicesD = 8;
+// for the K^-1 algebra, whose cond(K) ~ 1e8 amplification needs FP64-level products, and 7 (49 bits,
+// the accuracy of the double-float rotations they feed) for the d x d products M = Psi^T H Psi,
+// W = Psi C Psi^T and the re-orthonormalisation of Psi^T
+constexpr int kSlicesK = 9, kSlicesD = 7;
 
 // The mixed form uses the tensor cores for products whose output is at least one 128-row tile
 // each way: below that the slicing launches cost more than the FP64 kernels they replace.
