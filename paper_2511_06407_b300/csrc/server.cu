@@ -236,17 +236,36 @@ extern "C" rmhmc_status rmhmc_server_create(int device, size_t hbm_budget_bytes,
   if (!out || depth < 1 || hbm_budget_bytes == 0) return RMHMC_EINVAL;
   int n = 0;
   if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return RMHMC_EINVAL;
-  rmhmc_server* S = new rmhmc_server();
-  S->device = device;
-  S->budget = hbm_budget_bytes;
-  S->depth = depth;
-  S->t0 = std::chrono::steady_clock::now();
-  S->th = std::thread(scheduler, S);
+  rmhmc_server* S = nullptr;
+  try {  // no C++ exception may cross the C ABI
+    S = new rmhmc_server();
+    S->device = device;
+    S->budget = hbm_budget_bytes;
+    S->depth = depth;
+    S->t0 = std::chrono::steady_clock::now();
+    S->th = std::thread(scheduler, S);
+  } catch (...) {
+    delete S;
+    return RMHMC_ENOMEM;
+  }
   *out = S;
   return RMHMC_OK;
 }
 
+namespace {
+rmhmc_status submit_job(rmhmc_server* S, const rmhmc_job_desc* jd, int* job_id);
+}
+
 extern "C" rmhmc_status rmhmc_server_submit(rmhmc_server* S, const rmhmc_job_desc* jd, int* job_id) {
+  try {  // the deep copies allocate; no C++ exception may cross the C ABI
+    return submit_job(S, jd, job_id);
+  } catch (...) {
+    return RMHMC_ENOMEM;
+  }
+}
+
+namespace {
+rmhmc_status submit_job(rmhmc_server* S, const rmhmc_job_desc* jd, int* job_id) {
   if (!S || !jd || !job_id) return RMHMC_EINVAL;
   if ((jd->model == nullptr) == (jd->primal == nullptr)) return RMHMC_EINVAL;
   if (jd->n_chains < 1 || jd->n_iter < 0 || jd->n_burn < 0) return RMHMC_EINVAL;
@@ -308,6 +327,7 @@ extern "C" rmhmc_status rmhmc_server_submit(rmhmc_server* S, const rmhmc_job_des
   S->cv.notify_all();
   return RMHMC_OK;
 }
+}  // namespace
 
 extern "C" rmhmc_status rmhmc_server_poll(rmhmc_server* S, int job_id, int* state,
                                          rmhmc_status* job_error, double* times_host) {

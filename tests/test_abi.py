@@ -111,3 +111,15 @@ def test_invalid_descriptions_are_rejected_without_a_gpu():
     assert L.rmhmc_plan_bytes_primal(ctypes.byref(pd), 2, ctypes.byref(size)) == 0
     pd.prior_b[1] = 0.0
     assert L.rmhmc_plan_bytes_primal(ctypes.byref(pd), 2, ctypes.byref(size)) == 1
+
+
+def test_server_is_refused_cleanly_without_a_gpu():
+    """rmhmc_server_create validates the device before starting its scheduler thread: on a host
+    without a CUDA device it returns EINVAL (raised by the binding), nothing is left running."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2511_06407_b300 import build, rmhmc
+    build.build()
+    with pytest.raises(rmhmc.RmhmcError):
+        rmhmc.NativeServer(2**20)
