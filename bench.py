@@ -661,7 +661,8 @@ def run_serve(args):
                       "max_concurrent_jobs": stats["max_concurrent_jobs"],
                       "config": {"workload": f"Poisson trace, {args.jobs} jobs at {args.rate}/s, N~U{{50..200}}, "
                                              "1-3 kernels, 8 temperatures x 2 chains, 2+6 iterations x 4 leapfrogs, "
-                                             f"HBM budget {args.hbm_gb} GiB", "eps": integ.eps},
+                                             f"HBM budget {args.hbm_gb} GiB, native scheduler (rmhmc_server_*)",
+                                 "eps": integ.eps},
                       "chain_status_nonzero": bad}), flush=True)
     return 0
 
