@@ -85,16 +85,24 @@ __device__ __forceinline__ double recip_newton(double x) {
 
 // C = diag(g'/g) - (b b^T) o T on the first d indices (zero elsewhere), b = t / g, with T the
 // divided differences of Eq. d3_transform (near-equal eigenvalues take g' at the midpoint):
-// Psi C Psi^T = W2 - W1 (Eq. Betancourt_formula). Grid (32 x 32 tiles, C): the tile's b and g'/g
-// are formed once (64 divisions instead of two per element), and T_jl's division goes through
-// recip_newton.
+// Psi C Psi^T = W2 - W1 (Eq. Betancourt_formula). Grid (32 x 32 tiles of the lower triangle, C):
+// the tile's b and g'/g are formed once (64 divisions instead of two per element), T_jl's division
+// goes through recip_newton, and since every term is exactly symmetric in (j, l) (recip_newton is
+// odd, the products commute) each tile below the diagonal is written twice, the mirror through a
+// shared-memory transpose.
 __global__ void __launch_bounds__(256) k_build_c(const double* __restrict__ t, const double* __restrict__ lam,
                                                  const double* __restrict__ g, const double* __restrict__ gp,
                                                  double* __restrict__ Cm, int dp, int d, double alpha,
                                                  int kind) {
-  const int c = blockIdx.z, j0 = blockIdx.y * 32, l0 = blockIdx.x * 32;
+  const int c = blockIdx.y, tile = blockIdx.x;
+  int tj = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);  // tile (tj, tl), tl <= tj
+  while (tj * (tj + 1) / 2 > tile) --tj;
+  while ((tj + 1) * (tj + 2) / 2 <= tile) ++tj;
+  const int tl = tile - tj * (tj + 1) / 2;
+  const int j0 = tj * 32, l0 = tl * 32;
   const long long o = (long long)c * dp;
   __shared__ double sb[2][32], sl[2][32], sg[2][32], sgp[2][32];
+  __shared__ double tileC[32][33];
   if (threadIdx.x < 64) {
     const int side = threadIdx.x >> 5, idx = (side == 0 ? j0 : l0) + (threadIdx.x & 31);
     const bool in = idx < d;
@@ -107,11 +115,11 @@ __global__ void __launch_bounds__(256) k_build_c(const double* __restrict__ t, c
   __syncthreads();
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
   const int l = l0 + lane;
+  double* Cc = Cm + (long long)c * dp * dp;
   for (int r = wy; r < 32; r += 8) {
     const int j = j0 + r;
-    if (j >= dp || l >= dp) continue;
     double v = 0.0;
-    if (j < d && l < d) {
+    if (j < d && l < d && l <= j) {
       double T;
       if (j == l) {
         T = sgp[0][r];
@@ -129,7 +137,13 @@ __global__ void __launch_bounds__(256) k_build_c(const double* __restrict__ t, c
       v = -sb[0][r] * sb[1][lane] * T;
       if (j == l) v += sgp[0][r] / sg[0][r];
     }
-    Cm[(long long)c * dp * dp + (long long)j * dp + l] = v;
+    tileC[r][lane] = v;
+    if (j < dp && l < dp && (tj != tl || l <= j)) Cc[(long long)j * dp + l] = v;
+  }
+  __syncthreads();
+  for (int r = wy; r < 32; r += 8) {  // (l, j) = mirror of the tile's (j, l), strictly above the diagonal
+    const int lr = l0 + r, jc = j0 + lane;
+    if (lr < dp && jc < dp && jc > lr) Cc[(long long)lr * dp + jc] = tileC[lane][r];
   }
 }
 
@@ -830,9 +844,10 @@ void grad_h(rmhmc_model* m, const double* x, double* out) {
   const double df = m->d, Cf = C;
   PROF(m, CAT_VECTOR, 2.0 * Cf * df * df)
   gemv_f64(s, false, dp, dp, m->PsiT, dp, DD, x, dp, m->t1, dp, C, 1.0, 0.0);
+  const int ct = (dp + 31) / 32;
   PROF(m, CAT_VECTOR, 0)
-  k_build_c<<<dim3((dp + 31) / 32, (dp + 31) / 32, C), 256, 0, s>>>(m->t1, m->lam, m->g, m->gp, m->M, dp, m->d,
-                                                                   m->alpha, m->g_kind);
+  k_build_c<<<dim3(ct * (ct + 1) / 2, C), 256, 0, s>>>(m->t1, m->lam, m->g, m->gp, m->M, dp, m->d, m->alpha,
+                                                       m->g_kind);
   // W = Psi C Psi^T = PsiT^T (C PsiT)
   gemm_dd(m, false, false, m->M, m->PsiT, m->Y, false);
   gemm_dd(m, true, false, m->PsiT, m->Y, m->W, true);
