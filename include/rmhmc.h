@@ -329,7 +329,7 @@ rmhmc_status rmhmc_fp64_peak(void* cuda_stream, int ms_target, double* tflops_ho
 rmhmc_status rmhmc_fp32_peak(void* cuda_stream, int ms_target, double* tflops_host);
 /* The same for the double-float multiply-add (the Dot2 step of the RMHMC_MIXED kernels: FP32
  * two-product and two-sum with a compensation word), 2 flops per step: the denominator of the
- * double-float Jacobi and GEMMs. */
+ * double-float Jacobi. */
 rmhmc_status rmhmc_df_peak(void* cuda_stream, int ms_target, double* tflops_host);
 
 /* Allocation-free eigendecomposition of a batch of symmetric matrices, for callers that cannot

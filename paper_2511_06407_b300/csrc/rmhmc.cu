@@ -343,7 +343,7 @@ __global__ void k_fma_peak(T* __restrict__ sink, int iters, T b, T c) {
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 // Double-float multiply-add throughput probe: eight independent Dot2 accumulations per thread (the
-// inner step of the double-float GEMM and Jacobi tiles), counted as 2 flops per step.
+// inner step of the double-float Jacobi tiles), counted as 2 flops per step.
 __global__ void k_df_peak(float* __restrict__ sink, int iters, float2 b) {
   float s[8], c[8];
   float2 a[8];
