@@ -328,15 +328,18 @@ def run_b300(args):
     model, integ, d = runs[head]["model"], runs[head]["integ"], runs[head]["model"].d
     ms = runs[head]["ms"]
 
-    # ---- end to end: per step, momenta uploaded from pinned host memory, one leapfrog through the
-    # C ABI, position / momentum / Hamiltonian read back into pinned host memory
+    # ---- end to end: the host drives the trajectory. Per step the momenta are uploaded from pinned
+    # host memory, one leapfrog runs through the C ABI, and position, momentum and Hamiltonian are
+    # read back into pinned host memory; the momenta read back are the next step's upload (stream
+    # order makes the read-back land before the next upload reads it), so the chains continue the
+    # same trajectory as in the device-timed region.
     qo, po = torch.empty(C, d, dtype=torch.float64, device=dev), torch.empty(C, d, dtype=torch.float64, device=dev)
     Ho = torch.empty(C, dtype=torch.float64, device=dev)
     st = torch.empty(C, dtype=torch.int32, device=dev)
-    p_host = runs[head]["p"].cpu().pin_memory()
-    p_dev = torch.empty_like(runs[head]["p"])
+    model.leapfrog(0, qo, po, integ=integ)
+    p_host = po.cpu().pin_memory()
+    p_dev = torch.empty_like(po)
     q_host = torch.empty(C, d, dtype=torch.float64).pin_memory()
-    pout_host = torch.empty_like(q_host).pin_memory()
     H_host = torch.empty(C, dtype=torch.float64).pin_memory()
     e_steps = max(1, min(args.steps, 3))
     if ws > 1:
@@ -347,7 +350,7 @@ def run_b300(args):
         p_dev.copy_(p_host, non_blocking=True)
         model.leapfrog(1, qo, po, Ho, st, integ=integ, p_in=p_dev)
         q_host.copy_(qo, non_blocking=True)
-        pout_host.copy_(po, non_blocking=True)
+        p_host.copy_(po, non_blocking=True)
         H_host.copy_(Ho, non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -402,7 +405,7 @@ def run_b300(args):
         "cpu_baseline": cpu_baseline,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(p_host.numel() * 8),
-                "d2h_bytes_per_step": int((q_host.numel() + pout_host.numel() + H_host.numel()) * 8)},
+                "d2h_bytes_per_step": int((q_host.numel() + p_host.numel() + H_host.numel()) * 8)},
         "gpu_launches": gpu_launches,
         "chain_status_nonzero": int((status != 0).sum() + (runs[head]["status"] != 0).sum()),
         "valid": bool((status == 0).all() and (runs[head]["status"] == 0).all()),
