@@ -192,7 +192,9 @@ rmhmc_status rmhmc_set_state(rmhmc_model* m, const rmhmc_integrator* integ, cons
  * then copy the state out. p_in_dev (n_chains x d, may be NULL): momenta to start from instead of
  * the model's current ones (the geometry depends on q only, so nothing is recomputed). Outputs:
  * q_dev, p_dev (n_chains x d), H_dev (n_chains, Eq. Hamiltonian at the end), status_dev
- * (n_chains ints, RMHMC_CHAIN_* bits); each may be NULL. Errors: EINVAL, ECUDA. */
+ * (n_chains ints, RMHMC_CHAIN_* bits seen since rmhmc_set_state or the last Algorithm 1 iteration;
+ * RMHMC_CHAIN_NONFINITE when the chain's q, p, U or, if H_dev is given, H is not finite at the
+ * end); each may be NULL. Errors: EINVAL, ECUDA. */
 rmhmc_status rmhmc_leapfrog(rmhmc_model* m, const rmhmc_integrator* integ, int n_steps,
                             const double* p_in_dev, double* q_dev, double* p_dev, double* H_dev,
                             int* status_dev);

@@ -263,6 +263,31 @@ __global__ void k_accept(const double* __restrict__ H0, const double* __restrict
   status[c] = 0;
 }
 
+// After rmhmc_leapfrog: a chain whose position, momentum, potential U or (when computed) Hamiltonian
+// is not finite gets RMHMC_CHAIN_NONFINITE in the model's status (so that a later Metropolis-Hastings
+// step rejects it) and in the caller's copy (out, may be null). Finiteness from the exponent bits.
+__global__ void __launch_bounds__(128) k_flag_nonfinite(int* __restrict__ status, int* __restrict__ out,
+                                                        const double* __restrict__ q,
+                                                        const double* __restrict__ p,
+                                                        const double* __restrict__ U,
+                                                        const double* __restrict__ H, int dp, int d) {
+  const int c = blockIdx.x;
+  const long long o = (long long)c * dp;
+  auto inf_or_nan = [](double x) { return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000; };
+  bool bad = false;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) bad |= inf_or_nan(q[o + j]) || inf_or_nan(p[o + j]);
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) {
+    bad = bad || inf_or_nan(U[c]) || (H != nullptr && inf_or_nan(H[c]));
+    int st = status[c];
+    if (bad) {
+      st |= RMHMC_CHAIN_NONFINITE;
+      status[c] = st;
+    }
+    if (out) out[c] = st;
+  }
+}
+
 // Rejected chains return to the saved position and eigenvectors.
 __global__ void k_restore(const int* __restrict__ acc, double* __restrict__ q,
                           const double* __restrict__ q_save, double* __restrict__ PsiT,
@@ -1589,7 +1614,8 @@ rmhmc_status rmhmc_leapfrog(rmhmc_model* m, const rmhmc_integrator* integ, int n
     k_restride<<<nblk((long long)C * d), 256, 0, s>>>(p_dev, d, m->p, dp, d, C);
   }
   if (H_dev) hamiltonian(m, m->p, H_dev);
-  if (status_dev) cudaMemcpyAsync(status_dev, m->status, C * sizeof(int), cudaMemcpyDeviceToDevice, s);
+  PROF(m, CAT_VECTOR, 0)
+  k_flag_nonfinite<<<C, 128, 0, s>>>(m->status, status_dev, m->q, m->p, m->U, H_dev, dp, d);
   return check_launch();
 }
 

@@ -280,6 +280,7 @@ def test_failed_chains_are_flagged_not_fatal(rm, oracle_model):
     torch.cuda.synchronize()
     s = st.cpu().numpy()
     assert s[0] == 0 and s[1] != 0 and s[2] != 0, s
+    assert s[2] & rm.CHAIN_NONFINITE, s  # the NaN position stays NaN
     m = oracle_model(prob)
     ref_q, _, _ = leapfrog(m, Q[0], np.zeros(m.d), 0.05, 3)
     with mdl.inverse_method("cholesky"):
