@@ -132,15 +132,16 @@ def cpu_cores_used():
     return os.cpu_count() or 1
 
 
-def oracle_leapfrogs(seconds, max_leapfrogs=None):
+def oracle_leapfrogs(seconds, max_leapfrogs=None, seed=0):
     """Time the plain FP64 oracle on one chain of the benchmark workload for about `seconds`
-    (at least one leapfrog). Returns (substeps/s, leapfrogs done, seconds)."""
+    (at least one leapfrog); `seed` draws the chain's momenta. Returns (substeps/s, leapfrogs done,
+    seconds)."""
     from oracle.geometry import Geometry
     from oracle.integrator import leapfrog
     from oracle.model import from_problem
     prob = wl.gp_classification(N_INPUTS, seed=0)
     m = from_problem(prob)
-    rng = np.random.default_rng(0)
+    rng = np.random.default_rng(seed)
     geo0 = Geometry(m, np.zeros(m.d), 1.0)
     q, geo = np.zeros(m.d), geo0
     p = geo.sqrtG_z(rng.standard_normal(m.d))
@@ -159,6 +160,38 @@ def oracle_leapfrogs(seconds, max_leapfrogs=None):
         if (el >= seconds and n > 0) or (max_leapfrogs and n >= max_leapfrogs):
             break
     return SUBSTEPS_PER_LEAPFROG * n / el, n, el
+
+
+# Peak resident memory of one oracle process on the benchmark workload (d = 402: the full d^3
+# third-derivative tensor and its temporaries; 1.58 GB measured), with margin.
+ORACLE_PROCESS_BYTES = 2.0e9
+
+
+def _oracle_one_core(job):
+    """Worker of oracle_per_core: one chain, BLAS limited to one thread."""
+    seconds, seed = job
+    from threadpoolctl import threadpool_limits
+    with threadpool_limits(limits=1):
+        return oracle_leapfrogs(seconds, seed=seed)
+
+
+def oracle_per_core(seconds, max_procs=None):
+    """The many-chain CPU baseline: one chain per host core, each process with single-threaded
+    BLAS, all running at once for about `seconds`. The pool is started with `spawn` (never forked
+    from a process that holds a CUDA context), and its size is the core count, bounded by the
+    available host memory (ORACLE_PROCESS_BYTES per process). Returns (aggregate substeps/s,
+    processes, total leapfrogs, longest worker time)."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    try:
+        import psutil
+        n = min(n, int(0.8 * psutil.virtual_memory().available // ORACLE_PROCESS_BYTES))
+    except ImportError:
+        pass
+    n = max(1, min(n, max_procs) if max_procs else n)
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_oracle_one_core, [(seconds, 1 + i) for i in range(n)])
+    return sum(r[0] for r in res), n, sum(r[1] for r in res), max(r[2] for r in res)
 
 
 def run_reference(args):
@@ -380,12 +413,17 @@ def run_b300(args):
         k = min(4, C)
         traj = _trajectory_error(rmhmc, prob, runs["fp64"]["q"][:k].clone(), runs["fp64"]["p"][:k].clone())
     # CPU baseline: the oracle on this host's cores, bounded sample
-    cpu_baseline = None
+    cpu_baseline = cpu_baseline_per_core = None
     if not args.no_cpu_baseline:
         cb_value, cb_n, cb_s = oracle_leapfrogs(args.cpu_seconds)
         cpu_baseline = {"value": cb_value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
                         "sample": f"{cb_n} oracle leapfrog(s) of one chain of the workload in {cb_s:.1f} s "
                                   "(numpy/LAPACK FP64, full third-derivative tensor)"}
+        pc_value, pc_n, pc_l, pc_s = oracle_per_core(args.cpu_seconds)
+        cpu_baseline_per_core = {"value": pc_value, "unit": UNIT, "cores": pc_n, "kind": "oracle",
+                                 "sample": f"{pc_n} processes at once, one chain each with single-threaded "
+                                           f"BLAS, {pc_l} oracle leapfrogs in at most {pc_s:.1f} s; value = "
+                                           "sum of the processes' rates"}
     def prof_summary(prof):
         return ({k: round(v[0], 3) for k, v in prof.items() if v[2]},
                 {k: (v[1] / (v[0] * 1e-3) / 1e12 if v[0] > 0 else 0.0) for k, v in prof.items() if v[2]})
@@ -403,6 +441,7 @@ def run_b300(args):
         "roofline_tensor_gemm": _tensor_roofline(runs[head]["prof"]),
         "profile_ms": pms, "profile_tflops": ptf,
         "cpu_baseline": cpu_baseline,
+        "cpu_baseline_per_core": cpu_baseline_per_core,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(p_host.numel() * 8),
                 "d2h_bytes_per_step": int((q_host.numel() + p_host.numel() + H_host.numel()) * 8)},
