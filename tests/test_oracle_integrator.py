@@ -95,6 +95,29 @@ def test_gaussian_gp_posterior_moments(oracle_model):
     assert np.all(np.abs(dev2.mean(axis=0) - np.diag(cov)) < 4 * se2 + 1e-12)
 
 
+def test_metropolis_hastings_keeps_the_posterior_at_a_coarse_step(oracle_model):
+    """The accept/reject step makes Algorithm 1 exact at any step size: with one leapfrog per
+    iteration at eps = 1.2 about a quarter of the proposals carry an energy error large enough to
+    be rejected, and the chain still has the closed-form posterior mean and variance of the
+    Gaussian-likelihood GP (an accept test with the energy difference reversed, which the fine-step
+    moment check above cannot see, inflates the variances several times here)."""
+    prob = wl.gp_regression(3, seed=11, noise_var=0.2)
+    m = oracle_model(prob)
+    from oracle.kernels import kernel_derivs
+    K = kernel_derivs("se", m.X, m.u_fixed, 1e-6)[0]
+    A = np.linalg.solve(K + m.noise_var * np.eye(3), np.eye(3))
+    mean = K @ A @ m.y
+    var = np.diag(K - K @ A @ K)
+    res = sample(m, np.zeros(3), 2000, 50, seed=1, chain=0, eps=1.2, n_leapfrog=1, n_fp=2)
+    Q = res["q"]
+    assert 0.5 < res["accept"].mean() < 0.9  # a coarse step: a real share of rejections
+    se = _batch_se(Q)
+    assert np.all(np.abs(Q.mean(axis=0) - mean) < 4 * se + 1e-12), (Q.mean(axis=0), mean, se)
+    dev2 = (Q - mean) ** 2
+    se2 = _batch_se(dev2)
+    assert np.all(np.abs(dev2.mean(axis=0) - var) < 4 * se2 + 1e-12), (dev2.mean(axis=0), var, se2)
+
+
 @pytest.mark.slow
 def test_brute_force_quadrature_tiny_classification(oracle_model):
     """N = 2 Bernoulli-logistic GP with both hyperparameters sampled (d = 4): RMHMC posterior means
