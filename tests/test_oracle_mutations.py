@@ -190,6 +190,35 @@ MISTAKES += [
             ("data_derivs",), lambda om: pins_primal.test_meanvar_likelihood_derivatives_match_finite_differences()),
 ]
 
+MISTAKES += [
+    Mistake("primal-spectral-weight-exponent-as-printed", "oracle.primal",
+            "np.exp(-pi * pi * m * m * s / (16.0 * model.L ** 2))",
+            "np.exp(-pi * m * m * s / (16.0 * model.L ** 2))",
+            ("spectral_weights",),
+            lambda om: pins_primal.test_spectral_weights_are_the_fourier_transform_of_the_kernel(1.0)),
+    Mistake("primal-feature-frequency", "oracle.primal",
+            "(model.Xg[:, k:k + 1] + model.L) / (2.0 * model.L)", "(model.Xg[:, k:k + 1] + model.L) / model.L",
+            ("features",), lambda om: pins_primal.test_reduced_rank_features_reproduce_the_kernel()),
+    Mistake("tempered-mean-drops-posterior-variance", "oracle.bme",
+            "- 0.5 * (r @ r + np.trace(Sig)) / noise_var", "- 0.5 * (r @ r) / noise_var",
+            ("gaussian_tempered_loglik_mean",),
+            lambda om: pins_bme.test_gaussian_gp_evidence_is_the_integral_of_the_tempered_means()),
+    Mistake("jacobi-eigenvectors-not-rotated", "oracle.jacobi",
+            "Psi[:, l] = s * Pj + c * Pl", "Psi[:, l] = Pl",
+            ("jacobi_eigh",), lambda om: pins_rng.test_jacobi_matches_eigh(5)),
+    Mistake("jacobi-warm-start-ignored", "oracle.jacobi",
+            "Psi = np.eye(d) if Psi0 is None else np.array(Psi0, dtype=np.float64)", "Psi = np.eye(d)",
+            ("jacobi_eigh",),
+            lambda om: pins_rng.test_jacobi_warm_start_needs_one_to_two_sweeps_cold_grows_with_d()),
+    Mistake("momentum-drawn-from-identity", "oracle.sampler",
+            "p = geo.sqrtG_z(z)", "p = z",
+            ("sample",), lambda om: pins_int.test_metropolis_hastings_keeps_the_posterior_at_a_coarse_step(om)),
+    Mistake("log-det-G-from-absolute-eigenvalues", "oracle.geometry",
+            "return float(np.sum(np.log(self.g)))", "return float(np.sum(np.log(np.abs(self.lam))))",
+            ("Geometry.logdetG",),
+            lambda om: pins_geo.test_betancourt_traces_match_fd_of_metric(3.0, "coth", om)),
+]
+
 
 @pytest.mark.parametrize("mistake", MISTAKES, ids=[m.id for m in MISTAKES])
 def test_planted_mistake_fails_its_pin(mistake, monkeypatch, oracle_model):
