@@ -78,6 +78,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device):
+    """The largest of the ranks' values of x, returned on every rank (x itself when ws == 1): the
+    job's time is its slowest rank's."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, ws, steps, seconds):
+    """Whole-job throughput: the units every rank processed in `steps` steps over the job's time."""
+    return units_per_rank * ws * steps / seconds
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -242,10 +259,7 @@ def _time_leapfrogs(model, integ, steps, stream, local, ws, dev):
     if ws > 1:
         dist.barrier()
     clk = clocks.stop()
-    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item()), prof, clk
+    return max_over_ranks(e0.elapsed_time(e1), ws, dev), prof, clk
 
 
 def _measured_bf16_peak():
@@ -387,10 +401,7 @@ def run_b300(args):
         H_host.copy_(Ho, non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    e2e_s = max_over_ranks(e2e_s, ws, dev)
     status = st.cpu().numpy()
     for prec in precisions:
         x = torch.empty(C, dtype=torch.int32, device=dev)
@@ -404,17 +415,18 @@ def run_b300(args):
         return 0
 
     total_chains = C * ws
-    value = total_chains * SUBSTEPS_PER_LEAPFROG * args.steps / (ms * 1e-3)
-    e2e_value = total_chains * SUBSTEPS_PER_LEAPFROG * e_steps / e2e_s
+    value = job_value(C * SUBSTEPS_PER_LEAPFROG, ws, args.steps, ms * 1e-3)
+    e2e_value = job_value(C * SUBSTEPS_PER_LEAPFROG, ws, e_steps, e2e_s)
     roof = _roofline(rmhmc, runs[head]["prof"], C)
     gpu_launches = int(sum(v[2] for v in runs[head]["prof"].values()))
     traj = None
     if args.precision == "both":
         k = min(4, C)
         traj = _trajectory_error(rmhmc, prob, runs["fp64"]["q"][:k].clone(), runs["fp64"]["p"][:k].clone())
-    # CPU baseline: the oracle on this host's cores, bounded sample
+    # CPU baseline: the oracle on this host's cores, bounded sample (single-GPU runs only: with
+    # N > 1 ranks the host's cores are shared with the other ranks' processes)
     cpu_baseline = cpu_baseline_per_core = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and ws == 1:
         cb_value, cb_n, cb_s = oracle_leapfrogs(args.cpu_seconds)
         cpu_baseline = {"value": cb_value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
                         "sample": f"{cb_n} oracle leapfrog(s) of one chain of the workload in {cb_s:.1f} s "
