@@ -196,6 +196,8 @@ def _desc(problem):
     ks = (KernelDesc * len(problem["kernels"]))()
     for i, k in enumerate(problem["kernels"]):
         cols = list(k["cols"])
+        if not 1 <= len(cols) <= MAX_COLS:
+            raise RmhmcError(f"kernel {i}: {len(cols)} covariate columns (1..{MAX_COLS} supported)")
         ks[i].kind = KINDS[k["kind"]]
         ks[i].n_cols = len(cols)
         for j, cidx in enumerate(cols):

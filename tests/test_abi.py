@@ -113,6 +113,18 @@ def test_invalid_descriptions_are_rejected_without_a_gpu():
     assert L.rmhmc_plan_bytes_primal(ctypes.byref(pd), 2, ctypes.byref(size)) == 1
 
 
+def test_binding_rejects_kernels_with_too_many_columns():
+    import pytest
+    from paper_2511_06407_b300 import rmhmc, workloads as wl
+    prob = wl.gp_classification(8, seed=0)
+    prob["kernels"][0]["cols"] = list(range(rmhmc.MAX_COLS + 1))
+    with pytest.raises(rmhmc.RmhmcError):
+        rmhmc._desc(prob)
+    prob["kernels"][0]["cols"] = []
+    with pytest.raises(rmhmc.RmhmcError):
+        rmhmc._desc(prob)
+
+
 def test_server_is_refused_cleanly_without_a_gpu():
     """rmhmc_server_create validates the device before starting its scheduler thread: on a host
     without a CUDA device it returns EINVAL (raised by the binding), nothing is left running."""
