@@ -287,6 +287,52 @@ def _tensor_roofline(prof):
                              "the slicing kernels"}
 
 
+# The pipe whose measured peak bounds each timed category's counted FLOPs: FP64 FMA
+# (rmhmc_fp64_peak), the double-float multiply-add (rmhmc_df_peak), the bf16 tensor rate.
+CATEGORY_PIPE = {"gemm_f64": "fp64", "jacobi_f64": "fp64", "cholesky": "fp64", "trinv": "fp64",
+                 "jacobi_df": "df", "gemm_tc": "bf16"}
+
+
+def category_rooflines(prof, peaks, mixed=False):
+    """Per timed category ({name: (ms, flops, launches)}): its share of the step and, where the
+    library counts its FLOPs, the achieved TFLOP/s against the measured peak of its pipe; and the
+    step's flop-weighted total: the time every counted category would take at its pipe's peak over
+    the measured time (`frac`: of all categories, whose O(N^2) / O(d^2) memory-bound phases count
+    no FLOPs and only add time; `frac_counted`: of the counted ones). In the mixed form the
+    Cholesky and L^-1 count FP64-equivalent FLOPs of which most run on the tensor cores: they get
+    that rate but no single pipe."""
+    total = sum(v[0] for v in prof.values())
+    cats, ideal, counted = {}, 0.0, 0.0
+    for name, (ms, flops, launches) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
+        if not launches:
+            continue
+        e = {"ms": round(ms, 3), "share": ms / total if total else None}
+        pipe = CATEGORY_PIPE.get(name)
+        if mixed and name in ("cholesky", "trinv"):
+            pipe = None
+            if flops > 0 and ms > 0:
+                e["achieved_fp64_equivalent"] = flops / (ms * 1e-3) / 1e12
+        if pipe and flops > 0 and ms > 0 and peaks.get(pipe):
+            achieved = flops / (ms * 1e-3) / 1e12
+            e.update(pipe=pipe, achieved=achieved, peak=peaks[pipe], frac=achieved / peaks[pipe])
+            ideal += flops / (peaks[pipe] * 1e12) * 1e3
+            counted += ms
+        cats[name] = e
+    return {"unit": "TFLOP/s", "categories": cats,
+            "step": {"ideal_ms": ideal, "measured_ms": total, "frac": ideal / total if total else None,
+                     "frac_counted": ideal / counted if counted else None}}
+
+
+def _measured_pipe_peaks(rmhmc):
+    """{pipe: TFLOP/s} measured on this GPU (FP64 and double-float live, bf16 from the measured
+    sustained cuBLAS figure); {} if a probe fails."""
+    try:
+        return {"fp64": rmhmc.fp64_peak_tflops(300), "df": rmhmc.df_peak_tflops(300),
+                "bf16": _measured_bf16_peak()[0]}
+    except Exception:
+        return {}
+
+
 def _roofline(rmhmc, prof, C):
     """Roofline of the dominant kernel category (ALU bound; peaks measured live on this GPU)."""
     dom = max(prof, key=lambda k: prof[k][0])
@@ -418,6 +464,7 @@ def run_b300(args):
     value = job_value(C * SUBSTEPS_PER_LEAPFROG, ws, args.steps, ms * 1e-3)
     e2e_value = job_value(C * SUBSTEPS_PER_LEAPFROG, ws, e_steps, e2e_s)
     roof = _roofline(rmhmc, runs[head]["prof"], C)
+    pipe_peaks = _measured_pipe_peaks(rmhmc)
     gpu_launches = int(sum(v[2] for v in runs[head]["prof"].values()))
     traj = None
     if args.precision == "both":
@@ -452,6 +499,7 @@ def run_b300(args):
         "roofline": roof,
         "roofline_tensor_gemm": _tensor_roofline(runs[head]["prof"]),
         "profile_ms": pms, "profile_tflops": ptf,
+        "roofline_by_category": category_rooflines(runs[head]["prof"], pipe_peaks, mixed=head == "mixed"),
         "cpu_baseline": cpu_baseline,
         "cpu_baseline_per_core": cpu_baseline_per_core,
         "e2e": {"value": e2e_value, "unit": UNIT,
@@ -468,6 +516,7 @@ def run_b300(args):
         f_value = total_chains * SUBSTEPS_PER_LEAPFROG * args.steps / (r["ms"] * 1e-3)
         line["fp64"] = {"value": f_value, "ms_per_step": r["ms"] / args.steps, "roofline": _roofline(rmhmc, r["prof"], C),
                         "profile_ms": f_ms, "profile_tflops": f_tf,
+                        "roofline_by_category": category_rooflines(r["prof"], pipe_peaks),
                         "chain_status_nonzero": int((r["status"] != 0).sum()), "clocks": r["clk"]}
         line["speedup_vs_fp64"] = value / f_value
         line["trajectory_error_vs_fp64"] = traj

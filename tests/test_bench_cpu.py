@@ -23,3 +23,40 @@ def test_per_core_leg_runs_spawned_processes():
     assert leapfrogs >= procs and secs > 0
     # the sum of the processes' rates is at least what one process over the longest time gives
     assert rate >= bench.SUBSTEPS_PER_LEAPFROG * leapfrogs / secs / procs
+
+
+def _measured_mixed_profile():
+    """Category times (ms) and rates (TFLOP/s) of a measured mixed-form run (64 chains, N = 400,
+    5 leapfrogs) as {name: (ms, flops, launches)}."""
+    ms = {"cholesky": 86.216, "trinv": 36.026, "model": 26.797, "contract": 4.849, "vector": 25.2,
+          "reorth": 5.915, "jacobi_df": 545.957, "gemm_tc": 106.821}
+    tf = {"cholesky": 0.47509, "trinv": 1.13697, "vector": 0.10236, "jacobi_df": 1.45503, "gemm_tc": 639.9625}
+    return {k: (v, tf.get(k, 0.0) * 1e12 * v * 1e-3, 5) for k, v in ms.items()}
+
+
+def test_category_rooflines_of_a_measured_mixed_run():
+    peaks = {"fp64": 1.2006, "df": 6.4826, "bf16": 1372.4}
+    out = bench.category_rooflines(_measured_mixed_profile(), peaks, mixed=True)
+    cats = out["categories"]
+    assert abs(sum(c["share"] for c in cats.values()) - 1.0) < 1e-12
+    assert list(cats)[0] == "jacobi_df"  # ordered by time
+    assert abs(cats["jacobi_df"]["frac"] - 1.45503 / 6.4826) < 1e-9
+    assert abs(cats["gemm_tc"]["frac"] - 639.9625 / 1372.4) < 1e-9
+    # no pipe for the memory-bound phases, nor for the mixed Cholesky / L^-1
+    for name in ("model", "contract", "vector", "reorth", "cholesky", "trinv"):
+        assert "frac" not in cats[name]
+    assert abs(cats["trinv"]["achieved_fp64_equivalent"] - 1.13697) < 1e-9
+    st = out["step"]
+    ideal = 545.957 * 1.45503 / 6.4826 + 106.821 * 639.9625 / 1372.4
+    assert abs(st["ideal_ms"] - ideal) < 1e-6
+    assert abs(st["measured_ms"] - sum(v[0] for v in _measured_mixed_profile().values())) < 1e-9
+    assert st["frac"] < st["frac_counted"] < 1.0
+
+
+def test_category_rooflines_fp64_run_uses_the_fp64_pipe():
+    prof = {"gemm_f64": (1370.0, 0.8465e12 * 1.370, 40), "cholesky": (102.0, 0.4e12 * 0.102, 13),
+            "model": (27.0, 0.0, 30)}
+    out = bench.category_rooflines(prof, {"fp64": 1.2}, mixed=False)
+    assert out["categories"]["cholesky"]["pipe"] == "fp64"
+    assert abs(out["categories"]["gemm_f64"]["frac"] - 0.8465 / 1.2) < 1e-9
+    assert bench.category_rooflines(prof, {})["step"]["ideal_ms"] == 0.0  # no peaks measured
