@@ -18,8 +18,14 @@ Every function computes the plain definition with NumPy/LAPACK in float64:
   * sampler.py    Algorithm 1 with Metropolis-Hastings and momentum p ~ N(0, G)
   * philox.py     Philox4x64-10 counter-based generator (Salmon et al. 2011) + Box-Muller
   * jacobi.py     a separate cyclic Jacobi eigensolver used only for sweep-count checks (Sec. 2.4)
+  * primal.py     the reduced-rank (primal) model of Sec. 2.5: features, spectral weights, U and
+                  its derivatives, and the mean/variance model of Example 1 (J = 2)
+  * bme.py        thermodynamic integration for the model evidence (the BME appendix) and the
+                  closed-form tempered means of a Gaussian-likelihood GP
 
 Pins (see tests/test_oracle_*.py): finite differences of U and its derivatives, closed-form
 soft-abs limits, the Gaussian-likelihood GP posterior, brute-force quadrature at tiny N,
-leapfrog reversibility, eps^2 energy-error scaling, numpy's library Philox, scipy's MVN.
+leapfrog reversibility, eps^2 energy-error scaling, numpy's library Philox, scipy's MVN. The pins'
+sharpness is tested too: tests/test_oracle_mutations.py plants single-text mistakes in copies of
+these modules and requires a pin to fail for each.
 """
