@@ -192,20 +192,64 @@ def _oracle_one_core(job):
         return oracle_leapfrogs(seconds, seed=seed)
 
 
+# At most this many oracle processes at once, whatever the host reports.
+ORACLE_MAX_PROCS = 32
+
+
+def host_cores():
+    """Cores this process may run on: its CPU affinity set, bounded by the BLAS thread count the
+    single-chain leg uses (both follow the container's cpuset, unlike os.cpu_count())."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    return max(1, min(n, cpu_cores_used()))
+
+
+# cgroup memory limit and usage files (v2, then v1)
+CGROUP_MEMORY_FILES = (("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory.current"),
+                       ("/sys/fs/cgroup/memory/memory.limit_in_bytes",
+                        "/sys/fs/cgroup/memory/memory.usage_in_bytes"))
+
+
+def host_free_bytes(cgroup_files=CGROUP_MEMORY_FILES):
+    """Host memory this process may still use: the smaller of what the OS reports available and the
+    room left under each cgroup memory limit found, or None if neither is known."""
+    free = None
+    try:
+        import psutil
+        free = psutil.virtual_memory().available
+    except ImportError:
+        pass
+    for lim_path, use_path in cgroup_files:
+        try:
+            with open(lim_path) as f:
+                lim = f.read().strip()
+            if lim == "max":
+                continue
+            with open(use_path) as f:
+                room = int(lim) - int(f.read().strip())
+        except (OSError, ValueError):
+            continue
+        free = room if free is None else min(free, room)
+    return free
+
+
 def oracle_per_core(seconds, max_procs=None):
     """The many-chain CPU baseline: one chain per host core, each process with single-threaded
     BLAS, all running at once for about `seconds`. The pool is started with `spawn` (never forked
-    from a process that holds a CUDA context), and its size is the core count, bounded by the
-    available host memory (ORACLE_PROCESS_BYTES per process). Returns (aggregate substeps/s,
-    processes, total leapfrogs, longest worker time)."""
+    from a process that holds a CUDA context); its size is the usable core count, bounded by the
+    host memory this process may still use (ORACLE_PROCESS_BYTES per process) and by
+    ORACLE_MAX_PROCS. Returns (aggregate substeps/s, processes, total leapfrogs, longest worker
+    time)."""
     import multiprocessing as mp
-    n = os.cpu_count() or 1
-    try:
-        import psutil
-        n = min(n, int(0.8 * psutil.virtual_memory().available // ORACLE_PROCESS_BYTES))
-    except ImportError:
-        pass
-    n = max(1, min(n, max_procs) if max_procs else n)
+    n = min(host_cores(), ORACLE_MAX_PROCS)
+    free = host_free_bytes()
+    if free is not None:
+        n = min(n, int(0.8 * free // ORACLE_PROCESS_BYTES))
+    if max_procs:
+        n = min(n, max_procs)
+    n = max(1, n)
     with mp.get_context("spawn").Pool(n) as pool:
         res = pool.map(_oracle_one_core, [(seconds, 1 + i) for i in range(n)])
     return sum(r[0] for r in res), n, sum(r[1] for r in res), max(r[2] for r in res)

@@ -60,3 +60,20 @@ def test_category_rooflines_fp64_run_uses_the_fp64_pipe():
     assert out["categories"]["cholesky"]["pipe"] == "fp64"
     assert abs(out["categories"]["gemm_f64"]["frac"] - 0.8465 / 1.2) < 1e-9
     assert bench.category_rooflines(prof, {})["step"]["ideal_ms"] == 0.0  # no peaks measured
+
+
+def test_oracle_pool_is_bounded_by_the_container():
+    assert 1 <= bench.host_cores() <= len(os.sched_getaffinity(0))
+    free = bench.host_free_bytes()
+    assert free is None or free > 0
+
+
+def test_cgroup_memory_limit_bounds_the_free_bytes(tmp_path):
+    lim, use = tmp_path / "max", tmp_path / "current"
+    lim.write_text("10000000000\n")
+    use.write_text("4000000000\n")
+    got = bench.host_free_bytes(((str(lim), str(use)),))
+    assert got <= 6_000_000_000
+    lim.write_text("max\n")  # no limit: only what the OS reports
+    assert bench.host_free_bytes(((str(lim), str(use)),)) == bench.host_free_bytes(())
+    assert bench.host_free_bytes(((str(tmp_path / "missing"), str(use)),)) == bench.host_free_bytes(())
