@@ -38,6 +38,9 @@ N_INPUTS, N_CHAINS, EPS, N_FP = 400, 64, 0.005, 6
 JACOBI_DRAM_BYTES_PER_CHAIN = {"jacobi_f64": (22.255e6 + 2.149e6) / 8,
                                "jacobi_df": (22.273e6 + 2.176e6) / 8}
 SUBSTEPS_PER_LEAPFROG = 2 * N_FP + 1
+# The paper's settings for its simulated primal-model runs (Sec. 2.5): step size, and kappa of the
+# map g(lambda) = sqrt(kappa^2 + lambda^2) (passed as alpha = 1 / kappa).
+SOLIN_EPS, SOLIN_KAPPA = 0.001, 1.0
 METRIC = "RMHMC leapfrog substeps/s"
 UNIT = "substeps/s"
 WORKLOAD = (f"GP classification N={N_INPUTS} (d={N_INPUTS + 2}), SE kernel, {N_CHAINS} chains batched, "
@@ -710,7 +713,8 @@ def run_solin(args):
     out = {}
     for prec in ("mixed", "fp64"):
         model = rmhmc.Model(prob, C)
-        integ = rmhmc.Integrator(eps=args.eps or 0.001, n_fp=N_FP, n_leapfrog=1, g_kind="sqrt", alpha=1.0,
+        integ = rmhmc.Integrator(eps=args.eps or SOLIN_EPS, n_fp=N_FP, n_leapfrog=1, g_kind="sqrt",
+                                 alpha=1.0 / SOLIN_KAPPA,
                                  precision=prec)
         model.set_state(torch.zeros(C, model.d, dtype=torch.float64, device="cuda"), integ=integ)
         model.sample(1, 0, 5, integ=integ)

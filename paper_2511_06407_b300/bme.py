@@ -16,6 +16,16 @@ def power_schedule(S, power=5.0):
     return (np.arange(S) / (S - 1.0)) ** power
 
 
+def piecewise_schedule():
+    """The 101 inverse temperatures of the paper's own thermodynamic-integration runs (Sec. 2.5),
+    from 1 down to 0 in four linear pieces (steps 0.02, 0.005, 0.002, 0.001 from s = 1, 41, 71, 91):
+    finer near tau = 0, where the tempered mean of ln P changes fastest."""
+    s = np.arange(1, 102, dtype=np.float64)
+    return np.select([s <= 41, s <= 71, s <= 91],
+                     [1.0 - 0.02 * (s - 1), 0.2 - 0.005 * (s - 41), 0.05 - 0.002 * (s - 71)],
+                     0.01 - 0.001 * (s - 91))
+
+
 def _batch_var_of_mean(x, n_batches=10):
     x = np.asarray(x, dtype=np.float64)
     n = len(x) // n_batches * n_batches
