@@ -37,7 +37,10 @@ def _batch_var_of_mean(x, n_batches=10):
 
 def evidence(tau_per_chain, loglik):
     """tau_per_chain: (n_chains,), loglik: (n_iter, n_chains) untempered ln P(y | F) samples.
-    Returns (ln BME estimate, its standard error, per-temperature (tau, mean, var) table)."""
+    Returns (ln BME estimate, its standard error, per-temperature (tau, mean, var) table).
+    The variance of each temperature's mean comes from 10 batch means over its chains' series laid
+    end to end (a batch may span two chains), so the standard error, unlike the estimate, moves
+    with the order of the chains by its own sampling noise."""
     tau_per_chain = np.asarray(tau_per_chain, dtype=np.float64)
     loglik = np.asarray(loglik, dtype=np.float64)
     taus = np.unique(tau_per_chain)
