@@ -100,16 +100,24 @@ class Server:
                 if running or pending:
                     time.sleep(0.0005)
             stats = srv.stats()
-            makespan = max(j.finished for j in done) if done else 0.0
         finally:
             srv.close()
-        lat = np.array([j.latency for j in done])
-        substeps = sum((j.n_iter + j.n_burn) * j.n_chains * j.integ.n_leapfrog * (2 * j.integ.n_fp + 1)
-                       for j in done)
-        out = {"jobs": len(done), "makespan_s": makespan, "p50_latency_s": float(np.percentile(lat, 50)),
-               "p99_latency_s": float(np.percentile(lat, 99)), "substeps_per_s": substeps / makespan,
-               "max_concurrent_jobs": stats["max_active"]}
-        return sorted(done, key=lambda j: j.job_id), out
+        return sorted(done, key=lambda j: j.job_id), trace_summary(done, stats["max_active"])
+
+
+def trace_summary(done, max_active):
+    """Statistics of a served trace: p50 / p99 of the jobs' latencies (finish - arrival), the
+    makespan (the last finish on the server's clock) and the leapfrog substeps of all jobs per
+    second of makespan (n_fp fixed-point iterations for each implicit half plus the explicit one)."""
+    makespan = max(j.finished for j in done) if done else 0.0
+    lat = np.array([j.latency for j in done], dtype=np.float64)
+    substeps = sum((j.n_iter + j.n_burn) * j.n_chains * j.integ.n_leapfrog * (2 * j.integ.n_fp + 1)
+                   for j in done)
+    return {"jobs": len(done), "makespan_s": makespan,
+            "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "substeps_per_s": substeps / makespan if makespan > 0 else None,
+            "max_concurrent_jobs": max_active}
 
 
 def poisson_trace(problems, rate_per_s, seed=0):
