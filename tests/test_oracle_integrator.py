@@ -118,6 +118,22 @@ def test_metropolis_hastings_keeps_the_posterior_at_a_coarse_step(oracle_model):
     assert np.all(np.abs(dev2.mean(axis=0) - var) < 4 * se2 + 1e-12), (dev2.mean(axis=0), var, se2)
 
 
+def test_sampler_records_the_log_posterior_of_its_samples(oracle_model):
+    """The log P that Algorithm 1 records for each kept sample is the log posterior at the recorded
+    position: here scipy's densities (the GP prior's MVN and the Gaussian likelihood)."""
+    import scipy.stats as st
+    from oracle.kernels import kernel_derivs
+    prob = wl.gp_regression(3, seed=11, noise_var=0.2)
+    m = oracle_model(prob)
+    K = kernel_derivs("se", m.X, m.u_fixed, 1e-6)[0]
+    res = sample(m, np.zeros(3), 20, 5, seed=2, chain=0, eps=0.5, n_leapfrog=2, n_fp=2)
+    assert res["accept"].any()
+    for q, lp in zip(res["q"], res["logp"]):
+        want = (st.multivariate_normal(np.zeros(3), K).logpdf(q)
+                + st.norm.logpdf(m.y, loc=q, scale=np.sqrt(m.noise_var)).sum())
+        assert lp == pytest.approx(want, rel=1e-12, abs=1e-10)
+
+
 @pytest.mark.slow
 def test_brute_force_quadrature_tiny_classification(oracle_model):
     """N = 2 Bernoulli-logistic GP with both hyperparameters sampled (d = 4): RMHMC posterior means

@@ -219,6 +219,29 @@ MISTAKES += [
             lambda om: pins_geo.test_betancourt_traces_match_fd_of_metric(3.0, "coth", om)),
 ]
 
+MISTAKES += [
+    Mistake("sampler-records-U-not-log-P", "oracle.sampler",
+            "out_lp.append(-geo.U)", "out_lp.append(geo.U)",
+            ("sample",), lambda om: pins_int.test_sampler_records_the_log_posterior_of_its_samples(om)),
+    Mistake("linear-kernel-derivative-drops-amplitude", "oracle.kernels",
+            "D1 = np.full((N, N), c * th)", "D1 = np.full((N, N), th)",
+            ("kernel_derivs",), lambda om: pins_model.test_kernel_higher_derivatives_fd("linear")),
+    Mistake("overlap-third-kernel-derivative-drops-a-term", "oracle.kernels",
+            "D3 = c * E * (s ** 3 - 3.0 * s * s + s)", "D3 = c * E * (s ** 3 - 3.0 * s * s)",
+            ("kernel_derivs",), lambda om: pins_model.test_kernel_higher_derivatives_fd("overlap")),
+    Mistake("primal-potential-drops-bias-prior", "oracle.primal",
+            "U += 0.5 * b * b / model.bias_var + 0.5 * log(model.bias_var)",
+            "U += 0.5 * log(model.bias_var)",
+            ("potential",), lambda om: pins_primal.test_potential_matches_scipy_densities("bernoulli")),
+    Mistake("meanvar-cross-derivative-sign", "oracle.primal",
+            "(0, 1): r * rho / v,", "(0, 1): -r * rho / v,",
+            ("data_derivs",), lambda om: pins_primal.test_meanvar_likelihood_derivatives_match_finite_differences()),
+    Mistake("philox-weyl-increment", "oracle.philox",
+            "W0 = 0x9E3779B97F4A7C15", "W0 = 0x9E3779B97F4A7C17",
+            ("philox4x64_10",),
+            lambda om: pins_rng.test_philox_matches_numpy_library((7, 9), (5, 3, 2, 1))),
+]
+
 
 @pytest.mark.parametrize("mistake", MISTAKES, ids=[m.id for m in MISTAKES])
 def test_planted_mistake_fails_its_pin(mistake, monkeypatch, oracle_model):
