@@ -2,12 +2,13 @@
 """Benchmark: SoftAbs-RMHMC generalized-leapfrog substeps per second on B300.
 
 Workload (default): GP binary classification, N = 400 inputs x ~ U[-1, 1]^2, SE kernel with log
-amplitude and log lengthscale (d = 402), 64 chains in one batch, soft-abs alpha = 1e6, eps = 0.005,
-6 fixed-point iterations; the mixed-precision form (the headline value) and the plain FP64 path are
-timed one after the other, with the error of one 10-leapfrog trajectory between them. A step is one
-generalized leapfrog of every chain:
-13 substeps per chain (6 implicit-momentum iterations, 6 implicit-position iterations, 1 explicit
-half-step). value = chains x 13 x steps / seconds, whole job over all ranks.
+amplitude and log lengthscale (d = 402), 64 chains in one batch, soft-abs alpha = 1e6, eps = 0.001,
+6 fixed-point iterations. A step is one Algorithm 1 iteration of every chain: a momentum draw
+p ~ N(0, G), L = 10 generalized leapfrogs of 13 substeps each (6 implicit-momentum iterations, 6
+implicit-position iterations, 1 explicit half-step), the Metropolis-Hastings test and the return of
+rejected chains. value = chains x 10 x 13 x steps / seconds, whole job over all ranks. The
+mixed-precision form is the headline; the plain FP64 path is timed after it on the same workload
+(fewer iterations), with the error of one 10-leapfrog trajectory between the two.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
 
@@ -30,13 +31,16 @@ sys.path.insert(0, ROOT)
 
 from paper_2511_06407_b300 import workloads as wl  # noqa: E402
 
-N_INPUTS, N_CHAINS, EPS, N_FP = 400, 64, 0.005, 6
-# DRAM bytes per launch per chain of the Jacobi kernels, from the ncu captures summarised in
-# profiles/k_jacobi_N400_8chains.md and profiles/k_jacobi_df_N400_8chains.md (8 chains, mean of the
-# two captured launches; traffic grows with the number of chains, so a 64-chain launch is scaled
-# by 64 / 8).
-JACOBI_DRAM_BYTES_PER_CHAIN = {"jacobi_f64": (22.255e6 + 2.149e6) / 8,
-                               "jacobi_df": (22.273e6 + 2.176e6) / 8}
+# eps = 0.001 is the paper's step size for its simulated-data runs (Sec. 2.5); at N = 400 larger
+# steps lose the chains within a few Algorithm 1 iterations (0.005: acceptance below 0.15 and most
+# chains with a non-finite or non-positive-definite proposal after the first iteration; 0.002:
+# failures from the tenth), while 0.001 keeps every proposal finite and accepted over the run.
+N_INPUTS, N_CHAINS, EPS, N_FP, N_LEAPFROG = 400, 64, 0.001, 6, 10
+# DRAM bytes per launch per chain of the dominant kernels, as ncu's dram__bytes_read.sum +
+# dram__bytes_write.sum of single-kernel captures at 8 chains of this workload (traffic grows
+# with the number of chains, so a 64-chain launch is scaled by 64 / 8). A kernel enters here only
+# with counters taken from its current code.
+DRAM_BYTES_PER_CHAIN = {}
 SUBSTEPS_PER_LEAPFROG = 2 * N_FP + 1
 # The paper's settings for its simulated primal-model runs (Sec. 2.5): step size, and kappa of the
 # map g(lambda) = sqrt(kappa^2 + lambda^2) (passed as alpha = 1 / kappa).
@@ -44,7 +48,8 @@ SOLIN_EPS, SOLIN_KAPPA = 0.001, 1.0
 METRIC = "RMHMC leapfrog substeps/s"
 UNIT = "substeps/s"
 WORKLOAD = (f"GP classification N={N_INPUTS} (d={N_INPUTS + 2}), SE kernel, {N_CHAINS} chains batched, "
-            f"plain FP64, alpha=1e6, eps={EPS}, n_fp={N_FP}")
+            f"plain FP64, Algorithm 1 iterations of L={N_LEAPFROG} generalized leapfrogs (momentum "
+            f"refresh + Metropolis-Hastings), alpha=1e6, eps={EPS}, n_fp={N_FP}")
 
 
 MIXED_NOTE = ("mixed precision: Jacobi rotations in double-float (FP32 pairs, ~48-bit); the K^-1 algebra "
@@ -66,10 +71,16 @@ def dtype_of(prec):
 def arm_config(C, ws, head):
     """The workload description both arms print (the GPU arm and the oracle reference arm)."""
     workload = WORKLOAD if C == N_CHAINS else WORKLOAD.replace(f"{N_CHAINS} chains", f"{C} chains")
-    workload = workload.replace("plain FP64", "plain FP64" if head == "fp64" else "mixed precision")
+    names = {"fp64": "plain FP64", "mixed": "mixed precision", "oracle": "plain FP64 oracle (CPU)"}
+    workload = workload.replace("plain FP64", names[head])
+    precision = {"fp64": "plain FP64", "mixed": MIXED_NOTE,
+                 "oracle": "plain FP64 oracle: numpy/LAPACK on the host cores, one chain"}[head]
     return {"workload": workload, "N": N_INPUTS, "d": N_INPUTS + 2, "chains_per_gpu": C,
-            "precision": "plain FP64" if head == "fp64" else MIXED_NOTE,
-            "substeps_per_leapfrog": SUBSTEPS_PER_LEAPFROG,
+            "precision": precision,
+            "step": (f"one Algorithm 1 iteration of every chain: L={N_LEAPFROG} leapfrogs x "
+                     f"{SUBSTEPS_PER_LEAPFROG} substeps" if head != "oracle" else
+                     "one leapfrog of one chain's Algorithm 1 run (bounded sample)"),
+            "substeps_per_leapfrog": SUBSTEPS_PER_LEAPFROG, "n_leapfrog": N_LEAPFROG,
             "l2": "inputs larger than L2 (per-chain state ~16 MB, 64 chains ~1 GB > 126 MB)",
             "parallelism": f"replicas x{ws}"}
 
@@ -152,30 +163,68 @@ def cpu_cores_used():
     return os.cpu_count() or 1
 
 
-def oracle_leapfrogs(seconds, max_leapfrogs=None, seed=0):
-    """Time the plain FP64 oracle on one chain of the benchmark workload for about `seconds`
-    (at least one leapfrog); `seed` draws the chain's momenta. Returns (substeps/s, leapfrogs done,
-    seconds)."""
-    from oracle.geometry import Geometry
-    from oracle.integrator import leapfrog
-    from oracle.model import from_problem
-    prob = wl.gp_classification(N_INPUTS, seed=0)
-    m = from_problem(prob)
-    rng = np.random.default_rng(seed)
-    geo0 = Geometry(m, np.zeros(m.d), 1.0)
-    q, geo = np.zeros(m.d), geo0
-    p = geo.sqrtG_z(rng.standard_normal(m.d))
-    n, t0 = 0, time.perf_counter()
-    while True:
+class OracleChain:
+    """One chain of the benchmark workload run by the plain FP64 oracle through Algorithm 1, one
+    leapfrog at a time: every N_LEAPFROG leapfrogs the Metropolis-Hastings test of the trajectory
+    and a fresh momentum p = G^{1/2} z (the oracle's Philox draws, key (seed, 0)). The model and the
+    first geometry are built in the constructor, outside any timed region. A trajectory that leaves
+    the region where K is positive definite is a rejected proposal (as in the oracle's sampler)."""
+
+    def __init__(self, seed=0, n_inputs=None):
+        from oracle.geometry import Geometry
+        from oracle.model import from_problem
+        self.model = from_problem(wl.gp_classification(n_inputs or N_INPUTS, seed=0))
+        self.seed, self.it = seed, 0
+        self.q = np.zeros(self.model.d)
+        self.geo = Geometry(self.model, self.q, 1.0)
+        self.accepted = self.rejected = 0
+        self._refresh()
+
+    def _refresh(self):
+        from oracle.philox import normals
+        self.p = self.geo.sqrtG_z(normals(self.seed, 0, self.it, self.model.d))
+        self.H0 = self.geo.hamiltonian(self.p)
+        self.traj = (self.q, self.p, self.geo)
+        self.k = 0
+
+    def _finish(self, H1, new):
+        from oracle.philox import mh_uniform
+        with np.errstate(divide="ignore"):
+            logr = np.log(mh_uniform(self.seed, 0, self.it))
+        if new is not None and np.isfinite(H1) and logr < self.H0 - H1:
+            self.q, _, self.geo = new
+            self.accepted += 1
+        else:
+            self.rejected += 1
+        self.it += 1
+        self._refresh()
+
+    def leapfrog(self):
+        """One generalized leapfrog (and, after the trajectory's last, the MH test and momentum
+        refresh). Returns False when the trajectory failed numerically (proposal rejected; the
+        leapfrog is not counted)."""
+        from oracle.integrator import leapfrog
+        q, p, geo = self.traj
         try:
             with np.errstate(all="ignore"):
-                q, p, geo = leapfrog(m, q, p, EPS, N_FP, geo=geo)
-            n += 1
+                self.traj = leapfrog(self.model, q, p, EPS, N_FP, geo=geo)
         except np.linalg.LinAlgError:
-            # the trajectory left the region where K is positive definite: restart from f = 0,
-            # u = 0 with a fresh momentum (only completed leapfrogs are counted)
-            q, geo = np.zeros(m.d), geo0
-            p = geo.sqrtG_z(rng.standard_normal(m.d))
+            self._finish(np.inf, None)
+            return False
+        self.k += 1
+        if self.k == N_LEAPFROG:
+            self._finish(self.traj[2].hamiltonian(self.traj[1]), self.traj)
+        return True
+
+
+def oracle_leapfrogs(seconds, max_leapfrogs=None, seed=0):
+    """Time the plain FP64 oracle on one chain of the benchmark workload (Algorithm 1, continued
+    leapfrog by leapfrog) for about `seconds` (at least one leapfrog); the set-up (model, first
+    geometry) is outside the timed region. Returns (substeps/s, leapfrogs done, seconds)."""
+    chain = OracleChain(seed)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        n += 1 if chain.leapfrog() else 0
         el = time.perf_counter() - t0
         if (el >= seconds and n > 0) or (max_leapfrogs and n >= max_leapfrogs):
             break
@@ -186,11 +235,21 @@ def oracle_leapfrogs(seconds, max_leapfrogs=None, seed=0):
 # third-derivative tensor and its temporaries; 1.58 GB measured), with margin.
 ORACLE_PROCESS_BYTES = 2.0e9
 
+# Environment variables that fix the thread count of the BLAS libraries numpy may be linked with;
+# a `spawn` child reads them when it first imports numpy.
+BLAS_THREAD_VARS = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+                    "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")
+
 
 def _oracle_one_core(job):
-    """Worker of oracle_per_core: one chain, BLAS limited to one thread."""
+    """Worker of oracle_per_core: one chain with single-threaded BLAS. The parent sets
+    BLAS_THREAD_VARS to 1 before it spawns the pool; threadpoolctl, where installed, also limits
+    any BLAS pool already running."""
     seconds, seed = job
-    from threadpoolctl import threadpool_limits
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:
+        return oracle_leapfrogs(seconds, seed=seed)
     with threadpool_limits(limits=1):
         return oracle_leapfrogs(seconds, seed=seed)
 
@@ -253,8 +312,17 @@ def oracle_per_core(seconds, max_procs=None):
     if max_procs:
         n = min(n, max_procs)
     n = max(1, n)
-    with mp.get_context("spawn").Pool(n) as pool:
-        res = pool.map(_oracle_one_core, [(seconds, 1 + i) for i in range(n)])
+    saved = {k: os.environ.get(k) for k in BLAS_THREAD_VARS}
+    os.environ.update({k: "1" for k in BLAS_THREAD_VARS})
+    try:
+        with mp.get_context("spawn").Pool(n) as pool:
+            res = pool.map(_oracle_one_core, [(seconds, 1 + i) for i in range(n)])
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     return sum(r[0] for r in res), n, sum(r[1] for r in res), max(r[2] for r in res)
 
 
@@ -262,51 +330,84 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    # warm-up and timed steps: each step is a bounded sample (one oracle leapfrog of one chain)
+    # one chain of the workload, set up outside the timed region; each warm-up and timed step is a
+    # bounded sample: one leapfrog of that chain's Algorithm 1 run (momentum refresh and the
+    # Metropolis-Hastings test after every N_LEAPFROG-th), the trajectory continued across steps
+    chain = OracleChain(seed=0)
     for _ in range(args.warmup):
-        oracle_leapfrogs(0.0, max_leapfrogs=1)
-    t0 = time.perf_counter()
+        chain.leapfrog()
+    t0, done = time.perf_counter(), 0
     for _ in range(args.steps):
-        oracle_leapfrogs(0.0, max_leapfrogs=1)
+        done += 1 if chain.leapfrog() else 0
     el = time.perf_counter() - t0
-    value = SUBSTEPS_PER_LEAPFROG * args.steps / el
+    value = SUBSTEPS_PER_LEAPFROG * done / el
     cores = cpu_cores_used()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": arm_config(args.chains, args.gpus, "mixed" if args.precision == "both" else args.precision),
+            "config": arm_config(args.chains, args.gpus, "oracle"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "one chain of the workload, one leapfrog per step (numpy/LAPACK FP64, "
-                                       "full third-derivative tensor)"},
+                             "sample": f"one chain of the workload, one leapfrog of its Algorithm 1 run per step "
+                                       f"({done} of {args.steps} completed; numpy/LAPACK FP64, full "
+                                       "third-derivative tensor; set-up outside the timed region)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def _time_leapfrogs(model, integ, steps, stream, local, ws, dev):
-    """K timed leapfrogs of every chain (device-resident state), CUDA events on the model's stream,
-    clocks sampled meanwhile; returns (ms, profile, clocks), ms the max over ranks."""
+def _time_iterations(model, integ, steps, seed, stream, local, ws, dev):
+    """K timed Algorithm 1 iterations of every chain (device-resident state) in one rmhmc_sample
+    call, CUDA events on the model's stream, library profiling off, clocks sampled meanwhile.
+    Returns (ms as the max over ranks, accept (K x C), chain status (C), clocks)."""
     import torch
     import torch.distributed as dist
+    C = model.n_chains
+    acc = torch.zeros(steps, C, dtype=torch.int32, device=dev)
+    cs = torch.zeros(C, dtype=torch.int32, device=dev)
     clocks = ClockSampler(local)
     clocks.start()
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    model.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(steps):
-        model.leapfrog(1, integ=integ)
+    model.sample(steps, 0, seed, accept=acc, chain_status=cs, integ=integ)
     e1.record(stream)
     torch.cuda.synchronize()
-    prof = model.profile_read()
-    model.profile(False)
     if ws > 1:
         dist.barrier()
     clk = clocks.stop()
-    return max_over_ranks(e0.elapsed_time(e1), ws, dev), prof, clk
+    return max_over_ranks(e0.elapsed_time(e1), ws, dev), acc.cpu().numpy(), cs.cpu().numpy(), clk
+
+
+def _profile_iteration(model, integ, seed):
+    """One more Algorithm 1 iteration, outside the timed region, with the library's per-launch-site
+    events on (per-category time, counted FLOPs) and, where torch's profiler (CUPTI) works, the
+    kernels the device actually ran. Returns (category profile, {kernel: launches} or None)."""
+    import torch
+    kernels = None
+    model.profile(True)
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as tp:
+            model.sample(1, 0, seed, integ=integ)
+            torch.cuda.synchronize()
+        kernels = {}
+        for ev in tp.events():
+            if getattr(ev, "device_type", None) is not None and "CUDA" in str(ev.device_type):
+                name = ev.name.split("(")[0].split("<")[0].replace("void ", "").strip()
+                if name.startswith("Memcpy") or name.startswith("Memset") or name.startswith("["):
+                    continue
+                kernels[name] = kernels.get(name, 0) + 1
+        if not kernels:
+            kernels = None
+    except Exception:
+        model.sample(1, 0, seed, integ=integ)
+        kernels = None
+    prof = model.profile_read()
+    model.profile(False)
+    return prof, kernels
 
 
 def _measured_bf16_peak():
@@ -402,32 +503,116 @@ def _roofline(rmhmc, prof, C):
         out["achieved_note"] = ("executed work: 16x16x16 rotation-tile products x 8192 flops (skipped identity "
                                 "tiles not counted) + inner rotation rounds x 1952 flops; rotation angles, "
                                 "stopping tests and conversions not counted")
-    if dom in JACOBI_DRAM_BYTES_PER_CHAIN:
-        out["traffic"] = JACOBI_DRAM_BYTES_PER_CHAIN[dom] * C
+    if dom in DRAM_BYTES_PER_CHAIN:
+        out["traffic"] = DRAM_BYTES_PER_CHAIN[dom] * C
         out["traffic_note"] = "bytes per launch, ncu capture at 8 chains scaled to the chain count"
     return out
 
 
-def _trajectory_error(rmhmc, prob, q0, p0):
-    """One 10-leapfrog trajectory of the same chains from the same (q, p) in both precisions:
-    max over chains of ||x_mixed - x_fp64|| / ||x_fp64|| for x = q and p."""
+def _trajectory_error(rmhmc, prob, q0, seed=7):
+    """One 10-leapfrog trajectory of the same chains from the same (q, p) in both precisions, p
+    drawn from N(0, G(q)) with G of the FP64 geometry: max over chains of
+    ||x_mixed - x_fp64|| / ||x_fp64|| for x = q and p."""
     import torch
+    C, d = q0.shape
+    f64 = dict(dtype=torch.float64, device=q0.device)
+    m = rmhmc.Model(prob, C)
+    m.set_state(q0, integ=rmhmc.Integrator(eps=EPS, n_fp=N_FP, n_leapfrog=1, precision="fp64"))
+    G = torch.empty(C, d, d, **f64)
+    m.geometry(G=G)
+    torch.cuda.synchronize()
+    m.close()
+    gen = torch.Generator(device=q0.device).manual_seed(seed)
+    z = torch.randn(C, d, 1, generator=gen, **f64)
+    p0 = (torch.linalg.cholesky(G) @ z).squeeze(-1).contiguous()
     out = {}
     for prec in ("fp64", "mixed"):
         integ = rmhmc.Integrator(eps=EPS, n_fp=N_FP, n_leapfrog=1, precision=prec)
-        m = rmhmc.Model(prob, q0.shape[0])
+        m = rmhmc.Model(prob, C)
         m.set_state(q0, p0, integ=integ)
         m.leapfrog(10, integ=integ)
         q, p = torch.empty_like(q0), torch.empty_like(q0)
-        m.leapfrog(0, q, p, integ=integ)
+        st = torch.empty(C, dtype=torch.int32, device=q0.device)
+        m.leapfrog(0, q, p, status_out=st, integ=integ)
         torch.cuda.synchronize()
-        out[prec] = (q.cpu().numpy(), p.cpu().numpy())
+        out[prec] = (q.cpu().numpy(), p.cpu().numpy(), st.cpu().numpy())
         m.close()
+    ok = (out["fp64"][2] == 0) & (out["mixed"][2] == 0)
     rel = {}
     for k, name in enumerate(("q", "p")):
-        a, b = out["fp64"][k], out["mixed"][k]
-        rel[name] = float(np.max(np.linalg.norm(b - a, axis=1) / np.linalg.norm(a, axis=1)))
-    return {"chains": int(q0.shape[0]), "leapfrogs": 10, "max_rel_q": rel["q"], "max_rel_p": rel["p"]}
+        a, b = out["fp64"][k][ok], out["mixed"][k][ok]
+        rel[name] = float(np.max(np.linalg.norm(b - a, axis=1) / np.linalg.norm(a, axis=1))) if ok.any() else None
+    return {"chains": int(C), "chains_finite": int(ok.sum()), "leapfrogs": 10,
+            "max_rel_q": rel["q"], "max_rel_p": rel["p"]}
+
+
+def _e2e(rmhmc, prob, C, integ, steps, seed, stream, dev, ws):
+    """End to end through the public API, as a user runs the sampler from host data: the model is
+    created from the host arrays (X, y copied in), the chains' start q0 is copied from pinned host
+    memory, and every step is one Algorithm 1 iteration (rmhmc_sample) whose draws (q, log P,
+    accept, chain status) are copied back to pinned host memory. Returns (seconds as the max over
+    ranks, h2d bytes per step, d2h bytes per step, chain status)."""
+    import torch
+    import torch.distributed as dist
+    d = wl.dims(prob)[2]
+    q0_host = torch.zeros(C, d, dtype=torch.float64).pin_memory()
+    qs_host = torch.empty(1, C, d, dtype=torch.float64).pin_memory()
+    lp_host = torch.empty(1, C, dtype=torch.float64).pin_memory()
+    acc_host = torch.empty(1, C, dtype=torch.int32).pin_memory()
+    cs_host = torch.empty(C, dtype=torch.int32).pin_memory()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    model = rmhmc.Model(prob, C, stream=stream)
+    q0 = torch.empty(C, d, dtype=torch.float64, device=dev)
+    q0.copy_(q0_host, non_blocking=True)
+    model.set_state(q0, integ=integ)
+    qs = torch.empty(1, C, d, dtype=torch.float64, device=dev)
+    lp = torch.empty(1, C, dtype=torch.float64, device=dev)
+    acc = torch.empty(1, C, dtype=torch.int32, device=dev)
+    cs = torch.empty(C, dtype=torch.int32, device=dev)
+    status = np.zeros(C, dtype=np.int32)
+    for _ in range(steps):
+        model.sample(1, 0, seed, qs, lp, acc, chain_status=cs, integ=integ)
+        qs_host.copy_(qs, non_blocking=True)
+        lp_host.copy_(lp, non_blocking=True)
+        acc_host.copy_(acc, non_blocking=True)
+        cs_host.copy_(cs, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        status |= cs_host.numpy()
+    torch.cuda.synchronize()
+    el = max_over_ranks(time.perf_counter() - t0, ws, dev)
+    model.close()
+    X = np.asarray(prob["X"])
+    h2d = (X.size + np.asarray(prob["y"]).size + q0_host.numel()) * 8 / steps
+    d2h = (qs_host.numel() + lp_host.numel()) * 8 + (acc_host.numel() + cs_host.numel()) * 4
+    return el, int(h2d), int(d2h), status
+
+
+def _run_arm(rmhmc, prob, C, prec, warmup, steps, seed, stream, local, ws, dev):
+    """Warm-up and timed Algorithm 1 iterations of one precision, then one profiled iteration."""
+    import torch
+    model = rmhmc.Model(prob, C, stream=stream)
+    integ = rmhmc.Integrator(eps=EPS, n_fp=N_FP, n_leapfrog=N_LEAPFROG, precision=prec)
+    model.set_state(torch.zeros(C, model.d, dtype=torch.float64, device=dev), integ=integ)
+    warm_cs = torch.zeros(C, dtype=torch.int32, device=dev)
+    model.sample(warmup, 0, seed, chain_status=warm_cs, integ=integ)
+    ms, acc, cs, clk = _time_iterations(model, integ, steps, seed, stream, local, ws, dev)
+    prof, kernels = _profile_iteration(model, integ, seed)
+    q = torch.empty(C, model.d, dtype=torch.float64, device=dev)
+    model.leapfrog(0, q, integ=integ)
+    torch.cuda.synchronize()
+    model.close()
+    return {"ms": ms, "acc": acc, "status": cs, "warm_status": warm_cs.cpu().numpy(), "clk": clk,
+            "prof": prof, "kernels": kernels, "q": q}
+
+
+def _status_summary(status):
+    """Chains whose proposals failed numerically during the timed iterations, by failure kind."""
+    bits = (("not_pd", 1), ("jacobi_not_converged", 2), ("non_finite", 4), ("wait_timeout", 8))
+    return {"chains_with_failed_proposal": int((status != 0).sum()),
+            **{name: int(((status & bit) != 0).sum()) for name, bit in bits}}
 
 
 def run_b300(args):
@@ -446,60 +631,20 @@ def run_b300(args):
     stream = torch.cuda.current_stream()
     prob = wl.gp_classification(N_INPUTS, seed=0)
     C = args.chains
+    seed = 1234 + rank
     precisions = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
     runs = {}
     for prec in precisions:
-        model = rmhmc.Model(prob, C, stream=stream)
-        d = model.d
-        integ = rmhmc.Integrator(eps=EPS, n_fp=N_FP, n_leapfrog=1, precision=prec)
-        model.set_state(torch.zeros(C, d, dtype=torch.float64, device=dev), integ=integ)
-        # warm-up: one Algorithm 1 iteration (momenta p ~ N(0, G) drawn by the library, one
-        # leapfrog, Metropolis-Hastings), then plain leapfrogs
-        model.sample(1, 0, 1234 + rank, integ=integ)
-        if args.warmup > 1:
-            model.leapfrog(args.warmup - 1, integ=integ)
-        qo = torch.empty(C, d, dtype=torch.float64, device=dev)
-        po = torch.empty_like(qo)
-        model.leapfrog(0, qo, po, integ=integ)
-        torch.cuda.synchronize()
-        ms, prof, clk = _time_leapfrogs(model, integ, args.steps, stream, local, ws, dev)
-        runs[prec] = {"model": model, "integ": integ, "ms": ms, "prof": prof, "clk": clk, "q": qo, "p": po}
+        steps = args.steps if prec == precisions[0] else max(1, min(args.steps, args.fp64_steps))
+        warm = args.warmup if prec == precisions[0] else max(1, min(args.warmup, 2))
+        runs[prec] = _run_arm(rmhmc, prob, C, prec, warm, steps, seed, stream, local, ws, dev)
+        runs[prec]["steps"] = steps
     head = precisions[0]
-    model, integ, d = runs[head]["model"], runs[head]["integ"], runs[head]["model"].d
-    ms = runs[head]["ms"]
-
-    # ---- end to end: the host drives the trajectory. Per step the momenta are uploaded from pinned
-    # host memory, one leapfrog runs through the C ABI, and position, momentum and Hamiltonian are
-    # read back into pinned host memory; the momenta read back are the next step's upload (stream
-    # order makes the read-back land before the next upload reads it), so the chains continue the
-    # same trajectory as in the device-timed region.
-    qo, po = torch.empty(C, d, dtype=torch.float64, device=dev), torch.empty(C, d, dtype=torch.float64, device=dev)
-    Ho = torch.empty(C, dtype=torch.float64, device=dev)
-    st = torch.empty(C, dtype=torch.int32, device=dev)
-    model.leapfrog(0, qo, po, integ=integ)
-    p_host = po.cpu().pin_memory()
-    p_dev = torch.empty_like(po)
-    q_host = torch.empty(C, d, dtype=torch.float64).pin_memory()
-    H_host = torch.empty(C, dtype=torch.float64).pin_memory()
-    e_steps = max(1, min(args.steps, 3))
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e_steps):
-        p_dev.copy_(p_host, non_blocking=True)
-        model.leapfrog(1, qo, po, Ho, st, integ=integ, p_in=p_dev)
-        q_host.copy_(qo, non_blocking=True)
-        p_host.copy_(po, non_blocking=True)
-        H_host.copy_(Ho, non_blocking=True)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_s = max_over_ranks(e2e_s, ws, dev)
-    status = st.cpu().numpy()
-    for prec in precisions:
-        x = torch.empty(C, dtype=torch.int32, device=dev)
-        runs[prec]["model"].leapfrog(0, status_out=x, integ=runs[prec]["integ"])
-        runs[prec]["status"] = x.cpu().numpy()
+    h = runs[head]
+    ms = h["ms"]
+    integ = rmhmc.Integrator(eps=EPS, n_fp=N_FP, n_leapfrog=N_LEAPFROG, precision=head)
+    e_steps = max(1, min(args.steps, args.e2e_steps))
+    e2e_s, h2d, d2h, e2e_status = _e2e(rmhmc, prob, C, integ, e_steps, seed + 1, stream, dev, ws)
 
     if rank != 0:
         if ws > 1:
@@ -507,34 +652,37 @@ def run_b300(args):
             dist.destroy_process_group()
         return 0
 
-    total_chains = C * ws
-    value = job_value(C * SUBSTEPS_PER_LEAPFROG, ws, args.steps, ms * 1e-3)
-    e2e_value = job_value(C * SUBSTEPS_PER_LEAPFROG, ws, e_steps, e2e_s)
-    roof = _roofline(rmhmc, runs[head]["prof"], C)
+    units = C * N_LEAPFROG * SUBSTEPS_PER_LEAPFROG  # substeps per step on one rank
+    value = job_value(units, ws, args.steps, ms * 1e-3)
+    e2e_value = job_value(units, ws, e_steps, e2e_s)
+    roof = _roofline(rmhmc, h["prof"], C)
     pipe_peaks = _measured_pipe_peaks(rmhmc)
-    gpu_launches = int(sum(v[2] for v in runs[head]["prof"].values()))
+    per_iter_launches = (sum(h["kernels"].values()) if h["kernels"]
+                         else int(sum(v[2] for v in h["prof"].values())))
     traj = None
     if args.precision == "both":
         k = min(4, C)
-        traj = _trajectory_error(rmhmc, prob, runs["fp64"]["q"][:k].clone(), runs["fp64"]["p"][:k].clone())
-    # CPU baseline: the oracle on this host's cores, bounded sample (single-GPU runs only: with
+        traj = _trajectory_error(rmhmc, prob, runs["fp64"]["q"][:k].clone())
+    # CPU baselines: the oracle on this host's cores, bounded samples (single-GPU runs only: with
     # N > 1 ranks the host's cores are shared with the other ranks' processes)
     cpu_baseline = cpu_baseline_per_core = None
     if not args.no_cpu_baseline and ws == 1:
         cb_value, cb_n, cb_s = oracle_leapfrogs(args.cpu_seconds)
         cpu_baseline = {"value": cb_value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
-                        "sample": f"{cb_n} oracle leapfrog(s) of one chain of the workload in {cb_s:.1f} s "
-                                  "(numpy/LAPACK FP64, full third-derivative tensor)"}
+                        "sample": f"{cb_n} oracle leapfrog(s) of one chain's Algorithm 1 run in {cb_s:.1f} s "
+                                  "(numpy/LAPACK FP64, full third-derivative tensor; set-up untimed)"}
         pc_value, pc_n, pc_l, pc_s = oracle_per_core(args.cpu_seconds)
         cpu_baseline_per_core = {"value": pc_value, "unit": UNIT, "cores": pc_n, "kind": "oracle",
                                  "sample": f"{pc_n} processes at once, one chain each with single-threaded "
                                            f"BLAS, {pc_l} oracle leapfrogs in at most {pc_s:.1f} s; value = "
                                            "sum of the processes' rates"}
+
     def prof_summary(prof):
         return ({k: round(v[0], 3) for k, v in prof.items() if v[2]},
                 {k: (v[1] / (v[0] * 1e-3) / 1e12 if v[0] > 0 else 0.0) for k, v in prof.items() if v[2]})
 
-    pms, ptf = prof_summary(runs[head]["prof"])
+    pms, ptf = prof_summary(h["prof"])
+    failed = _status_summary(h["status"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -542,32 +690,44 @@ def run_b300(args):
         "dtype": "f64" if head == "fp64" else DTYPE_MIXED,
         "data": "synthetic",
         "config": arm_config(C, ws, head),
-        "leapfrogs_per_s": total_chains * args.steps / (ms * 1e-3),
+        "leapfrogs_per_s": C * ws * N_LEAPFROG * args.steps / (ms * 1e-3),
+        "acceptance": float(h["acc"].mean()),
+        "timed_region_failures": failed,
+        "valid": failed["chains_with_failed_proposal"] == 0,
         "roofline": roof,
-        "roofline_tensor_gemm": _tensor_roofline(runs[head]["prof"]),
+        "roofline_tensor_gemm": _tensor_roofline(h["prof"]),
+        "profile_note": "per-category times and FLOPs from one further profiled iteration (library "
+                        "events around each launch site), outside the timed region",
         "profile_ms": pms, "profile_tflops": ptf,
-        "roofline_by_category": category_rooflines(runs[head]["prof"], pipe_peaks, mixed=head == "mixed"),
+        "roofline_by_category": category_rooflines(h["prof"], pipe_peaks, mixed=head == "mixed"),
         "cpu_baseline": cpu_baseline,
         "cpu_baseline_per_core": cpu_baseline_per_core,
-        "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": int(p_host.numel() * 8),
-                "d2h_bytes_per_step": int((q_host.numel() + p_host.numel() + H_host.numel()) * 8)},
-        "gpu_launches": gpu_launches,
-        "chain_status_nonzero": int((status != 0).sum() + (runs[head]["status"] != 0).sum()),
-        "valid": bool((status == 0).all() and (runs[head]["status"] == 0).all()),
-        "clocks": runs[head]["clk"],
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e_steps,
+                "note": "model created from host X, y and q0 (pinned) inside the timed region, then one "
+                        "rmhmc_sample iteration per step with its draws copied to pinned host memory",
+                "chains_with_failed_proposal": int((e2e_status != 0).sum())},
+        "gpu_launches": per_iter_launches * args.steps,
+        "gpu_launches_note": ("kernels per iteration counted by torch's CUDA profiler (CUPTI) in the "
+                              "profiled iteration, times the timed iterations" if h["kernels"] else
+                              "launch sites counted by the library's profiler, times the timed iterations"),
+        "clocks": h["clk"],
     }
     if "fp64" in runs and head != "fp64":
         r = runs["fp64"]
         f_ms, f_tf = prof_summary(r["prof"])
-        f_value = total_chains * SUBSTEPS_PER_LEAPFROG * args.steps / (r["ms"] * 1e-3)
-        line["fp64"] = {"value": f_value, "ms_per_step": r["ms"] / args.steps, "roofline": _roofline(rmhmc, r["prof"], C),
+        f_value = job_value(units, ws, r["steps"], r["ms"] * 1e-3)
+        line["fp64"] = {"value": f_value, "steps": r["steps"], "ms_per_step": r["ms"] / r["steps"],
+                        "acceptance": float(r["acc"].mean()), "roofline": _roofline(rmhmc, r["prof"], C),
                         "profile_ms": f_ms, "profile_tflops": f_tf,
                         "roofline_by_category": category_rooflines(r["prof"], pipe_peaks),
-                        "chain_status_nonzero": int((r["status"] != 0).sum()), "clocks": r["clk"]}
+                        "timed_region_failures": _status_summary(r["status"]), "clocks": r["clk"]}
         line["speedup_vs_fp64"] = value / f_value
         line["trajectory_error_vs_fp64"] = traj
     print(json.dumps(line), flush=True)
+    if not line["valid"]:
+        print(f"bench: {failed['chains_with_failed_proposal']} chain(s) had a numerically failed proposal "
+              "in the timed region; the value is not a valid measurement", file=sys.stderr)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -825,6 +985,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="timed iterations of the plain FP64 comparison leg (at most --steps)")
+    ap.add_argument("--e2e-steps", type=int, default=5,
+                    help="iterations of the end-to-end leg (at most --steps)")
     ap.add_argument("--chains", type=int, default=N_CHAINS,
                     help="chains per GPU (the workload is 64; smaller values are for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")

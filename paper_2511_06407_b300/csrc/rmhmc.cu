@@ -1636,9 +1636,13 @@ rmhmc_status rmhmc_sample(rmhmc_model* m, const rmhmc_integrator* integ, int n_i
     const bool rec = it >= n_burn;
     const long long ro = rec ? (long long)(it - n_burn) : 0;
     // p = G^{1/2} z (symmetric root)
+    PROF(m, CAT_VECTOR, 0)
     k_normals<<<dim3(nblk((dp + 3) / 4, 128), C), 128, 0, s>>>(m->z, dp, d, C, seed, l);
+    PROF(m, CAT_VECTOR, 2.0 * C * (double)d * d)
     gemv_f64(s, false, dp, dp, m->PsiT, dp, DD, m->z, dp, m->t1, dp, C, 1.0, 0.0);
+    PROF(m, CAT_VECTOR, 0)
     k_scale_g<<<nblk(nv), 256, 0, s>>>(m->t1, m->g, dp, d, C, 1);
+    PROF(m, CAT_VECTOR, 2.0 * C * (double)d * d)
     gemv_f64(s, true, dp, dp, m->PsiT, dp, DD, m->t1, dp, m->p, dp, C, 1.0, 0.0);
     hamiltonian(m, m->p, m->Ham0);
     cudaMemcpyAsync(m->q_save, m->q, nv * sizeof(double), cudaMemcpyDeviceToDevice, s);
@@ -1647,14 +1651,17 @@ rmhmc_status rmhmc_sample(rmhmc_model* m, const rmhmc_integrator* integ, int n_i
     cudaMemsetAsync(m->sweeps_acc, 0, C * sizeof(int), s);
     for (int L = 0; L < integ->n_leapfrog; ++L) leapfrog_step(m, integ->eps, integ->n_fp);
     hamiltonian(m, m->p, m->Ham1);
+    PROF(m, CAT_VECTOR, 0)
     k_accept<<<nblk(C), 256, 0, s>>>(m->Ham0, m->Ham1, m->status, m->acc, C, seed, l,
                                      (rec && accept_dev) ? accept_dev + ro * C : nullptr,
                                      (rec && sweeps_dev) ? sweeps_dev + ro * C : nullptr,
                                      m->sweeps_acc, chain_status_dev);
+    PROF(m, CAT_VECTOR, 0)
     k_restore<<<dim3(nblk(DD), C), 256, 0, s>>>(m->acc, m->q, m->q_save, m->PsiT, m->PsiT_save,
                                                 m->eig_count, m->eig_save, dp);
     eval_geometry(m, true);
     if (rec && (q_samples_dev || logp_dev || loglik_dev))
+      PROF(m, CAT_VECTOR, 0)
       k_record<<<nblk((long long)C * d), 256, 0, s>>>(m->q, m->U, m->LL, dp, d, C,
                                                        q_samples_dev ? q_samples_dev + ro * C * d : nullptr,
                                                        logp_dev ? logp_dev + ro * C : nullptr,

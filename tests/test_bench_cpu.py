@@ -77,3 +77,33 @@ def test_cgroup_memory_limit_bounds_the_free_bytes(tmp_path):
     lim.write_text("max\n")  # no limit: only what the OS reports
     assert bench.host_free_bytes(((str(lim), str(use)),)) == bench.host_free_bytes(())
     assert bench.host_free_bytes(((str(tmp_path / "missing"), str(use)),)) == bench.host_free_bytes(())
+
+
+def test_per_core_worker_runs_without_threadpoolctl(monkeypatch):
+    # the GPU hosts may not have threadpoolctl: the worker then relies on the BLAS thread
+    # variables its parent sets before spawning it
+    monkeypatch.setitem(sys.modules, "threadpoolctl", None)
+    rate, n, secs = bench._oracle_one_core((0.0, 1))
+    assert n == 1 and rate > 0 and secs > 0
+
+
+def test_per_core_leg_restores_the_blas_thread_variables(monkeypatch):
+    monkeypatch.setenv("OMP_NUM_THREADS", "3")
+    monkeypatch.delenv("OPENBLAS_NUM_THREADS", raising=False)
+    bench.oracle_per_core(0.0, max_procs=1)
+    assert os.environ["OMP_NUM_THREADS"] == "3"
+    assert "OPENBLAS_NUM_THREADS" not in os.environ
+
+
+def test_oracle_chain_is_algorithm_1():
+    # ten leapfrogs of the timed chain make one Algorithm 1 iteration: the same proposal, test and
+    # kept state as the oracle's sampler with the same seed
+    import numpy as np
+    from oracle.sampler import sample
+    chain = bench.OracleChain(seed=3, n_inputs=12)
+    for _ in range(bench.N_LEAPFROG):
+        assert chain.leapfrog()
+    assert chain.it == 1 and chain.accepted + chain.rejected == 1
+    ref = sample(chain.model, np.zeros(chain.model.d), 1, 0, 3, 0, bench.EPS, bench.N_LEAPFROG, bench.N_FP)
+    assert bool(ref["accept"][0]) == (chain.accepted == 1)
+    assert np.array_equal(ref["q"][0], chain.q)
