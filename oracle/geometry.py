@@ -56,6 +56,10 @@ class Geometry:
         self.U = ops.potential(model, q, tau)
         self.dU = ops.gradient(model, q, tau)
         self.H = ops.hessian(model, q, tau)
+        if not (np.all(np.isfinite(self.H)) and np.isfinite(self.U)):
+            # a numerically failed point (Algorithm 1 rejects the proposal that reaches it); LAPACK's
+            # eigensolvers are not defined on non-finite input
+            raise np.linalg.LinAlgError("non-finite potential or Hessian")
         if _EIG["driver"] == "evd":
             self.lam, self.Psi = np.linalg.eigh(self.H)
         else:
