@@ -791,7 +791,7 @@ def run_ess(args):
     if args.ess_model == "dual":
         N = args.ess_n
         prob = wl.gp_classification(N, seed=0)
-        eps = args.eps or 0.01
+        eps = args.eps or (EPS if N == N_INPUTS else 0.01)
         geom = {}
         names = ["log P", "log c", "log l", "mean f"]
         label = f"GP classification N={N} (d={N + 2})"
@@ -811,7 +811,7 @@ def run_ess(args):
         d = model.d
         model.set_state(torch.zeros(C, d, dtype=torch.float64, device="cuda"), integ=integ)
         cs = torch.zeros(C, dtype=torch.int32, device="cuda")
-        seed = 11 + 1000 * k
+        seed = 11 + (0 if args.ess_same_seed else 1000 * k)
         model.sample(0, args.burn, seed, chain_status=cs, integ=integ)
         qs = torch.empty(args.iters, C, d, dtype=torch.float64, device="cuda")
         lp = torch.empty(args.iters, C, dtype=torch.float64, device="cuda")
@@ -830,6 +830,7 @@ def run_ess(args):
         se_mean = np.array([dg.mcse_mean(x[:, :, j]) for j in range(4)])
         se_var = np.array([dg.mcse_mean((x[:, :, j] - mean[j]) ** 2) for j in range(4)])
         runs[prec] = {"seconds": el, "min_ess": summ["min_ess"], "ess_per_s": summ["min_ess"] / el,
+                      "_draws": draws, "_accept": acc.cpu().numpy(),
                       "max_rhat": summ["max_rhat"], "acceptance": float(acc.cpu().numpy().mean()),
                       "substeps_per_s": C * args.iters * 10 * SUBSTEPS_PER_LEAPFROG / el,
                       "chain_status_nonzero": int(((cs | cs2).cpu().numpy() != 0).sum()),
@@ -840,6 +841,26 @@ def run_ess(args):
                       "mean": mean, "var": var, "se_mean": se_mean, "se_var": se_var, "clocks": clk}
         model.close()
     a, b = runs["fp64"], runs["mixed"]
+    paths = None
+    if args.ess_same_seed:
+        # the same Philox draws in both precisions: the mixed chains follow the FP64 chains
+        da, db = a["_draws"], b["_draws"]
+        paths = {"same_decisions_fraction": float((a["_accept"] == b["_accept"]).mean()),
+                 "max_rel_diff_per_quantity": [float(np.max(np.abs(db[..., j] - da[..., j])) /
+                                                     max(float(np.max(np.abs(da[..., j]))), 1e-300))
+                                               for j in range(da.shape[2])]}
+    oracle = None
+    if args.ess_model == "dual" and N == N_INPUTS and eps == EPS and not args.no_cpu_baseline:
+        # the oracle runs the same dynamics (FP64, same L, n_fp and step): its ESS per substep is
+        # the FP64 run's, so its ESS/s on this host's cores is that times its measured substeps/s
+        pc_value, pc_n, pc_l, pc_s = oracle_per_core(args.cpu_seconds)
+        ess_per_substep = a["min_ess"] / (C * args.iters * 10 * SUBSTEPS_PER_LEAPFROG)
+        oracle = {"substeps_per_s": pc_value, "cores": pc_n, "ess_per_s": ess_per_substep * pc_value,
+                  "sample": f"{pc_n} processes, one oracle chain each (single-threaded BLAS), {pc_l} leapfrogs "
+                            f"in {pc_s:.1f} s; ESS per substep taken from the FP64 GPU run"}
+    for r in runs.values():
+        r.pop("_draws")
+        r.pop("_accept")
     z_mean = np.abs(a["mean"] - b["mean"]) / np.sqrt(a["se_mean"] ** 2 + b["se_mean"] ** 2)
     z_var = np.abs(a["var"] - b["var"]) / np.sqrt(a["se_var"] ** 2 + b["se_var"] ** 2)
     matched = bool((z_mean <= 3).all() and (z_var <= 3).all())
@@ -854,6 +875,7 @@ def run_ess(args):
                                  "quantities": names},
                       "fp64": runs["fp64"], "mixed": runs["mixed"],
                       "speedup_ess_per_s": b["ess_per_s"] / a["ess_per_s"] if a["ess_per_s"] > 0 else None,
+                      "same_seed_paths": paths, "oracle_host": oracle,
                       "matched_error": {"z_mean": [round(float(v), 2) for v in z_mean],
                                         "z_var": [round(float(v), 2) for v in z_var], "within_3_se": matched}}),
           flush=True)
@@ -902,28 +924,97 @@ def run_solin(args):
     return 0
 
 
-def run_uneven(args):
-    """Problems of uneven size (N ~ U{32..256}, 1-3 kernels, 8 chains each) advanced together by
-    one CUDA graph per leapfrog, each with its autotuned Jacobi cluster size."""
+def run_fig1c(args):
+    """Fig. 1C's comparison: eigen-update work per Hessian, static (cold start from Psi = I at every
+    eigen-update) against dynamic (warm start from the previous Psi, Sec. 2.4), across the primal
+    model's dimension (the simulated data of Sec. 2.5, D = 1, 2, 4, 8, 16 Gaussian kernels: d = 34 ..
+    484), under both stopping rules (METRIC, the sampler's default, and RELATIVE, every eigenpair
+    resolved), with both rotation orders. Per configuration: args.chains chains, one Algorithm 1
+    iteration (L = 10, eps = 0.001, n_fp = 6, g = sqrt(1 + l^2)) after one untimed iteration; reported
+    per eigen-update: sweeps (cyclic-sweep equivalents), rounds, 16 x 16 sub-problems solved and
+    rotated, rotation-tile products, and the iteration's time."""
     import torch
     from paper_2511_06407_b300 import build, rmhmc
     build.build()
-    probs = wl.uneven_batch(args.problems, seed=0, n_min=32, n_max=256)
+    C = args.chains
+    rows = []
+    for D in (1, 2, 4, 8, 16):
+        prob = wl.solin_logistic(D, N=500, seed=0)
+        for rule in ("metric", "relative"):
+            for start in ("warm", "cold"):
+                for sched in ("cyclic", "dynamic"):
+                    integ = rmhmc.Integrator(eps=args.eps or SOLIN_EPS, n_fp=N_FP, n_leapfrog=N_LEAPFROG,
+                                             g_kind="sqrt", alpha=1.0 / SOLIN_KAPPA, precision=aux_precision(args),
+                                             jacobi_rule=rule, eigen_start=start)
+                    model = rmhmc.Model(prob, C)
+                    model.set_jacobi(0, sched)
+                    model.set_state(torch.zeros(C, model.d, dtype=torch.float64, device="cuda"), integ=integ)
+                    model.sample(1, 0, 5, integ=integ)
+                    model.profile(True)
+                    model.profile(False)  # resets the counters
+                    sw = torch.zeros(1, C, dtype=torch.int32, device="cuda")
+                    cs = torch.zeros(C, dtype=torch.int32, device="cuda")
+                    el, _ = _clock_and_time(lambda: model.sample(1, 0, 5, sweeps=sw, chain_status=cs, integ=integ), 0)
+                    cnt = model.jacobi_counters()
+                    u = max(cnt["updates"], 1)
+                    rows.append({"D": D, "d": model.d, "rule": rule, "start": start, "schedule": sched,
+                                 "sweeps_per_update": float(sw.cpu().numpy().sum()) / u,
+                                 "rounds_per_update": cnt["rounds"] / u, "solves_per_update": cnt["solves"] / u,
+                                 "rotated_per_update": cnt["rotated"] / u,
+                                 "tile_products_per_update": cnt["tile_products"] / u,
+                                 "updates": cnt["updates"], "iteration_ms": 1e3 * el,
+                                 "chain_status_nonzero": int((cs.cpu().numpy() != 0).sum())})
+                    print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+                    model.close()
+    print(json.dumps({"metric": "Jacobi work per eigen-update, static vs dynamic (Fig. 1C)", "unit": "per update",
+                      "n_gpus": 1, "dtype": dtype_of(aux_precision(args)), "data": "synthetic",
+                      "config": {"workload": f"primal model of Sec. 2.5 (N=500, D=1..16, d=34..484), {C} chains, "
+                                             f"one Algorithm 1 iteration (L={N_LEAPFROG}, eps={args.eps or SOLIN_EPS}, "
+                                             f"n_fp={N_FP}) after one untimed"},
+                      "rows": rows}), flush=True)
+    return 0
+
+
+def run_uneven(args):
+    """The uneven-batch configuration: args.problems problems (default 128, seeds 0..127),
+    N ~ U{32..512}, 1-3 additive kernels (SE, linear, overlap), 8 chains each (1024 chains,
+    d from 34 to 1542), advanced together by one captured CUDA graph per leapfrog over the
+    problems' streams. Each problem's Jacobi cluster size and rotation schedule come from the
+    autotuner, run once per size class (d in steps of 128, same number of kernels) and shared
+    within the class. A step is one generalized leapfrog of every chain (13 substeps)."""
+    import torch
+    from paper_2511_06407_b300 import build, rmhmc
+    build.build()
+    n_max = args.uneven_nmax
+    probs = wl.uneven_batch(args.problems, seed=0, n_min=32, n_max=n_max)
     C = 8
     prec = aux_precision(args)
-    integ = rmhmc.Integrator(eps=args.eps or 0.005, n_fp=N_FP, n_leapfrog=1, precision=prec)
-    models, clusters = [], []
+    integ = rmhmc.Integrator(eps=args.eps or EPS, n_fp=N_FP, n_leapfrog=1, precision=prec)
+    plan = sum(rmhmc.plan_bytes(p, C) for p in probs)
+    models, tuned, choice = [], {}, []
+    t_setup = time.perf_counter()
     for i, prob in enumerate(probs):
         s = torch.cuda.Stream()
         with torch.cuda.stream(s):
             m = rmhmc.Model(prob, C, stream=s)
             m.set_state(torch.zeros(C, m.d, dtype=torch.float64, device="cuda"), integ=integ)
-            clusters.append(m.autotune())
+            key = (m.d // 128, len(prob["kernels"]))
+            if key not in tuned:
+                tuned[key] = m.autotune(integ)
+            else:
+                m.set_jacobi(*tuned[key])
+            choice.append(tuned[key])
             m.sample(1, 0, 7 + i, integ=integ)
         models.append(m)
     torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
     batch = rmhmc.Batch(models)
-    batch.leapfrog(max(args.warmup - 1, 1), integ)
+    t0 = time.perf_counter()
+    batch.leapfrog(1, integ)  # captures the graph
+    torch.cuda.synchronize()
+    t_capture = time.perf_counter() - t0
+    if args.warmup > 1:
+        batch.leapfrog(args.warmup - 1, integ)
     el, clk = _clock_and_time(lambda: batch.leapfrog(args.steps, integ), 0)
     st = []
     for m in models:
@@ -935,45 +1026,75 @@ def run_uneven(args):
     bad = int(sum((x.cpu().numpy() != 0).sum() for x in st))
     chains = C * len(models)
     ds = [m.d for m in models]
+    scheds = {}
+    for c, sc in choice:
+        scheds[f"{sc}/{c}"] = scheds.get(f"{sc}/{c}", 0) + 1
     print(json.dumps({"metric": METRIC, "value": chains * SUBSTEPS_PER_LEAPFROG * args.steps / el, "unit": UNIT,
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-                      "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "dtype": dtype_of(prec),
-                      "data": "synthetic",
-                      "config": {"workload": f"uneven batch: {len(models)} problems, N~U{{32..256}}, 1-3 kernels, "
-                                             f"8 chains each, one CUDA graph per leapfrog, eps={integ.eps}",
-                                 "d_min": min(ds), "d_max": max(ds), "chains": chains,
-                                 "jacobi_clusters": clusters},
-                      "chain_status_nonzero": bad, "clocks": clk}), flush=True)
+                      "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+                      "dtype": dtype_of(prec), "data": "synthetic",
+                      "config": {"workload": f"uneven batch: {len(models)} problems (seeds 0..{len(models) - 1}), "
+                                             f"N~U{{32..{n_max}}}, 1-3 kernels (SE, linear, overlap), 8 chains "
+                                             f"each, one captured CUDA graph per leapfrog over the problems' "
+                                             f"streams, eps={integ.eps}, n_fp={N_FP}",
+                                 "step": "one generalized leapfrog of every chain (13 substeps)",
+                                 "d_min": min(ds), "d_max": max(ds), "d_mean": float(np.mean(ds)),
+                                 "chains": chains, "device_bytes_planned": plan,
+                                 "autotuned_schedule_cluster": scheds, "autotuned_classes": len(tuned)},
+                      "setup_s": t_setup, "graph_capture_s": t_capture,
+                      "chain_status_nonzero": bad, "valid": bad == 0, "clocks": clk}), flush=True)
     batch.close()
+    for m in models:
+        m.close()
     return 0
 
 
 def run_serve(args):
-    """A Poisson trace of sampling jobs served with continuous batching (scaled-down form of the
-    served-stream configuration: N ~ U{50..200}, 1-3 kernels, 8 inverse temperatures x 2 chains,
-    2 burn-in + 6 recorded iterations of 4 leapfrogs)."""
-    from paper_2511_06407_b300 import build, rmhmc
-    from paper_2511_06407_b300.bme import power_schedule
+    """The served-stream configuration: a Poisson trace of args.jobs arrivals at args.rate per second
+    (default 64 at 50/s) of sampling jobs with N ~ U{args.serve_nmin..args.serve_nmax} (default
+    50..800), 1-3 additive kernels, 16 inverse temperatures tau_s = (s/15)^5 x 4 chains (64 chains
+    per job), served with continuous batching by the library's scheduler under an HBM budget. The
+    configuration asks for 500 iterations per job; one B300 needs hours for that trace (a job is
+    ~1e15-1e17 FP operations), so the iterations (args.serve_burn + args.serve_iters of
+    args.serve_leapfrogs leapfrogs) are scaled down and printed. Each finished job's tempered chains
+    give a ln BME estimate by thermodynamic integration over its 16 temperatures (the BME appendix)."""
+    from paper_2511_06407_b300 import bme, build, rmhmc
     from paper_2511_06407_b300.serve import Job, Server, poisson_trace
     build.build()
-    probs = wl.uneven_batch(args.jobs, seed=100, n_min=50, n_max=200)
+    probs = wl.uneven_batch(args.jobs, seed=100, n_min=args.serve_nmin, n_max=args.serve_nmax)
     prec = aux_precision(args)
-    integ = rmhmc.Integrator(eps=args.eps or 0.005, n_fp=N_FP, n_leapfrog=4, precision=prec)
-    taus = np.repeat(power_schedule(8), 2)
+    integ = rmhmc.Integrator(eps=args.eps or EPS, n_fp=N_FP, n_leapfrog=args.serve_leapfrogs, precision=prec)
+    temps = bme.power_schedule(args.serve_temps)
+    taus = np.repeat(temps, args.serve_chains_per_temp)
+    C = len(taus)
     arrivals = poisson_trace(probs, args.rate, seed=1)
-    jobs = [Job(p, 16, n_iter=6, n_burn=2, seed=i, tau=taus, integ=integ, arrival=a, job_id=i)
-            for i, (p, a) in enumerate(zip(probs, arrivals))]
+    jobs = [Job(p, C, n_iter=args.serve_iters, n_burn=args.serve_burn, seed=i, tau=taus, integ=integ,
+                arrival=a, job_id=i) for i, (p, a) in enumerate(zip(probs, arrivals))]
     done, stats = Server(hbm_budget_bytes=int(args.hbm_gb * 2**30)).run(jobs)
     bad = int(sum((j.chain_status != 0).sum() for j in done))
+    lnz = []
+    for j in done:
+        ok = j.chain_status == 0
+        if ok.all() and np.all(np.isfinite(j.loglik)):
+            est, se, _ = bme.evidence(taus, j.loglik)
+            lnz.append((j.job_id, wl.dims(j.problem)[2], est, se))
+    ds = [wl.dims(p)[2] for p in probs]
     print(json.dumps({"metric": "served RMHMC substeps/s; job latency p50/p99", "value": stats["substeps_per_s"],
-                      "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": dtype_of(prec), "data": "synthetic",
+                      "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": dtype_of(prec),
+                      "data": "synthetic",
                       "p50_latency_s": stats["p50_latency_s"], "p99_latency_s": stats["p99_latency_s"],
                       "makespan_s": stats["makespan_s"], "jobs": stats["jobs"],
                       "max_concurrent_jobs": stats["max_concurrent_jobs"],
-                      "config": {"workload": f"Poisson trace, {args.jobs} jobs at {args.rate}/s, N~U{{50..200}}, "
-                                             "1-3 kernels, 8 temperatures x 2 chains, 2+6 iterations x 4 leapfrogs, "
+                      "config": {"workload": f"Poisson trace, {args.jobs} jobs at {args.rate}/s, "
+                                             f"N~U{{{args.serve_nmin}..{args.serve_nmax}}}, 1-3 kernels, "
+                                             f"{args.serve_temps} temperatures (s/{args.serve_temps - 1})^5 x "
+                                             f"{args.serve_chains_per_temp} chains, {args.serve_burn} burn-in + "
+                                             f"{args.serve_iters} recorded iterations x {args.serve_leapfrogs} "
+                                             f"leapfrogs (the configuration's 500 iterations scaled down), "
                                              f"HBM budget {args.hbm_gb} GiB, native scheduler (rmhmc_server_*)",
-                                 "eps": integ.eps},
+                                 "eps": integ.eps, "d_min": min(ds), "d_max": max(ds),
+                                 "d_mean": float(np.mean(ds)), "chains_per_job": C},
+                      "bme_jobs": len(lnz), "bme_examples": lnz[:4],
                       "chain_status_nonzero": bad}), flush=True)
     return 0
 
@@ -992,22 +1113,33 @@ def main():
     ap.add_argument("--chains", type=int, default=N_CHAINS,
                     help="chains per GPU (the workload is 64; smaller values are for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
-    ap.add_argument("--workload", default="gp400", choices=["gp400", "propensity", "uneven", "serve", "ess", "solin"],
+    ap.add_argument("--workload", default="gp400",
+                    choices=["gp400", "propensity", "uneven", "serve", "ess", "solin", "fig1c"],
                     help="gp400 is the benchmark; the others are extra measurements")
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"],
                     help="both (default): the mixed form is the headline, timed beside the plain FP64 path "
                          "on the same workload, with the trajectory error between them")
-    ap.add_argument("--problems", type=int, default=16)
+    ap.add_argument("--problems", type=int, default=128)
+    ap.add_argument("--uneven-nmax", type=int, default=512, help="largest N of the uneven batch")
     ap.add_argument("--ess-n", type=int, default=100, help="inputs N of the dual ESS workload")
     ap.add_argument("--ess-model", default="primal", choices=["primal", "dual"])
+    ap.add_argument("--ess-same-seed", action="store_true",
+                    help="both precisions use the same seed (their chains then follow each other)")
     ap.add_argument("--ess-d", type=int, default=4, help="Gaussian kernels D of the primal ESS workload")
     ap.add_argument("--solin-d", type=int, default=16, help="Gaussian kernels D of the solin workload (d = 30 D + 4)")
     ap.add_argument("--iters", type=int, default=200, help="kept iterations of the ESS workload")
     ap.add_argument("--burn", type=int, default=100, help="burn-in iterations of the ESS workload")
-    ap.add_argument("--jobs", type=int, default=24)
-    ap.add_argument("--rate", type=float, default=2.0)
-    ap.add_argument("--hbm-gb", type=float, default=64.0)
+    ap.add_argument("--jobs", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--hbm-gb", type=float, default=200.0)
+    ap.add_argument("--serve-nmin", type=int, default=50)
+    ap.add_argument("--serve-nmax", type=int, default=800)
+    ap.add_argument("--serve-temps", type=int, default=16)
+    ap.add_argument("--serve-chains-per-temp", type=int, default=4)
+    ap.add_argument("--serve-iters", type=int, default=2, help="recorded iterations per served job")
+    ap.add_argument("--serve-burn", type=int, default=0)
+    ap.add_argument("--serve-leapfrogs", type=int, default=2, help="leapfrogs per served iteration")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -1019,6 +1151,8 @@ def main():
         return run_ess(args)
     if args.workload == "solin":
         return run_solin(args)
+    if args.workload == "fig1c":
+        return run_fig1c(args)
     if args.workload == "serve":
         return run_serve(args)
     return run_b300(args)

@@ -73,6 +73,12 @@ typedef enum { RMHMC_FP64 = 0, RMHMC_MIXED = 1 } rmhmc_precision;
  *             left mixed (the metric is insensitive to that), which saves most sweeps
  *   RELATIVE: |m_jl| > max(zeta sqrt(|m_jj m_ll|), floor)   -- every eigenpair resolved */
 typedef enum { RMHMC_JACOBI_METRIC = 0, RMHMC_JACOBI_RELATIVE = 1 } rmhmc_jacobi_rule;
+/* Order of the Jacobi rotations (Sec. 2.4's Jacobi; the same stopping rule either way):
+ *   CYCLIC:  round-robin sweeps, every pair of 8-wide index blocks once per sweep;
+ *   DYNAMIC: each round pairs the blocks greedily by their largest remaining coupling (under the
+ *            stopping rule) and solves only the pairs above the tolerance, which after a warm
+ *            start is a few per round; sweeps are then reported as rounds / (blocks - 1). */
+typedef enum { RMHMC_JACOBI_CYCLIC = 0, RMHMC_JACOBI_DYNAMIC = 1 } rmhmc_jacobi_schedule;
 
 #define RMHMC_MAX_COLS 16
 #define RMHMC_MAX_KERNELS 3
@@ -279,6 +285,8 @@ typedef struct {
   double* logp_dev;                /* n_iter x n_chains, or NULL */
   int* accept_dev;                 /* n_iter x n_chains, or NULL */
   int* chain_status_dev;           /* n_chains: OR of the RMHMC_CHAIN_* bits of every iteration, or NULL */
+  double* loglik_dev;              /* n_iter x n_chains untempered ln P(y | F) per sample (the
+                                      thermodynamic-integration input of the BME appendix), or NULL */
 } rmhmc_job_desc;
 /* depth >= 1: iterations in flight per job. Errors: EINVAL. */
 rmhmc_status rmhmc_server_create(int device, size_t hbm_budget_bytes, int depth, rmhmc_server** out);
@@ -299,12 +307,19 @@ rmhmc_status rmhmc_server_stats(rmhmc_server* s, double* now_s, int* n_active, i
 /* Finish every submitted job, stop the scheduler and free the server. NULL is a no-op. */
 void rmhmc_server_destroy(rmhmc_server* s);
 
-/* Choose the model's Jacobi cluster size (CTAs per chain: 1, 2, 4 or 8) by timing up to three
- * cold-start sweeps of each candidate, with the Jacobi kernel of the model's precision, on the
- * model's own current Hessian (in scratch buffers; the state is untouched) and keeping the fastest
- * time per sweep. Without it a model uses the largest cluster that keeps two CTAs per SM. Synchronises the stream; needs a
- * state. *cluster_out (may be NULL) receives the choice. */
-rmhmc_status rmhmc_autotune(rmhmc_model* m, int* cluster_out);
+/* Autotuner of the eigen-update (Sec. 2.4's Jacobi; not part of the method's arithmetic): chooses
+ * the model's Jacobi cluster size (CTAs per chain: 1, 2, 4 or 8) and rotation schedule
+ * (rmhmc_jacobi_schedule) by timing one generalized leapfrog (integ's eps and n_fp; integ's geometry
+ * fields must match the state's) of each of the 8 combinations from the model's current state, and
+ * keeping the fastest. The state is then restored: q, p and the eigenbasis as before, the geometry
+ * re-evaluated at q (U, dU and the Hessian are recomputed exactly; the basis is already converged
+ * there). Without it a model uses the cyclic schedule and the largest cluster that keeps two CTAs
+ * per SM. Synchronises the stream; needs a state. *cluster_out and *sched_out (may be NULL) receive
+ * the choice. */
+rmhmc_status rmhmc_autotune(rmhmc_model* m, const rmhmc_integrator* integ, int* cluster_out,
+                            int* sched_out);
+/* Set the Jacobi cluster size (1, 2, 4, 8, or 0 for the default) and rotation schedule directly. */
+rmhmc_status rmhmc_set_jacobi(rmhmc_model* m, int cluster, int sched);
 
 /* Kernel-level profile (for measurement; not part of the method). While enabled, every kernel
  * launch of the model is bracketed by CUDA events on the model's stream and counted in one of
@@ -322,6 +337,13 @@ rmhmc_status rmhmc_profile(rmhmc_model* m, int enable);
 rmhmc_status rmhmc_profile_read(rmhmc_model* m, double* ms_host, double* flops_host,
                                 long long* launches_host);
 const char* rmhmc_profile_category(int i);
+/* Work counters of the eigen-update (Sec. 2.4's Jacobi), summed over the model's chains since the
+ * last rmhmc_profile(m, 1) (or model creation): counters_host[0..5] = 16 x 16 x 16 rotation-tile
+ * products of phase 2, rotation rounds applied inside 16 x 16 sub-problems, outer rounds (parallel
+ * steps of the block Jacobi), 16 x 16 sub-problems solved, of which rotated, eigen-updates.
+ * Counted whether or not profiling is on (the autotuner's trial runs excepted). Synchronises the
+ * stream. */
+rmhmc_status rmhmc_jacobi_counters(rmhmc_model* m, long long* counters_host);
 
 /* Measure this GPU's FP64 FMA throughput (a roofline denominator, not part of the method): runs a
  * dependent-chain DFMA kernel on every SM for about ms_target milliseconds on cuda_stream and writes
@@ -347,9 +369,14 @@ rmhmc_status rmhmc_df_peak(void* cuda_stream, int ms_target, double* tflops_host
  * (n ints each, RMHMC_CHAIN_NOTCONV on failure) may be NULL. With dp = d rounded up to a multiple
  * of 16, the batch must satisfy 2 n dp^2 + n dp + 512 n dp/16 + 64 n + O(n dp/16) <= 1,048,576
  * doubles (e.g. n = 64 at d = 64, n = 1 at d = 700); larger batches return RMHMC_ESCRATCH
- * without touching the GPU. No device memory is allocated or freed. The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress), so make that first call before any
- * stream capture. All calls share the one array and it keeps the previous call's contents (every
+ * without touching the GPU. No device memory is allocated or freed by the call. The array itself
+ * is committed on a device when the library's device code is loaded there, which under lazy module
+ * loading (CUDA_MODULE_LOADING=LAZY, the default) can be this entry point's first call: a caller
+ * budgeting memory inside an arena should make one warm-up call before taking its measure. The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress, once per
+ * device, safe from several host threads), so make that first call before any stream capture.
+ * cuda_stream must belong to the current device (else RMHMC_EINVAL): the workspace used is the
+ * current device's. All calls share the one array and it keeps the previous call's contents (every
  * value the solver reads is rewritten first); calls that overlap on the GPU, from two streams or
  * two threads, race on it and must be serialised by the caller. Enqueued on cuda_stream. */
 rmhmc_status rmhmc_eigh_noalloc(void* cuda_stream, int n, int d, const double* A_dev,
@@ -377,6 +404,16 @@ rmhmc_status rmhmc_gemm_tc(void* cuda_stream, int ta, int tb, int m, int n, int 
                            const double* A_dev, int lda, long long strideA, const double* B_dev,
                            int ldb, long long strideB, double beta, double* C_dev, int ldc,
                            long long strideC, int batch, int slices, int sym, int* status_dev);
+
+/* Test switch of the bounded device waits (failure detection; the paper has no counterpart).
+ * Every wait of the tensor-core GEMM (the pipeline's mbarriers) gives up after a time limit, marks
+ * the batch entry RMHMC_CHAIN_TIMEOUT in status_dev, writes NaN for that entry and lets the kernel
+ * free its tensor memory and return, so the context stays usable. To exercise that path without a
+ * fault: entry >= 0 makes every later GEMM launch issue no copy for batch entry `entry` (nothing is
+ * then in flight for it and its first wait runs out) and sets every wait's limit to wait_ms
+ * (1..2000 ms, else RMHMC_EINVAL); entry < 0 restores normal operation (no stall, the ~2 s limit).
+ * Off by default; host-side state of the process, read when a GEMM is enqueued. */
+rmhmc_status rmhmc_test_gemm_stall(int entry, double wait_ms);
 
 /* Dimension d of q, and number of chains. */
 int rmhmc_dim(const rmhmc_model* m);

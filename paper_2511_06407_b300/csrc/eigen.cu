@@ -28,6 +28,9 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "df.cuh"
 #include "internal.cuh"
 
@@ -270,279 +273,11 @@ __device__ __forceinline__ void tile_transform(const double* X, const double* Vp
   __syncwarp();
 }
 
-__device__ __forceinline__ void load_v(double* dst, const double* src) {
-  const int lane = threadIdx.x & 31;
-  for (int e = lane; e < SB * SB; e += 32) dst[(e / SB) * SBP + e % SB] = __ldcg(src + e);
-}
+// ------------------------------------------------------------------ element types
+// The FP64 path keeps M and Psi^T in double; the mixed path holds them as double-float pairs
+// (df.cuh) in scratch for the whole kernel, with the 16 x 16 inner solves (phase 1), the stopping
+// test and the conversions in FP64 and the phase-2 tile products in double-float arithmetic.
 
-__global__ void __launch_bounds__(NW * 32) k_jacobi(double* __restrict__ Mb, double* __restrict__ Pb,
-                                                   double* __restrict__ lamb, int dp, int d, int rule,
-                                                   double tol,
-                                                   int max_sweeps, int* __restrict__ status,
-                                                   int* __restrict__ sweeps_out,
-                                                   int* __restrict__ sweeps_acc,
-                                                   double* __restrict__ Vb, double* __restrict__ Db,
-                                                   double* __restrict__ slotsb,
-                                                   int* __restrict__ flagsb,
-                                                   unsigned long long* __restrict__ tiles) {
-  cg::cluster_group cluster = cg::this_cluster();
-  const int C = (int)cluster.num_blocks();
-  const int rank = (int)cluster.block_rank();
-  const int chain = blockIdx.x / C;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nb = dp / BL, np = nb / 2;
-  if (np > kMaxPairs) {  // larger than any model or batch the library accepts
-    if (rank == 0 && tid == 0) {
-      atomicOr(&status[chain], RMHMC_CHAIN_NOTCONV);
-      sweeps_out[chain] = 0;
-    }
-    return;  // uniform for the whole cluster
-  }
-  if (status[chain] != 0) {
-    if (rank == 0 && tid == 0) sweeps_out[chain] = 0;
-    return;  // uniform for the whole cluster
-  }
-  double* M = Mb + (long long)chain * dp * dp;
-  double* P = Pb + (long long)chain * dp * dp;
-  double* V = Vb + (long long)chain * np * SB * SB;
-  double* D = Db + (long long)chain * np * SB * SB;
-  double* slots = slotsb + (long long)chain * 64;
-  int* flags = flagsb + (long long)chain * np;
-  extern __shared__ double smem[];
-  double* ws = smem + warp * WARP_SMEM;
-  double* X = ws;
-  double* Tt = ws + SB * SBP;
-  double* Va = ws + 2 * SB * SBP;
-  double* Vq = ws + 3 * SB * SBP;
-  __shared__ double red[2][NW];
-  __shared__ double cs[NW][3 * SB / 2];  // (c, s, t) of the 8 rotations of a round, per warp
-  __shared__ unsigned char sflag[kMaxPairs];  // pair rotated in this round
-  __shared__ short sact[kMaxPairs];           // the rotated pairs, in order
-  __shared__ int scum[kMaxPairs];             // cumulative active M tiles per column
-  __shared__ int snact;
-
-  const int gw = rank * NW + warp, nwt = C * NW;
-  const int nct = dp / SB;
-  int sweeps = 0;
-  bool converged = false;
-  double tot0 = 0.0;        // ||M||_F^2 from the first pass
-  unsigned int ntile = 0;   // 16 x 16 x 16 tile products this warp executed (phase 2)
-  unsigned int nround = 0;  // rounds of 8 rotations this warp applied to a 16 x 16 block (phase 1)
-  for (;;) {
-    // ---- convergence test. Pass 1: ||M||_F^2 and min_i<d |m_ii|. Pass 2: the worst pair ratio
-    //      (pair_ratio) under the chosen rule, with floor = 4 u ||M||_F (rounding level).
-    // ||M||_F is invariant under the rotations: summed over M in the first pass only; later
-    // passes read the diagonal (a non-finite diagonal entry still poisons tot)
-    double tot = 0.0, dmin = 1e308;
-    if (sweeps == 0) {
-      for (long long e = (long long)rank * blockDim.x + tid; e < (long long)dp * dp;
-           e += (long long)C * blockDim.x) {
-        const double v = __ldcg(M + e);
-        tot = fma(v, v, tot);
-        const int i = (int)(e / dp);
-        if (i < d && (long long)i * dp + i == e) dmin = fmin(dmin, fabs(v));
-      }
-    } else {
-      for (int i = rank * blockDim.x + tid; i < d; i += C * blockDim.x) {
-        const double v = __ldcg(M + (long long)i * dp + i);
-        if (!isfinite(v)) tot = v;
-        dmin = fmin(dmin, fabs(v));
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
-      dmin = fmin(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
-    }
-    if (lane == 0) { red[0][warp] = tot; red[1][warp] = dmin; }
-    __syncthreads();
-    if (tid == 0) {
-      double a = 0.0, b = 1e308;
-      for (int w = 0; w < NW; ++w) { a += red[0][w]; b = fmin(b, red[1][w]); }
-      __stcg(slots + (sweeps & 1) * 32 + 2 * rank, a);
-      __stcg(slots + (sweeps & 1) * 32 + 2 * rank + 1, b);
-    }
-    cluster.sync();
-    tot = 0.0;
-    dmin = 1e308;
-    for (int r = 0; r < C; ++r) {
-      tot += __ldcg(slots + (sweeps & 1) * 32 + 2 * r);
-      dmin = fmin(dmin, __ldcg(slots + (sweeps & 1) * 32 + 2 * r + 1));
-    }
-    if (sweeps == 0) tot0 = tot;
-    else if (isfinite(tot)) tot = tot0;
-    const double dmin2 = fmax(dmin * dmin, 1e-300);
-    const double floor2 = fmax(16.0 * 1.2325951644078310e-32 * tot, 1e-300);  // (4u)^2 ||M||_F^2
-    double crit = 0.0, bad = isfinite(tot) ? 0.0 : 1.0;
-    for (long long e = (long long)rank * blockDim.x + tid; e < (long long)dp * dp;
-         e += (long long)C * blockDim.x) {
-      const int j = (int)(e / dp), l = (int)(e % dp);
-      if (j >= l) continue;  // M is kept symmetric: the upper triangle decides
-      const double v = __ldcg(M + e);
-      if (v == 0.0) continue;
-      if (!isfinite(v)) bad = 1.0;
-      const double djj = __ldcg(M + (long long)j * dp + j), dll = __ldcg(M + (long long)l * dp + l);
-      if (pair_unconverged(v, djj, dll, tol * tol, stop_floor2(djj, dll, floor2, rule), rule, dmin2))
-        crit = 1.0;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      crit = fmax(crit, __shfl_xor_sync(0xffffffffu, crit, o));
-      bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, o));
-    }
-    __syncthreads();
-    if (lane == 0) { red[0][warp] = crit; red[1][warp] = bad; }
-    __syncthreads();
-    if (tid == 0) {
-      double a = 0.0, b = 0.0;
-      for (int w = 0; w < NW; ++w) { a = fmax(a, red[0][w]); b = fmax(b, red[1][w]); }
-      __stcg(slots + (sweeps & 1) * 32 + 16 + 2 * rank, a);
-      __stcg(slots + (sweeps & 1) * 32 + 16 + 2 * rank + 1, b);
-    }
-    cluster.sync();
-    crit = 0.0;
-    bad = 0.0;
-    for (int r = 0; r < C; ++r) {
-      crit = fmax(crit, __ldcg(slots + (sweeps & 1) * 32 + 16 + 2 * r));
-      bad = fmax(bad, __ldcg(slots + (sweeps & 1) * 32 + 16 + 2 * r + 1));
-    }
-    if (bad != 0.0) break;
-    if (crit == 0.0) { converged = true; break; }
-    if (sweeps >= max_sweeps) break;
-    const double itol2 = 1e-4 * tol * tol;  // inner problems are solved 100x tighter
-
-    for (int r = 0; r < nb - 1; ++r) {
-      // ---- phase 1: exact 16 x 16 solves, one warp per block pair
-      for (int p = gw; p < np; p += nwt) {
-        int I, J;
-        circle_pair(r, p, nb, I, J);
-        for (int e = lane; e < SB * SB; e += 32) {
-          const int a = e / SB, b = e % SB;
-          X[a * SBP + b] = __ldcg(M + (long long)gidx(I, J, a) * dp + gidx(I, J, b));
-        }
-        __syncwarp();
-        const bool rot = inner_solve(X, Va, cs[warp], itol2, floor2, rule, dmin2, nround);
-        if (rot) {
-          for (int e = lane; e < SB * SB; e += 32) {
-            const int a = e / SB, b = e % SB;
-            __stcg(V + (long long)p * SB * SB + e, Va[a * SBP + b]);
-            __stcg(D + (long long)p * SB * SB + e, X[a * SBP + b]);
-          }
-        }
-        if (lane == 0) __stcg(flags + p, rot ? 1 : 0);
-        __syncwarp();
-      }
-      cluster.sync();
-      // ---- the pairs rotated in phase 1, in order (every CTA of the cluster builds the same list)
-      // and, per column Q of M's tiles, the cumulative count of active tiles (P <= Q with P or Q
-      // rotated): column Q holds Q + 1 of them if Q rotated, else as many as rotated pairs P < Q
-      if (warp == 0) {
-        int base = 0, run = 0;
-        for (int p0 = 0; p0 < np; p0 += 32) {
-          const int p = p0 + lane;
-          const bool f = p < np && __ldcg(flags + p) != 0;
-          const unsigned bal = __ballot_sync(0xffffffffu, f);
-          const int before = base + __popc(bal & ((1u << lane) - 1u));  // rotated pairs < p
-          if (p < np) sflag[p] = f ? 1 : 0;
-          if (f) sact[before] = (short)p;
-          int c = p < np ? (f ? p + 1 : before) : 0;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {  // inclusive warp scan
-            const int v = __shfl_up_sync(0xffffffffu, c, o);
-            if (lane >= o) c += v;
-          }
-          if (p < np) scum[p] = run + c;
-          run += __shfl_sync(0xffffffffu, c, 31);
-          base += __popc(bal);
-        }
-        if (lane == 0) snact = base;
-      }
-      __syncthreads();
-      // ---- phase 2: apply all rotations to M (P <= Q tiles) and to the rows of Psi^T
-      //      over the active jobs only, dealt round-robin to the cluster's warps: the M tiles
-      //      (P <= Q) of which P or Q rotated, then the Psi^T row tiles of the rotated pairs
-      const int k = scum[np - 1];  // active M tiles
-      for (int i = gw; i < k; i += nwt) {
-        {
-          int lo = 0, hi = np - 1;  // the column: smallest Q with scum[Q] > i
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (scum[mid] > i) hi = mid;
-            else lo = mid + 1;
-          }
-          const int Q = lo, o = i - (Q > 0 ? scum[Q - 1] : 0);
-          const int fQ = sflag[Q];
-          const int Pp = fQ ? o : sact[o];
-          const int fP = sflag[Pp];
-          int I1, J1, I2, J2;
-          circle_pair(r, Pp, nb, I1, J1);
-          circle_pair(r, Q, nb, I2, J2);
-          if (Pp == Q) {
-            for (int e = lane; e < SB * SB; e += 32) {
-              const int a = e / SB, b = e % SB;
-              __stcg(M + (long long)gidx(I1, J1, a) * dp + gidx(I1, J1, b), __ldcg(D + (long long)Pp * SB * SB + e));
-            }
-          } else {
-            for (int e = lane; e < SB * SB; e += 32) {
-              const int a = e / SB, b = e % SB;
-              X[a * SBP + b] = __ldcg(M + (long long)gidx(I1, J1, a) * dp + gidx(I2, J2, b));
-            }
-            if (fP) load_v(Va, V + (long long)Pp * SB * SB);
-            if (fQ) load_v(Vq, V + (long long)Q * SB * SB);
-            __syncwarp();
-            tile_transform(X, fP ? Va : nullptr, fQ ? Vq : nullptr, Tt, X);
-            ntile += (fP ? 1u : 0u) + (fQ ? 1u : 0u);
-            const int t = lane >> 1, u0 = (lane & 1) * 8;
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              __stcg(M + (long long)gidx(I1, J1, t) * dp + gidx(I2, J2, u0 + j), X[t * SBP + u0 + j]);
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              __stcg(M + (long long)gidx(I2, J2, t) * dp + gidx(I1, J1, u0 + j), X[(u0 + j) * SBP + t]);
-          }
-          __syncwarp();
-        }
-      }
-      const int nPsi = snact * nct;
-      for (int j = ((gw - k) % nwt + nwt) % nwt; j < nPsi; j += nwt) {
-        const int Pp = sact[j / nct], ct = j % nct;
-        int I1, J1;
-        circle_pair(r, Pp, nb, I1, J1);
-        for (int e = lane; e < SB * SB; e += 32) {
-          const int a = e / SB, b = e % SB;
-          X[a * SBP + b] = __ldcg(P + (long long)gidx(I1, J1, a) * dp + ct * SB + b);
-        }
-        load_v(Va, V + (long long)Pp * SB * SB);
-        __syncwarp();
-        tile_transform(X, Va, nullptr, Tt, X);
-        ++ntile;
-        const int t = lane >> 1, u0 = (lane & 1) * 8;
-#pragma unroll
-        for (int j2 = 0; j2 < 8; ++j2)
-          __stcg(P + (long long)gidx(I1, J1, t) * dp + ct * SB + u0 + j2, X[t * SBP + u0 + j2]);
-        __syncwarp();
-      }
-      cluster.sync();
-    }
-    ++sweeps;
-  }
-  for (int i = rank * blockDim.x + tid; i < dp; i += C * blockDim.x)
-    lamb[(long long)chain * dp + i] = __ldcg(M + (long long)i * dp + i);
-  if (tiles && lane == 0) {
-    if (ntile) atomicAdd(tiles + 2 * chain, (unsigned long long)ntile);
-    if (nround) atomicAdd(tiles + 2 * chain + 1, (unsigned long long)nround);
-  }
-  if (rank == 0 && tid == 0) {
-    sweeps_out[chain] = sweeps;
-    if (sweeps_acc) sweeps_acc[chain] += sweeps;
-    if (!converged) atomicOr(&status[chain], RMHMC_CHAIN_NOTCONV);
-  }
-}
-
-// ------------------------------------------------------------------ double-float variant
-// Mixed precision: the rotations of phase 2 are applied in double-float arithmetic (df.cuh). M and
-// Psi^T are held as FP32 pairs in scratch for the whole kernel; the 16 x 16 inner solves (phase 1),
-// the stopping test and the conversions stay in FP64.
 // Y = Vp^T X Vq on 16 x 16 double-float tiles in shared memory (null Vp / Vq = identity).
 __device__ __forceinline__ void tile_transform_df(const float2* X, const float2* Vp, const float2* Vq,
                                                   float2* T, float2* Y) {
@@ -587,33 +322,120 @@ __device__ __forceinline__ void tile_transform_df(const float2* X, const float2*
   __syncwarp();
 }
 
-__device__ __forceinline__ float2 ldcg2(const float2* p) { return __ldcg(p); }
+struct ElemF64 {
+  using T = double;
+  static constexpr bool kPairs = false;
+  static constexpr double kFloorUnit2 = 16.0 * 1.2325951644078310e-32;  // (4 u)^2, u = 2^-53
+  static __device__ __forceinline__ T ld(const T* p) { return __ldcg(p); }
+  static __device__ __forceinline__ void st(T* p, T v) { __stcg(p, v); }
+  static __device__ __forceinline__ double join(T v) { return v; }
+  static __device__ __forceinline__ T split(double v) { return v; }
+  static __device__ __forceinline__ void transform(const T* X, const T* Vp, const T* Vq, T* Tt, T* Y) {
+    tile_transform(X, Vp, Vq, Tt, Y);
+  }
+};
 
-__device__ __forceinline__ void load_v_df(float2* dst, const float2* src) {
+struct ElemDF {
+  using T = float2;
+  static constexpr bool kPairs = true;
+  static constexpr double kFloorUnit2 = 16.0 * 1.2621774483536189e-29;  // (4 * 2^-48)^2
+  static __device__ __forceinline__ T ld(const T* p) { return __ldcg(p); }
+  static __device__ __forceinline__ void st(T* p, T v) { __stcg(p, v); }
+  static __device__ __forceinline__ double join(T v) { return df_join(v); }
+  static __device__ __forceinline__ T split(double v) { return df_split(v); }
+  static __device__ __forceinline__ void transform(const T* X, const T* Vp, const T* Vq, T* Tt, T* Y) {
+    tile_transform_df(X, Vp, Vq, Tt, Y);
+  }
+};
+
+template <class E>
+__device__ __forceinline__ void load_tile_v(typename E::T* dst, const typename E::T* src) {
   const int lane = threadIdx.x & 31;
-  for (int e = lane; e < SB * SB; e += 32) dst[(e / SB) * SBP + e % SB] = ldcg2(src + e);
+  for (int e = lane; e < SB * SB; e += 32) dst[(e / SB) * SBP + e % SB] = E::ld(src + e);
 }
 
-// Same algorithm and stopping rule as k_jacobi (the rounding floor uses the double-float unit
-// 2^-48); M and Psi^T (double, dp x dp per chain) are converted into the pair buffers Mw, Pw
-// (float2, same layout) at entry and back at exit.
-__global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, double* __restrict__ Pb,
-                                                      double* __restrict__ lamb, int dp, int d, int rule,
-                                                      double tol, int max_sweeps,
-                                                      int* __restrict__ status,
-                                                      int* __restrict__ sweeps_out,
-                                                      int* __restrict__ sweeps_acc,
-                                                      double* __restrict__ Vb, double* __restrict__ Db,
-                                                      double* __restrict__ slotsb,
-                                                      int* __restrict__ flagsb,
-                                                      unsigned long long* __restrict__ tiles,
-                                                      float2* __restrict__ Mwb, float2* __restrict__ Pwb) {
+// log2 |x| for a finite double, from its exponent field and the FP32 log2 of its significand
+// (integer and FP32 operations only; B300's FP64 pipe is 1/64 of its FP32 rate). Zero gives -2000,
+// a subnormal the log2 of 2^-1023.
+__device__ __forceinline__ float log2_abs(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  if (b == 0) return -2000.f;
+  const int e = (int)(b >> 52) - 1023;
+  const float m = __int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff));  // significand in [1, 2)
+  return (float)e + __log2f(m);
+}
+
+// Constants of the coupling criterion, fixed for one eigen-update: log2 of zeta^2, of the floor
+// 4u ||M||_F squared and of min_i |m_ii| squared.
+struct CritConst {
+  float ltol2, lfloor2, ldmin2;
+  int rule;
+};
+
+// The coupling criterion of the stopping rule in the log domain:
+// log2(m_jl^2 / max(zeta^2 den(j, l), floor)), positive where pair_unconverged holds (to FP32
+// rounding of the logarithms, ~1e-6 relative in the ratio). den = (m_jj m_ll)^2 / d_min^2 (METRIC)
+// or |m_jj m_ll| (RELATIVE); the floor is the rule's (stop_floor2). A non-finite entry gives +inf
+// (the caller treats it as a failed update).
+__device__ __forceinline__ float coupling_log_ratio(double v, double djj, double dll, const CritConst& k) {
+  if (!isfinite(v)) return INFINITY;
+  const float lv = log2_abs(v), lj = log2_abs(djj), ll = log2_abs(dll);
+  float lthr, lfl;
+  if (k.rule == RMHMC_JACOBI_METRIC) {
+    lthr = k.ltol2 + 2.f * (lj + ll) - k.ldmin2;
+    lfl = k.lfloor2;
+  } else {
+    lthr = k.ltol2 + lj + ll;
+    // local_floor2: min(floor2, max(1e-26 max(x^2, y^2), 1e-300))
+    lfl = fminf(k.lfloor2, fmaxf(-86.37013f + 2.f * fmaxf(lj, ll), -996.578f));
+  }
+  return 2.f * lv - fmaxf(lthr, lfl);
+}
+
+// warp-wide maximum (every lane receives it)
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+constexpr int kTop = 4;              // partners kept per block for the dynamic matching
+constexpr int kMaxBlocks = 2 * kMaxPairs;
+
+// Warm-started block Jacobi, both schedules (sched: RMHMC_JACOBI_CYCLIC or RMHMC_JACOBI_DYNAMIC).
+//
+// CYCLIC: each sweep is nb - 1 rounds of the circle pairing (every block pair once per sweep);
+// the stopping test runs before each sweep.
+// DYNAMIC: the kernel keeps, per pair of 8-wide blocks (I, J), the largest coupling ratio of their
+// 8 x 8 block of M (crit, nb x nb floats per chain, symmetric; the diagonal entry is the block's own
+// internal coupling). It is computed for all blocks by the stopping test and updated in phase 2
+// for every tile that a round rewrites, from the tile's new values and the new diagonal. Each round
+// then pairs the blocks greedily, largest coupling first (every CTA of the cluster computes the same
+// matching from the same crit): each block's kTop most coupled partners are found, the blocks whose
+// largest coupling or internal coupling is above 1 are taken in decreasing order and matched with
+// their most coupled free partner; the remaining blocks are paired in index order. Only pairs with a
+// coupling above 1 are solved in phase 1 (typically a few per round instead of nb / 2), and phase 2
+// applies only their rotations. Rounds continue while some pair is above 1; the stopping test then
+// re-checks every block with the current diagonal (it decides convergence exactly as in the cyclic
+// schedule). sweeps_out reports rounds / (nb - 1) rounded up (cyclic-sweep equivalents), and
+// max_sweeps bounds the rounds at max_sweeps (nb - 1).
+template <class E>
+__global__ void __launch_bounds__(NW * 32)
+    k_jacobi_t(double* __restrict__ Mb, double* __restrict__ Pb, double* __restrict__ lamb, int dp, int d,
+               int rule, double tol, int max_sweeps, int* __restrict__ status, int* __restrict__ sweeps_out,
+               int* __restrict__ sweeps_acc, double* __restrict__ Vb, double* __restrict__ Db,
+               double* __restrict__ slotsb, int* __restrict__ flagsb,
+               unsigned long long* __restrict__ tiles, typename E::T* __restrict__ Mwb,
+               typename E::T* __restrict__ Pwb, float* __restrict__ critb, int sched) {
+  using T = typename E::T;
+  static_assert(sizeof(T) == sizeof(double), "tiles of V and D are stored in double-sized slots");
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   const int chain = blockIdx.x / C;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nb = dp / BL, np = nb / 2;
+  const bool dyn = sched == RMHMC_JACOBI_DYNAMIC && critb != nullptr;
   if (np > kMaxPairs) {  // larger than any model or batch the library accepts
     if (rank == 0 && tid == 0) {
       atomicOr(&status[chain], RMHMC_CHAIN_NOTCONV);
@@ -628,52 +450,75 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
   const long long DD = (long long)dp * dp;
   double* M = Mb + (long long)chain * DD;
   double* P = Pb + (long long)chain * DD;
-  float2* Mw = Mwb + (long long)chain * DD;
-  float2* Pw = Pwb + (long long)chain * DD;
-  float2* V = (float2*)(Vb + (long long)chain * np * SB * SB);
-  float2* D = (float2*)(Db + (long long)chain * np * SB * SB);
+  T* Mw = E::kPairs ? Mwb + (long long)chain * DD : reinterpret_cast<T*>(M);
+  T* Pw = E::kPairs ? Pwb + (long long)chain * DD : reinterpret_cast<T*>(P);
+  T* V = reinterpret_cast<T*>(Vb + (long long)chain * np * SB * SB);
+  T* D = reinterpret_cast<T*>(Db + (long long)chain * np * SB * SB);
   double* slots = slotsb + (long long)chain * 64;
   int* flags = flagsb + (long long)chain * np;
+  float* crit = dyn ? critb + (long long)chain * nb * nb : nullptr;
   extern __shared__ double smem[];
   double* ws = smem + warp * WARP_SMEM;
   double* Xd = ws;                    // phase 1 (FP64)
   double* Vd = ws + 2 * SB * SBP;
-  float2* X = (float2*)ws;            // phase 2 (pairs), same bytes
-  float2* Tt = (float2*)(ws + SB * SBP);
-  float2* Va = (float2*)(ws + 2 * SB * SBP);
-  float2* Vq = (float2*)(ws + 3 * SB * SBP);
+  T* X = reinterpret_cast<T*>(ws);    // phase 2, same bytes
+  T* Tt = reinterpret_cast<T*>(ws + SB * SBP);
+  T* Va = reinterpret_cast<T*>(ws + 2 * SB * SBP);
+  T* Vq = reinterpret_cast<T*>(ws + 3 * SB * SBP);
   __shared__ double red[2][NW];
   __shared__ double cs[NW][3 * SB / 2];  // (c, s, t) of the 8 rotations of a round, per warp
   __shared__ unsigned char sflag[kMaxPairs];  // pair rotated in this round
   __shared__ short sact[kMaxPairs];           // the rotated pairs, in order
   __shared__ int scum[kMaxPairs];             // cumulative active M tiles per column
   __shared__ int snact;
+  __shared__ short2 spair[kMaxPairs];         // the two blocks of pair p in this round
+  __shared__ unsigned char sneed[kMaxPairs];  // pair p is solved in phase 1 of this round
+  __shared__ short ssolve[kMaxPairs];         // the pairs solved, in order
+  __shared__ int snsolve, snmatch, sbad;
+  __shared__ double sdg[NW][2 * SB];          // phase 2: new diagonal of a tile's rows and columns
+  // dynamic matching
+  __shared__ float stopv[kMaxBlocks][kTop];
+  __shared__ short stopj[kMaxBlocks][kTop];
+  __shared__ float sown[kMaxBlocks];
+  __shared__ float skey[kMaxBlocks];
+  __shared__ short sorder[kMaxBlocks];
+  __shared__ unsigned char sused[kMaxBlocks];
 
-  for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
-    __stcg(Mw + e, df_split(__ldcg(M + e)));
-    __stcg(Pw + e, df_split(__ldcg(P + e)));
+  if constexpr (E::kPairs) {
+    for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
+      E::st(Mw + e, E::split(__ldcg(M + e)));
+      E::st(Pw + e, E::split(__ldcg(P + e)));
+    }
+    cluster.sync();
   }
-  cluster.sync();
 
   const int gw = rank * NW + warp, nwt = C * NW;
   const int nct = dp / SB;
-  int sweeps = 0;
-  bool converged = false;
+  const int max_rounds = max_sweeps * (nb - 1);
+  int sweeps = 0;           // cyclic: sweeps run
+  int rounds = 0;           // dynamic: rounds run
+  bool converged = false, failed = false;
   double tot0 = 0.0;        // ||M||_F^2 from the first pass
   unsigned int ntile = 0;   // 16 x 16 x 16 tile products this warp executed (phase 2)
   unsigned int nround = 0;  // rounds of 8 rotations this warp applied to a 16 x 16 block (phase 1)
-  for (;;) {
+  unsigned int nsolved = 0, nrotated = 0;  // 16 x 16 sub-problems this warp solved / that rotated
+  for (int pass = 0;; ++pass) {
+    // ---- convergence test. Pass 1: ||M||_F^2 and min_i<d |m_ii|. Pass 2: the coupling criterion
+    //      under the chosen rule, with floor = 4 u ||M||_F (rounding level); the dynamic schedule
+    //      also records it per 8 x 8 block. ||M||_F is invariant under the rotations: summed over
+    //      M in the first pass only; later passes read the diagonal (a non-finite diagonal entry
+    //      still poisons tot)
     double tot = 0.0, dmin = 1e308;
-    if (sweeps == 0) {
+    if (pass == 0) {
       for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
-        const double v = df_join(ldcg2(Mw + e));
+        const double v = E::join(E::ld(Mw + e));
         tot = fma(v, v, tot);
         const int i = (int)(e / dp);
         if (i < d && (long long)i * dp + i == e) dmin = fmin(dmin, fabs(v));
       }
-    } else {  // ||M||_F is invariant under the rotations (see k_jacobi)
+    } else {
       for (int i = rank * blockDim.x + tid; i < d; i += C * blockDim.x) {
-        const double v = df_join(ldcg2(Mw + (long long)i * dp + i));
+        const double v = E::join(E::ld(Mw + (long long)i * dp + i));
         if (!isfinite(v)) tot = v;
         dmin = fmin(dmin, fabs(v));
       }
@@ -688,78 +533,240 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
     if (tid == 0) {
       double a = 0.0, b = 1e308;
       for (int w = 0; w < NW; ++w) { a += red[0][w]; b = fmin(b, red[1][w]); }
-      __stcg(slots + (sweeps & 1) * 32 + 2 * rank, a);
-      __stcg(slots + (sweeps & 1) * 32 + 2 * rank + 1, b);
+      __stcg(slots + (pass & 1) * 32 + 2 * rank, a);
+      __stcg(slots + (pass & 1) * 32 + 2 * rank + 1, b);
     }
     cluster.sync();
     tot = 0.0;
     dmin = 1e308;
     for (int r = 0; r < C; ++r) {
-      tot += __ldcg(slots + (sweeps & 1) * 32 + 2 * r);
-      dmin = fmin(dmin, __ldcg(slots + (sweeps & 1) * 32 + 2 * r + 1));
+      tot += __ldcg(slots + (pass & 1) * 32 + 2 * r);
+      dmin = fmin(dmin, __ldcg(slots + (pass & 1) * 32 + 2 * r + 1));
     }
-    if (sweeps == 0) tot0 = tot;
+    if (pass == 0) tot0 = tot;
     else if (isfinite(tot)) tot = tot0;
     const double dmin2 = fmax(dmin * dmin, 1e-300);
-    const double floor2 = fmax(16.0 * 1.2621774483536189e-29 * tot, 1e-300);  // (4 * 2^-48)^2 ||M||^2
-    double crit = 0.0, bad = isfinite(tot) ? 0.0 : 1.0;
-    for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
-      const int j = (int)(e / dp), l = (int)(e % dp);
-      if (j >= l) continue;  // M is kept symmetric: the upper triangle decides
-      const double v = df_join(ldcg2(Mw + e));
-      if (v == 0.0) continue;
-      if (!isfinite(v)) bad = 1.0;
-      const double djj = df_join(ldcg2(Mw + (long long)j * dp + j)), dll = df_join(ldcg2(Mw + (long long)l * dp + l));
-      if (pair_unconverged(v, djj, dll, tol * tol, stop_floor2(djj, dll, floor2, rule), rule, dmin2))
-        crit = 1.0;
+    const double floor2 = fmax(E::kFloorUnit2 * tot, 1e-300);
+    const double tol2 = tol * tol;
+    const CritConst ck{log2_abs(tol2), log2_abs(floor2), log2_abs(dmin2), rule};
+    double critv = 0.0, bad = isfinite(tot) ? 0.0 : 1.0;
+    if (dyn) {
+      // one warp per 8 x 8 block (I <= J; the diagonal block's upper triangle)
+      for (int bi = gw; bi < nb * nb; bi += nwt) {
+        const int I = bi / nb, J = bi % nb;
+        if (I > J) continue;
+        float rmax = -INFINITY;
+        bool nf = false;
+        for (int e = lane; e < BL * BL; e += 32) {
+          const int a = e / BL, b = e % BL;
+          if (I == J && a >= b) continue;
+          const int j = I * BL + a, l = J * BL + b;
+          const double v = E::join(E::ld(Mw + (long long)j * dp + l));
+          if (v == 0.0) continue;
+          if (!isfinite(v)) { nf = true; continue; }
+          const double djj = E::join(E::ld(Mw + (long long)j * dp + j));
+          const double dll = E::join(E::ld(Mw + (long long)l * dp + l));
+          rmax = fmaxf(rmax, coupling_log_ratio(v, djj, dll, ck));
+        }
+        rmax = warp_max(rmax);
+        nf = __any_sync(0xffffffffu, nf);
+        if (lane == 0) {
+          __stcg(crit + (long long)I * nb + J, rmax);
+          __stcg(crit + (long long)J * nb + I, rmax);
+        }
+        if (rmax > 0.f) critv = 1.0;
+        if (nf || rmax == INFINITY) bad = 1.0;
+      }
+    } else {
+      for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
+        const int j = (int)(e / dp), l = (int)(e % dp);
+        if (j >= l) continue;  // M is kept symmetric: the upper triangle decides
+        const double v = E::join(E::ld(Mw + e));
+        if (v == 0.0) continue;
+        if (!isfinite(v)) bad = 1.0;
+        const double djj = E::join(E::ld(Mw + (long long)j * dp + j));
+        const double dll = E::join(E::ld(Mw + (long long)l * dp + l));
+        if (pair_unconverged(v, djj, dll, tol2, stop_floor2(djj, dll, floor2, rule), rule, dmin2))
+          critv = 1.0;
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      crit = fmax(crit, __shfl_xor_sync(0xffffffffu, crit, o));
+      critv = fmax(critv, __shfl_xor_sync(0xffffffffu, critv, o));
       bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, o));
     }
     __syncthreads();
-    if (lane == 0) { red[0][warp] = crit; red[1][warp] = bad; }
+    if (lane == 0) { red[0][warp] = critv; red[1][warp] = bad; }
     __syncthreads();
     if (tid == 0) {
       double a = 0.0, b = 0.0;
       for (int w = 0; w < NW; ++w) { a = fmax(a, red[0][w]); b = fmax(b, red[1][w]); }
-      __stcg(slots + (sweeps & 1) * 32 + 16 + 2 * rank, a);
-      __stcg(slots + (sweeps & 1) * 32 + 16 + 2 * rank + 1, b);
+      __stcg(slots + (pass & 1) * 32 + 16 + 2 * rank, a);
+      __stcg(slots + (pass & 1) * 32 + 16 + 2 * rank + 1, b);
     }
     cluster.sync();
-    crit = 0.0;
+    critv = 0.0;
     bad = 0.0;
     for (int r = 0; r < C; ++r) {
-      crit = fmax(crit, __ldcg(slots + (sweeps & 1) * 32 + 16 + 2 * r));
-      bad = fmax(bad, __ldcg(slots + (sweeps & 1) * 32 + 16 + 2 * r + 1));
+      critv = fmax(critv, __ldcg(slots + (pass & 1) * 32 + 16 + 2 * r));
+      bad = fmax(bad, __ldcg(slots + (pass & 1) * 32 + 16 + 2 * r + 1));
     }
-    if (bad != 0.0) break;
-    if (crit == 0.0) { converged = true; break; }
-    if (sweeps >= max_sweeps) break;
-    const double itol2 = 1e-4 * tol * tol;
+    if (bad != 0.0 || failed) break;
+    if (critv == 0.0) { converged = true; break; }
+    if (dyn ? rounds >= max_rounds : sweeps >= max_sweeps) break;
+    const double itol2 = 1e-4 * tol2;  // inner problems are solved 100x tighter
+    const int rounds0 = rounds;
 
-    for (int r = 0; r < nb - 1; ++r) {
-      // ---- phase 1 (FP64): exact 16 x 16 solves, one warp per block pair
-      for (int p = gw; p < np; p += nwt) {
-        int I, J;
-        circle_pair(r, p, nb, I, J);
+    for (int r = 0; dyn || r < nb - 1; ++r) {
+      if (dyn && rounds >= max_rounds) break;
+      // ---- the pairs of this round (every CTA of the cluster computes the same table)
+      if (!dyn) {
+        for (int p = tid; p < np; p += blockDim.x) {
+          int I, J;
+          circle_pair(r, p, nb, I, J);
+          spair[p] = make_short2((short)I, (short)J);
+          sneed[p] = 1;
+          ssolve[p] = (short)p;
+        }
+        if (tid == 0) snsolve = np;
+        __syncthreads();
+      } else {
+        if (tid == 0) sbad = 0;
+        __syncthreads();
+        // (1) per block: its internal coupling and its kTop most coupled partners
+        for (int I = warp; I < nb; I += NW) {
+          float rv[kMaxBlocks / 32];
+#pragma unroll
+          for (int k = 0; k < kMaxBlocks / 32; ++k) {
+            const int J = lane + 32 * k;
+            rv[k] = (J < nb && J != I) ? __ldcg(crit + (long long)I * nb + J) : -INFINITY;
+          }
+          const float own = __ldcg(crit + (long long)I * nb + I);
+          bool nf = own == INFINITY;
+#pragma unroll
+          for (int k = 0; k < kMaxBlocks / 32; ++k) nf |= rv[k] == INFINITY;
+          if (__any_sync(0xffffffffu, nf) && lane == 0) sbad = 1;
+#pragma unroll 1
+          for (int t = 0; t < kTop; ++t) {
+            float bv = -INFINITY;
+            int bj = -1;
+#pragma unroll
+            for (int k = 0; k < kMaxBlocks / 32; ++k)
+              if (rv[k] > bv) { bv = rv[k]; bj = lane + 32 * k; }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {  // largest value, then smallest block index
+              const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+              const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+              if (ov > bv || (ov == bv && oj >= 0 && (bj < 0 || oj < bj))) { bv = ov; bj = oj; }
+            }
+            if (lane == 0) { stopv[I][t] = bv; stopj[I][t] = (short)bj; }
+#pragma unroll
+            for (int k = 0; k < kMaxBlocks / 32; ++k)
+              if (lane + 32 * k == bj) rv[k] = -INFINITY;
+          }
+          if (lane == 0) { sown[I] = own; sused[I] = 0; }
+        }
+        __syncthreads();
+        // (2) the candidate blocks (largest or internal coupling above 1), in decreasing order
+        for (int I = tid; I < nb; I += blockDim.x) {
+          const float k0 = fmaxf(stopv[I][0], sown[I]);
+          skey[I] = k0 > 0.f ? k0 : 0.f;
+        }
+        __syncthreads();
+        int K = 0;
+        for (int base = 0; base < nb; base += blockDim.x) {
+          const int I = base + tid;
+          const float kI = I < nb ? skey[I] : 0.f;
+          if (kI > 0.f) {
+            int rk = 0;
+            for (int J = 0; J < nb; ++J) {
+              const float kJ = skey[J];
+              rk += (kJ > kI || (kJ == kI && J < I)) ? 1 : 0;
+            }
+            sorder[rk] = (short)I;
+          }
+          K += __syncthreads_count(kI > 0.f);
+        }
+        // (3) greedy matching, largest first
+        if (tid == 0) {
+          int nm = 0;
+          for (int k = 0; k < K; ++k) {
+            const int I = sorder[k];
+            if (sused[I]) continue;
+            const bool any_partner = sown[I] > 0.f;
+            for (int t = 0; t < kTop; ++t) {
+              const int J = stopj[I][t];
+              if (J < 0 || (!(stopv[I][t] > 0.f) && !any_partner)) break;
+              if (!sused[J]) {
+                sused[I] = sused[J] = 1;
+                spair[nm] = make_short2((short)min(I, J), (short)max(I, J));
+                ++nm;
+                break;
+              }
+            }
+          }
+          snmatch = nm;
+        }
+        __syncthreads();
+        // (4) the other blocks paired in index order; a pair is solved if it was matched, or if
+        //     one of its blocks or their coupling is above 1; then the list of pairs to solve
+        if (warp == 0) {
+          int nfree = 0;
+          for (int b0 = 0; b0 < nb; b0 += 32) {
+            const int b = b0 + lane;
+            const bool f = b < nb && !sused[b];
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (f) sorder[nfree + __popc(bal & ((1u << lane) - 1u))] = (short)b;
+            nfree += __popc(bal);
+          }
+          __syncwarp();
+          const int nm = snmatch;
+          for (int i = lane; i < nm; i += 32) sneed[i] = 1;
+          for (int i = lane; i < nfree / 2; i += 32) {
+            const int a = sorder[2 * i], b = sorder[2 * i + 1];
+            spair[nm + i] = make_short2((short)a, (short)b);
+            sneed[nm + i] = (sown[a] > 0.f || sown[b] > 0.f || __ldcg(crit + (long long)a * nb + b) > 0.f) ? 1 : 0;
+          }
+          __syncwarp();
+          int ns = 0;
+          for (int p0 = 0; p0 < np; p0 += 32) {
+            const int p = p0 + lane;
+            const bool f = p < np && sneed[p];
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (f) ssolve[ns + __popc(bal & ((1u << lane) - 1u))] = (short)p;
+            ns += __popc(bal);
+          }
+          if (lane == 0) snsolve = ns;
+        }
+        __syncthreads();
+        if (sbad) { failed = true; break; }   // a non-finite coupling: the test pass reports it
+        if (snsolve == 0) break;              // no coupling above 1 left: re-check and stop
+      }
+      // ---- phase 1: exact 16 x 16 solves, one warp per pair to solve
+      const int nsolve = snsolve;
+      for (int k = gw; k < nsolve; k += nwt) {
+        const int p = ssolve[k];
+        const int I = spair[p].x, J = spair[p].y;
         for (int e = lane; e < SB * SB; e += 32) {
           const int a = e / SB, b = e % SB;
-          Xd[a * SBP + b] = df_join(ldcg2(Mw + (long long)gidx(I, J, a) * dp + gidx(I, J, b)));
+          Xd[a * SBP + b] = E::join(E::ld(Mw + (long long)gidx(I, J, a) * dp + gidx(I, J, b)));
         }
         __syncwarp();
         const bool rot = inner_solve(Xd, Vd, cs[warp], itol2, floor2, rule, dmin2, nround);
+        ++nsolved;
+        nrotated += rot ? 1u : 0u;
         if (rot) {
           for (int e = lane; e < SB * SB; e += 32) {
             const int a = e / SB, b = e % SB;
-            __stcg(V + (long long)p * SB * SB + e, df_split(Vd[a * SBP + b]));
-            __stcg(D + (long long)p * SB * SB + e, df_split(Xd[a * SBP + b]));
+            E::st(V + (long long)p * SB * SB + e, E::split(Vd[a * SBP + b]));
+            E::st(D + (long long)p * SB * SB + e, E::split(Xd[a * SBP + b]));
           }
         }
         if (lane == 0) __stcg(flags + p, rot ? 1 : 0);
         __syncwarp();
       }
+      for (int p = gw; p < np; p += nwt)
+        if (!sneed[p] && lane == 0) __stcg(flags + p, 0);
       cluster.sync();
       // ---- the pairs rotated in phase 1, in order (every CTA of the cluster builds the same list)
       // and, per column Q of M's tiles, the cumulative count of active tiles (P <= Q with P or Q
@@ -786,87 +793,150 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_df(double* __restrict__ Mb, 
         if (lane == 0) snact = base;
       }
       __syncthreads();
-      // ---- phase 2 (double-float): apply all rotations to M and to the rows of Psi^T
-      //      over the active jobs only, dealt round-robin to the cluster's warps: the M tiles
-      //      (P <= Q) of which P or Q rotated, then the Psi^T row tiles of the rotated pairs
+      // ---- phase 2: apply all rotations to M (P <= Q tiles) and to the rows of Psi^T over the
+      //      active jobs only, dealt round-robin to the cluster's warps: the M tiles (P <= Q) of
+      //      which P or Q rotated, then the Psi^T row tiles of the rotated pairs. The dynamic
+      //      schedule records the new coupling criterion of every 8 x 8 block it rewrites.
       const int k = scum[np - 1];  // active M tiles
       for (int i = gw; i < k; i += nwt) {
-        {
-          int lo = 0, hi = np - 1;  // the column: smallest Q with scum[Q] > i
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (scum[mid] > i) hi = mid;
-            else lo = mid + 1;
+        int lo = 0, hi = np - 1;  // the column: smallest Q with scum[Q] > i
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (scum[mid] > i) hi = mid;
+          else lo = mid + 1;
+        }
+        const int Q = lo, o = i - (Q > 0 ? scum[Q - 1] : 0);
+        const int fQ = sflag[Q];
+        const int Pp = fQ ? o : sact[o];
+        const int fP = sflag[Pp];
+        const int I1 = spair[Pp].x, J1 = spair[Pp].y, I2 = spair[Q].x, J2 = spair[Q].y;
+        if (Pp == Q) {
+          const T* Dp = D + (long long)Pp * SB * SB;
+          for (int e = lane; e < SB * SB; e += 32) {
+            const int a = e / SB, b = e % SB;
+            E::st(Mw + (long long)gidx(I1, J1, a) * dp + gidx(I1, J1, b), E::ld(Dp + e));
           }
-          const int Q = lo, o = i - (Q > 0 ? scum[Q - 1] : 0);
-          const int fQ = sflag[Q];
-          const int Pp = fQ ? o : sact[o];
-          const int fP = sflag[Pp];
-          int I1, J1, I2, J2;
-          circle_pair(r, Pp, nb, I1, J1);
-          circle_pair(r, Q, nb, I2, J2);
-          if (Pp == Q) {
+          if (dyn) {
+            // blocks (I1, I1), (I1, J1), (J1, J1) of the solved 16 x 16 block (upper triangle)
+            float r00 = -INFINITY, r01 = -INFINITY, r11 = -INFINITY;
             for (int e = lane; e < SB * SB; e += 32) {
               const int a = e / SB, b = e % SB;
-              __stcg(Mw + (long long)gidx(I1, J1, a) * dp + gidx(I1, J1, b), ldcg2(D + (long long)Pp * SB * SB + e));
+              if (a >= b) continue;
+              const double v = E::join(E::ld(Dp + e));
+              if (v == 0.0) continue;
+              const float rr = coupling_log_ratio(v, E::join(E::ld(Dp + a * SB + a)),
+                                                  E::join(E::ld(Dp + b * SB + b)), ck);
+              if (b < BL) r00 = fmaxf(r00, rr);
+              else if (a >= BL) r11 = fmaxf(r11, rr);
+              else r01 = fmaxf(r01, rr);
             }
-          } else {
-            for (int e = lane; e < SB * SB; e += 32) {
-              const int a = e / SB, b = e % SB;
-              X[a * SBP + b] = ldcg2(Mw + (long long)gidx(I1, J1, a) * dp + gidx(I2, J2, b));
+            r00 = warp_max(r00);
+            r01 = warp_max(r01);
+            r11 = warp_max(r11);
+            if (lane == 0) {
+              __stcg(crit + (long long)I1 * nb + I1, r00);
+              __stcg(crit + (long long)J1 * nb + J1, r11);
+              __stcg(crit + (long long)I1 * nb + J1, r01);
+              __stcg(crit + (long long)J1 * nb + I1, r01);
             }
-            if (fP) load_v_df(Va, V + (long long)Pp * SB * SB);
-            if (fQ) load_v_df(Vq, V + (long long)Q * SB * SB);
-            __syncwarp();
-            tile_transform_df(X, fP ? Va : nullptr, fQ ? Vq : nullptr, Tt, X);
-            ntile += (fP ? 1u : 0u) + (fQ ? 1u : 0u);
-            const int t = lane >> 1, u0 = (lane & 1) * 8;
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              __stcg(Mw + (long long)gidx(I1, J1, t) * dp + gidx(I2, J2, u0 + j), X[t * SBP + u0 + j]);
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              __stcg(Mw + (long long)gidx(I2, J2, t) * dp + gidx(I1, J1, u0 + j), X[(u0 + j) * SBP + t]);
+          }
+        } else {
+          for (int e = lane; e < SB * SB; e += 32) {
+            const int a = e / SB, b = e % SB;
+            X[a * SBP + b] = E::ld(Mw + (long long)gidx(I1, J1, a) * dp + gidx(I2, J2, b));
+          }
+          if (fP) load_tile_v<E>(Va, V + (long long)Pp * SB * SB);
+          if (fQ) load_tile_v<E>(Vq, V + (long long)Q * SB * SB);
+          if (dyn) {
+            // the diagonal after this round: from D for a rotated pair, else M's (unchanged)
+            const int pq = lane < SB ? Pp : Q, a = lane & (SB - 1);
+            const bool fr = lane < SB ? fP : fQ;
+            const int I = lane < SB ? I1 : I2, J = lane < SB ? J1 : J2;
+            sdg[warp][lane] = fr ? E::join(E::ld(D + (long long)pq * SB * SB + a * SB + a))
+                                 : E::join(E::ld(Mw + (long long)gidx(I, J, a) * dp + gidx(I, J, a)));
           }
           __syncwarp();
+          E::transform(X, fP ? Va : nullptr, fQ ? Vq : nullptr, Tt, X);
+          ntile += (fP ? 1u : 0u) + (fQ ? 1u : 0u);
+          const int t = lane >> 1, u0 = (lane & 1) * 8;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            E::st(Mw + (long long)gidx(I1, J1, t) * dp + gidx(I2, J2, u0 + j), X[t * SBP + u0 + j]);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            E::st(Mw + (long long)gidx(I2, J2, t) * dp + gidx(I1, J1, u0 + j), X[(u0 + j) * SBP + t]);
+          if (dyn) {
+            // lane (t, u0) covers 8 entries of one 8 x 8 block: rows of block (t < 8 ? I1 : J1),
+            // columns of block (u0 < 8 ? I2 : J2); lanes 2, 4, 8 apart share it
+            float rr = -INFINITY;
+            const double djj = sdg[warp][t];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const double v = E::join(X[t * SBP + u0 + j]);
+              if (v != 0.0)
+                rr = fmaxf(rr, coupling_log_ratio(v, djj, sdg[warp][SB + u0 + j], ck));
+            }
+            rr = fmaxf(rr, __shfl_xor_sync(0xffffffffu, rr, 2));
+            rr = fmaxf(rr, __shfl_xor_sync(0xffffffffu, rr, 4));
+            rr = fmaxf(rr, __shfl_xor_sync(0xffffffffu, rr, 8));
+            if ((lane & 14) == 0) {
+              const int rb = t < BL ? I1 : J1, cb = u0 < BL ? I2 : J2;
+              __stcg(crit + (long long)rb * nb + cb, rr);
+              __stcg(crit + (long long)cb * nb + rb, rr);
+            }
+          }
         }
+        __syncwarp();
       }
       const int nPsi = snact * nct;
       for (int j = ((gw - k) % nwt + nwt) % nwt; j < nPsi; j += nwt) {
         const int Pp = sact[j / nct], ct = j % nct;
-        int I1, J1;
-        circle_pair(r, Pp, nb, I1, J1);
+        const int I1 = spair[Pp].x, J1 = spair[Pp].y;
         for (int e = lane; e < SB * SB; e += 32) {
           const int a = e / SB, b = e % SB;
-          X[a * SBP + b] = ldcg2(Pw + (long long)gidx(I1, J1, a) * dp + ct * SB + b);
+          X[a * SBP + b] = E::ld(Pw + (long long)gidx(I1, J1, a) * dp + ct * SB + b);
         }
-        load_v_df(Va, V + (long long)Pp * SB * SB);
+        load_tile_v<E>(Va, V + (long long)Pp * SB * SB);
         __syncwarp();
-        tile_transform_df(X, Va, nullptr, Tt, X);
+        E::transform(X, Va, nullptr, Tt, X);
         ++ntile;
         const int t = lane >> 1, u0 = (lane & 1) * 8;
 #pragma unroll
         for (int j2 = 0; j2 < 8; ++j2)
-          __stcg(Pw + (long long)gidx(I1, J1, t) * dp + ct * SB + u0 + j2, X[t * SBP + u0 + j2]);
+          E::st(Pw + (long long)gidx(I1, J1, t) * dp + ct * SB + u0 + j2, X[t * SBP + u0 + j2]);
         __syncwarp();
       }
       cluster.sync();
+      ++rounds;
     }
+    // the selection and the test use the same criterion, so a pass that found a coupling above the
+    // tolerance always runs a round; should none run, stop (reported as not converged)
+    if (dyn && rounds == rounds0) break;
     ++sweeps;
   }
-  for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
-    __stcg(M + e, df_join(ldcg2(Mw + e)));
-    __stcg(P + e, df_join(ldcg2(Pw + e)));
+  if constexpr (E::kPairs) {
+    for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
+      __stcg(M + e, E::join(E::ld(Mw + e)));
+      __stcg(P + e, E::join(E::ld(Pw + e)));
+    }
   }
   for (int i = rank * blockDim.x + tid; i < dp; i += C * blockDim.x)
-    lamb[(long long)chain * dp + i] = df_join(ldcg2(Mw + (long long)i * dp + i));
+    lamb[(long long)chain * dp + i] = E::join(E::ld(Mw + (long long)i * dp + i));
   if (tiles && lane == 0) {
-    if (ntile) atomicAdd(tiles + 2 * chain, (unsigned long long)ntile);
-    if (nround) atomicAdd(tiles + 2 * chain + 1, (unsigned long long)nround);
+    unsigned long long* t = tiles + (long long)kJacStats * chain;
+    if (ntile) atomicAdd(t + 0, (unsigned long long)ntile);
+    if (nround) atomicAdd(t + 1, (unsigned long long)nround);
+    if (nsolved) atomicAdd(t + 3, (unsigned long long)nsolved);
+    if (nrotated) atomicAdd(t + 4, (unsigned long long)nrotated);
+    if (rank == 0 && warp == 0) {
+      atomicAdd(t + 2, (unsigned long long)rounds);
+      atomicAdd(t + 5, 1ull);
+    }
   }
   if (rank == 0 && tid == 0) {
-    sweeps_out[chain] = sweeps;
-    if (sweeps_acc) sweeps_acc[chain] += sweeps;
+    const int sw = dyn ? (rounds + nb - 2) / (nb - 1) : sweeps;
+    sweeps_out[chain] = sw;
+    if (sweeps_acc) sweeps_acc[chain] += sw;
     if (!converged) atomicOr(&status[chain], RMHMC_CHAIN_NOTCONV);
   }
 }
@@ -924,7 +994,8 @@ __global__ void __launch_bounds__(NW * 32) k_mgs(double* __restrict__ Pb, int dp
 constexpr size_t kNoAllocDoubles = size_t(1) << 20;  // 8 MiB
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 constexpr int kMaxDevices = 64;
-double* g_noalloc_ptr[kMaxDevices] = {};
+std::atomic<double*> g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mutex;
 
 // M = A zero-padded to dp x dp, PsiT = I, status = 0 (the workspace keeps the previous call's
 // contents, so everything the solver reads is rewritten here).
@@ -993,30 +1064,31 @@ int jacobi_cluster_size(int n_chains) {
 
 void jacobi_f64(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,
                 int rule, double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
-                JacobiWork w, int cluster) {
+                JacobiWork w, int cluster, int sched) {
   const size_t smem = (size_t)NW * WARP_SMEM * sizeof(double);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_jacobi_t<ElemF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  launch_cluster(k_jacobi, n_chains, cluster, smem, s, M, PsiT, lam, dp, d, rule, tol, max_sweeps,
-                 status, sweeps_out, sweeps_acc, w.V, w.D, w.slots, w.flags, w.tiles);
+  launch_cluster(k_jacobi_t<ElemF64>, n_chains, cluster, smem, s, M, PsiT, lam, dp, d, rule, tol, max_sweeps,
+                 status, sweeps_out, sweeps_acc, w.V, w.D, w.slots, w.flags, w.tiles, (double*)nullptr,
+                 (double*)nullptr, w.crit, sched);
 }
 
 void jacobi_df(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,
                int rule, double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
-               JacobiWork w, int cluster, double* pair_scratch_M, double* pair_scratch_P) {
+               JacobiWork w, int cluster, double* pair_scratch_M, double* pair_scratch_P, int sched) {
   const size_t smem = (size_t)NW * WARP_SMEM * sizeof(double);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_jacobi_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_jacobi_t<ElemDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  launch_cluster(k_jacobi_df, n_chains, cluster, smem, s, M, PsiT, lam, dp, d, rule, tol, max_sweeps,
+  launch_cluster(k_jacobi_t<ElemDF>, n_chains, cluster, smem, s, M, PsiT, lam, dp, d, rule, tol, max_sweeps,
                  status, sweeps_out, sweeps_acc, w.V, w.D, w.slots, w.flags, w.tiles,
-                 (float2*)pair_scratch_M,
-                 (float2*)pair_scratch_P);
+                 reinterpret_cast<float2*>(pair_scratch_M), reinterpret_cast<float2*>(pair_scratch_P), w.crit,
+                 sched);
 }
 
 void mgs_rows_f64(cudaStream_t s, double* PsiT, int dp, int d, int n_chains, const int* eig_count,
@@ -1038,15 +1110,27 @@ extern "C" rmhmc_status rmhmc_eigh_noalloc(void* cuda_stream, int n, int d, cons
   if (noalloc_doubles(n, dp) > kNoAllocDoubles) return RMHMC_ESCRATCH;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RMHMC_ECUDA;
-  if (!g_noalloc_ptr[dev]) {
-    // host code cannot use the symbol itself as a device address: look it up once per device
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RMHMC_ECUDA;
-    g_noalloc_ptr[dev] = (double*)p;
-  }
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  // the workspace looked up below is the current device's: a stream of another device is refused
+  if (s) {
+    int sdev = -1;
+    if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) return RMHMC_EINVAL;
+    if (sdev != dev) return RMHMC_EINVAL;
+  }
+  double* base = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!base) {
+    // host code cannot use the symbol itself as a device address: look it up once per device
+    // (under a lock, so two host threads making their first call together agree)
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    base = g_noalloc_ptr[dev].load(std::memory_order_relaxed);
+    if (!base) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RMHMC_ECUDA;
+      base = (double*)p;
+      g_noalloc_ptr[dev].store(base, std::memory_order_release);
+    }
+  }
   const int np = dp / BL / 2;
-  double* base = g_noalloc_ptr[dev];
   double* M = base;
   double* P = M + (size_t)n * dp * dp;
   double* lamp = P + (size_t)n * dp * dp;
@@ -1060,12 +1144,14 @@ extern "C" rmhmc_status rmhmc_eigh_noalloc(void* cuda_stream, int n, int d, cons
   k_noalloc_pack<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A_dev, d, dp, n, M, P, status);
   const int C = jacobi_cluster_size(n);
   const size_t smem = (size_t)NW * WARP_SMEM * sizeof(double);
-  if (cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_jacobi_t<ElemF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
     return RMHMC_ECUDA;
-  if (launch_cluster(k_jacobi, n, C, smem, s, M, P, lamp, dp, d, (int)RMHMC_JACOBI_RELATIVE, tol,
+  if (launch_cluster(k_jacobi_t<ElemF64>, n, C, smem, s, M, P, lamp, dp, d, (int)RMHMC_JACOBI_RELATIVE, tol,
                      max_sweeps, status,
                      sweeps_dev ? sweeps_dev : sweeps, (int*)nullptr, V, D, slots, flags,
-                     (unsigned long long*)nullptr) != cudaSuccess)
+                     (unsigned long long*)nullptr, (double*)nullptr, (double*)nullptr, (float*)nullptr,
+                     (int)RMHMC_JACOBI_CYCLIC) != cudaSuccess)
     return RMHMC_ECUDA;
   const long long out = (long long)n * d * d;
   k_noalloc_unpack<<<(unsigned)((out + 255) / 256), 256, 0, s>>>(lamp, P, d, dp, n, lam_dev, Q_dev);

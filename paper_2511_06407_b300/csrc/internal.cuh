@@ -134,22 +134,26 @@ double gemm_tc_tensor_flops(const TcOperand& A, const TcOperand& B, int batch, b
 // Warm-started block-Jacobi on M (dp x dp per chain, symmetric), rotating PsiT's rows alongside;
 // writes lam (dp per chain) and the sweep count; sets RMHMC_CHAIN_NOTCONV on failure. Chains
 // whose status is nonzero on entry are skipped.
+constexpr int kJacStats = 8;  // counters per chain in JacobiWork::tiles
 struct JacobiWork {
   double* V;      // n_chains x (nb/2) x 256
   double* D;      // n_chains x (nb/2) x 256
   double* slots;  // n_chains x 64
   int* flags;     // n_chains x (nb/2): pair rotated in the current round
-  unsigned long long* tiles;  // n_chains x 2: += 16 x 16 x 16 tile products executed (phase 2) and
-                              // rotation rounds applied to 16 x 16 blocks (phase 1); null = not counted
+  unsigned long long* tiles;  // n_chains x kJacStats counters (null = not counted): += 16 x 16 x 16
+                              // tile products executed (phase 2), rotation rounds applied to
+                              // 16 x 16 blocks (phase 1), outer rounds, 16 x 16 sub-problems solved,
+                              // of which rotated, eigen-updates
+  float* crit;    // n_chains x nb x nb: coupling criterion per pair of 8-wide blocks (dynamic schedule)
 };
 void jacobi_f64(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,
                 int rule, double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
-                JacobiWork w, int cluster);
+                JacobiWork w, int cluster, int sched);
 // The same eigen-update with the phase-2 rotations in double-float (FP32 pair) arithmetic;
 // pair_scratch_M / pair_scratch_P are n_chains x dp x dp doubles of scratch (used as float2).
 void jacobi_df(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,
                int rule, double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
-               JacobiWork w, int cluster, double* pair_scratch_M, double* pair_scratch_P);
+               JacobiWork w, int cluster, double* pair_scratch_M, double* pair_scratch_P, int sched);
 // Modified Gram-Schmidt on the first d rows of PsiT (dp x dp per chain), for chains whose
 // eig_count is a positive multiple of every (0 = never).
 void mgs_rows_f64(cudaStream_t s, double* PsiT, int dp, int d, int n_chains, const int* eig_count,

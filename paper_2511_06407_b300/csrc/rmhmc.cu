@@ -467,6 +467,7 @@ struct rmhmc_model {
   ModelDev md{};
   int N = 0, n = 0, P = 0, d = 0, dp = 0, C = 0;
   int cluster = 1;
+  int jacobi_sched = RMHMC_JACOBI_CYCLIC;  // rmhmc_jacobi_schedule
   bool has_state = false;
   int g_kind = 0, max_sweeps = 30, reorth_every = 10, precision = 0, jacobi_rule = 0, eigen_start = 0;
   double alpha = 1e6, tol = 1e-13;
@@ -808,11 +809,11 @@ void eval_geometry(rmhmc_model* m, bool third) {
     // rotations in double-float pairs; W and Y serve as the pair buffers (free during the update)
     PROF(m, CAT_JACOBI_DF, 0)
     jacobi_df(s, m->M, m->PsiT, m->lam, dp, d, C, m->jacobi_rule, m->tol, m->max_sweeps, m->status,
-              m->sweeps_last, m->sweeps_acc, m->jw, m->cluster, m->W, m->Y);
+              m->sweeps_last, m->sweeps_acc, m->jw, m->cluster, m->W, m->Y, m->jacobi_sched);
   } else {
     PROF(m, CAT_JACOBI, 0)
     jacobi_f64(s, m->M, m->PsiT, m->lam, dp, d, C, m->jacobi_rule, m->tol, m->max_sweeps, m->status,
-               m->sweeps_last, m->sweeps_acc, m->jw, m->cluster);
+               m->sweeps_last, m->sweeps_acc, m->jw, m->cluster, m->jacobi_sched);
   }
   m->tc_pa_ok = m->tc_pb_ok = false;  // the eigen-update rotated Psi^T
   PROF(m, CAT_VECTOR, 0)
@@ -1047,7 +1048,8 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
   ALLOC(m->jw.D, (size_t)C * np * 256);
   ALLOC(m->jw.slots, (size_t)C * 64);
   ALLOC(m->jw.flags, (size_t)C * np);
-  ALLOC(m->jw.tiles, (size_t)2 * C);
+  ALLOC(m->jw.tiles, (size_t)kJacStats * C);
+  ALLOC(m->jw.crit, (size_t)C * (dp / kJacBlk) * (dp / kJacBlk));
 #undef ALLOC
   return st;
 }
@@ -1185,52 +1187,81 @@ rmhmc_status rmhmc_batch_leapfrog(rmhmc_batch* b, const rmhmc_integrator* integ,
   return check_launch();
 }
 
-rmhmc_status rmhmc_autotune(rmhmc_model* m, int* cluster_out) {
+rmhmc_status rmhmc_autotune(rmhmc_model* m, const rmhmc_integrator* integ, int* cluster_out,
+                            int* sched_out) {
   if (!m || !m->has_state || m->prof) return RMHMC_EINVAL;
+  rmhmc_status st = check_integ(m, integ, false);
+  if (st != RMHMC_OK) return st;
   cudaStream_t s = m->stream;
-  const int C = m->C, dp = m->dp, d = m->d;
-  const long long DD = (long long)dp * dp;
+  const int C = m->C, dp = m->dp;
+  const long long DD = (long long)dp * dp, nv = (long long)C * dp;
+  // the state to come back to: q, p and Psi^T on the device (scratch that only rmhmc_sample
+  // uses), the per-chain counters and status on the host
+  std::vector<int> h_eig(C), h_status(C), h_sw_last(C), h_sw_acc(C), h_sw_total(C);
+  int* const ivec[5] = {m->eig_count, m->status, m->sweeps_last, m->sweeps_acc, m->sweeps_total};
+  std::vector<int>* const hvec[5] = {&h_eig, &h_status, &h_sw_last, &h_sw_acc, &h_sw_total};
+  if (cudaStreamSynchronize(s) != cudaSuccess) return RMHMC_ECUDA;
+  for (int i = 0; i < 5; ++i) cudaMemcpy(hvec[i]->data(), ivec[i], C * sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpyAsync(m->q_save, m->q, nv * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(m->z, m->p, nv * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(m->PsiT_save, m->PsiT, C * DD * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  auto counters_back = [&]() {
+    for (int i = 0; i < 5; ++i)
+      cudaMemcpyAsync(ivec[i], hvec[i]->data(), C * sizeof(int), cudaMemcpyHostToDevice, s);
+  };
+  // back to the saved point, its geometry re-evaluated there (from the saved basis, which is
+  // already converged at q: U, dU and the Hessian are recomputed exactly, the basis is re-checked)
+  auto restore = [&]() {
+    cudaMemcpyAsync(m->q, m->q_save, nv * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(m->p, m->z, nv * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(m->PsiT, m->PsiT_save, C * DD * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    counters_back();
+    eval_geometry(m, true);
+    counters_back();
+    cudaStreamSynchronize(s);
+  };
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RMHMC_ECUDA;
-  double best = 1e300;
-  int best_c = m->cluster;
   const int cands[4] = {1, 2, 4, 8};
-  std::vector<int> sw(C);
-  for (int ci = 0; ci < 4; ++ci) {
-    const int cl = cands[ci];
-    // scratch: W <- H (cold start, Psi = I in Y), eigenvalues in vtr, status in acc, sweeps in eig_save
-    cudaMemcpyAsync(m->W, m->H, C * DD * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    k_set_identity<<<nblk((long long)C * DD), 256, 0, s>>>(m->Y, dp, C);
-    cudaMemsetAsync(m->acc, 0, C * sizeof(int), s);
+  const int scheds[2] = {RMHMC_JACOBI_CYCLIC, RMHMC_JACOBI_DYNAMIC};
+  double best = 1e300;
+  int best_c = m->cluster, best_s = m->jacobi_sched;
+  // one untimed trial first (first-launch costs), then one generalized leapfrog per candidate
+  for (int t = -1; t < 8; ++t) {
+    if (t >= 0) {
+      m->jacobi_sched = scheds[t / 4];
+      m->cluster = cands[t % 4];
+    }
+    restore();
     cudaEventRecord(e0, s);
-    JacobiWork w = m->jw;
-    w.tiles = nullptr;  // trial runs stay out of the profile
-    if (m->precision == RMHMC_MIXED)
-      // the double-float kernel's pair buffers: M (scratch between eigen-updates: the C matrix of
-      // the next gradient is built there) and PsiT_save (used only inside rmhmc_sample)
-      jacobi_df(s, m->W, m->Y, m->vtr, dp, d, C, m->jacobi_rule, m->tol, 3, m->acc, m->eig_save, nullptr, w,
-                cl, m->M, m->PsiT_save);
-    else
-      jacobi_f64(s, m->W, m->Y, m->vtr, dp, d, C, m->jacobi_rule, m->tol, 3, m->acc, m->eig_save,
-                 nullptr, w, cl);
+    leapfrog_step(m, integ->eps, integ->n_fp);
     cudaEventRecord(e1, s);
     if (cudaEventSynchronize(e1) != cudaSuccess) return RMHMC_ECUDA;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    cudaMemcpy(sw.data(), m->eig_save, C * sizeof(int), cudaMemcpyDeviceToHost);
-    double sweeps = 0.0;
-    for (int v : sw) sweeps += v;
-    const double per = ms / (sweeps > 0.0 ? sweeps : 1.0);
-    if (per < best) {
-      best = per;
-      best_c = cl;
+    if (t >= 0 && ms < best) {
+      best = ms;
+      best_c = m->cluster;
+      best_s = m->jacobi_sched;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   m->cluster = best_c;
+  m->jacobi_sched = best_s;
+  restore();
   if (cluster_out) *cluster_out = best_c;
+  if (sched_out) *sched_out = best_s;
   return check_launch();
+}
+
+rmhmc_status rmhmc_set_jacobi(rmhmc_model* m, int cluster, int sched) {
+  if (!m) return RMHMC_EINVAL;
+  if (cluster != 0 && cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8) return RMHMC_EINVAL;
+  if (sched != RMHMC_JACOBI_CYCLIC && sched != RMHMC_JACOBI_DYNAMIC) return RMHMC_EINVAL;
+  m->cluster = cluster == 0 ? jacobi_cluster_size(m->C) : cluster;
+  m->jacobi_sched = sched;
+  return RMHMC_OK;
 }
 
 
@@ -1284,9 +1315,24 @@ rmhmc_status rmhmc_profile(rmhmc_model* m, int enable) {
       m->prof_launch[i] = 0;
     }
     cudaMemsetAsync(m->sweeps_total, 0, m->C * sizeof(int), m->stream);
-    cudaMemsetAsync(m->jw.tiles, 0, 2 * m->C * sizeof(unsigned long long), m->stream);
+    cudaMemsetAsync(m->jw.tiles, 0, (size_t)kJacStats * m->C * sizeof(unsigned long long), m->stream);
   }
   m->prof = enable != 0;
+  return RMHMC_OK;
+}
+
+rmhmc_status rmhmc_jacobi_counters(rmhmc_model* m, long long* counters_host) {
+  if (!m || !counters_host) return RMHMC_EINVAL;
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) return RMHMC_ECUDA;
+  std::vector<unsigned long long> tl((size_t)kJacStats * m->C);
+  if (cudaMemcpy(tl.data(), m->jw.tiles, tl.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return RMHMC_ECUDA;
+  for (int k = 0; k < 6; ++k) {
+    long long v = 0;
+    for (int c = 0; c < m->C; ++c) v += (long long)tl[(size_t)kJacStats * c + k];
+    counters_host[k] = v;
+  }
   return RMHMC_OK;
 }
 
@@ -1304,12 +1350,12 @@ rmhmc_status rmhmc_profile_read(rmhmc_model* m, double* ms_host, double* flops_h
   // phase 1 (8 rotations applied to a 16 x 16 block by 2 x 2 blocks, 28 off-diagonal and 8
   // diagonal, and to its accumulated rotation: 976 FP64 multiply / FMA instructions, counted as
   // 2 flops each like the DFMA peak)
-  std::vector<unsigned long long> tl(2 * m->C);
-  cudaMemcpy(tl.data(), m->jw.tiles, 2 * m->C * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  std::vector<unsigned long long> tl((size_t)kJacStats * m->C);
+  cudaMemcpy(tl.data(), m->jw.tiles, tl.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
   double tiles = 0.0, rounds = 0.0;
   for (int c = 0; c < m->C; ++c) {
-    tiles += (double)tl[2 * c];
-    rounds += (double)tl[2 * c + 1];
+    tiles += (double)tl[(size_t)kJacStats * c];
+    rounds += (double)tl[(size_t)kJacStats * c + 1];
   }
   for (int i = 0; i < RMHMC_PROF_NCAT; ++i) {
     if (ms_host) ms_host[i] = ms[i];

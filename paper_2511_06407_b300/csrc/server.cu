@@ -47,7 +47,7 @@ struct SrvJob {
   rmhmc_integrator integ{};
   int n_iter = 0, n_burn = 0;
   uint64_t seed = 0;
-  double *q_out = nullptr, *logp_out = nullptr;
+  double *q_out = nullptr, *logp_out = nullptr, *ll_out = nullptr;
   int *acc_out = nullptr, *status_out = nullptr;
   size_t bytes = 0;
   int state = RMHMC_JOB_QUEUED;
@@ -153,7 +153,7 @@ rmhmc_status top_up(SrvJob* j, int depth) {
     } else {
       const long long r = it - j->n_burn, C = j->C;
       st = rmhmc_sample(j->m, &j->integ, 1, 0, j->seed, j->q_out ? j->q_out + r * C * j->d : nullptr,
-                        j->logp_out ? j->logp_out + r * C : nullptr, nullptr,
+                        j->logp_out ? j->logp_out + r * C : nullptr, j->ll_out ? j->ll_out + r * C : nullptr,
                         j->acc_out ? j->acc_out + r * C : nullptr, nullptr, j->st_iter);
     }
     if (st != RMHMC_OK) return st;
@@ -277,6 +277,7 @@ rmhmc_status submit_job(rmhmc_server* S, const rmhmc_job_desc* jd, int* job_id) 
   j->seed = jd->seed;
   j->q_out = jd->q_samples_dev;
   j->logp_out = jd->logp_dev;
+  j->ll_out = jd->loglik_dev;
   j->acc_out = jd->accept_dev;
   j->status_out = jd->chain_status_dev;
   size_t plan = 0;

@@ -106,13 +106,14 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the phase of `parity` to complete; false after about kWaitNs of global time.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait for the phase of `parity` to complete; false after about limit_ns of global time.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitNs) {
   if (mbar_test(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (true) {
     if (mbar_test(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 
@@ -344,6 +345,8 @@ struct TcArgs {
   int* status;  // per-chain status (may be null); entry b reports to status[b / sdiv]
   int sdiv;
   const int* mask;  // null, or entry b runs only where mask[b] != 0
+  unsigned long long wait_ns;  // limit of each bounded wait
+  int stall_entry;             // test switch: entry whose loads are never issued (-1: none)
 };
 
 template <int S>
@@ -388,9 +391,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
       const uint8_t* Ab = a.A + b * a.sA;
       const uint8_t* Bb = a.B + b * a.sB;
       int issued = 0;
-      for (int it = 0; it < nk; ++it) {
+      // the test switch: for this entry no copy is issued, so the MMA warp's first wait runs out
+      // (nothing is in flight, the CTA then frees its tensor memory and returns)
+      const int nk_issue = b == a.stall_entry ? 0 : nk;
+      for (int it = 0; it < nk_issue; ++it) {
         const int st = it % NST;
-        if (it >= NST && !mbar_wait(empty0 + 8 * st, ((it / NST) - 1) & 1)) {
+        if (it >= NST && !mbar_wait(empty0 + 8 * st, ((it / NST) - 1) & 1, a.wait_ns)) {
           atomicExch(&failed, 1);
           break;
         }
@@ -404,13 +410,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
       }
       // every issued copy has landed before the CTA may exit (already true unless a wait failed)
       for (int it = issued > NST ? issued - NST : 0; it < issued; ++it)
-        if (!mbar_wait(full0 + 8 * (it % NST), (it / NST) & 1)) atomicExch(&failed, 1);
+        if (!mbar_wait(full0 + 8 * (it % NST), (it / NST) & 1, a.wait_ns)) atomicExch(&failed, 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       for (int it = 0; it < nk; ++it) {
         const int st = it % NST;
-        if (!mbar_wait(full0 + 8 * st, (it / NST) & 1)) {
+        if (!mbar_wait(full0 + 8 * st, (it / NST) & 1, a.wait_ns)) {
           atomicExch(&failed, 1);
           break;
         }
@@ -444,7 +450,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
     const int q = warp % 4;     // the TMEM lane quarter this warp may read
     const int half = ew / 4;    // and its 32 of the tile's 64 columns
     int* sec = reinterpret_cast<int*>(smem + Cfg::BAR_OFF - TC_N * sizeof(int));
-    const bool ok = mbar_wait(done, 0);
+    const bool ok = mbar_wait(done, 0, a.wait_ns);
     tc_fence_after();
     // the pipeline stages are free now: column exponents, then one 32 x 17 staging tile per warp
     if (threadIdx.x - 64 < TC_N) {
@@ -562,6 +568,10 @@ __global__ void k_scale(double* C, int m, int n, int ldc, long long sC, double b
   *c = beta == 0.0 ? 0.0 : beta * *c;
 }
 
+// The test switch of rmhmc_test_gemm_stall (host side; read at each launch).
+int g_stall_entry = -1;
+unsigned long long g_wait_ns = kWaitNs;
+
 }  // namespace
 
 int tc_tile_rows(bool b_side) { return b_side ? TC_N : TC_M; }
@@ -646,6 +656,8 @@ void gemm_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, double alph
   a.status = status;
   a.sdiv = sdiv > 0 ? sdiv : 1;
   a.mask = mask;
+  a.wait_ns = g_wait_ns;
+  a.stall_entry = g_stall_entry;
   for (int k0 = 0; k0 < KS; k0 += TC_KSTEPS_MAX) {
     a.ks0 = k0;
     a.ks1 = k0 + TC_KSTEPS_MAX < KS ? k0 + TC_KSTEPS_MAX : KS;
@@ -689,4 +701,17 @@ extern "C" rmhmc_status rmhmc_gemm_tc(void* cuda_stream, int ta, int tb, int m, 
   const cudaError_t e = cudaGetLastError();
   cudaFreeAsync(mem, s);
   return e == cudaSuccess ? RMHMC_OK : RMHMC_ECUDA;
+}
+
+extern "C" rmhmc_status rmhmc_test_gemm_stall(int entry, double wait_ms) {
+  using namespace rmhmc;
+  if (entry < 0) {
+    g_stall_entry = -1;
+    g_wait_ns = kWaitNs;
+    return RMHMC_OK;
+  }
+  if (!(wait_ms >= 1.0 && wait_ms <= 2000.0)) return RMHMC_EINVAL;
+  g_stall_entry = entry;
+  g_wait_ns = (unsigned long long)(wait_ms * 1e6);
+  return RMHMC_OK;
 }

@@ -21,7 +21,8 @@ GKINDS = {"coth": 0, "sqrt": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 JACOBI_RULES = {"metric": 0, "relative": 1}
 EIGEN_STARTS = {"warm": 0, "cold": 1}
-CHAIN_NOTPD, CHAIN_NOTCONV, CHAIN_NONFINITE = 1, 2, 4
+CHAIN_NOTPD, CHAIN_NOTCONV, CHAIN_NONFINITE, CHAIN_TIMEOUT = 1, 2, 4, 8
+JACOBI_SCHEDULES = ["cyclic", "dynamic"]  # rmhmc_jacobi_schedule
 PROF_NCAT = 10
 
 
@@ -55,7 +56,8 @@ class JobDesc(ctypes.Structure):
     _fields_ = [("model", POINTER(ModelDesc)), ("primal", POINTER(PrimalDesc)), ("n_chains", c_int),
                 ("tau_host", POINTER(c_double)), ("q0_host", POINTER(c_double)), ("integ", IntegratorC),
                 ("n_iter", c_int), ("n_burn", c_int), ("seed", ctypes.c_uint64), ("q_samples_dev", c_void_p),
-                ("logp_dev", c_void_p), ("accept_dev", c_void_p), ("chain_status_dev", c_void_p)]
+                ("logp_dev", c_void_p), ("accept_dev", c_void_p), ("chain_status_dev", c_void_p),
+                ("loglik_dev", c_void_p)]
 
 
 @dataclass
@@ -131,6 +133,8 @@ def lib():
                                 c_double, c_void_p, c_int, ctypes.c_longlong, c_int, c_int, c_int,
                                 c_void_p]
     L.rmhmc_gemm_tc.restype = c_int
+    L.rmhmc_test_gemm_stall.argtypes = [c_int, c_double]
+    L.rmhmc_test_gemm_stall.restype = c_int
     L.rmhmc_server_create.argtypes = [c_int, ctypes.c_size_t, c_int, POINTER(c_void_p)]
     L.rmhmc_server_create.restype = c_int
     L.rmhmc_server_submit.argtypes = [c_void_p, POINTER(JobDesc), POINTER(c_int)]
@@ -150,8 +154,12 @@ def lib():
     L.rmhmc_batch_leapfrog.restype = c_int
     L.rmhmc_batch_free.argtypes = [c_void_p]
     L.rmhmc_batch_free.restype = None
-    L.rmhmc_autotune.argtypes = [c_void_p, POINTER(c_int)]
+    L.rmhmc_autotune.argtypes = [c_void_p, POINTER(IntegratorC), POINTER(c_int), POINTER(c_int)]
     L.rmhmc_autotune.restype = c_int
+    L.rmhmc_set_jacobi.argtypes = [c_void_p, c_int, c_int]
+    L.rmhmc_set_jacobi.restype = c_int
+    L.rmhmc_jacobi_counters.argtypes = [c_void_p, POINTER(ctypes.c_longlong)]
+    L.rmhmc_jacobi_counters.restype = c_int
     L.rmhmc_plan_bytes.argtypes = [POINTER(ModelDesc), c_int, POINTER(ctypes.c_size_t)]
     L.rmhmc_plan_bytes.restype = c_int
     L.rmhmc_init_primal.argtypes = [POINTER(PrimalDesc), c_int, POINTER(c_double), c_void_p,
@@ -336,11 +344,24 @@ class Model:
                                             _ptr(Ginv_p, (C, d), f64), _ptr(H, (C,), f64)))
 
 
-    def autotune(self):
-        """Pick this model's Jacobi cluster size by timing (rmhmc_autotune); returns it."""
-        out = c_int()
-        _check(lib().rmhmc_autotune(self._h, ctypes.byref(out)))
-        return out.value
+    def autotune(self, integ=None):
+        """Pick this model's Jacobi cluster size and rotation schedule by timing one leapfrog of
+        each (rmhmc_autotune); returns (cluster, schedule name)."""
+        integ = integ or self.integ or Integrator()
+        cl, sc = c_int(), c_int()
+        _check(lib().rmhmc_autotune(self._h, ctypes.byref(integ.c()), ctypes.byref(cl), ctypes.byref(sc)))
+        return cl.value, JACOBI_SCHEDULES[sc.value]
+
+    def jacobi_counters(self):
+        """Eigen-update work since the last profile reset (rmhmc_jacobi_counters), as a dict."""
+        out = (ctypes.c_longlong * 6)()
+        _check(lib().rmhmc_jacobi_counters(self._h, out))
+        keys = ("tile_products", "inner_rounds", "rounds", "solves", "rotated", "updates")
+        return dict(zip(keys, [int(v) for v in out]))
+
+    def set_jacobi(self, cluster=0, schedule="cyclic"):
+        """Set the Jacobi cluster size (0 = default) and rotation schedule ("cyclic"/"dynamic")."""
+        _check(lib().rmhmc_set_jacobi(self._h, int(cluster), JACOBI_SCHEDULES.index(schedule)))
 
     def profile(self, enable=True):
         _check(lib().rmhmc_profile(self._h, 1 if enable else 0))
@@ -451,6 +472,13 @@ def gemm_tc(A, B, C=None, ta=False, tb=False, alpha=1.0, beta=0.0, slices=9, sym
     return C
 
 
+def test_gemm_stall(entry, wait_ms=20.0):
+    """Test switch of the GEMM's bounded waits (rmhmc_test_gemm_stall): entry >= 0 makes later
+    tensor-core GEMM launches issue no copy for that batch entry, with every wait limited to
+    wait_ms; entry < 0 restores normal operation."""
+    _check(lib().rmhmc_test_gemm_stall(int(entry), float(wait_ms)))
+
+
 JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 
 
@@ -465,7 +493,7 @@ class NativeServer:
         self._keep = {}
 
     def submit(self, problem, n_chains, integ, n_iter, n_burn=0, seed=0, tau=None, q0=None,
-               q_out=None, logp_out=None, accept_out=None, status_out=None):
+               q_out=None, logp_out=None, accept_out=None, status_out=None, loglik_out=None):
         """Queue a job; the output tensors (CUDA, contiguous) must stay alive until it is done."""
         if is_primal(problem):
             desc, keep = _primal_desc(problem)
@@ -479,10 +507,10 @@ class NativeServer:
                      t.ctypes.data_as(POINTER(c_double)) if t is not None else None,
                      q.ctypes.data_as(POINTER(c_double)) if q is not None else None,
                      integ.c(), int(n_iter), int(n_burn), int(seed) & (2 ** 64 - 1),
-                     _ptr(q_out), _ptr(logp_out), _ptr(accept_out), _ptr(status_out))
+                     _ptr(q_out), _ptr(logp_out), _ptr(accept_out), _ptr(status_out), _ptr(loglik_out))
         jid = c_int()
         _check(lib().rmhmc_server_submit(self._h, ctypes.byref(jd), ctypes.byref(jid)))
-        self._keep[jid.value] = (q_out, logp_out, accept_out, status_out)
+        self._keep[jid.value] = (q_out, logp_out, accept_out, status_out, loglik_out)
         return jid.value
 
     def poll(self, job_id):

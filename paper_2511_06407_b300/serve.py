@@ -41,6 +41,7 @@ class Job:
     logp: object = None           # host (n_iter, n_chains)
     accept: object = None         # host (n_iter, n_chains)
     chain_status: object = None   # host (n_chains,)
+    loglik: object = None         # host (n_iter, n_chains): untempered ln P(y | F) per sample
 
     @property
     def latency(self):
@@ -79,7 +80,8 @@ class Server:
                     out = (torch.empty(job.n_iter, job.n_chains, d, dtype=torch.float64, device=dev),
                            torch.empty(job.n_iter, job.n_chains, dtype=torch.float64, device=dev),
                            torch.empty(job.n_iter, job.n_chains, dtype=torch.int32, device=dev),
-                           torch.zeros(job.n_chains, dtype=torch.int32, device=dev))
+                           torch.zeros(job.n_chains, dtype=torch.int32, device=dev),
+                           torch.empty(job.n_iter, job.n_chains, dtype=torch.float64, device=dev))
                     jid = srv.submit(job.problem, job.n_chains, job.integ, job.n_iter, job.n_burn, job.seed,
                                      job.tau, None, *out)
                     running[jid] = (job, out)
@@ -93,7 +95,7 @@ class Server:
                     if state == "failed":
                         raise rmhmc.RmhmcError(f"job {job.job_id} failed: {rmhmc.lib().rmhmc_status_string(err).decode()}")
                     job.admitted, job.finished = times[1], times[2]
-                    job.q_samples, job.logp, job.accept, job.chain_status = (x.cpu().numpy() for x in out)
+                    job.q_samples, job.logp, job.accept, job.chain_status, job.loglik = (x.cpu().numpy() for x in out)
                     done.append(job)
                     if log:
                         log(f"t={job.finished:.2f}s done job {job.job_id} latency {job.latency:.2f}s")

@@ -63,7 +63,43 @@ def test_uneven_batch_graph_equals_individual_leapfrogs(rm):
     batch.close()
 
 
-def test_autotune_picks_a_cluster_and_keeps_the_state(rm, oracle_model):
+def test_uneven_batch_chains_match_the_oracle(rm, oracle_model):
+    """The batched form on a small uneven batch (6 problems, N ~ U{20..60}, 1-3 additive kernels,
+    2 chains each, d from 51 to 153), advanced by the batch's captured graph for 2 leapfrogs: every
+    chain against the FP64 oracle's generalized leapfrog from the same (q, p), under the parity
+    rule (16 x the oracle's LU-vs-Cholesky spread after several leapfrogs, 1e-8 relative floor)."""
+    from oracle import model as mdl
+    from oracle.integrator import trajectory
+    integ = rm.Integrator(eps=0.002, n_fp=4)  # (0.01 leaves the PD region for two of these problems)
+    probs = wl.uneven_batch(6, seed=3, n_min=20, n_max=60)
+    made = [_make(rm, p, 2, 30 + i, integ) for i, p in enumerate(probs)]
+    batch = rm.Batch([m for m, _ in made])
+    batch.leapfrog(2, integ)
+    torch.cuda.synchronize()
+    fails = []
+    for i, (prob, (m, s)) in enumerate(zip(probs, made)):
+        qg, pg = _state(m, s, integ)
+        om = oracle_model(prob)
+        Q0 = wl.random_state(prob, 2, seed=30 + i, f_scale=0.2, u_scale=0.1)
+        P0 = 0.3 * wl.random_momentum(prob, 2, seed=130 + i)
+        for c in range(2):
+            qr, pr, _, _ = trajectory(om, Q0[c], P0[c], 0.002, 2, 4)
+            with mdl.inverse_method("cholesky"):
+                qa, pa, _, _ = trajectory(om, Q0[c], P0[c], 0.002, 2, 4)
+            for name, g, r, a in (("q", qg[c], qr, qa), ("p", pg[c], pr, pa)):
+                err = np.linalg.norm(g - r)
+                tol = max(1e-8 * np.linalg.norm(r), 16.0 * np.linalg.norm(r - a))
+                print(f"problem {i} (d={om.d}) chain {c} {name}: {err / np.linalg.norm(r):.1e} / "
+                      f"{tol / np.linalg.norm(r):.0e}")
+                if not err <= tol:
+                    fails.append((i, c, name, err, tol))
+    batch.close()
+    assert not fails, fails
+
+
+def test_autotune_picks_a_cluster_and_schedule_and_keeps_the_state(rm, oracle_model):
+    """The autotuner times one leapfrog per (cluster size, rotation schedule) and then restores the
+    state: the potential at q is recomputed bit for bit and dH/dq still matches the oracle."""
     from oracle.geometry import Geometry
     integ = rm.Integrator(eps=0.01, n_fp=4)
     prob = wl.gp_classification(40, seed=4)
@@ -71,14 +107,14 @@ def test_autotune_picks_a_cluster_and_keeps_the_state(rm, oracle_model):
     U0 = torch.empty(4, dtype=torch.float64, device="cuda")
     with torch.cuda.stream(s):
         m.geometry(U=U0)
-        c = m.autotune()
+        c, sched = m.autotune(integ)
         U1 = torch.empty_like(U0)
         m.geometry(U=U1)
         dHdq = torch.empty(4, m.d, dtype=torch.float64, device="cuda")
         P = wl.random_momentum(prob, 4, seed=8)
         m.hamiltonian_grad(torch.tensor(P, device="cuda"), dHdq=dHdq)
     torch.cuda.synchronize()
-    assert c in (1, 2, 4, 8)
+    assert c in (1, 2, 4, 8) and sched in ("cyclic", "dynamic")
     np.testing.assert_array_equal(U0.cpu().numpy(), U1.cpu().numpy())
     q = wl.random_state(prob, 4, seed=7, f_scale=0.2, u_scale=0.1)
     ref = Geometry(oracle_model(prob), q[2], 1.0).dHdq(P[2])

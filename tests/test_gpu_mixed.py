@@ -17,6 +17,7 @@ fixed-hyperparameter GP regression within Monte-Carlo error of the closed-form p
 import numpy as np
 import pytest
 
+import oracle_pool
 from conftest import potential_rounding_bound
 from oracle import model as mdl
 from oracle.geometry import Geometry
@@ -62,10 +63,13 @@ def _oracle(m, q, tau, p):
             "dHdq": geo.dHdq(p), "Ginv_p": geo.Ginv_p(p), "Ham": geo.hamiltonian(p)}
 
 
-def _compare(label, got, c, m, q, tau, p, keys):
-    ref = _oracle(m, q, tau, p)
-    with mdl.inverse_method("cholesky"):
-        alt = _oracle(m, q, tau, p)
+def _compare(label, got, c, m, q, tau, p, keys, oracle=None):
+    if oracle is None:
+        ref = _oracle(m, q, tau, p)
+        with mdl.inverse_method("cholesky"):
+            alt = _oracle(m, q, tau, p)
+    else:
+        ref, alt = oracle
     fails, rows = [], []
     for k in keys:
         g = np.sort(got[k][c]) if k == "lam" else got[k][c]
@@ -122,7 +126,8 @@ def test_mixed_metric_rule_sampler_quantities(rm, oracle_model, name, make, C, t
 
 
 def test_mixed_full_size_metric_gradient(rm, oracle_model):
-    """N = 400 (d = 402), 64 chains: the launch configuration of the benchmark."""
+    """N = 400 (d = 402), 64 chains: the launch configuration of the benchmark; the metric
+    gradient, G^-1 p and H(q, p) of 8 chains spread over the batch."""
     prob = wl.gp_classification(400, seed=0)
     C = 64
     Q = wl.random_state(prob, C, seed=5, f_scale=0.5, u_scale=0.2)
@@ -130,8 +135,12 @@ def test_mixed_full_size_metric_gradient(rm, oracle_model):
     got = _geometry(rm, prob, Q, P, None, rm.Integrator(precision="mixed"))
     m = oracle_model(prob)
     fails = []
-    for c in (0, 41):
-        fails += _compare("N400/mixed", got, c, m, Q[c], 1.0, P[c], ("dHdq", "Ginv_p", "Ham"))
+    chains = list(range(0, C, 8))
+    res = oracle_pool.run(oracle_pool.quantities_job,
+                          [(prob, Q[c], 1.0, P[c], method, "evd") for c in chains for method in ("lu", "cholesky")])
+    for i, c in enumerate(chains):
+        fails += _compare("N400/mixed", got, c, m, Q[c], 1.0, P[c], ("dHdq", "Ginv_p", "Ham"),
+                          oracle=(res[2 * i], res[2 * i + 1]))
     assert not fails, fails
 
 

@@ -28,12 +28,12 @@ independent amount. Accept/reject decisions must be identical.
 import numpy as np
 import pytest
 
+import oracle_pool
 from conftest import eigen_backward_bound, potential_rounding_bound
 from oracle import model as mdl
 from oracle.geometry import Geometry, eigen_driver
 from oracle.integrator import trajectory
 from oracle.philox import normals
-from oracle.sampler import sample
 from paper_2511_06407_b300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -61,7 +61,7 @@ def check(name, got, ref, alt, base, factor=8.0):
 
 
 def oracle_quantities(m, q, tau, p):
-    geo = Geometry(m, q, tau, 1e6, "coth")
+    geo = Geometry(m, q, tau, 1e6, "coth", with_third=p is not None)
     out = {"U": geo.U, "dU": geo.dU, "H": geo.H, "lam": geo.lam, "G": geo.G()}
     if p is not None:
         out.update(dHdq=geo.dHdq(p), Ginv_p=geo.Ginv_p(p), Ham=geo.hamiltonian(p))
@@ -71,9 +71,10 @@ def oracle_quantities(m, q, tau, p):
 RELATIVE = dict(jacobi_rule="relative")
 
 
-def run_geometry(rm, prob, Q, tau=None, integ=None, P=None):
+def run_geometry(rm, prob, Q, tau=None, integ=None, P=None, schedule="cyclic"):
     C, d = Q.shape
     m = rm.Model(prob, C, tau)
+    m.set_jacobi(0, schedule)
     m.set_state(torch.tensor(Q, device="cuda"), integ=integ or rm.Integrator(**RELATIVE))
     f64 = dict(dtype=torch.float64, device="cuda")
     out = {"U": torch.empty(C, **f64), "dU": torch.empty(C, d, **f64),
@@ -89,12 +90,27 @@ def run_geometry(rm, prob, Q, tau=None, integ=None, P=None):
     return res
 
 
-def compare_chain(label, got, c, m, q, tau, p, keys=None):
-    ref = oracle_quantities(m, q, tau, p)
-    with mdl.inverse_method("cholesky"):
-        alt = oracle_quantities(m, q, tau, p)
-    with eigen_driver("ev"):
-        alt_eig = oracle_quantities(m, q, tau, p)
+def oracle_triplets(prob, Q, taus, P, chains, with_p):
+    """{chain: (X_lu, X_ch, X_ev)}, the three oracle evaluations of every compared chain, computed
+    side by side in the single-BLAS-thread worker pool; with_p(c): include dH/dq, G^-1 p, H(q, p)."""
+    jobs = []
+    for c in chains:
+        p = P[c] if with_p(c) else None
+        for method, driver in (("lu", "evd"), ("cholesky", "evd"), ("lu", "ev")):
+            jobs.append((prob, Q[c], taus[c], p, method, driver))
+    res = oracle_pool.run(oracle_pool.quantities_job, jobs)
+    return {c: tuple(res[3 * i:3 * i + 3]) for i, c in enumerate(chains)}
+
+
+def compare_chain(label, got, c, m, q, tau, p, keys=None, record=None, oracle=None):
+    if oracle is None:
+        ref = oracle_quantities(m, q, tau, p)
+        with mdl.inverse_method("cholesky"):
+            alt = oracle_quantities(m, q, tau, p)
+        with eigen_driver("ev"):
+            alt_eig = oracle_quantities(m, q, tau, p)
+    else:
+        ref, alt, alt_eig = (dict(x) for x in oracle)
     # per quantity, the farther of the two alternative evaluations sets the spread
     for k in alt:
         if k != "lam" and np.linalg.norm(np.asarray(alt_eig[k]) - ref[k]) > np.linalg.norm(np.asarray(alt[k]) - ref[k]):
@@ -108,10 +124,17 @@ def compare_chain(label, got, c, m, q, tau, p, keys=None):
             t = max(t, ubound)
             ok = e <= t
         if k == "Ginv_p":
-            t = max(t, eigen_backward_bound(ref["H"], ref["G"], ref["Ginv_p"], got["sweeps"][c]))
+            eb = eigen_backward_bound(ref["H"], ref["G"], ref["Ginv_p"], got["sweeps"][c])
+            if e > t:
+                print(f"{label} chain {c}: G^-1 p error {e:.2e} is within the eigensolver backward "
+                      f"bound {eb:.2e} only (calibrated tolerance {t:.2e}, 1e-8 base "
+                      f"{1e-8 * np.linalg.norm(ref[k]):.2e})")
+            t = max(t, eb)
             ok = e <= t
         scale = max(float(np.linalg.norm(ref[k])), 1e-300)
         rows.append(f"{k}={e / scale:.1e}/{t / scale:.0e}")
+        if record is not None:
+            record.setdefault(k, []).append(e / scale)
         if not ok:
             fails.append((label, c, k, e, t))
     print(label, "chain", c, "sweeps", got["sweeps"][c], " ".join(rows))
@@ -145,14 +168,15 @@ def test_geometry_and_gradient_parity(rm, oracle_model, name, prob, C, tau):
     assert not fails, fails
 
 
+@pytest.mark.parametrize("schedule", ["cyclic", "dynamic"])
 @pytest.mark.parametrize("name,prob,C,tau", CASES[:2], ids=[c[0] for c in CASES[:2]])
-def test_metric_rule_keeps_sampler_quantities_at_parity(rm, oracle_model, name, prob, C, tau):
+def test_metric_rule_keeps_sampler_quantities_at_parity(rm, oracle_model, name, prob, C, tau, schedule):
     """With the METRIC Jacobi rule (the sampler's default) every quantity the Hamiltonian and its
     gradient use stays at the same tolerance; only eigenvalues inside near-degenerate clusters, and
-    G itself, are left partly unresolved."""
+    G itself, are left partly unresolved. Both rotation orders (cold start from Psi = I)."""
     Q = wl.random_state(prob, C, seed=10)
     P = wl.random_momentum(prob, C, seed=11)
-    got = run_geometry(rm, prob, Q, tau, integ=rm.Integrator(), P=P)
+    got = run_geometry(rm, prob, Q, tau, integ=rm.Integrator(), P=P, schedule=schedule)
     m = oracle_model(prob)
     taus = tau or [1.0] * C
     fails = []
@@ -169,8 +193,10 @@ def test_cold_jacobi_takes_several_sweeps(rm):
     assert np.all(got["sweeps"] >= 3) and np.all(got["sweeps"] <= 30)
 
 
-def test_trajectory_parity_c0(rm, oracle_model):
-    """One 10-leapfrog trajectory (eps = 0.1, 6 fixed-point iterations) of the N = 50 problem."""
+@pytest.mark.parametrize("schedule", ["cyclic", "dynamic"])
+def test_trajectory_parity_c0(rm, oracle_model, schedule):
+    """One 10-leapfrog trajectory (eps = 0.1, 6 fixed-point iterations) of the N = 50 problem, with
+    each order of the Jacobi rotations (every eigen-update after the first is warm-started)."""
     prob = wl.gp_classification(50, seed=0)
     m = oracle_model(prob)
     q0 = wl.random_state(prob, 1, seed=4, f_scale=0.3, u_scale=0.2)[0]
@@ -179,6 +205,7 @@ def test_trajectory_parity_c0(rm, oracle_model):
     with mdl.inverse_method("cholesky"):
         _, _, _, path_alt = trajectory(m, q0, p0, 0.1, 10, 6)
     model = rm.Model(prob, 1)
+    model.set_jacobi(0, schedule)
     model.set_state(torch.tensor(q0[None], device="cuda"), torch.tensor(p0[None], device="cuda"),
                     rm.Integrator(eps=0.1, n_fp=6))
     q = torch.empty(1, m.d, dtype=torch.float64, device="cuda")
@@ -199,9 +226,8 @@ def test_trajectory_parity_c0(rm, oracle_model):
 
 def _sampler_case(rm, m, prob, eps, n_iter, seed=0):
     integ = rm.Integrator(eps=eps, n_leapfrog=10, n_fp=6)
-    ref = sample(m, np.zeros(m.d), n_iter, 0, seed=seed, chain=0, eps=eps, n_leapfrog=10, n_fp=6)
-    with mdl.inverse_method("cholesky"):
-        alt = sample(m, np.zeros(m.d), n_iter, 0, seed=seed, chain=0, eps=eps, n_leapfrog=10, n_fp=6)
+    kw = dict(n_iter=n_iter, n_burn=0, seed=seed, chain=0, eps=eps, n_leapfrog=10, n_fp=6)
+    ref, alt = oracle_pool.run(oracle_pool.sample_job, [(prob, "lu", kw), (prob, "cholesky", kw)])
     model = rm.Model(prob, 1)
     model.set_state(torch.zeros(1, m.d, dtype=torch.float64, device="cuda"), integ=integ)
     f64 = dict(dtype=torch.float64, device="cuda")
@@ -220,46 +246,82 @@ def _sampler_case(rm, m, prob, eps, n_iter, seed=0):
 
 
 def test_sampler_parity_c0(rm, oracle_model):
-    """Algorithm 1 on the N = 50 problem from f = 0, u = 0 (L = 10, 6 fixed-point iterations,
-    seed 0) at eps = 0.01: same Philox draws, same accept/reject decisions, the same chain."""
+    """Config 0's full run: Algorithm 1 on the N = 50 problem from f = 0, u = 0 (L = 10, 6
+    fixed-point iterations, seed 0, 200 iterations) at eps = 0.01: same Philox draws, the same 200
+    accept/reject decisions, and every kept sample and its log posterior within the rule (16 s:
+    the oracle's LU and Cholesky chains drift apart along the run, and so may the CUDA chain)."""
     prob = wl.gp_classification(50, seed=0)
     m = oracle_model(prob)
-    n_iter = 6
+    n_iter = 200
     ref, alt, got = _sampler_case(rm, m, prob, 0.01, n_iter)
     np.testing.assert_array_equal(got["accept"], ref["accept"])
-    assert ref["accept"].any()
+    assert ref["accept"].sum() >= n_iter // 4
+    worst = {"q": 0.0, "logp": 0.0}
     for i in range(n_iter):
-        e, t, ok = check("q", got["q"][i], ref["q"][i], alt["q"][i], 1e-8, 16.0)
-        assert ok, (i, e, t)
-        e, t, ok = check("logp", got["logp"][i], ref["logp"][i], alt["logp"][i], 1e-10, 16.0)
-        assert ok, (i, e, t)
+        for k, base in (("q", 1e-8), ("logp", 1e-10)):
+            e, t, ok = check(k, got[k][i], ref[k][i], alt[k][i], base, 16.0)
+            assert ok, (i, k, e, t)
+            worst[k] = max(worst[k], e / max(float(np.linalg.norm(ref[k][i])), 1e-300))
+    print("config 0, eps 0.01, 200 iterations: acceptance", ref["accept"].mean(),
+          "largest relative error q %.1e, log P %.1e" % (worst["q"], worst["logp"]))
 
 
-def test_sampler_rejects_diverging_proposals_c0(rm, oracle_model):
-    """At eps = 0.1 the trajectories from f = 0, u = 0 leave the region where K is positive
-    definite within two or three leapfrogs (the oracle agrees): every proposal is rejected and the
-    chain stays at its start, with the failure reported in the chain status, not as an error."""
+def test_sampler_decisions_c0_stated_step(rm, oracle_model):
+    """Config 0's full run at its stated step eps = 0.1 (200 iterations, seed 0, from f = 0, u = 0).
+    Most trajectories leave the region where K is positive definite within a few leapfrogs (those
+    proposals are rejected and flagged in the chain status, not raised as errors), and the ones
+    that do not are chaotic. Three FP64 evaluations of the oracle (LU, Cholesky for K^-1, and the
+    QR-iteration eigensolver) reach different trajectory outcomes from some iteration k0 on (69 with
+    this seed: two of them leave the positive-definite region, one ends with a finite energy error
+    of -17); from there no FP64 method fixes the chain. Up to k0 the CUDA chain must take the
+    oracle's decisions and stay within the rule, and the comparison must cover a quarter of the run."""
     prob = wl.gp_classification(50, seed=0)
     m = oracle_model(prob)
-    ref, alt, got = _sampler_case(rm, m, prob, 0.1, 3)
-    np.testing.assert_array_equal(got["accept"], ref["accept"])
-    assert not got["accept"].any()
-    np.testing.assert_array_equal(got["q"], 0.0)
-    assert got["status"] != 0
+    n_iter = 200
+    ref, alt, got = _sampler_case(rm, m, prob, 0.1, n_iter)
+    kw = dict(n_iter=n_iter, n_burn=0, seed=0, chain=0, eps=0.1, n_leapfrog=10, n_fp=6)
+    (ev,) = oracle_pool.run(oracle_pool.sample_job, [(prob, "lu", kw, "ev")])
+
+    def outcome_differs(i):
+        dh = [r["H0"][i] - r["H1"][i] for r in (ref, alt, ev)]
+        fin = [np.isfinite(x) for x in dh]
+        if any(fin) != all(fin):
+            return True
+        return all(fin) and (max(dh) - min(dh)) > 1e-6 * max(1.0, max(abs(x) for x in dh))
+    k0 = next((i for i in range(n_iter) if outcome_differs(i)), n_iter)
+    print(f"eps 0.1: the oracle's three evaluations reach the same outcome on the first {k0} iterations; "
+          f"accepted there: oracle {int(ref['accept'][:k0].sum())}, CUDA {int(got['accept'][:k0].sum())}")
+    assert k0 >= n_iter // 4
+    np.testing.assert_array_equal(got["accept"][:k0], ref["accept"][:k0])
+    for i in range(k0):
+        e, t, ok = check("q", got["q"][i], ref["q"][i], alt["q"][i], 1e-8, 16.0)
+        assert ok, (i, e, t)
+    assert got["status"] != 0  # the failed proposals are reported
+    assert np.all(np.isfinite(got["q"]))
 
 
-def test_full_size_sampled_chains(rm, oracle_model):
-    """N = 400 (d = 402), 64 chains in one batch (the benchmark's launch configuration): sampled
-    chains against the oracle."""
+def test_full_size_all_chains(rm, oracle_model):
+    """N = 400 (d = 402), 64 chains in one batch (the benchmark's launch configuration): every
+    chain's U, dU, Hessian, eigenvalues and G against the oracle, and dH/dq, G^-1 p and H(q, p)
+    (which need the oracle's full d^3 third-derivative tensor) for 16 chains spread over the batch.
+    Prints, per quantity, the largest relative error over the chains."""
     prob = wl.gp_classification(400, seed=0)
     C = 64
     Q = wl.random_state(prob, C, seed=5, f_scale=0.5, u_scale=0.2)
     P = wl.random_momentum(prob, C, seed=6)
     got = run_geometry(rm, prob, Q, P=P)
     m = oracle_model(prob)
-    fails = []
-    for c in (0, 37):
-        fails += compare_chain("N400", got, c, m, Q[c], 1.0, P[c])
+    fails, rec = [], {}
+    third = set(range(0, C, 4))
+    orc = oracle_triplets(prob, Q, [1.0] * C, P, range(C), lambda c: c in third)
+    for c in range(C):
+        if c in third:
+            fails += compare_chain("N400", got, c, m, Q[c], 1.0, P[c], record=rec, oracle=orc[c])
+        else:
+            fails += compare_chain("N400", got, c, m, Q[c], 1.0, None, keys=("U", "dU", "H", "lam", "G"),
+                                   record=rec, oracle=orc[c])
+    print("N400, 64 chains: largest relative error " +
+          " ".join(f"{k}={max(v):.1e} ({len(v)} chains)" for k, v in rec.items()))
     assert not fails, fails
 
 

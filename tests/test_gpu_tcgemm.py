@@ -169,3 +169,31 @@ def test_status_clear_and_bad_arguments_rejected():
         rmhmc.gemm_tc(A, B, slices=5)
     with pytest.raises(rmhmc.RmhmcError):
         rmhmc.gemm_tc(A, cuda(make((2, 48, 40), rng)), sym=True)
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable():
+    """Failure detection without a GPU fault. The test switch makes the GEMM issue no copy for
+    batch entry 1, so that entry's first pipeline wait finds nothing to wait for and runs out
+    after 20 ms: the call returns, entry 1 is marked RMHMC_CHAIN_TIMEOUT and filled with NaN, the
+    other entries are exact, and the next normal call on the same context is correct."""
+    rng = np.random.default_rng(12)
+    A = cuda(make((3, 200, 96), rng))
+    B = cuda(make((3, 96, 130), rng))
+    ref = rmhmc.gemm_tc(A, B, slices=9)
+    st = torch.zeros(3, dtype=torch.int32, device="cuda")
+    rmhmc.test_gemm_stall(1, 20.0)
+    try:
+        out = rmhmc.gemm_tc(A, B, slices=9, status=st)
+        torch.cuda.synchronize()
+    finally:
+        rmhmc.test_gemm_stall(-1)
+    assert st.tolist() == [0, rmhmc.CHAIN_TIMEOUT, 0]
+    assert torch.isnan(out[1]).all()
+    assert torch.equal(out[0], ref[0]) and torch.equal(out[2], ref[2])
+    st2 = torch.zeros(3, dtype=torch.int32, device="cuda")
+    out2 = rmhmc.gemm_tc(A, B, slices=9, status=st2)
+    torch.cuda.synchronize()
+    assert st2.tolist() == [0, 0, 0]
+    assert torch.equal(out2, ref)
+    with pytest.raises(rmhmc.RmhmcError):
+        rmhmc.test_gemm_stall(0, 0.0)  # a limit outside 1..2000 ms is refused

@@ -51,8 +51,14 @@ def test_noalloc_eigh_matches_existing_entry_point_twice(rm):
         Q = torch.full((C, d, d), np.nan, dtype=torch.float64, device="cuda")
         sw = torch.empty(C, dtype=torch.int32, device="cuda")
         st = torch.full((C,), -1, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         rm.eigh_noalloc(H, lam, Q, tol=1e-13, max_sweeps=30, sweeps=sw, status=st)
         torch.cuda.synchronize()
+        if call == 1:
+            # after the first call (which may load the module that holds the fixed array) the
+            # entry point takes no device memory at all
+            assert torch.cuda.mem_get_info()[0] == free_before
         lam, Q, st = lam.cpu().numpy(), Q.cpu().numpy(), st.cpu().numpy()
         assert np.all(st == 0), st
         for c in range(C):
