@@ -546,7 +546,7 @@ def _trajectory_error(rmhmc, prob, q0, seed=7):
             "max_rel_q": rel["q"], "max_rel_p": rel["p"]}
 
 
-def _e2e(rmhmc, prob, C, integ, steps, seed, stream, dev, ws):
+def _e2e(rmhmc, prob, C, integ, steps, seed, stream, dev, ws, jacobi=None):
     """End to end through the public API, as a user runs the sampler from host data: the model is
     created from the host arrays (X, y copied in), the chains' start q0 is copied from pinned host
     memory, and every step is one Algorithm 1 iteration (rmhmc_sample) whose draws (q, log P,
@@ -565,6 +565,8 @@ def _e2e(rmhmc, prob, C, integ, steps, seed, stream, dev, ws):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     model = rmhmc.Model(prob, C, stream=stream)
+    if jacobi:  # the autotuned Jacobi settings of the device-timed arm
+        model.set_jacobi(jacobi["cluster"], jacobi["schedule"])
     q0 = torch.empty(C, d, dtype=torch.float64, device=dev)
     q0.copy_(q0_host, non_blocking=True)
     model.set_state(q0, integ=integ)
@@ -596,6 +598,9 @@ def _run_arm(rmhmc, prob, C, prec, warmup, steps, seed, stream, local, ws, dev):
     model = rmhmc.Model(prob, C, stream=stream)
     integ = rmhmc.Integrator(eps=EPS, n_fp=N_FP, n_leapfrog=N_LEAPFROG, precision=prec)
     model.set_state(torch.zeros(C, model.d, dtype=torch.float64, device=dev), integ=integ)
+    # the library's autotuner picks the Jacobi cluster size and rotation order for this model by
+    # timing one leapfrog of each combination (untimed set-up; the state is restored)
+    jacobi = dict(zip(("cluster", "schedule"), model.autotune(integ)))
     warm_cs = torch.zeros(C, dtype=torch.int32, device=dev)
     model.sample(warmup, 0, seed, chain_status=warm_cs, integ=integ)
     ms, acc, cs, clk = _time_iterations(model, integ, steps, seed, stream, local, ws, dev)
@@ -605,7 +610,7 @@ def _run_arm(rmhmc, prob, C, prec, warmup, steps, seed, stream, local, ws, dev):
     torch.cuda.synchronize()
     model.close()
     return {"ms": ms, "acc": acc, "status": cs, "warm_status": warm_cs.cpu().numpy(), "clk": clk,
-            "prof": prof, "kernels": kernels, "q": q}
+            "prof": prof, "kernels": kernels, "q": q, "jacobi": jacobi}
 
 
 def _status_summary(status):
@@ -644,7 +649,7 @@ def run_b300(args):
     ms = h["ms"]
     integ = rmhmc.Integrator(eps=EPS, n_fp=N_FP, n_leapfrog=N_LEAPFROG, precision=head)
     e_steps = max(1, min(args.steps, args.e2e_steps))
-    e2e_s, h2d, d2h, e2e_status = _e2e(rmhmc, prob, C, integ, e_steps, seed + 1, stream, dev, ws)
+    e2e_s, h2d, d2h, e2e_status = _e2e(rmhmc, prob, C, integ, e_steps, seed + 1, stream, dev, ws, jacobi=h["jacobi"])
 
     if rank != 0:
         if ws > 1:
@@ -692,6 +697,7 @@ def run_b300(args):
         "config": arm_config(C, ws, head),
         "leapfrogs_per_s": C * ws * N_LEAPFROG * args.steps / (ms * 1e-3),
         "acceptance": float(h["acc"].mean()),
+        "jacobi_autotuned": h["jacobi"],
         "timed_region_failures": failed,
         "valid": failed["chains_with_failed_proposal"] == 0,
         "roofline": roof,
@@ -719,6 +725,7 @@ def run_b300(args):
         f_value = job_value(units, ws, r["steps"], r["ms"] * 1e-3)
         line["fp64"] = {"value": f_value, "steps": r["steps"], "ms_per_step": r["ms"] / r["steps"],
                         "acceptance": float(r["acc"].mean()), "roofline": _roofline(rmhmc, r["prof"], C),
+                        "jacobi_autotuned": r["jacobi"],
                         "profile_ms": f_ms, "profile_tflops": f_tf,
                         "roofline_by_category": category_rooflines(r["prof"], pipe_peaks),
                         "timed_region_failures": _status_summary(r["status"]), "clocks": r["clk"]}
@@ -993,8 +1000,10 @@ def run_uneven(args):
     plan = sum(rmhmc.plan_bytes(p, C) for p in probs)
     models, tuned, choice = [], {}, []
     t_setup = time.perf_counter()
+    streams = []
     for i, prob in enumerate(probs):
-        s = torch.cuda.Stream()
+        s = rmhmc.new_stream()  # one distinct stream per problem (torch's pool has 32)
+        streams.append(s)
         with torch.cuda.stream(s):
             m = rmhmc.Model(prob, C, stream=s)
             m.set_state(torch.zeros(C, m.d, dtype=torch.float64, device="cuda"), integ=integ)
@@ -1046,6 +1055,9 @@ def run_uneven(args):
     batch.close()
     for m in models:
         m.close()
+    torch.cuda.synchronize()
+    for s in streams:
+        rmhmc.release_stream(s)
     return 0
 
 

@@ -318,6 +318,11 @@ void rmhmc_server_destroy(rmhmc_server* s);
  * the choice. */
 rmhmc_status rmhmc_autotune(rmhmc_model* m, const rmhmc_integrator* integ, int* cluster_out,
                             int* sched_out);
+/* A new non-blocking CUDA stream on the current device (for batches of many models: each model of
+ * a batch needs a stream of its own, and a framework's stream pool may hand out the same stream
+ * twice), and its release (after the work on it is done). Errors: EINVAL, ECUDA. */
+rmhmc_status rmhmc_stream_create(void** stream_out);
+rmhmc_status rmhmc_stream_destroy(void* stream);
 /* Set the Jacobi cluster size (1, 2, 4, 8, or 0 for the default) and rotation schedule directly. */
 rmhmc_status rmhmc_set_jacobi(rmhmc_model* m, int cluster, int sched);
 

@@ -742,9 +742,11 @@ __global__ void __launch_bounds__(NW * 32)
         if (sbad) { failed = true; break; }   // a non-finite coupling: the test pass reports it
         if (snsolve == 0) break;              // no coupling above 1 left: re-check and stop
       }
-      // ---- phase 1: exact 16 x 16 solves, one warp per pair to solve
+      // ---- phase 1: exact 16 x 16 solves, one warp per pair to solve, dealt to the cluster's CTAs
+      //      in turn (warp w of CTA r takes solves w C + r, ...) so that the FP64-heavy solves of a
+      //      round with few of them spread over the cluster's SMs instead of sharing one SM's FP64 pipe
       const int nsolve = snsolve;
-      for (int k = gw; k < nsolve; k += nwt) {
+      for (int k = warp * C + rank; k < nsolve; k += nwt) {
         const int p = ssolve[k];
         const int I = spair[p].x, J = spair[p].y;
         for (int e = lane; e < SB * SB; e += 32) {

@@ -1255,6 +1255,22 @@ rmhmc_status rmhmc_autotune(rmhmc_model* m, const rmhmc_integrator* integ, int* 
   return check_launch();
 }
 
+rmhmc_status rmhmc_stream_create(void** stream_out) {
+  if (!stream_out) return RMHMC_EINVAL;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return RMHMC_ECUDA;
+  }
+  *stream_out = s;
+  return RMHMC_OK;
+}
+
+rmhmc_status rmhmc_stream_destroy(void* stream) {
+  if (!stream) return RMHMC_EINVAL;
+  return cudaStreamDestroy((cudaStream_t)stream) == cudaSuccess ? RMHMC_OK : RMHMC_ECUDA;
+}
+
 rmhmc_status rmhmc_set_jacobi(rmhmc_model* m, int cluster, int sched) {
   if (!m) return RMHMC_EINVAL;
   if (cluster != 0 && cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8) return RMHMC_EINVAL;

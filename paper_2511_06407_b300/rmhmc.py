@@ -158,6 +158,10 @@ def lib():
     L.rmhmc_autotune.restype = c_int
     L.rmhmc_set_jacobi.argtypes = [c_void_p, c_int, c_int]
     L.rmhmc_set_jacobi.restype = c_int
+    L.rmhmc_stream_create.argtypes = [POINTER(c_void_p)]
+    L.rmhmc_stream_create.restype = c_int
+    L.rmhmc_stream_destroy.argtypes = [c_void_p]
+    L.rmhmc_stream_destroy.restype = c_int
     L.rmhmc_jacobi_counters.argtypes = [c_void_p, POINTER(ctypes.c_longlong)]
     L.rmhmc_jacobi_counters.restype = c_int
     L.rmhmc_plan_bytes.argtypes = [POINTER(ModelDesc), c_int, POINTER(ctypes.c_size_t)]
@@ -428,6 +432,21 @@ def df_peak_tflops(ms_target=200, stream=None):
     out = c_double()
     _check(lib().rmhmc_df_peak(c_void_p(stream.cuda_stream), int(ms_target), ctypes.byref(out)))
     return out.value
+
+
+def new_stream():
+    """A fresh non-blocking CUDA stream (rmhmc_stream_create) as a torch ExternalStream: unlike
+    torch.cuda.Stream(), which takes streams from a pool of 32 in turn, every call gives a distinct
+    stream, as a batch of many models needs. Release it with release_stream once its work is done."""
+    import torch
+    h = c_void_p()
+    _check(lib().rmhmc_stream_create(ctypes.byref(h)))
+    return torch.cuda.ExternalStream(h.value)
+
+
+def release_stream(stream):
+    """Destroy a stream made by new_stream (its queued work completes first)."""
+    _check(lib().rmhmc_stream_destroy(c_void_p(stream.cuda_stream)))
 
 
 def eigh_noalloc(A, lam=None, Q=None, tol=1e-13, max_sweeps=30, sweeps=None, status=None,
