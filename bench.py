@@ -565,8 +565,9 @@ def _e2e(rmhmc, prob, C, integ, steps, seed, stream, dev, ws, jacobi=None):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     model = rmhmc.Model(prob, C, stream=stream)
-    if jacobi:  # the autotuned Jacobi settings of the device-timed arm
+    if jacobi:  # the autotuned settings of the device-timed arm
         model.set_jacobi(jacobi["cluster"], jacobi["schedule"])
+        model.set_gemm_tile(jacobi["gemm_tile"])
     q0 = torch.empty(C, d, dtype=torch.float64, device=dev)
     q0.copy_(q0_host, non_blocking=True)
     model.set_state(q0, integ=integ)
@@ -600,7 +601,7 @@ def _run_arm(rmhmc, prob, C, prec, warmup, steps, seed, stream, local, ws, dev):
     model.set_state(torch.zeros(C, model.d, dtype=torch.float64, device=dev), integ=integ)
     # the library's autotuner picks the Jacobi cluster size and rotation order for this model by
     # timing one leapfrog of each combination (untimed set-up; the state is restored)
-    jacobi = dict(zip(("cluster", "schedule"), model.autotune(integ)))
+    jacobi = dict(zip(("cluster", "schedule", "gemm_tile"), model.autotune(integ)))
     warm_cs = torch.zeros(C, dtype=torch.int32, device=dev)
     model.sample(warmup, 0, seed, chain_status=warm_cs, integ=integ)
     ms, acc, cs, clk = _time_iterations(model, integ, steps, seed, stream, local, ws, dev)
@@ -1011,7 +1012,8 @@ def run_uneven(args):
             if key not in tuned:
                 tuned[key] = m.autotune(integ)
             else:
-                m.set_jacobi(*tuned[key])
+                m.set_jacobi(*tuned[key][:2])
+                m.set_gemm_tile(tuned[key][2])
             choice.append(tuned[key])
             m.sample(1, 0, 7 + i, integ=integ)
         models.append(m)
@@ -1036,8 +1038,8 @@ def run_uneven(args):
     chains = C * len(models)
     ds = [m.d for m in models]
     scheds = {}
-    for c, sc in choice:
-        scheds[f"{sc}/{c}"] = scheds.get(f"{sc}/{c}", 0) + 1
+    for c, sc, nt in choice:
+        scheds[f"{sc}/{c}/{nt}"] = scheds.get(f"{sc}/{c}/{nt}", 0) + 1
     print(json.dumps({"metric": METRIC, "value": chains * SUBSTEPS_PER_LEAPFROG * args.steps / el, "unit": UNIT,
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -1049,7 +1051,7 @@ def run_uneven(args):
                                  "step": "one generalized leapfrog of every chain (13 substeps)",
                                  "d_min": min(ds), "d_max": max(ds), "d_mean": float(np.mean(ds)),
                                  "chains": chains, "device_bytes_planned": plan,
-                                 "autotuned_schedule_cluster": scheds, "autotuned_classes": len(tuned)},
+                                 "autotuned_schedule_cluster_tile": scheds, "autotuned_classes": len(tuned)},
                       "setup_s": t_setup, "graph_capture_s": t_capture,
                       "chain_status_nonzero": bad, "valid": bad == 0, "clocks": clk}), flush=True)
     batch.close()

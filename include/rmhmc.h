@@ -77,7 +77,9 @@ typedef enum { RMHMC_JACOBI_METRIC = 0, RMHMC_JACOBI_RELATIVE = 1 } rmhmc_jacobi
  *   CYCLIC:  round-robin sweeps, every pair of 8-wide index blocks once per sweep;
  *   DYNAMIC: each round pairs the blocks greedily by their largest remaining coupling (under the
  *            stopping rule) and solves only the pairs above the tolerance, which after a warm
- *            start is a few per round; sweeps are then reported as rounds / (blocks - 1). */
+ *            start is a few per round; sweeps are then reported as rounds / (blocks - 1).
+ * The order applies to warm eigen-updates; a cold start (rmhmc_set_state, or every update of the
+ * static ablation, eigen_start = 1) always takes the cyclic order. */
 typedef enum { RMHMC_JACOBI_CYCLIC = 0, RMHMC_JACOBI_DYNAMIC = 1 } rmhmc_jacobi_schedule;
 
 #define RMHMC_MAX_COLS 16
@@ -307,22 +309,36 @@ rmhmc_status rmhmc_server_stats(rmhmc_server* s, double* now_s, int* n_active, i
 /* Finish every submitted job, stop the scheduler and free the server. NULL is a no-op. */
 void rmhmc_server_destroy(rmhmc_server* s);
 
-/* Autotuner of the eigen-update (Sec. 2.4's Jacobi; not part of the method's arithmetic): chooses
- * the model's Jacobi cluster size (CTAs per chain: 1, 2, 4 or 8) and rotation schedule
- * (rmhmc_jacobi_schedule) by timing one generalized leapfrog (integ's eps and n_fp; integ's geometry
- * fields must match the state's) of each of the 8 combinations from the model's current state, and
- * keeping the fastest. The state is then restored: q, p and the eigenbasis as before, the geometry
- * re-evaluated at q (U, dU and the Hessian are recomputed exactly; the basis is already converged
- * there). Without it a model uses the cyclic schedule and the largest cluster that keeps two CTAs
- * per SM. Synchronises the stream; needs a state. *cluster_out and *sched_out (may be NULL) receive
- * the choice. */
+/* Autotuner (not part of the method's arithmetic): chooses the model's Jacobi cluster size (CTAs
+ * per chain: 1, 2, 4 or 8) and rotation schedule (rmhmc_jacobi_schedule) by timing one generalized
+ * leapfrog (integ's eps and n_fp; integ's geometry fields must match the state's) of each of the 8
+ * combinations from the model's current state, then, in the RMHMC_MIXED form, the output tile width
+ * of its tensor-core GEMMs (128 x 64 or 128 x 32 tiles) with the best of those, keeping the fastest.
+ * The state is then restored: q, p and the eigenbasis as before, the geometry re-evaluated at q
+ * (U, dU and the Hessian are recomputed exactly; the basis is already converged there). Without it
+ * a model uses the cyclic schedule, the largest cluster that keeps two CTAs per SM and 64-column
+ * tiles. Synchronises the stream; needs a state. *cluster_out, *sched_out and *tile_out (may be
+ * NULL) receive the choice. */
 rmhmc_status rmhmc_autotune(rmhmc_model* m, const rmhmc_integrator* integ, int* cluster_out,
-                            int* sched_out);
+                            int* sched_out, int* tile_out);
+/* Set the output tile width of the model's tensor-core GEMMs (64 or 32 columns, else EINVAL). */
+rmhmc_status rmhmc_set_gemm_tile(rmhmc_model* m, int nt);
 /* A new non-blocking CUDA stream on the current device (for batches of many models: each model of
  * a batch needs a stream of its own, and a framework's stream pool may hand out the same stream
  * twice), and its release (after the work on it is done). Errors: EINVAL, ECUDA. */
 rmhmc_status rmhmc_stream_create(void** stream_out);
 rmhmc_status rmhmc_stream_destroy(void* stream);
+/* First-order pre-rotation of warm eigen-updates in the RMHMC_MIXED form (on by default; enable 0
+ * or 1, else EINVAL). After a warm start M = Psi^T H Psi is diagonal up to small couplings: every
+ * pair (j, l) that fails the Jacobi stopping rule gets the angle theta_jl = atan(2 m_jl / (m_ll -
+ * m_jj)) / 2 that zeroes its coupling to first order; with the skew matrix A of these angles,
+ * X = I + A + A^2 / 2 (orthogonal up to A^4 / 4) is applied as M <- X^T M X and Psi <- Psi X by
+ * tensor-core GEMMs, and the Jacobi then checks the stopping rule and rotates whatever is left.
+ * Pairs whose angle exceeds 1e-5 (nearly equal diagonal entries) are left to the Jacobi; a chain
+ * takes it only when ||A||_F <= 1e-4 (so that A^4 / 4 is below FP64 rounding); cold starts
+ * and the FP64 path use the Jacobi alone. Not part of the paper's method, which this accelerates:
+ * the eigen-update's result still satisfies the same stopping rule. */
+rmhmc_status rmhmc_set_prerotation(rmhmc_model* m, int enable);
 /* Set the Jacobi cluster size (1, 2, 4, 8, or 0 for the default) and rotation schedule directly. */
 rmhmc_status rmhmc_set_jacobi(rmhmc_model* m, int cluster, int sched);
 
@@ -343,9 +359,10 @@ rmhmc_status rmhmc_profile_read(rmhmc_model* m, double* ms_host, double* flops_h
                                 long long* launches_host);
 const char* rmhmc_profile_category(int i);
 /* Work counters of the eigen-update (Sec. 2.4's Jacobi), summed over the model's chains since the
- * last rmhmc_profile(m, 1) (or model creation): counters_host[0..5] = 16 x 16 x 16 rotation-tile
+ * last rmhmc_profile(m, 1) (or model creation): counters_host[0..7] = 16 x 16 x 16 rotation-tile
  * products of phase 2, rotation rounds applied inside 16 x 16 sub-problems, outer rounds (parallel
- * steps of the block Jacobi), 16 x 16 sub-problems solved, of which rotated, eigen-updates.
+ * steps of the block Jacobi), 16 x 16 sub-problems solved, of which rotated, eigen-updates,
+ * eigen-updates that took the first-order pre-rotation, pairs it rotated.
  * Counted whether or not profiling is on (the autotuner's trial runs excepted). Synchronises the
  * stream. */
 rmhmc_status rmhmc_jacobi_counters(rmhmc_model* m, long long* counters_host);

@@ -124,11 +124,13 @@ void tc_split(cudaStream_t s, const double* X, int ld, long long sX, bool kmaj, 
 // K); sym: the product is symmetric, written as the mirror of its lower triangle. A bounded wait
 // that gives up sets RMHMC_CHAIN_TIMEOUT in status[b / sdiv] (status may be null).
 // mask (optional, batch ints): entries with mask[b] == 0 are skipped by the split and the product.
+// nt: output tile width, 64 (default) or 32 (twice the tiles, half the columns each; the same
+// operands).
 void gemm_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, double alpha, double beta,
              double* C, int ldc, long long sC, int batch, bool sym, int* status, int sdiv,
-             const int* mask = nullptr);
+             const int* mask = nullptr, int nt = 64);
 // bf16 tensor-core FLOPs gemm_tc executes for these operands (padded tiles, all slice products).
-double gemm_tc_tensor_flops(const TcOperand& A, const TcOperand& B, int batch, bool sym);
+double gemm_tc_tensor_flops(const TcOperand& A, const TcOperand& B, int batch, bool sym, int nt = 64);
 
 // ---------------------------------------------------------------- eigen (eigen.cu)
 // Warm-started block-Jacobi on M (dp x dp per chain, symmetric), rotating PsiT's rows alongside;
@@ -143,7 +145,7 @@ struct JacobiWork {
   unsigned long long* tiles;  // n_chains x kJacStats counters (null = not counted): += 16 x 16 x 16
                               // tile products executed (phase 2), rotation rounds applied to
                               // 16 x 16 blocks (phase 1), outer rounds, 16 x 16 sub-problems solved,
-                              // of which rotated, eigen-updates
+                              // of which rotated, eigen-updates, pre-rotated updates and pairs
   float* crit;    // n_chains x nb x nb: coupling criterion per pair of 8-wide blocks (dynamic schedule)
 };
 void jacobi_f64(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,

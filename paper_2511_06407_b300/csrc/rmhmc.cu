@@ -365,6 +365,106 @@ __global__ void k_fma_peak(T* __restrict__ sink, int iters, T b, T c) {
   if (s == (T)12345.678) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// ---- first-order pre-rotation of a warm eigen-update (mixed form)
+// After a warm start M = Psi^T H Psi differs from a diagonal matrix by small couplings. Every pair
+// (j, l) whose coupling fails the Jacobi stopping rule gets the rotation angle that zeroes it to
+// first order, theta_jl = atan(2 m_jl / (m_ll - m_jj)) / 2 (antisymmetric in j, l); with the skew
+// matrix A of these angles, X = I + A + A^2 / 2 is orthogonal up to A^4 / 4 (X^T X = I + A^4 / 4),
+// and X^T M X has every such coupling reduced to second order. The Jacobi that follows checks the
+// stopping rule as usual and rotates whatever is left. A chain takes the pre-rotation only when
+// ||A||_F <= 1e-4 (then ||A^4|| / 4 is below FP64 rounding), i.e. after a warm start; a cold start
+// (Psi = I) is left to the Jacobi. A pair whose first-order angle exceeds kPrerotMaxTheta (nearly
+// equal diagonal entries: the first-order step would be poor) is left out of A for the Jacobi.
+constexpr double kPrerotMaxA = 1e-4;
+constexpr double kPrerotMaxTheta = 1e-5;
+
+// Per chain (one CTA each): ||M||_F^2 and min_{i < d} |m_ii|.
+__global__ void __launch_bounds__(256) k_prerot_norms(const double* __restrict__ Mb, int dp, int d,
+                                                      double* __restrict__ out) {
+  const int c = blockIdx.x;
+  const double* M = Mb + (long long)c * dp * dp;
+  double tot = 0.0, dmin = 1e308;
+  for (long long e = threadIdx.x; e < (long long)dp * dp; e += blockDim.x) {
+    const double v = M[e];
+    tot = fma(v, v, tot);
+  }
+  for (int i = threadIdx.x; i < d; i += blockDim.x) dmin = fmin(dmin, fabs(M[(long long)i * dp + i]));
+  __shared__ double r0[8], r1[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    dmin = fmin(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    r0[threadIdx.x >> 5] = tot;
+    r1[threadIdx.x >> 5] = dmin;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 1e308;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += r0[w];
+      b = fmin(b, r1[w]);
+    }
+    out[4 * c] = a;
+    out[4 * c + 1] = b;
+    out[4 * c + 2] = 0.0;  // sum of theta^2 (filled by k_prerot_gen)
+    out[4 * c + 3] = 0.0;  // pairs rotated
+  }
+}
+
+// A (skew) and X = I + A for every chain; the coupling test is the Jacobi's (METRIC or RELATIVE,
+// with the double-float rounding floor 4 * 2^-48 ||M||_F). Grid (blocks over dp^2, chains).
+__global__ void k_prerot_gen(const double* __restrict__ Mb, const double* __restrict__ nrm, int dp, int d,
+                             int rule, double tol, const int* __restrict__ status, double* __restrict__ Ab,
+                             double* __restrict__ Xb, double* __restrict__ acc) {
+  const int c = blockIdx.y;
+  const long long DD = (long long)dp * dp;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= DD) return;
+  const int j = (int)(e / dp), l = (int)(e % dp);
+  const double* M = Mb + c * DD;
+  double th = 0.0;
+  if (j != l && j < d && l < d && status[c] == 0) {
+    const double v = M[e];
+    const double djj = M[(long long)j * dp + j], dll = M[(long long)l * dp + l];
+    const double floor2 = fmax(16.0 * 1.2621774483536189e-29 * nrm[4 * c], 1e-300);
+    const double dmin2 = fmax(nrm[4 * c + 1] * nrm[4 * c + 1], 1e-300);
+    const double v2 = v * v, p = fabs(djj * dll);
+    const double fl = rule == RMHMC_JACOBI_RELATIVE
+                          ? fmin(floor2, fmax(1e-26 * fmax(djj * djj, dll * dll), 1e-300))
+                          : floor2;
+    const bool unconv = v2 > fl && (rule == RMHMC_JACOBI_METRIC ? v2 * dmin2 > tol * tol * p * p
+                                                                 : v2 > tol * tol * p);
+    if (unconv) {
+      th = 0.5 * atan(2.0 * v / (dll - djj));
+      if (!isfinite(th)) th = 1.0;  // (a non-finite coupling: too large, the chain is left alone)
+      else if (fabs(th) > kPrerotMaxTheta) th = 0.0;  // left to the Jacobi
+    }
+  }
+  Ab[c * DD + e] = th;
+  Xb[c * DD + e] = (j == l ? 1.0 : 0.0) + th;
+  if (th != 0.0) {
+    atomicAdd(&acc[4 * c + 2], th * th);
+    atomicAdd(&acc[4 * c + 3], 1.0);
+  }
+}
+
+// mask[c] = 1 for the chains that take the pre-rotation (some pair above the tolerance and
+// ||A||_F <= kPrerotMaxA)
+// (and, where counted, adds the chains and pairs pre-rotated to the eigen-update's counters)
+__global__ void k_prerot_mask(const double* __restrict__ acc, int C, int* __restrict__ mask,
+                              unsigned long long* __restrict__ counters) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const int on = (acc[4 * c + 3] > 0.0 && acc[4 * c + 2] <= kPrerotMaxA * kPrerotMaxA) ? 1 : 0;
+  mask[c] = on;
+  if (counters && on) {
+    counters[(long long)kJacStats * c + 6] += 1ull;
+    counters[(long long)kJacStats * c + 7] += (unsigned long long)(acc[4 * c + 3] * 0.5);
+  }
+}
+
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 // Double-float multiply-add throughput probe: eight independent Dot2 accumulations per thread (the
@@ -468,6 +568,9 @@ struct rmhmc_model {
   int N = 0, n = 0, P = 0, d = 0, dp = 0, C = 0;
   int cluster = 1;
   int jacobi_sched = RMHMC_JACOBI_CYCLIC;  // rmhmc_jacobi_schedule
+  int prerot = 1;  // first-order pre-rotation of warm eigen-updates in the mixed form
+  bool cold = false;  // the next eigen-update starts from Psi = I (rmhmc_set_state)
+  int tc_nt = 64;  // output tile width of the model's tensor-core GEMMs (64 or 32; rmhmc_autotune)
   bool has_state = false;
   int g_kind = 0, max_sweeps = 30, reorth_every = 10, precision = 0, jacobi_rule = 0, eigen_start = 0;
   double alpha = 1e6, tol = 1e-13;
@@ -520,6 +623,11 @@ struct rmhmc_model {
   uint8_t *tcPhiT = nullptr, *tcPhi = nullptr;
   bool tc_phi_ok = false;
   int* tcmask = nullptr;  // per chain: re-orthonormalisation due at this eigen-update
+  // the pre-rotation: X^T M X product scratch (dp x dp per chain), per-chain norms and counts, and
+  // the chains that take it
+  double* Zp = nullptr;
+  double* pr_acc = nullptr;
+  int* pr_mask = nullptr;
 };
 
 namespace {
@@ -626,8 +734,8 @@ void dual_model_layer(rmhmc_model* m, bool third) {
   if (tc) {  // row i of op(A) and row j of op(B)^T are columns of L^-1
     PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Aux, N, NN, false, B, ka);
     PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Aux, N, NN, false, B, kb);
-    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(ka, kb, B, true))
-    gemm_tc(s, ka, kb, 1.0, 0.0, m->Kinv, N, NN, B, true, m->status, n);
+    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(ka, kb, B, true, m->tc_nt))
+    gemm_tc(s, ka, kb, 1.0, 0.0, m->Kinv, N, NN, B, true, m->status, n, nullptr, m->tc_nt);
   } else {
     PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, true, true))
     gemm_f64(s, true, false, N, N, N, 1.0, m->Aux, N, NN, m->Aux, N, NN, 0.0, m->Kinv, N, NN, B, true, true);
@@ -639,8 +747,8 @@ void dual_model_layer(rmhmc_model* m, bool third) {
   if (tc) {
     PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Kinv, N, NN, true, B, ka);
     PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->D1, N, NN, false, B, kb);
-    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(ka, kb, B, false))
-    gemm_tc(s, ka, kb, 1.0, 0.0, m->S, N, NN, B, false, m->status, n);
+    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(ka, kb, B, false, m->tc_nt))
+    gemm_tc(s, ka, kb, 1.0, 0.0, m->S, N, NN, B, false, m->status, n, nullptr, m->tc_nt);
   } else {
     PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, false, false))
     gemm_f64(s, false, false, N, N, N, 1.0, m->Kinv, N, NN, m->D1, N, NN, 0.0, m->S, N, NN, B, false, false);
@@ -650,11 +758,11 @@ void dual_model_layer(rmhmc_model* m, bool third) {
     // slices of S's rows reused
     PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->S, N, NN, true, B, ka);
     PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Kinv, N, NN, true, B, kb);
-    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(ka, kb, B, true))
-    gemm_tc(s, ka, kb, 1.0, 0.0, m->Aux, N, NN, B, true, m->status, n);
+    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(ka, kb, B, true, m->tc_nt))
+    gemm_tc(s, ka, kb, 1.0, 0.0, m->Aux, N, NN, B, true, m->status, n, nullptr, m->tc_nt);
     PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->S, N, NN, false, B, kb);
-    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(ka, kb, B, false))
-    gemm_tc(s, ka, kb, 1.0, 0.0, m->S2, N, NN, B, false, m->status, n);
+    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(ka, kb, B, false, m->tc_nt))
+    gemm_tc(s, ka, kb, 1.0, 0.0, m->S2, N, NN, B, false, m->status, n, nullptr, m->tc_nt);
   } else if (third) {
     PROF(m, CAT_GEMM, Bf * gemm_flops(Nf, Nf, Nf, true, false))
     gemm_f64(s, false, false, N, N, N, 1.0, m->S, N, NN, m->Kinv, N, NN, 0.0, m->Aux, N, NN, B, true, false);
@@ -747,11 +855,11 @@ void primal_model_layer(rmhmc_model* m) {
         const TcOperand pa = phi_operand(m, true);
         const TcOperand zb = tc_operand(m->tcB, P, N, kSlicesK, C, true);
         PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Z, P, NP, false, C, zb);
-        PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(pa, zb, C, true) * (k != j ? 2 : 1))
+        PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(pa, zb, C, true, m->tc_nt) * (k != j ? 2 : 1))
         {
-          gemm_tc(s, pa, zb, 1.0, 0.0, m->H + (long long)j * P * dp + k * P, dp, DD, C, true, m->status, 1);
+          gemm_tc(s, pa, zb, 1.0, 0.0, m->H + (long long)j * P * dp + k * P, dp, DD, C, true, m->status, 1, nullptr, m->tc_nt);
           if (k != j)
-            gemm_tc(s, pa, zb, 1.0, 0.0, m->H + (long long)k * P * dp + j * P, dp, DD, C, true, m->status, 1);
+            gemm_tc(s, pa, zb, 1.0, 0.0, m->H + (long long)k * P * dp + j * P, dp, DD, C, true, m->status, 1, nullptr, m->tc_nt);
         }
         continue;
       }
@@ -772,6 +880,47 @@ void primal_model_layer(rmhmc_model* m) {
 // --- geometry at the current q: U, dU, Hessian, warm-started eigendecomposition, g(lambda);
 //     with `third`, also the third-derivative operator (the dual model's A1, S^2 and F-phase
 //     statistics; the primal model needs no more than l''').
+// The first-order pre-rotation of a warm eigen-update (see k_prerot_gen), on the tensor cores:
+// A and X = I + A (W and Y are free during the eigen-update), X += A A / 2, then M <- X^T (M X)
+// and Psi^T <- X^T Psi^T for the chains in pr_mask. The products read their operands' slices, so the
+// outputs may overwrite M and Psi^T.
+void prerotate(rmhmc_model* m) {
+  cudaStream_t s = m->stream;
+  const int C = m->C, dp = m->dp, d = m->d;
+  const long long DD = (long long)dp * dp;
+  const int S = kSlicesD;
+  double* A = m->W;
+  double* X = m->Y;
+  PROF(m, CAT_JACOBI_DF, 0)
+  k_prerot_norms<<<C, 256, 0, s>>>(m->M, dp, d, m->pr_acc);
+  PROF(m, CAT_JACOBI_DF, 0)
+  k_prerot_gen<<<dim3(nblk(DD), C), 256, 0, s>>>(m->M, m->pr_acc, dp, d, m->jacobi_rule, m->tol, m->status, A, X,
+                                                 m->pr_acc);
+  PROF(m, CAT_JACOBI_DF, 0)
+  k_prerot_mask<<<nblk(C), 256, 0, s>>>(m->pr_acc, C, m->pr_mask, m->jw.tiles);
+  const int* mk = m->pr_mask;
+  TcOperand oa = tc_operand(m->tcA, dp, dp, S, C, false), ob = tc_operand(m->tcB, dp, dp, S, C, true);
+  // X += A A / 2
+  PROF(m, CAT_GEMM_TC, 0) tc_split(s, A, dp, DD, true, C, oa, mk);
+  PROF(m, CAT_GEMM_TC, 0) tc_split(s, A, dp, DD, false, C, ob, mk);
+  PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(oa, ob, C, false, m->tc_nt))
+  gemm_tc(s, oa, ob, 0.5, 1.0, X, dp, DD, C, false, m->status, 1, mk, m->tc_nt);
+  // Z = M X
+  PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->M, dp, DD, true, C, oa, mk);
+  PROF(m, CAT_GEMM_TC, 0) tc_split(s, X, dp, DD, false, C, ob, mk);
+  PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(oa, ob, C, false, m->tc_nt))
+  gemm_tc(s, oa, ob, 1.0, 0.0, m->Zp, dp, DD, C, false, m->status, 1, mk, m->tc_nt);
+  // M = X^T Z (symmetric)
+  PROF(m, CAT_GEMM_TC, 0) tc_split(s, X, dp, DD, false, C, oa, mk);
+  PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Zp, dp, DD, false, C, ob, mk);
+  PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(oa, ob, C, true, m->tc_nt))
+  gemm_tc(s, oa, ob, 1.0, 0.0, m->M, dp, DD, C, true, m->status, 1, mk, m->tc_nt);
+  // Psi^T = X^T Psi^T (op(A) = X^T is still split in oa)
+  PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->PsiT, dp, DD, false, C, ob, mk);
+  PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(oa, ob, C, false, m->tc_nt))
+  gemm_tc(s, oa, ob, 1.0, 0.0, m->PsiT, dp, DD, C, false, m->status, 1, mk, m->tc_nt);
+}
+
 void eval_geometry(rmhmc_model* m, bool third) {
   cudaStream_t s = m->stream;
   const int C = m->C, dp = m->dp, d = m->d;
@@ -793,27 +942,37 @@ void eval_geometry(rmhmc_model* m, bool third) {
     TcOperand pa = tc_operand(m->tcA, d, dp, S, C, false), pb = tc_operand(m->tcB, d, dp, S, C, true);
     PROF(m, CAT_MGS, 0) tc_split(s, m->PsiT, dp, DD, true, C, pa, m->tcmask);
     PROF(m, CAT_MGS, 0) tc_split(s, m->PsiT, dp, DD, true, C, pb, m->tcmask);
-    PROF(m, CAT_MGS, 0) gemm_tc(s, pa, pb, 1.0, 0.0, m->Y, dp, DD, C, true, m->status, 1, m->tcmask);
+    PROF(m, CAT_MGS, 0) gemm_tc(s, pa, pb, 1.0, 0.0, m->Y, dp, DD, C, true, m->status, 1, m->tcmask, m->tc_nt);
     pa = tc_operand(m->tcA, d, d, S, C, false);
     pb = tc_operand(m->tcB, dp, d, S, C, true);
     PROF(m, CAT_MGS, 0) tc_split(s, m->Y, dp, DD, true, C, pa, m->tcmask);
     PROF(m, CAT_MGS, 0) tc_split(s, m->PsiT, dp, DD, false, C, pb, m->tcmask);
-    PROF(m, CAT_MGS, 0) gemm_tc(s, pa, pb, -0.5, 1.5, m->PsiT, dp, DD, C, false, m->status, 1, m->tcmask);
+    PROF(m, CAT_MGS, 0) gemm_tc(s, pa, pb, -0.5, 1.5, m->PsiT, dp, DD, C, false, m->status, 1, m->tcmask, m->tc_nt);
   } else if (m->reorth_every > 0) {
     PROF(m, CAT_MGS, 0)
     mgs_rows_f64(s, m->PsiT, dp, d, C, m->eig_count, m->reorth_every, m->cluster);
   }
   gemm_dd(m, false, true, m->H, m->PsiT, m->Y, false);
   gemm_dd(m, false, false, m->PsiT, m->Y, m->M, true);
+  // a cold start (Psi = I: rmhmc_set_state, or every update of the static ablation) takes the
+  // cyclic order: the dynamic order's greedy matching is for the few couplings a warm start leaves
+  // (on the dual model's cold start it can exceed the round limit), and the pre-rotation needs small
+  // angles
+  const bool cold = m->cold || m->eigen_start == 1;
+  const int sched = cold ? RMHMC_JACOBI_CYCLIC : m->jacobi_sched;
+  if (m->prerot && !cold && use_tc(m, dp, dp)) {
+    prerotate(m);
+    m->tc_pa_ok = m->tc_pb_ok = false;
+  }
   if (m->precision == RMHMC_MIXED) {
     // rotations in double-float pairs; W and Y serve as the pair buffers (free during the update)
     PROF(m, CAT_JACOBI_DF, 0)
     jacobi_df(s, m->M, m->PsiT, m->lam, dp, d, C, m->jacobi_rule, m->tol, m->max_sweeps, m->status,
-              m->sweeps_last, m->sweeps_acc, m->jw, m->cluster, m->W, m->Y, m->jacobi_sched);
+              m->sweeps_last, m->sweeps_acc, m->jw, m->cluster, m->W, m->Y, sched);
   } else {
     PROF(m, CAT_JACOBI, 0)
     jacobi_f64(s, m->M, m->PsiT, m->lam, dp, d, C, m->jacobi_rule, m->tol, m->max_sweeps, m->status,
-               m->sweeps_last, m->sweeps_acc, m->jw, m->cluster, m->jacobi_sched);
+               m->sweeps_last, m->sweeps_acc, m->jw, m->cluster, sched);
   }
   m->tc_pa_ok = m->tc_pb_ok = false;  // the eigen-update rotated Psi^T
   PROF(m, CAT_VECTOR, 0)
@@ -840,8 +999,8 @@ void gemm_dd(rmhmc_model* m, bool ta, bool tb, const double* A, const double* B,
       PROF(m, CAT_GEMM_TC, 0) tc_split(m->stream, B, dp, DD, tb, m->C, ob);
       if (pb) m->tc_pb_ok = true;
     }
-    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(oa, ob, m->C, sym))
-    gemm_tc(m->stream, oa, ob, 1.0, 0.0, out, dp, DD, m->C, sym, m->status, 1);
+    PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(oa, ob, m->C, sym, m->tc_nt))
+    gemm_tc(m->stream, oa, ob, 1.0, 0.0, out, dp, DD, m->C, sym, m->status, 1, nullptr, m->tc_nt);
   } else {
     PROF(m, CAT_GEMM, fl)
     gemm_f64(m->stream, ta, tb, dp, dp, dp, 1.0, A, dp, DD, B, dp, DD, 0.0, out, dp, DD, m->C, sym, false);
@@ -890,8 +1049,8 @@ void grad_h(rmhmc_model* m, const double* x, double* out) {
           const TcOperand pa = phi_operand(m, false);
           const TcOperand wb = tc_operand(m->tcB, P, P, kSlicesK, C, true);
           PROF(m, CAT_GEMM_TC, 0) tc_split(s, Wjk, dp, DD, false, C, wb);
-          PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(pa, wb, C, false))
-          gemm_tc(s, pa, wb, 1.0, 0.0, m->Z, P, NP, C, false, m->status, 1);
+          PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(pa, wb, C, false, m->tc_nt))
+          gemm_tc(s, pa, wb, 1.0, 0.0, m->Z, P, NP, C, false, m->status, 1, nullptr, m->tc_nt);
         } else {
           PROF(m, CAT_GEMM, 2.0 * Cf * Nf * Pf * Pf)
           gemm_f64(s, false, false, N, P, P, 1.0, m->Phi, P, 0, Wjk, dp, DD, 0.0, m->Z, P, NP, C, false, false);
@@ -1050,6 +1209,9 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
   ALLOC(m->jw.flags, (size_t)C * np);
   ALLOC(m->jw.tiles, (size_t)kJacStats * C);
   ALLOC(m->jw.crit, (size_t)C * (dp / kJacBlk) * (dp / kJacBlk));
+  ALLOC(m->Zp, (size_t)C * DD);
+  ALLOC(m->pr_acc, (size_t)4 * C);
+  ALLOC(m->pr_mask, (size_t)C);
 #undef ALLOC
   return st;
 }
@@ -1188,7 +1350,7 @@ rmhmc_status rmhmc_batch_leapfrog(rmhmc_batch* b, const rmhmc_integrator* integ,
 }
 
 rmhmc_status rmhmc_autotune(rmhmc_model* m, const rmhmc_integrator* integ, int* cluster_out,
-                            int* sched_out) {
+                            int* sched_out, int* tile_out) {
   if (!m || !m->has_state || m->prof) return RMHMC_EINVAL;
   rmhmc_status st = check_integ(m, integ, false);
   if (st != RMHMC_OK) return st;
@@ -1224,34 +1386,53 @@ rmhmc_status rmhmc_autotune(rmhmc_model* m, const rmhmc_integrator* integ, int* 
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RMHMC_ECUDA;
   const int cands[4] = {1, 2, 4, 8};
   const int scheds[2] = {RMHMC_JACOBI_CYCLIC, RMHMC_JACOBI_DYNAMIC};
+  const int tiles[2] = {64, 32};
   double best = 1e300;
-  int best_c = m->cluster, best_s = m->jacobi_sched;
-  // one untimed trial first (first-launch costs), then one generalized leapfrog per candidate
-  for (int t = -1; t < 8; ++t) {
-    if (t >= 0) {
-      m->jacobi_sched = scheds[t / 4];
-      m->cluster = cands[t % 4];
-    }
+  int best_c = m->cluster, best_s = m->jacobi_sched, best_t = m->tc_nt;
+  auto trial = [&](float* ms) -> bool {
     restore();
     cudaEventRecord(e0, s);
     leapfrog_step(m, integ->eps, integ->n_fp);
     cudaEventRecord(e1, s);
-    if (cudaEventSynchronize(e1) != cudaSuccess) return RMHMC_ECUDA;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (t >= 0 && ms < best) {
+    if (cudaEventSynchronize(e1) != cudaSuccess) return false;
+    cudaEventElapsedTime(ms, e0, e1);
+    return true;
+  };
+  // one untimed trial first (first-launch costs); then one generalized leapfrog per (cluster size,
+  // rotation order) at the current tile width, then the other tile width with the best of those
+  // (a tile width only matters where the mixed form's products run on the tensor cores)
+  float ms = 0.f;
+  if (!trial(&ms)) return RMHMC_ECUDA;
+  for (int t = 0; t < 8; ++t) {
+    m->jacobi_sched = scheds[t / 4];
+    m->cluster = cands[t % 4];
+    if (!trial(&ms)) return RMHMC_ECUDA;
+    if (ms < best) {
       best = ms;
       best_c = m->cluster;
       best_s = m->jacobi_sched;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   m->cluster = best_c;
   m->jacobi_sched = best_s;
+  if (m->precision == RMHMC_MIXED) {
+    for (int t : tiles) {
+      if (t == best_t) continue;
+      m->tc_nt = t;
+      if (!trial(&ms)) return RMHMC_ECUDA;
+      if (ms < best) {
+        best = ms;
+        best_t = t;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  m->tc_nt = best_t;
   restore();
   if (cluster_out) *cluster_out = best_c;
   if (sched_out) *sched_out = best_s;
+  if (tile_out) *tile_out = best_t;
   return check_launch();
 }
 
@@ -1269,6 +1450,18 @@ rmhmc_status rmhmc_stream_create(void** stream_out) {
 rmhmc_status rmhmc_stream_destroy(void* stream) {
   if (!stream) return RMHMC_EINVAL;
   return cudaStreamDestroy((cudaStream_t)stream) == cudaSuccess ? RMHMC_OK : RMHMC_ECUDA;
+}
+
+rmhmc_status rmhmc_set_gemm_tile(rmhmc_model* m, int nt) {
+  if (!m || (nt != 64 && nt != 32)) return RMHMC_EINVAL;
+  m->tc_nt = nt;
+  return RMHMC_OK;
+}
+
+rmhmc_status rmhmc_set_prerotation(rmhmc_model* m, int enable) {
+  if (!m || (enable != 0 && enable != 1)) return RMHMC_EINVAL;
+  m->prerot = enable;
+  return RMHMC_OK;
 }
 
 rmhmc_status rmhmc_set_jacobi(rmhmc_model* m, int cluster, int sched) {
@@ -1344,7 +1537,7 @@ rmhmc_status rmhmc_jacobi_counters(rmhmc_model* m, long long* counters_host) {
   if (cudaMemcpy(tl.data(), m->jw.tiles, tl.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
       cudaSuccess)
     return RMHMC_ECUDA;
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < 8; ++k) {
     long long v = 0;
     for (int c = 0; c < m->C; ++c) v += (long long)tl[(size_t)kJacStats * c + k];
     counters_host[k] = v;
@@ -1649,7 +1842,9 @@ rmhmc_status rmhmc_set_state(rmhmc_model* m, const rmhmc_integrator* integ, cons
   cudaMemsetAsync(m->eig_count, 0, C * sizeof(int), s);
   cudaMemsetAsync(m->sweeps_acc, 0, C * sizeof(int), s);
   k_set_identity<<<nblk((long long)C * dp * dp), 256, 0, s>>>(m->PsiT, dp, C);
+  m->cold = true;
   eval_geometry(m, true);
+  m->cold = false;
   m->has_state = true;
   return check_launch();
 }

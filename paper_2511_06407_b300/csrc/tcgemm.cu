@@ -43,27 +43,31 @@ namespace rmhmc {
 namespace {
 
 constexpr int TC_M = 128;             // output tile rows = MMA M (one TMEM lane per row)
-constexpr int TC_N = 64;              // output tile columns = MMA N
+constexpr int TC_N = 64;              // rows of a B-operand tile in the split layout (output columns)
 constexpr int TC_K = 16;              // K of one bf16 MMA
 constexpr int TC_NACC = 8;            // accumulators: groups 2..8, then one for groups >= 9
-constexpr int TC_COLS = 512;          // tensor-memory columns allocated (TC_NACC * TC_N <= 512)
+// A launch computes output tiles of 128 x NT, NT = 64 (one B-operand tile) or 32 (half of one: the
+// finer grid of the tile-width choice); the accumulators take TC_NACC * NT tensor-memory columns.
 constexpr int TC_THREADS = 320;        // warp 0 loads, warp 1 issues MMAs, warps 2..9 epilogue
 constexpr int TC_KSTEPS_MAX = 32;     // K steps per launch (k <= 512: exact group sums)
 constexpr int kExpBad = 0x7fffffff;   // exponent marker of a row holding a non-finite value
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 constexpr int A_SLICE = TC_M * TC_K * 2;  // bytes of one slice of an A stage (4096)
-constexpr int B_SLICE = TC_N * TC_K * 2;  // (2048)
+constexpr int B_SLICE = TC_N * TC_K * 2;  // (2048), of which a 32-row half is 1024 contiguous bytes
 
-template <int S>
+template <int S, int NT>
 struct TcCfg {
-  static constexpr int STAGE = S * (A_SLICE + B_SLICE);
+  static constexpr int BS = NT * TC_K * 2;  // bytes of one B slice in a stage
+  static constexpr int COLS = TC_NACC * NT;  // tensor-memory columns (a power of two >= 32)
+  static constexpr int STAGE = S * (A_SLICE + BS);
   static constexpr int NST_FIT = (226 * 1024) / STAGE;
   static constexpr int NST = NST_FIT > 4 ? 4 : NST_FIT;
   static constexpr int BAR_OFF = NST * STAGE;
   static constexpr int SMEM = BAR_OFF + 256;
   static constexpr int NA = S < TC_NACC ? S : TC_NACC;  // accumulators in use
   static_assert(NST >= 2, "at least two pipeline stages");
+  static_assert(NT == 64 || NT == 32, "output tile width");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -349,13 +353,13 @@ struct TcArgs {
   int stall_entry;             // test switch: entry whose loads are never issued (-1: none)
 };
 
-template <int S>
+template <int S, int NT>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
-  using Cfg = TcCfg<S>;
+  using Cfg = TcCfg<S, NT>;
   constexpr int NST = Cfg::NST;
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tn = blockIdx.x, tm = blockIdx.y, b = blockIdx.z;
-  const int m0 = tm * TC_M, n0 = tn * TC_N;
+  const int m0 = tm * TC_M, n0 = tn * NT;
   if (a.sym && m0 + TC_M - 1 < n0) return;  // strictly above the diagonal: mirrored by others
   if (a.mask && !a.mask[b]) return;          // entry skipped (before any allocation)
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -376,7 +380,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_addr(tmem_slot)),
-                 "r"(TC_COLS)
+                 "r"(Cfg::COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -401,11 +405,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
           break;
         }
         const uint32_t full = full0 + 8 * st;
-        mbar_expect_tx(full, S * (A_SLICE + B_SLICE));
+        mbar_expect_tx(full, S * (A_SLICE + Cfg::BS));
         const uint32_t sa = smem_addr(smem + st * Cfg::STAGE), sb = sa + S * A_SLICE;
         const long long ks = a.ks0 + it;
         bulk_load(sa, Ab + ((long long)tm * a.KS + ks) * S * A_SLICE, S * A_SLICE, full);
-        bulk_load(sb, Bb + ((long long)tn * a.KS + ks) * S * B_SLICE, S * B_SLICE, full);
+        if (NT == TC_N) {
+          bulk_load(sb, Bb + ((long long)tn * a.KS + ks) * S * B_SLICE, S * B_SLICE, full);
+        } else {  // the 32-row half (tn % 2) of B tile tn / 2, slice by slice
+          const uint8_t* src = Bb + ((long long)(tn >> 1) * a.KS + ks) * S * B_SLICE + (tn & 1) * Cfg::BS;
+#pragma unroll
+          for (int i = 0; i < S; ++i) bulk_load(sb + i * Cfg::BS, src + i * B_SLICE, Cfg::BS, full);
+        }
         issued = it + 1;
       }
       // every issued copy has landed before the CTA may exit (already true unless a wait failed)
@@ -422,8 +432,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
         }
         tc_fence_after();
         const uint32_t sa = smem_addr(smem + st * Cfg::STAGE), sb = sa + S * A_SLICE;
-        // Accumulator g sits at TMEM column 64 g and the B slices follow each other in shared
-        // memory, so one MMA with N = 64 c multiplies A_i by B_j .. B_(j+c-1) straight into the
+        // Accumulator g sits at TMEM column NT g and the B slices follow each other in shared
+        // memory, so one MMA with N = NT c multiplies A_i by B_j .. B_(j+c-1) straight into the
         // accumulators of groups i + j .. i + j + c - 1. Pairs past the last separate group go one
         // by one into the shared accumulator. At the first K step the i = 0 products overwrite.
 #pragma unroll
@@ -434,11 +444,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
 #pragma unroll
           for (int j0 = 0; j0 <= jmax; j0 += 4) {
             const int c = (jmax - j0 + 1) < 4 ? (jmax - j0 + 1) : 4;
-            tc_mma(tmem + (i + j0) * TC_N, da, smem_desc(sb + j0 * B_SLICE), idesc_bf16(c * TC_N), en);
+            tc_mma(tmem + (i + j0) * NT, da, smem_desc(sb + j0 * Cfg::BS), idesc_bf16(c * NT), en);
           }
 #pragma unroll
           for (int j = jmax + 1; j < S - i; ++j)
-            tc_mma(tmem + (TC_NACC - 1) * TC_N, da, smem_desc(sb + j * B_SLICE), idesc_bf16(TC_N), 1u);
+            tc_mma(tmem + (TC_NACC - 1) * NT, da, smem_desc(sb + j * Cfg::BS), idesc_bf16(NT), 1u);
         }
         tc_commit(empty0 + 8 * st);  // frees the stage once these MMAs have read it
       }
@@ -448,12 +458,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
   } else {
     const int ew = warp - 2;    // epilogue warp 0..7
     const int q = warp % 4;     // the TMEM lane quarter this warp may read
-    const int half = ew / 4;    // and its 32 of the tile's 64 columns
-    int* sec = reinterpret_cast<int*>(smem + Cfg::BAR_OFF - TC_N * sizeof(int));
+    const int half = ew / 4;    // and its half of the tile's NT columns
+    int* sec = reinterpret_cast<int*>(smem + Cfg::BAR_OFF - NT * sizeof(int));
     const bool ok = mbar_wait(done, 0, a.wait_ns);
     tc_fence_after();
     // the pipeline stages are free now: column exponents, then one 32 x 17 staging tile per warp
-    if (threadIdx.x - 64 < TC_N) {
+    if (threadIdx.x - 64 < NT) {
       const int col = n0 + threadIdx.x - 64;
       sec[threadIdx.x - 64] = col < a.n ? a.eB[b * a.eBs + col] : 0;
     }
@@ -466,8 +476,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
     const bool bad_run = __any_sync(0xffffffffu, !ok || (volatile int&)failed);
     double* Cb = a.C + b * a.sC;
 #pragma unroll 1
-    for (int cc = 0; cc < 2; ++cc) {
-      const int c = half * 2 + cc;  // 16-column chunk of the tile
+    for (int cc = 0; cc < NT / 32; ++cc) {
+      const int c = half * (NT / 32) + cc;  // 16-column chunk of the tile
       // Accumulator g < 7 holds n_g 2^(-7g) with |n_g| < 2^25 exact; the shared one is rounded to
       // units of 2^-49. Exact integers: hi = n_0 2^21 + n_1 2^14 + n_2 2^7 + n_3 (units 2^-21),
       // lo = n_4 2^21 + n_5 2^14 + n_6 2^7 + m (units 2^-49).
@@ -478,7 +488,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
 #pragma unroll
         for (int g = 0; g < Cfg::NA; ++g) {
           float f[16];
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + g * TC_N + c * 16, f);
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + g * NT + c * 16, f);
           const float sc = __int_as_float((127 + (g < TC_NACC - 1 ? 7 * g : 49)) << 23);
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
@@ -533,7 +543,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
   if (threadIdx.x == 0 && failed && a.status) atomicOr(&a.status[b / a.sdiv], RMHMC_CHAIN_TIMEOUT);
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::COLS)
                  : "memory");
   }
 }
@@ -547,18 +557,18 @@ void launch_split(cudaStream_t s, const double* X, int ld, long long sX, bool km
                                      op.bytes_per_entry, mask);
 }
 
-template <int S>
+template <int S, int NT>
 void launch_gemm(cudaStream_t s, const TcArgs& args, int batch) {
-  using Cfg = TcCfg<S>;
+  using Cfg = TcCfg<S, NT>;
   static bool attr[64] = {};  // per device: the shared-memory opt-in is a per-device attribute
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !attr[dev]) {
-    cudaFuncSetAttribute(k_gemm_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    cudaFuncSetAttribute(k_gemm_tc<S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
-  dim3 grid((args.n + TC_N - 1) / TC_N, (args.m + TC_M - 1) / TC_M, batch);
-  k_gemm_tc<S><<<grid, TC_THREADS, Cfg::SMEM, s>>>(args);
+  dim3 grid((args.n + NT - 1) / NT, (args.m + TC_M - 1) / TC_M, batch);
+  k_gemm_tc<S, NT><<<grid, TC_THREADS, Cfg::SMEM, s>>>(args);
 }
 
 __global__ void k_scale(double* C, int m, int n, int ldc, long long sC, double beta) {
@@ -614,18 +624,19 @@ void tc_split(cudaStream_t s, const double* X, int ld, long long sX, bool kmaj, 
   }
 }
 
-double gemm_tc_tensor_flops(const TcOperand& A, const TcOperand& B, int batch, bool sym) {
-  const int tm = (A.R + TC_M - 1) / TC_M, tn = (B.R + TC_N - 1) / TC_N;
+double gemm_tc_tensor_flops(const TcOperand& A, const TcOperand& B, int batch, bool sym, int nt) {
+  nt = nt == 32 ? 32 : TC_N;
+  const int tm = (A.R + TC_M - 1) / TC_M, tn = (B.R + nt - 1) / nt;
   long long tiles = 0;  // per batch entry
   for (int i = 0; i < tm; ++i)
     for (int j = 0; j < tn; ++j)
-      if (!sym || i * TC_M + TC_M - 1 >= j * TC_N) ++tiles;
-  return (double)tiles * batch * A.KS * (A.S * (A.S + 1) / 2) * 2.0 * TC_M * TC_N * TC_K;
+      if (!sym || i * TC_M + TC_M - 1 >= j * nt) ++tiles;
+  return (double)tiles * batch * A.KS * (A.S * (A.S + 1) / 2) * 2.0 * TC_M * nt * TC_K;
 }
 
 void gemm_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, double alpha, double beta,
              double* C, int ldc, long long sC, int batch, bool sym, int* status, int sdiv,
-             const int* mask) {
+             const int* mask, int nt) {
   const int m = A.R, n = B.R, KS = A.KS;
   if (m <= 0 || n <= 0 || batch <= 0) return;
   if (A.TR != TC_M || B.TR != TC_N || B.KS != KS || B.S != A.S) return;  // wrong roles: no launch
@@ -662,11 +673,20 @@ void gemm_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, double alph
     a.ks0 = k0;
     a.ks1 = k0 + TC_KSTEPS_MAX < KS ? k0 + TC_KSTEPS_MAX : KS;
     a.beta = k0 == 0 ? beta : 1.0;
-    switch (A.S) {
-      case 6: launch_gemm<6>(s, a, batch); break;
-      case 7: launch_gemm<7>(s, a, batch); break;
-      case 8: launch_gemm<8>(s, a, batch); break;
-      default: launch_gemm<9>(s, a, batch); break;
+    if (nt == 32) {
+      switch (A.S) {
+        case 6: launch_gemm<6, 32>(s, a, batch); break;
+        case 7: launch_gemm<7, 32>(s, a, batch); break;
+        case 8: launch_gemm<8, 32>(s, a, batch); break;
+        default: launch_gemm<9, 32>(s, a, batch); break;
+      }
+    } else {
+      switch (A.S) {
+        case 6: launch_gemm<6, 64>(s, a, batch); break;
+        case 7: launch_gemm<7, 64>(s, a, batch); break;
+        case 8: launch_gemm<8, 64>(s, a, batch); break;
+        default: launch_gemm<9, 64>(s, a, batch); break;
+      }
     }
   }
 }

@@ -154,10 +154,14 @@ def lib():
     L.rmhmc_batch_leapfrog.restype = c_int
     L.rmhmc_batch_free.argtypes = [c_void_p]
     L.rmhmc_batch_free.restype = None
-    L.rmhmc_autotune.argtypes = [c_void_p, POINTER(IntegratorC), POINTER(c_int), POINTER(c_int)]
+    L.rmhmc_autotune.argtypes = [c_void_p, POINTER(IntegratorC), POINTER(c_int), POINTER(c_int), POINTER(c_int)]
+    L.rmhmc_set_gemm_tile.argtypes = [c_void_p, c_int]
+    L.rmhmc_set_gemm_tile.restype = c_int
     L.rmhmc_autotune.restype = c_int
     L.rmhmc_set_jacobi.argtypes = [c_void_p, c_int, c_int]
     L.rmhmc_set_jacobi.restype = c_int
+    L.rmhmc_set_prerotation.argtypes = [c_void_p, c_int]
+    L.rmhmc_set_prerotation.restype = c_int
     L.rmhmc_stream_create.argtypes = [POINTER(c_void_p)]
     L.rmhmc_stream_create.restype = c_int
     L.rmhmc_stream_destroy.argtypes = [c_void_p]
@@ -349,18 +353,29 @@ class Model:
 
 
     def autotune(self, integ=None):
-        """Pick this model's Jacobi cluster size and rotation schedule by timing one leapfrog of
-        each (rmhmc_autotune); returns (cluster, schedule name)."""
+        """Pick this model's Jacobi cluster size, rotation schedule and (mixed form) GEMM tile width
+        by timing one leapfrog of each (rmhmc_autotune); returns (cluster, schedule name, tile)."""
         integ = integ or self.integ or Integrator()
-        cl, sc = c_int(), c_int()
-        _check(lib().rmhmc_autotune(self._h, ctypes.byref(integ.c()), ctypes.byref(cl), ctypes.byref(sc)))
-        return cl.value, JACOBI_SCHEDULES[sc.value]
+        cl, sc, nt = c_int(), c_int(), c_int()
+        _check(lib().rmhmc_autotune(self._h, ctypes.byref(integ.c()), ctypes.byref(cl), ctypes.byref(sc),
+                                    ctypes.byref(nt)))
+        return cl.value, JACOBI_SCHEDULES[sc.value], nt.value
+
+    def set_gemm_tile(self, nt=64):
+        """Output tile width of the model's tensor-core GEMMs, 64 or 32 (rmhmc_set_gemm_tile)."""
+        _check(lib().rmhmc_set_gemm_tile(self._h, int(nt)))
+
+    def set_prerotation(self, enable=True):
+        """Turn the mixed form's first-order pre-rotation of warm eigen-updates on or off
+        (rmhmc_set_prerotation)."""
+        _check(lib().rmhmc_set_prerotation(self._h, 1 if enable else 0))
 
     def jacobi_counters(self):
         """Eigen-update work since the last profile reset (rmhmc_jacobi_counters), as a dict."""
-        out = (ctypes.c_longlong * 6)()
+        out = (ctypes.c_longlong * 8)()
         _check(lib().rmhmc_jacobi_counters(self._h, out))
-        keys = ("tile_products", "inner_rounds", "rounds", "solves", "rotated", "updates")
+        keys = ("tile_products", "inner_rounds", "rounds", "solves", "rotated", "updates",
+                "prerotated_updates", "prerotated_pairs")
         return dict(zip(keys, [int(v) for v in out]))
 
     def set_jacobi(self, cluster=0, schedule="cyclic"):

@@ -107,14 +107,14 @@ def test_autotune_picks_a_cluster_and_schedule_and_keeps_the_state(rm, oracle_mo
     U0 = torch.empty(4, dtype=torch.float64, device="cuda")
     with torch.cuda.stream(s):
         m.geometry(U=U0)
-        c, sched = m.autotune(integ)
+        c, sched, tile = m.autotune(integ)
         U1 = torch.empty_like(U0)
         m.geometry(U=U1)
         dHdq = torch.empty(4, m.d, dtype=torch.float64, device="cuda")
         P = wl.random_momentum(prob, 4, seed=8)
         m.hamiltonian_grad(torch.tensor(P, device="cuda"), dHdq=dHdq)
     torch.cuda.synchronize()
-    assert c in (1, 2, 4, 8) and sched in ("cyclic", "dynamic")
+    assert c in (1, 2, 4, 8) and sched in ("cyclic", "dynamic") and tile in (64, 32)
     np.testing.assert_array_equal(U0.cpu().numpy(), U1.cpu().numpy())
     q = wl.random_state(prob, 4, seed=7, f_scale=0.2, u_scale=0.1)
     ref = Geometry(oracle_model(prob), q[2], 1.0).dHdq(P[2])

@@ -202,3 +202,80 @@ def test_posterior_moments_match_closed_form(rm, oracle_model, precision):
     z_var = np.abs(chain_var.mean(axis=0) - var) / se_var
     print(precision, "max z mean", z_mean.max(), "max z var", z_var.max())
     assert z_mean.max() < 5.0 and z_var.max() < 5.0
+
+
+def test_mixed_warm_updates_with_and_without_prerotation(rm, oracle_model):
+    """Warm-started eigen-updates in the mixed form at N = 130 (d = 132: the d x d products span
+    tensor-core tiles, so the first-order pre-rotation applies): 5 leapfrogs (eps = 0.01, 4
+    fixed-point iterations, 24 warm eigen-updates) of 2 chains, with the pre-rotation and without,
+    against the oracle's trajectory from the same (q, p): within 1e-6 relative or 16x the oracle's
+    LU-vs-Cholesky spread (the mixed form's trajectory bound). With the pre-rotation the Jacobi
+    that follows it runs fewer rounds per eigen-update."""
+    from oracle.integrator import trajectory
+    from oracle.philox import normals
+    prob = wl.gp_classification(130, seed=4)
+    m = oracle_model(prob)
+    C = 2
+    Q = wl.random_state(prob, C, seed=9, f_scale=0.3, u_scale=0.2)
+    P = np.stack([Geometry(m, Q[c], 1.0, with_third=False).sqrtG_z(normals(3, c, 0, m.d)) for c in range(C)])
+    refs = []
+    for c in range(C):
+        qr, pr, _, _ = trajectory(m, Q[c], P[c], 0.01, 5, 4)
+        with mdl.inverse_method("cholesky"):
+            qa, pa, _, _ = trajectory(m, Q[c], P[c], 0.01, 5, 4)
+        refs.append((qr, pr, qa, pa))
+    rounds = {}
+    for prerot in (True, False):
+        model = rm.Model(prob, C)
+        model.set_prerotation(prerot)
+        integ = rm.Integrator(eps=0.01, n_fp=4, precision="mixed")
+        model.set_state(torch.tensor(Q, device="cuda"), torch.tensor(P, device="cuda"), integ)
+        model.profile(True)
+        model.profile(False)  # resets the Jacobi counters
+        q = torch.empty(C, m.d, dtype=torch.float64, device="cuda")
+        p = torch.empty_like(q)
+        st = torch.empty(C, dtype=torch.int32, device="cuda")
+        model.leapfrog(5, q, p, status_out=st, integ=integ)
+        torch.cuda.synchronize()
+        cnt = model.jacobi_counters()
+        rounds[prerot] = cnt["rounds"] / max(cnt["updates"], 1)
+        q, p, st = q.cpu().numpy(), p.cpu().numpy(), st.cpu().numpy()
+        model.close()
+        assert np.all(st == 0), st
+        for c in range(C):
+            qr, pr, qa, pa = refs[c]
+            for name, g, r, a in (("q", q[c], qr, qa), ("p", p[c], pr, pa)):
+                err = np.linalg.norm(g - r)
+                tol = max(1e-6 * np.linalg.norm(r), 16.0 * np.linalg.norm(r - a))
+                print(f"prerotation {prerot} chain {c} {name}: {err / np.linalg.norm(r):.1e} / "
+                      f"{tol / np.linalg.norm(r):.0e}")
+                assert err <= tol, (prerot, c, name, err, tol)
+    print("Jacobi rounds per eigen-update: with pre-rotation", rounds[True], "without", rounds[False])
+    assert rounds[True] < rounds[False]
+
+
+def test_gemm_tile_widths_give_identical_results(rm):
+    """The mixed form's tensor-core GEMMs with 128 x 32 output tiles (the autotuner's other tile
+    width) against 128 x 64: every output element is the same exact sum of the same slice products,
+    so U, dU, the Hessian, dH/dq and G^-1 p of the N = 130 problem (K^-1 algebra and the d x d
+    products on the tensor cores, symmetric and general outputs) must agree bit for bit."""
+    prob = wl.gp_classification(130, seed=4)
+    Q = wl.random_state(prob, 2, seed=10)
+    P = wl.random_momentum(prob, 2, seed=11)
+    outs = []
+    for nt in (64, 32):
+        m = rm.Model(prob, 2)
+        m.set_gemm_tile(nt)
+        integ = rm.Integrator(precision="mixed", jacobi_rule="relative")
+        m.set_state(torch.tensor(Q, device="cuda"), integ=integ)
+        f64 = dict(dtype=torch.float64, device="cuda")
+        d = m.d
+        U, dU, H = torch.empty(2, **f64), torch.empty(2, d, **f64), torch.empty(2, d, d, **f64)
+        dHdq, Gp = torch.empty(2, d, **f64), torch.empty(2, d, **f64)
+        m.geometry(U, dU, H)
+        m.hamiltonian_grad(torch.tensor(P, device="cuda"), dHdq, Gp)
+        torch.cuda.synchronize()
+        outs.append([x.cpu().numpy() for x in (U, dU, H, dHdq, Gp)])
+        m.close()
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
