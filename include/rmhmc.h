@@ -311,8 +311,9 @@ void rmhmc_server_destroy(rmhmc_server* s);
 
 /* Autotuner (not part of the method's arithmetic): chooses the model's Jacobi cluster size (CTAs
  * per chain: 1, 2, 4 or 8) and rotation schedule (rmhmc_jacobi_schedule) by timing one generalized
- * leapfrog (integ's eps and n_fp; integ's geometry fields must match the state's) of each of the 8
- * combinations from the model's current state, then, in the RMHMC_MIXED form, the output tile width
+ * leapfrog (integ's eps and n_fp; integ's geometry fields must match the state's; the better of two
+ * from the same state) of each combination from the model's current state (cluster sizes whose CTAs
+ * would not all be resident at two per SM are skipped), then, in the RMHMC_MIXED form, the output tile width
  * of its tensor-core GEMMs (128 x 64 or 128 x 32 tiles) with the best of those, keeping the fastest.
  * The state is then restored: q, p and the eigenbasis as before, the geometry re-evaluated at q
  * (U, dU and the Hessian are recomputed exactly; the basis is already converged there). Without it

@@ -101,51 +101,70 @@ constexpr int CB = 32;  // Cholesky / triangular-inverse block
 // that the factor stays finite. Larger N: panel steps (k_chol_diag + k_chol_rows) with the
 // trailing update A22 -= L21 L21^T between them as a batched symmetric GEMM over all matrices (so
 // every SM takes part).
-// The panel step split for parallelism. k_chol_diag: one warp per matrix factors the kb x kb
-// diagonal block at (k0, k0) (right-looking, lane = row), writes it back with zeros above its
-// diagonal, keeps the reciprocal pivots in rdiag (kb per matrix) and adds its share of log|A|.
-__global__ void __launch_bounds__(32) k_chol_diag(double* __restrict__ Ab, int N, int k0,
-                                                 double* __restrict__ rdiag,
-                                                 double* __restrict__ logdet, int lds,
-                                                 int* __restrict__ status, int per_chain) {
-  const int b = blockIdx.x, lane = threadIdx.x;
+// The panel step split for parallelism. k_chol_diag: one CTA of 128 threads per matrix factors the
+// kb x kb diagonal block at (k0, k0) in shared memory (right-looking; each column's trailing update
+// spread over the four warps, so four FP64 pipes of the SM share it), writes it back with zeros
+// above its diagonal, keeps the reciprocal pivots in rdiag (kb per matrix) and adds its share of
+// log|A|. The pivot's reciprocal square root comes from the FP32 one refined by two FP64 Newton
+// steps and the root from one more (FP64 square root and division are long multi-instruction
+// sequences on this part); pivots outside [1e-30, 1e30] take the FP64 square root and division.
+__global__ void __launch_bounds__(128) k_chol_diag(double* __restrict__ Ab, int N, int k0,
+                                                  double* __restrict__ rdiag,
+                                                  double* __restrict__ logdet, int lds,
+                                                  int* __restrict__ status, int per_chain) {
+  const int b = blockIdx.x, tid = threadIdx.x;
   double* A = Ab + (long long)b * N * N;
   const int kb = min(CB, N - k0);
   __shared__ double Dk[CB][CB + 1];
-  for (int e = lane; e < kb * kb; e += 32) Dk[e / kb][e % kb] = A[(long long)(k0 + e / kb) * N + k0 + e % kb];
-  __syncwarp();
   __shared__ double sir;
+  for (int e = tid; e < kb * kb; e += blockDim.x) Dk[e / kb][e % kb] = A[(long long)(k0 + e / kb) * N + k0 + e % kb];
+  __syncthreads();
   bool bad = false;
   double pm = 1.0;  // product of the pivots' square roots as pm 2^pe (one log at the end)
   int pe = 0;
   for (int j = 0; j < kb; ++j) {
-    if (lane == 0) {  // pivot arithmetic in one lane (FP64 sqrt and division are costly here)
+    if (tid == 0) {
       double piv = Dk[j][j];
       if (!(piv > 0.0) || !isfinite(piv)) { bad = true; piv = 1.0; }
-      const double r = sqrt(piv);
+      double r, y;
+      if (piv > 1e-30 && piv < 1e30) {
+        y = (double)rsqrtf((float)piv);
+        y = y * fma(-0.5 * piv, y * y, 1.5);
+        y = y * fma(-0.5 * piv, y * y, 1.5);
+        r = piv * y;
+        r = fma(0.5 * y, fma(-r, r, piv), r);
+      } else {
+        r = sqrt(piv);
+        y = 1.0 / r;
+      }
       Dk[j][j] = r;
-      sir = 1.0 / r;
-      rdiag[(long long)b * CB + j] = sir;
+      sir = y;
+      rdiag[(long long)b * CB + j] = y;
       int ex;
       pm = frexp(pm * r, &ex);
       pe += ex;
     }
-    __syncwarp();
+    __syncthreads();
     const double ir = sir;
-    if (lane > j && lane < kb) Dk[lane][j] *= ir;
-    __syncwarp();
-    if (lane > j && lane < kb) {
-      const double lij = Dk[lane][j];
-      for (int l = j + 1; l <= lane; ++l) Dk[lane][l] -= lij * Dk[l][j];
+    if (tid > j && tid < kb) Dk[tid][j] *= ir;
+    __syncthreads();
+    // trailing lower triangle (i, l), j < l <= i < kb, as a flat index over 128 threads
+    const int m = kb - j - 1, cnt = m * (m + 1) / 2;
+    for (int e = tid; e < cnt; e += blockDim.x) {
+      int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      while (i * (i + 1) / 2 > e) --i;
+      const int gi = j + 1 + i, gl = j + 1 + (e - i * (i + 1) / 2);
+      Dk[gi][gl] -= Dk[gi][j] * Dk[gl][j];
     }
-    __syncwarp();
+    __syncthreads();
   }
-  const double ldacc = log(pm) + pe * 0.69314718055994530942;  // log of the product of the roots
-  for (int e = lane; e < kb * kb; e += 32) {
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
     const int i = e / kb, j = e % kb;
     A[(long long)(k0 + i) * N + k0 + j] = (j <= i) ? Dk[i][j] : 0.0;
   }
-  if (lane == 0) {
+  if (tid == 0) {
+    const double ldacc = log(pm) + pe * 0.69314718055994530942;  // log of the product of the roots
     double* ldp = logdet + (long long)b * lds;
     *ldp = (k0 == 0 ? 0.0 : *ldp) + 2.0 * ldacc;
     if (bad) atomicOr(&status[b / per_chain], RMHMC_CHAIN_NOTPD);
@@ -477,7 +496,7 @@ __global__ void k_zero_upper(double* __restrict__ Xb, int N);
 // upper triangle.
 void chol_panel(cudaStream_t s, double* A, int N, int k0, int batch, double* rdiag, double* logdet,
                 int lds, int* status, int per_chain) {
-  k_chol_diag<<<batch, 32, 0, s>>>(A, N, k0, rdiag, logdet, lds, status, per_chain);
+  k_chol_diag<<<batch, 128, 0, s>>>(A, N, k0, rdiag, logdet, lds, status, per_chain);
   const int kb = CB < N - k0 ? CB : N - k0, rows = N - k0 - kb;
   if (rows > 0) k_chol_rows<CB><<<dim3((rows + 127) / 128, batch), 128, 0, s>>>(A, N, k0, rdiag);
   else k_zero_upper<<<dim3((unsigned)(((long long)N * N + 255) / 256), batch), 256, 0, s>>>(A, N);

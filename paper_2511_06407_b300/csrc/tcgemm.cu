@@ -56,13 +56,20 @@ constexpr unsigned long long kWaitNs = 2000000000ull;
 constexpr int A_SLICE = TC_M * TC_K * 2;  // bytes of one slice of an A stage (4096)
 constexpr int B_SLICE = TC_N * TC_K * 2;  // (2048), of which a 32-row half is 1024 contiguous bytes
 
+// NT = 64: one CTA per SM (all 512 tensor-memory columns, a 4-stage ring). NT = 32: two CTAs per SM
+// (256 columns each, a ring of at most 3 stages that fits twice in shared memory, an epilogue in
+// 8-column chunks to stay within half the register file), so that one CTA's epilogue overlaps the
+// other's MMAs.
 template <int S, int NT>
 struct TcCfg {
   static constexpr int BS = NT * TC_K * 2;  // bytes of one B slice in a stage
   static constexpr int COLS = TC_NACC * NT;  // tensor-memory columns (a power of two >= 32)
+  static constexpr int CTAS = NT == 32 ? 2 : 1;  // CTAs per SM
+  static constexpr int CW = NT == 32 ? 8 : 16;   // epilogue chunk width (columns)
   static constexpr int STAGE = S * (A_SLICE + BS);
-  static constexpr int NST_FIT = (226 * 1024) / STAGE;
-  static constexpr int NST = NST_FIT > 4 ? 4 : NST_FIT;
+  static constexpr int NST_FIT = (CTAS == 2 ? 111 * 1024 : 226 * 1024) / STAGE;
+  static constexpr int NST_MAX = CTAS == 2 ? 3 : 4;
+  static constexpr int NST = NST_FIT > NST_MAX ? NST_MAX : NST_FIT;
   static constexpr int BAR_OFF = NST * STAGE;
   static constexpr int SMEM = BAR_OFF + 256;
   static constexpr int NA = S < TC_NACC ? S : TC_NACC;  // accumulators in use
@@ -173,6 +180,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <int W>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[W]) {
+  if constexpr (W == 16) tmem_ld16(taddr, v);
+  else tmem_ld8(taddr, v);
 }
 
 // ---------------------------------------------------------------- splitting
@@ -354,7 +379,7 @@ struct TcArgs {
 };
 
 template <int S, int NT>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, TcCfg<S, NT>::CTAS) k_gemm_tc(TcArgs a) {
   using Cfg = TcCfg<S, NT>;
   constexpr int NST = Cfg::NST;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -476,22 +501,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
     const bool bad_run = __any_sync(0xffffffffu, !ok || (volatile int&)failed);
     double* Cb = a.C + b * a.sC;
 #pragma unroll 1
-    for (int cc = 0; cc < NT / 32; ++cc) {
-      const int c = half * (NT / 32) + cc;  // 16-column chunk of the tile
+    constexpr int CW = Cfg::CW;
+#pragma unroll 1
+    for (int cc = 0; cc < NT / 2 / CW; ++cc) {
+      const int c = half * (NT / 2 / CW) + cc;  // CW-column chunk of the tile
       // Accumulator g < 7 holds n_g 2^(-7g) with |n_g| < 2^25 exact; the shared one is rounded to
       // units of 2^-49. Exact integers: hi = n_0 2^21 + n_1 2^14 + n_2 2^7 + n_3 (units 2^-21),
       // lo = n_4 2^21 + n_5 2^14 + n_6 2^7 + m (units 2^-49).
-      long long hi[16], lo[16];
+      long long hi[CW], lo[CW];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+      for (int j = 0; j < CW; ++j) hi[j] = lo[j] = 0;
       if (!bad_run) {
 #pragma unroll
         for (int g = 0; g < Cfg::NA; ++g) {
-          float f[16];
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + g * NT + c * 16, f);
+          float f[CW];
+          tmem_ld<CW>(tmem + ((uint32_t)(q * 32) << 16) + g * NT + c * CW, f);
           const float sc = __int_as_float((127 + (g < TC_NACC - 1 ? 7 * g : 49)) << 23);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
+          for (int j = 0; j < CW; ++j) {
             const long long n = __float2int_rn(f[j] * sc);
             if (g < 4) hi[j] += n << (7 * (3 - g));
             else if (g < TC_NACC - 1) lo[j] += n << (7 * (7 - g));
@@ -500,9 +527,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
         }
       }
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int col = n0 + c * 16 + j;
-        const int ec = sec[c * 16 + j];
+      for (int j = 0; j < CW; ++j) {
+        const int col = n0 + c * CW + j;
+        const int ec = sec[c * CW + j];
         double x;
         if (bad_run || er == kExpBad || ec == kExpBad) {
           x = __longlong_as_double(0x7ff8000000000000ll);
@@ -514,11 +541,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
         stg[lane * 17 + j] = (row_in && col < a.n) ? x : 0.0;
       }
       __syncwarp();
-      // coalesced: each step writes two 16-column row segments; alpha and beta applied here
+      // coalesced: each step writes 32 / CW row segments of CW columns; alpha and beta applied here
 #pragma unroll 1
-      for (int i = 0; i < 16; ++i) {
-        const int rl = 2 * i + lane / 16, j = lane % 16;
-        const int rr = m0 + q * 32 + rl, col = n0 + c * 16 + j;
+      for (int i = 0; i < CW; ++i) {
+        const int rl = (32 / CW) * i + lane / CW, j = lane % CW;
+        const int rr = m0 + q * 32 + rl, col = n0 + c * CW + j;
         if (rr < a.m && col < a.n && (!a.sym || col <= rr)) {
           double* cp = Cb + (long long)rr * a.ldc + col;
           double x = a.alpha * stg[rl * 17 + j];
@@ -530,8 +557,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
       __syncwarp();
       if (a.sym && row_in) {  // mirror: lanes are consecutive rows, so these stores coalesce
 #pragma unroll 1
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c * 16 + j;
+        for (int j = 0; j < CW; ++j) {
+          const int col = n0 + c * CW + j;
           if (col < r) Cb[(long long)col * a.ldc + r] = stg[lane * 17 + j];
         }
       }
