@@ -500,7 +500,6 @@ __global__ void __launch_bounds__(TC_THREADS, TcCfg<S, NT>::CTAS) k_gemm_tc(TcAr
     // warp-uniform, since tcgen05.ld is executed by the whole warp
     const bool bad_run = __any_sync(0xffffffffu, !ok || (volatile int&)failed);
     double* Cb = a.C + b * a.sC;
-#pragma unroll 1
     constexpr int CW = Cfg::CW;
 #pragma unroll 1
     for (int cc = 0; cc < NT / 2 / CW; ++cc) {
