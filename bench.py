@@ -40,7 +40,7 @@ N_INPUTS, N_CHAINS, EPS, N_FP, N_LEAPFROG = 400, 64, 0.001, 6, 10
 # dram__bytes_write.sum of single-kernel captures at 8 chains of this workload (traffic grows
 # with the number of chains, so a 64-chain launch is scaled by 64 / 8). A kernel enters here only
 # with counters taken from its current code.
-DRAM_BYTES_PER_CHAIN = {}
+DRAM_BYTES_PER_CHAIN = {"jacobi_df": 22.704896e6 / 8}  # k_jacobi_t<ElemDF>, warm update, 8 chains
 SUBSTEPS_PER_LEAPFROG = 2 * N_FP + 1
 # The paper's settings for its simulated primal-model runs (Sec. 2.5): step size, and kappa of the
 # map g(lambda) = sqrt(kappa^2 + lambda^2) (passed as alpha = 1 / kappa).
@@ -371,9 +371,11 @@ def _time_iterations(model, integ, steps, seed, stream, local, ws, dev):
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")  # (lets a profiler select the timed region: ncu --nvtx-include timed/)
     e0.record(stream)
     model.sample(steps, 0, seed, accept=acc, chain_status=cs, integ=integ)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -568,6 +570,7 @@ def _e2e(rmhmc, prob, C, integ, steps, seed, stream, dev, ws, jacobi=None):
     if jacobi:  # the autotuned settings of the device-timed arm
         model.set_jacobi(jacobi["cluster"], jacobi["schedule"])
         model.set_gemm_tile(jacobi["gemm_tile"])
+        model.set_prerotation(jacobi["prerotation"])
     q0 = torch.empty(C, d, dtype=torch.float64, device=dev)
     q0.copy_(q0_host, non_blocking=True)
     model.set_state(q0, integ=integ)
@@ -601,7 +604,7 @@ def _run_arm(rmhmc, prob, C, prec, warmup, steps, seed, stream, local, ws, dev):
     model.set_state(torch.zeros(C, model.d, dtype=torch.float64, device=dev), integ=integ)
     # the library's autotuner picks the Jacobi cluster size and rotation order for this model by
     # timing one leapfrog of each combination (untimed set-up; the state is restored)
-    jacobi = dict(zip(("cluster", "schedule", "gemm_tile"), model.autotune(integ)))
+    jacobi = dict(zip(("cluster", "schedule", "gemm_tile", "prerotation"), model.autotune(integ)))
     warm_cs = torch.zeros(C, dtype=torch.int32, device=dev)
     model.sample(warmup, 0, seed, chain_status=warm_cs, integ=integ)
     ms, acc, cs, clk = _time_iterations(model, integ, steps, seed, stream, local, ws, dev)
@@ -763,21 +766,25 @@ def run_propensity(args):
     C = 32
     model = rmhmc.Model(prob, C)
     prec = aux_precision(args)
-    integ = rmhmc.Integrator(eps=args.eps or 0.005, n_fp=N_FP, n_leapfrog=1, precision=prec)
+    integ = rmhmc.Integrator(eps=args.eps or EPS, n_fp=N_FP, n_leapfrog=1, precision=prec)
     model.set_state(torch.zeros(C, model.d, dtype=torch.float64, device="cuda"), integ=integ)
+    tuned = model.autotune(integ)
     model.sample(1, 0, 99, integ=integ)
     model.leapfrog(max(args.warmup - 1, 0), integ=integ)
     st = torch.empty(C, dtype=torch.int32, device="cuda")
-    model.profile(True)
     el, clk = _clock_and_time(lambda: model.leapfrog(args.steps, status_out=st, integ=integ), 0)
-    prof = model.profile_read()
     status = st.cpu().numpy()
+    model.profile(True)  # one more leapfrog with the per-launch events, outside the timed region
+    model.leapfrog(1, integ=integ)
+    prof = model.profile_read()
+    model.profile(False)
     value = C * SUBSTEPS_PER_LEAPFROG * args.steps / el
     print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
                       "dtype": dtype_of(prec), "data": "synthetic",
                       "config": {"workload": "propensity model N=500, SE+linear+overlap (d=1506), 32 chains, "
-                                             f"{prec}, eps={integ.eps}", "d": model.d, "chains": C},
+                                             f"{prec}, eps={integ.eps}", "d": model.d, "chains": C,
+                                 "autotuned_cluster_schedule_tile": tuned},
                       "profile_ms": {k: round(v[0], 1) for k, v in prof.items()},
                       "profile_tflops": {k: (v[1] / (v[0] * 1e-3) / 1e12 if v[0] > 0 else 0.0) for k, v in prof.items()},
                       "chain_status_nonzero": int((status != 0).sum()), "clocks": clk}), flush=True)
@@ -907,16 +914,19 @@ def run_solin(args):
                                  alpha=1.0 / SOLIN_KAPPA,
                                  precision=prec)
         model.set_state(torch.zeros(C, model.d, dtype=torch.float64, device="cuda"), integ=integ)
+        tuned = model.autotune(integ)
         model.sample(1, 0, 5, integ=integ)
         model.leapfrog(max(args.warmup - 1, 0), integ=integ)
         st = torch.empty(C, dtype=torch.int32, device="cuda")
-        model.profile(True)
         el, clk = _clock_and_time(lambda: model.leapfrog(args.steps, status_out=st, integ=integ), 0)
+        model.profile(True)  # one more leapfrog with the per-launch events, outside the timed region
+        model.leapfrog(1, integ=integ)
         prof = model.profile_read()
+        model.profile(False)
         out[prec] = {"value": C * SUBSTEPS_PER_LEAPFROG * args.steps / el,
                      "leapfrogs_per_s_per_chain": args.steps / el, "ms_per_step": 1e3 * el / args.steps,
                      "profile_ms": {k: round(v[0], 1) for k, v in prof.items() if v[2]},
-                     "roofline": _roofline(rmhmc, prof, C),
+                     "roofline": _roofline(rmhmc, prof, C), "autotuned_cluster_schedule_tile": tuned,
                      "chain_status_nonzero": int((st.cpu().numpy() != 0).sum()), "clocks": clk}
         d = model.d
         model.close()
@@ -1014,6 +1024,7 @@ def run_uneven(args):
             else:
                 m.set_jacobi(*tuned[key][:2])
                 m.set_gemm_tile(tuned[key][2])
+                m.set_prerotation(tuned[key][3])
             choice.append(tuned[key])
             m.sample(1, 0, 7 + i, integ=integ)
         models.append(m)
@@ -1038,8 +1049,9 @@ def run_uneven(args):
     chains = C * len(models)
     ds = [m.d for m in models]
     scheds = {}
-    for c, sc, nt in choice:
-        scheds[f"{sc}/{c}/{nt}"] = scheds.get(f"{sc}/{c}/{nt}", 0) + 1
+    for c, sc, nt, pr in choice:
+        key = f"{sc}/{c}/{nt}/{'pre' if pr else 'nopre'}"
+        scheds[key] = scheds.get(key, 0) + 1
     print(json.dumps({"metric": METRIC, "value": chains * SUBSTEPS_PER_LEAPFROG * args.steps / el, "unit": UNIT,
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -314,14 +314,15 @@ void rmhmc_server_destroy(rmhmc_server* s);
  * leapfrog (integ's eps and n_fp; integ's geometry fields must match the state's; the better of two
  * from the same state) of each combination from the model's current state (cluster sizes whose CTAs
  * would not all be resident at two per SM are skipped), then, in the RMHMC_MIXED form, the output tile width
- * of its tensor-core GEMMs (128 x 64 or 128 x 32 tiles) with the best of those, keeping the fastest.
+ * of its tensor-core GEMMs (128 x 64 or 128 x 32 tiles) with the best of those, then the first-order
+ * pre-rotation on or off (rmhmc_set_prerotation), keeping the fastest at each step.
  * The state is then restored: q, p and the eigenbasis as before, the geometry re-evaluated at q
  * (U, dU and the Hessian are recomputed exactly; the basis is already converged there). Without it
- * a model uses the cyclic schedule, the largest cluster that keeps two CTAs per SM and 64-column
- * tiles. Synchronises the stream; needs a state. *cluster_out, *sched_out and *tile_out (may be
- * NULL) receive the choice. */
+ * a model uses the cyclic schedule, the largest cluster that keeps two CTAs per SM, 64-column
+ * tiles and the pre-rotation. Synchronises the stream; needs a state. *cluster_out, *sched_out,
+ * *tile_out and *prerot_out (each may be NULL) receive the choice. */
 rmhmc_status rmhmc_autotune(rmhmc_model* m, const rmhmc_integrator* integ, int* cluster_out,
-                            int* sched_out, int* tile_out);
+                            int* sched_out, int* tile_out, int* prerot_out);
 /* Set the output tile width of the model's tensor-core GEMMs (64 or 32 columns, else EINVAL). */
 rmhmc_status rmhmc_set_gemm_tile(rmhmc_model* m, int nt);
 /* A new non-blocking CUDA stream on the current device (for batches of many models: each model of

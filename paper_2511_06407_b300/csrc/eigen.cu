@@ -354,17 +354,6 @@ __device__ __forceinline__ void load_tile_v(typename E::T* dst, const typename E
   for (int e = lane; e < SB * SB; e += 32) dst[(e / SB) * SBP + e % SB] = E::ld(src + e);
 }
 
-// log2 |x| for a finite double, from its exponent field and the FP32 log2 of its significand
-// (integer and FP32 operations only; B300's FP64 pipe is 1/64 of its FP32 rate). Zero gives -2000,
-// a subnormal the log2 of 2^-1023.
-__device__ __forceinline__ float log2_abs(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-  if (b == 0) return -2000.f;
-  const int e = (int)(b >> 52) - 1023;
-  const float m = __int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff));  // significand in [1, 2)
-  return (float)e + __log2f(m);
-}
-
 // Constants of the coupling criterion, fixed for one eigen-update: log2 of zeta^2, of the floor
 // 4u ||M||_F squared and of min_i |m_ii| squared.
 struct CritConst {

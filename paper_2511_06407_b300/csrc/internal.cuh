@@ -7,6 +7,18 @@
 
 namespace rmhmc {
 
+// log2 |x| for a finite double, from its exponent field and the FP32 log2 of its significand
+// (integer and FP32 operations only; B300's FP64 pipe is 1/64 of its FP32 rate). Zero gives -2000,
+// a subnormal the log2 of 2^-1023.
+__device__ __forceinline__ float log2_abs(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  if (b == 0) return -2000.f;
+  const int e = (int)(b >> 52) - 1023;
+  const float m = __int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff));  // significand in [1, 2)
+  return (float)e + __log2f(m);
+}
+
+
 constexpr int kMaxN = 1024;       // inputs per problem (FP64 path)
 constexpr int kJacBlk = 8;        // Jacobi index block b; a rotated pair of blocks is 16 x 16
 constexpr int kJacSB = 2 * kJacBlk;

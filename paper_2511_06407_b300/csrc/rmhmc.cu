@@ -422,23 +422,29 @@ __global__ void __launch_bounds__(256) k_prerot_gen(const double* __restrict__ M
                                                     double* __restrict__ Xb, double* __restrict__ acc) {
   const int c = blockIdx.y;
   const long long DD = (long long)dp * dp;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;  // dp^2 < 2^31
   const bool in = e < DD;
-  const int j = in ? (int)(e / dp) : 0, l = in ? (int)(e % dp) : 0;
+  const int j = in ? e / dp : 0, l = in ? e % dp : 0;
   const double* M = Mb + c * DD;
   double th = 0.0;
   if (in && j != l && j < d && l < d && status[c] == 0) {
+    // the stopping rule's test in the log domain (exponent fields and FP32 logarithms: FP64
+    // arithmetic runs at 1/64 of the FP32 rate here), the angle in FP64 for the pairs that fail it
     const double v = M[e];
     const double djj = M[(long long)j * dp + j], dll = M[(long long)l * dp + l];
-    const double floor2 = fmax(16.0 * 1.2621774483536189e-29 * nrm[4 * c], 1e-300);
-    const double dmin2 = fmax(nrm[4 * c + 1] * nrm[4 * c + 1], 1e-300);
-    const double v2 = v * v, p = fabs(djj * dll);
-    const double fl = rule == RMHMC_JACOBI_RELATIVE
-                          ? fmin(floor2, fmax(1e-26 * fmax(djj * djj, dll * dll), 1e-300))
-                          : floor2;
-    const bool unconv = v2 > fl && (rule == RMHMC_JACOBI_METRIC ? v2 * dmin2 > tol * tol * p * p
-                                                                 : v2 > tol * tol * p);
-    if (unconv) {
+    const double dmin = nrm[4 * c + 1];
+    const float lfloor2 = log2_abs(16.0 * 1.2621774483536189e-29 * nrm[4 * c]);
+    const float ltol2 = 2.f * log2_abs(tol), ldmin2 = 2.f * log2_abs(dmin);
+    const float lv = log2_abs(v), lj = log2_abs(djj), ll = log2_abs(dll);
+    float lthr, lfl;
+    if (rule == RMHMC_JACOBI_RELATIVE) {
+      lthr = ltol2 + lj + ll;
+      lfl = fminf(lfloor2, fmaxf(-86.37013f + 2.f * fmaxf(lj, ll), -996.578f));
+    } else {
+      lthr = ltol2 + 2.f * (lj + ll) - fmaxf(ldmin2, -996.578f);
+      lfl = lfloor2;
+    }
+    if (!isfinite(v) || 2.f * lv > fmaxf(lthr, lfl)) {
       th = 0.5 * atan(2.0 * v / (dll - djj));
       if (!isfinite(th)) th = 1.0;  // (a non-finite coupling: too large, the chain is left alone)
       else if (fabs(th) > kPrerotMaxTheta) th = 0.0;  // left to the Jacobi
@@ -448,27 +454,29 @@ __global__ void __launch_bounds__(256) k_prerot_gen(const double* __restrict__ M
     Ab[c * DD + e] = th;
     Xb[c * DD + e] = (j == l ? 1.0 : 0.0) + th;
   }
-  double t2 = th * th, n1 = th != 0.0 ? 1.0 : 0.0;
+  // (in FP32: the sum only decides the ||A||_F <= 1e-4 test, and the count is an integer)
+  const float tf = (float)th;
+  float t2 = tf * tf;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    t2 += __shfl_xor_sync(0xffffffffu, t2, o);
-    n1 += __shfl_xor_sync(0xffffffffu, n1, o);
-  }
-  __shared__ double r0[8], r1[8];
+  for (int o = 16; o > 0; o >>= 1) t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+  const int n1 = __popc(__ballot_sync(0xffffffffu, th != 0.0));
+  __shared__ float r0[8];
+  __shared__ int r1[8];
   if ((threadIdx.x & 31) == 0) {
     r0[threadIdx.x >> 5] = t2;
     r1[threadIdx.x >> 5] = n1;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
+    float a = 0.f;
+    int b = 0;
     for (int w = 0; w < 8; ++w) {
       a += r0[w];
       b += r1[w];
     }
-    if (b != 0.0) {
-      atomicAdd(&acc[4 * c + 2], a);
-      atomicAdd(&acc[4 * c + 3], b);
+    if (b != 0) {
+      atomicAdd(&acc[4 * c + 2], (double)a);
+      atomicAdd(&acc[4 * c + 3], (double)b);
     }
   }
 }
@@ -1373,7 +1381,7 @@ rmhmc_status rmhmc_batch_leapfrog(rmhmc_batch* b, const rmhmc_integrator* integ,
 }
 
 rmhmc_status rmhmc_autotune(rmhmc_model* m, const rmhmc_integrator* integ, int* cluster_out,
-                            int* sched_out, int* tile_out) {
+                            int* sched_out, int* tile_out, int* prerot_out) {
   if (!m || !m->has_state || m->prof) return RMHMC_EINVAL;
   rmhmc_status st = check_integ(m, integ, false);
   if (st != RMHMC_OK) return st;
@@ -1448,6 +1456,7 @@ rmhmc_status rmhmc_autotune(rmhmc_model* m, const rmhmc_integrator* integ, int* 
   }
   m->cluster = best_c;
   m->jacobi_sched = best_s;
+  int best_p = m->prerot;
   if (m->precision == RMHMC_MIXED) {
     for (int t : tiles) {
       if (t == best_t) continue;
@@ -1458,14 +1467,24 @@ rmhmc_status rmhmc_autotune(rmhmc_model* m, const rmhmc_integrator* integ, int* 
         best_t = t;
       }
     }
+    m->tc_nt = best_t;
+    // and the first-order pre-rotation of warm eigen-updates, on or off
+    m->prerot = 1 - best_p;
+    if (!trial(&ms)) return RMHMC_ECUDA;
+    if (ms < best) {
+      best = ms;
+      best_p = m->prerot;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   m->tc_nt = best_t;
+  m->prerot = best_p;
   restore();
   if (cluster_out) *cluster_out = best_c;
   if (sched_out) *sched_out = best_s;
   if (tile_out) *tile_out = best_t;
+  if (prerot_out) *prerot_out = best_p;
   return check_launch();
 }
 

@@ -154,7 +154,8 @@ def lib():
     L.rmhmc_batch_leapfrog.restype = c_int
     L.rmhmc_batch_free.argtypes = [c_void_p]
     L.rmhmc_batch_free.restype = None
-    L.rmhmc_autotune.argtypes = [c_void_p, POINTER(IntegratorC), POINTER(c_int), POINTER(c_int), POINTER(c_int)]
+    L.rmhmc_autotune.argtypes = [c_void_p, POINTER(IntegratorC), POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                                 POINTER(c_int)]
     L.rmhmc_set_gemm_tile.argtypes = [c_void_p, c_int]
     L.rmhmc_set_gemm_tile.restype = c_int
     L.rmhmc_autotune.restype = c_int
@@ -354,12 +355,13 @@ class Model:
 
     def autotune(self, integ=None):
         """Pick this model's Jacobi cluster size, rotation schedule and (mixed form) GEMM tile width
-        by timing one leapfrog of each (rmhmc_autotune); returns (cluster, schedule name, tile)."""
+        and pre-rotation by timing leapfrogs (rmhmc_autotune); returns (cluster, schedule name, tile,
+        pre-rotation on)."""
         integ = integ or self.integ or Integrator()
-        cl, sc, nt = c_int(), c_int(), c_int()
+        cl, sc, nt, pr = c_int(), c_int(), c_int(), c_int()
         _check(lib().rmhmc_autotune(self._h, ctypes.byref(integ.c()), ctypes.byref(cl), ctypes.byref(sc),
-                                    ctypes.byref(nt)))
-        return cl.value, JACOBI_SCHEDULES[sc.value], nt.value
+                                    ctypes.byref(nt), ctypes.byref(pr)))
+        return cl.value, JACOBI_SCHEDULES[sc.value], nt.value, bool(pr.value)
 
     def set_gemm_tile(self, nt=64):
         """Output tile width of the model's tensor-core GEMMs, 64 or 32 (rmhmc_set_gemm_tile)."""

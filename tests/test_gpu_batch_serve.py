@@ -107,7 +107,7 @@ def test_autotune_picks_a_cluster_and_schedule_and_keeps_the_state(rm, oracle_mo
     U0 = torch.empty(4, dtype=torch.float64, device="cuda")
     with torch.cuda.stream(s):
         m.geometry(U=U0)
-        c, sched, tile = m.autotune(integ)
+        c, sched, tile, pre = m.autotune(integ)
         U1 = torch.empty_like(U0)
         m.geometry(U=U1)
         dHdq = torch.empty(4, m.d, dtype=torch.float64, device="cuda")
