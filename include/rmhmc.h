@@ -310,9 +310,9 @@ rmhmc_status rmhmc_server_stats(rmhmc_server* s, double* now_s, int* n_active, i
 void rmhmc_server_destroy(rmhmc_server* s);
 
 /* Autotuner (not part of the method's arithmetic): chooses the model's Jacobi cluster size (CTAs
- * per chain: 1, 2, 4 or 8) and rotation schedule (rmhmc_jacobi_schedule) by timing one generalized
- * leapfrog (integ's eps and n_fp; integ's geometry fields must match the state's; the better of two
- * from the same state) of each combination from the model's current state (cluster sizes whose CTAs
+ * per chain: 1, 2, 4 or 8) and rotation schedule (rmhmc_jacobi_schedule) by timing generalized
+ * leapfrogs (integ's eps and n_fp; integ's geometry fields must match the state's; two timed after
+ * one untimed, from the model's current state) of each combination (cluster sizes whose CTAs
  * would not all be resident at two per SM are skipped), then, in the RMHMC_MIXED form, the output tile width
  * of its tensor-core GEMMs (128 x 64 or 128 x 32 tiles) with the best of those, then the first-order
  * pre-rotation on or off (rmhmc_set_prerotation), keeping the fastest at each step.

@@ -1420,19 +1420,17 @@ rmhmc_status rmhmc_autotune(rmhmc_model* m, const rmhmc_integrator* integ, int* 
   const int tiles[2] = {64, 32};
   double best = 1e300;
   int best_c = m->cluster, best_s = m->jacobi_sched, best_t = m->tc_nt;
-  // a candidate's time: the better of two leapfrogs, each from the restored state
+  // a candidate's time: from the restored state, one untimed leapfrog (the eigen-updates settle
+  // into the candidate's steady state), then two timed ones
   auto trial = [&](float* ms) -> bool {
-    *ms = 3.0e38f;
-    for (int rep = 0; rep < 2; ++rep) {
-      restore();
-      cudaEventRecord(e0, s);
-      leapfrog_step(m, integ->eps, integ->n_fp);
-      cudaEventRecord(e1, s);
-      if (cudaEventSynchronize(e1) != cudaSuccess) return false;
-      float t = 0.f;
-      cudaEventElapsedTime(&t, e0, e1);
-      *ms = t < *ms ? t : *ms;
-    }
+    restore();
+    leapfrog_step(m, integ->eps, integ->n_fp);
+    cudaEventRecord(e0, s);
+    leapfrog_step(m, integ->eps, integ->n_fp);
+    leapfrog_step(m, integ->eps, integ->n_fp);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return false;
+    cudaEventElapsedTime(ms, e0, e1);
     return true;
   };
   int sms = 148;

@@ -194,3 +194,61 @@ def test_native_server_jobs_equal_one_sample_call(rm):
     with pytest.raises(rm.RmhmcError):
         small.submit(probs[0], C, integ, 1, 0, 0)
     small.close()
+
+
+def test_served_tempered_job_matches_the_oracle(rm):
+    """A served job against the FP64 oracle's Algorithm 1 directly: the N = 30 problem, 2 chains at
+    inverse temperatures 1 and 0.5, 1 burn-in + 4 recorded iterations (L = 3, eps = 0.01, 3
+    fixed-point iterations) from f = 0, u = 0, seed 5, submitted together with a second job. Same
+    accept/reject decisions, the samples and log posteriors within the parity rule (16 x the oracle's
+    LU-vs-Cholesky spread, 1e-8 / 1e-10 floors; log P also its first-order change with the sample's
+    own deviation and the error of rounding K to FP64),
+    and the recorded untempered ln P(y|F) per sample."""
+    import oracle_pool
+    from conftest import potential_rounding_bound
+    from oracle import model as mdl
+    prob = wl.gp_classification(30, seed=1)
+    taus = np.array([1.0, 0.5])
+    C, n_iter, n_burn, seed = 2, 4, 1, 5
+    integ = rm.Integrator(eps=0.01, n_leapfrog=3, n_fp=3)
+    f64 = dict(dtype=torch.float64, device="cuda")
+    i32 = dict(dtype=torch.int32, device="cuda")
+    d = wl.dims(prob)[2]
+    srv = rm.NativeServer(2**30, depth=2)
+    out = (torch.empty(n_iter, C, d, **f64), torch.empty(n_iter, C, **f64), torch.empty(n_iter, C, **i32),
+           torch.zeros(C, **i32), torch.empty(n_iter, C, **f64))
+    srv.submit(prob, C, integ, n_iter, n_burn, seed, taus, None, *out)
+    other = wl.gp_classification(45, seed=2)  # a second job in the mix
+    o2 = (torch.empty(2, 3, wl.dims(other)[2], **f64), torch.empty(2, 3, **f64), torch.empty(2, 3, **i32),
+          torch.zeros(3, **i32))
+    srv.submit(other, 3, integ, 2, 0, 9, None, None, *o2)
+    srv.wait()
+    srv.close()
+    q, lp, acc, cs, ll = (x.cpu().numpy() for x in out)
+    assert not cs.any(), cs
+    jobs = []
+    for c in range(C):
+        kw = dict(n_iter=n_iter, n_burn=n_burn, seed=seed, chain=c, eps=0.01, n_leapfrog=3, n_fp=3,
+                  tau=float(taus[c]))
+        jobs += [(prob, "lu", kw), (prob, "cholesky", kw)]
+    res = oracle_pool.run(oracle_pool.sample_job, jobs)
+    m = mdl.from_problem(prob)
+    for c in range(C):
+        ref, alt = res[2 * c], res[2 * c + 1]
+        np.testing.assert_array_equal(acc[:, c].astype(bool), ref["accept"])
+        for i in range(n_iter):
+            for name, g, r, a, base in (("q", q[i, c], ref["q"][i], alt["q"][i], 1e-8),
+                                        ("logp", lp[i, c], ref["logp"][i], alt["logp"][i], 1e-10)):
+                err = float(np.linalg.norm(np.asarray(g) - r))
+                tol = max(base * float(np.linalg.norm(r)), 16.0 * float(np.linalg.norm(np.asarray(r) - a)))
+                if name == "logp":
+                    # log P at the kept sample also moves with the sample's own (validated) deviation,
+                    # to first order |dU . dq|, and rounding K to FP64 bounds any evaluation of U
+                    dq = q[i, c] - ref["q"][i]
+                    du = mdl.gradient(m, ref["q"][i], float(taus[c]))
+                    tol = max(tol, 2.0 * abs(float(du @ dq)) + potential_rounding_bound(m, ref["q"][i]))
+                assert err <= tol, (c, i, name, err, tol)
+            # the recorded untempered log-likelihood -sum l(F) of the kept sample (Bernoulli-logistic)
+            f, _ = mdl.split(m, q[i, c])
+            want = -float(np.sum(mdl.lik_derivs(m, f.sum(axis=0))[0]))
+            assert abs(ll[i, c] - want) <= 1e-10 * max(1.0, abs(want)), (c, i, ll[i, c], want)
