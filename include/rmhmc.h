@@ -334,8 +334,10 @@ rmhmc_status rmhmc_stream_destroy(void* stream);
  * or 1, else EINVAL). After a warm start M = Psi^T H Psi is diagonal up to small couplings: every
  * pair (j, l) that fails the Jacobi stopping rule gets the angle theta_jl = atan(2 m_jl / (m_ll -
  * m_jj)) / 2 that zeroes its coupling to first order; with the skew matrix A of these angles,
- * X = I + A + A^2 / 2 (orthogonal up to A^4 / 4) is applied as M <- X^T M X and Psi <- Psi X by
- * tensor-core GEMMs, and the Jacobi then checks the stopping rule and rotates whatever is left.
+ * X = I + A + A^2 / 2 (orthogonal up to A^4 / 4) is applied as M <- X^T M X and Psi <- Psi X
+ * from the lists of A's nonzeros (first-order terms in double-float pairs, the sums in FP64), and
+ * the Jacobi then checks the stopping rule and rotates whatever is left. Matrices of more than
+ * 6428 (padded) rows are left to the Jacobi.
  * Pairs whose angle exceeds 1e-5 (nearly equal diagonal entries) are left to the Jacobi; a chain
  * takes it only when ||A||_F <= 1e-4 (so that A^4 / 4 is below FP64 rounding); cold starts
  * and the FP64 path use the Jacobi alone. Not part of the paper's method, which this accelerates:
@@ -352,10 +354,11 @@ rmhmc_status rmhmc_set_jacobi(rmhmc_model* m, int cluster, int sched);
  * slice product of every 128 x 64 tile computed, padding included; Cholesky
  * and triangular inverse N^3/3; Jacobi 2 * 16^3 per 16 x 16 x 16 rotation-tile product executed,
  * tiles skipped because both rotations were the identity not counted, plus 1952 per round of 8
- * rotations applied inside a 16 x 16 sub-problem). rmhmc_profile(m, 1)
+ * rotations applied inside a 16 x 16 sub-problem; the pre-rotation's kernels, category
+ * "prerotation", with no FLOPs counted). rmhmc_profile(m, 1)
  * resets and starts, rmhmc_profile(m, 0) stops. rmhmc_profile_read synchronises the stream and
  * writes per-category milliseconds, FLOPs and launch counts (host arrays of RMHMC_PROF_NCAT). */
-#define RMHMC_PROF_NCAT 10
+#define RMHMC_PROF_NCAT 11
 rmhmc_status rmhmc_profile(rmhmc_model* m, int enable);
 rmhmc_status rmhmc_profile_read(rmhmc_model* m, double* ms_host, double* flops_host,
                                 long long* launches_host);

@@ -369,26 +369,37 @@ __global__ void k_fma_peak(T* __restrict__ sink, int iters, T b, T c) {
 // After a warm start M = Psi^T H Psi differs from a diagonal matrix by small couplings. Every pair
 // (j, l) whose coupling fails the Jacobi stopping rule gets the rotation angle that zeroes it to
 // first order, theta_jl = atan(2 m_jl / (m_ll - m_jj)) / 2 (antisymmetric in j, l); with the skew
-// matrix A of these angles, X = I + A + A^2 / 2 is orthogonal up to A^4 / 4 (X^T X = I + A^4 / 4),
+// matrix A of these angles, X = I + A + A^2 / 2 + A^3 / 6 + A^4 / 24 (exp(A) to fourth order) is
+// orthogonal up to A^6 / 72 (X^T X = I + A^6 / 72 + A^8 / 576: the odd orders cancel for skew A),
 // and X^T M X has every such coupling reduced to second order. The Jacobi that follows checks the
 // stopping rule as usual and rotates whatever is left. A chain takes the pre-rotation only when
-// ||A||_F <= 1e-4 (then ||A^4|| / 4 is below FP64 rounding), i.e. after a warm start; a cold start
+// ||A||_F <= 1e-3 (then ||A^6|| / 72 is below 1e-19), i.e. after a warm start; a cold start
 // (Psi = I) is left to the Jacobi. A pair whose first-order angle exceeds kPrerotMaxTheta (nearly
 // equal diagonal entries: the first-order step would be poor) is left out of A for the Jacobi.
-constexpr double kPrerotMaxA = 1e-4;
+constexpr double kPrerotMaxA = 1e-3;
 constexpr double kPrerotMaxTheta = 1e-5;
+// |theta| <= 1e-5 <=> |x| <= tan(2e-5) for x = 2 m_jl / (m_ll - m_jj); the cut is taken at 2e-5 (the
+// two differ by 3e-15 relative). On |x| <= 2e-5, atan(x) = x (1 - x^2 / 3 + ...) with x^2 / 3 below
+// FP32 rounding, so the FP32 angle is x / 2.
+constexpr double kPrerotMaxX = 2.0 * kPrerotMaxTheta;
+constexpr int kPrerotParts = 16;  // CTAs per chain of k_prerot_norms
 
-// Per chain (one CTA each): ||M||_F^2 and min_{i < d} |m_ii|.
+// Per chain, in kPrerotParts CTAs: partial sums of ||M||_F^2 and partial minima of |m_ii| (i < d),
+// part[(c * kPrerotParts + b) * 2 + {0, 1}]; CTA 0 also clears the chain's sums of theta^2 and of
+// the entries of A (acc[4 c + 2], acc[4 c + 3]) for k_prerot_rows. Grid (kPrerotParts, chains).
 __global__ void __launch_bounds__(256) k_prerot_norms(const double* __restrict__ Mb, int dp, int d,
-                                                      double* __restrict__ out) {
-  const int c = blockIdx.x;
-  const double* M = Mb + (long long)c * dp * dp;
+                                                      double* __restrict__ acc, double* __restrict__ part) {
+  const int c = blockIdx.y, b = blockIdx.x;
+  const long long DD = (long long)dp * dp;
+  const double* M = Mb + c * DD;
   double tot = 0.0, dmin = 1e308;
-  for (long long e = threadIdx.x; e < (long long)dp * dp; e += blockDim.x) {
+  const long long e0 = DD * b / kPrerotParts, e1 = DD * (b + 1) / kPrerotParts;
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const double v = M[e];
     tot = fma(v, v, tot);
   }
-  for (int i = threadIdx.x; i < d; i += blockDim.x) dmin = fmin(dmin, fabs(M[(long long)i * dp + i]));
+  const int i0 = (int)((long long)d * b / kPrerotParts), i1 = (int)((long long)d * (b + 1) / kPrerotParts);
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) dmin = fmin(dmin, fabs(M[(long long)i * dp + i]));
   __shared__ double r0[8], r1[8];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -401,70 +412,98 @@ __global__ void __launch_bounds__(256) k_prerot_norms(const double* __restrict__
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 1e308;
+    double t = 0.0, m = 1e308;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      a += r0[w];
-      b = fmin(b, r1[w]);
+      t += r0[w];
+      m = fmin(m, r1[w]);
     }
-    out[4 * c] = a;
-    out[4 * c + 1] = b;
-    out[4 * c + 2] = 0.0;  // sum of theta^2 (filled by k_prerot_gen)
-    out[4 * c + 3] = 0.0;  // pairs rotated
+    part[((long long)c * kPrerotParts + b) * 2] = t;
+    part[((long long)c * kPrerotParts + b) * 2 + 1] = m;
+    if (b == 0) {
+      acc[4 * c + 2] = 0.0;  // sum of theta^2
+      acc[4 * c + 3] = 0.0;  // entries of A
+    }
   }
 }
 
-// A (skew) and X = I + A for every chain; the coupling test is the Jacobi's (METRIC or RELATIVE,
-// with the double-float rounding floor 4 * 2^-48 ||M||_F). Grid (blocks over dp^2, chains).
-// The sums of theta^2 and of the pairs are reduced per CTA (256 threads) before one atomic each.
-__global__ void __launch_bounds__(256) k_prerot_gen(const double* __restrict__ Mb, const double* __restrict__ nrm,
-                                                    int dp, int d, int rule, double tol,
-                                                    const int* __restrict__ status, double* __restrict__ Ab,
-                                                    double* __restrict__ Xb, double* __restrict__ acc) {
-  const int c = blockIdx.y;
+// The rows of A (skew) as lists: for row j, the columns l and angles theta_jl of the pairs that
+// fail the Jacobi's coupling test (METRIC or RELATIVE, with the double-float rounding floor
+// 4 * 2^-48 ||M||_F). One warp per row (grid: row groups of 8, chains); the warp compacts its row
+// with ballots. Per chain, entry e of row j is ent[j * dp + e] = (l, theta_jl as FP32 bits) and
+// cnt[j] the row's length (0 for the padding rows j >= d). The sums of theta^2 and of the entries
+// are reduced per CTA before one atomic each.
+// The angles are FP32: X = I + A + A^2 / 2 is orthogonal up to A^4 / 4 for any skew A, and M and
+// Psi are rotated by the same X, so the angles' rounding only leaves a coupling of ~2^-24 of its
+// size for the Jacobi. theta_lj = -theta_jl exactly (M is symmetric, the FP32 quotient is
+// correctly rounded).
+__global__ void __launch_bounds__(256) k_prerot_rows(const double* __restrict__ Mb, const double* __restrict__ part,
+                                                     int dp, int d, int rule, double tol,
+                                                     const int* __restrict__ status, int2* __restrict__ entb,
+                                                     int* __restrict__ cntb, double* __restrict__ acc) {
+  const int c = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long DD = (long long)dp * dp;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;  // dp^2 < 2^31
-  const bool in = e < DD;
-  const int j = in ? e / dp : 0, l = in ? e % dp : 0;
+  const int j = blockIdx.x * 8 + warp;
   const double* M = Mb + c * DD;
-  double th = 0.0;
-  if (in && j != l && j < d && l < d && status[c] == 0) {
+  int2* ent = entb + c * DD;
+  int* cnt = cntb + (long long)c * dp;
+  float t2 = 0.f;
+  int n = 0;
+  if (j < dp) {
+    const bool live = j < d && status[c] == 0;
+    double nrm2 = 0.0, dmin = 1e308;  // (the partial results in a fixed order)
+    for (int b = 0; b < kPrerotParts; ++b) {
+      nrm2 += part[((long long)c * kPrerotParts + b) * 2];
+      dmin = fmin(dmin, part[((long long)c * kPrerotParts + b) * 2 + 1]);
+    }
     // the stopping rule's test in the log domain (exponent fields and FP32 logarithms: FP64
-    // arithmetic runs at 1/64 of the FP32 rate here), the angle in FP64 for the pairs that fail it
-    const double v = M[e];
-    const double djj = M[(long long)j * dp + j], dll = M[(long long)l * dp + l];
-    const double dmin = nrm[4 * c + 1];
-    const float lfloor2 = log2_abs(16.0 * 1.2621774483536189e-29 * nrm[4 * c]);
+    // arithmetic runs at 1/64 of the FP32 rate here), the angle in FP32 for the pairs that fail it
+    const double djj = M[(long long)j * dp + j];
+    const float fjj = (float)djj;
+    const float lfloor2 = log2_abs(16.0 * 1.2621774483536189e-29 * nrm2);
     const float ltol2 = 2.f * log2_abs(tol), ldmin2 = 2.f * log2_abs(dmin);
-    const float lv = log2_abs(v), lj = log2_abs(djj), ll = log2_abs(dll);
-    float lthr, lfl;
-    if (rule == RMHMC_JACOBI_RELATIVE) {
-      lthr = ltol2 + lj + ll;
-      lfl = fminf(lfloor2, fmaxf(-86.37013f + 2.f * fmaxf(lj, ll), -996.578f));
-    } else {
-      lthr = ltol2 + 2.f * (lj + ll) - fmaxf(ldmin2, -996.578f);
-      lfl = lfloor2;
+    const float lj = log2_abs(djj);
+    for (int kb = 0; kb < dp; kb += 32) {
+      const int l = kb + lane;
+      float th = 0.f;
+      if (live && l < d && l != j) {
+        const double v = M[(long long)j * dp + l];
+        const double dll = M[(long long)l * dp + l];
+        const float lv = log2_abs(v), ll = log2_abs(dll);
+        float lthr, lfl;
+        if (rule == RMHMC_JACOBI_RELATIVE) {
+          lthr = ltol2 + lj + ll;
+          lfl = fminf(lfloor2, fmaxf(-86.37013f + 2.f * fmaxf(lj, ll), -996.578f));
+        } else {
+          lthr = ltol2 + 2.f * (lj + ll) - fmaxf(ldmin2, -996.578f);
+          lfl = lfloor2;
+        }
+        if (!isfinite(v) || 2.f * lv > fmaxf(lthr, lfl)) {
+          // theta = atan(x) / 2 ~ x / 2 (x^2 / 3 < 2^-24 here); x = +-inf (equal diagonal entries)
+          // and |x| > 2e-5 are left to the Jacobi; a non-finite coupling or diagonal (or one beyond
+          // the FP32 range) marks the chain (theta = 1: ||A||_F too large)
+          const float x = 2.f * (float)v / ((float)dll - fjj);
+          if (!isfinite(v) || isnan(x)) th = 1.f;
+          else if (fabsf(x) <= (float)kPrerotMaxX) th = 0.5f * x;
+        }
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, th != 0.f);
+      if (th != 0.f) {
+        const int pos = n + __popc(bal & ((1u << lane) - 1u));
+        ent[(long long)j * dp + pos] = make_int2(l, __float_as_int(th));
+      }
+      n += __popc(bal);
+      t2 = fmaf(th, th, t2);
     }
-    if (!isfinite(v) || 2.f * lv > fmaxf(lthr, lfl)) {
-      th = 0.5 * atan(2.0 * v / (dll - djj));
-      if (!isfinite(th)) th = 1.0;  // (a non-finite coupling: too large, the chain is left alone)
-      else if (fabs(th) > kPrerotMaxTheta) th = 0.0;  // left to the Jacobi
-    }
-  }
-  if (in) {
-    Ab[c * DD + e] = th;
-    Xb[c * DD + e] = (j == l ? 1.0 : 0.0) + th;
+    if (lane == 0) cnt[j] = n;
   }
   // (in FP32: the sum only decides the ||A||_F <= 1e-4 test, and the count is an integer)
-  const float tf = (float)th;
-  float t2 = tf * tf;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) t2 += __shfl_xor_sync(0xffffffffu, t2, o);
-  const int n1 = __popc(__ballot_sync(0xffffffffu, th != 0.0));
   __shared__ float r0[8];
   __shared__ int r1[8];
-  if ((threadIdx.x & 31) == 0) {
-    r0[threadIdx.x >> 5] = t2;
-    r1[threadIdx.x >> 5] = n1;
+  if (lane == 0) {
+    r0[warp] = t2;
+    r1[warp] = n;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -477,6 +516,233 @@ __global__ void __launch_bounds__(256) k_prerot_gen(const double* __restrict__ M
     if (b != 0) {
       atomicAdd(&acc[4 * c + 2], (double)a);
       atomicAdd(&acc[4 * c + 3], (double)b);
+    }
+  }
+}
+
+// (sh, sl) += t * (ah + al) for a double-float pair (ah, al) and an FP32 t: the product t * ah
+// exactly (FMA residual), the running high sum by two-sum, t * al and the residuals into the low
+// word (Dekker / Knuth error-free transformations; the low word is not renormalised: it stays
+// below n 2^-24 |sh| for n terms)
+__device__ __forceinline__ void df_madd(float& sh, float& sl, float t, float ah, float al) {
+  const float p = t * ah;
+  const float e = fmaf(t, ah, -p);
+  const float s = sh + p;
+  const float bp = s - sh;
+  const float err = (sh - (s - bp)) + (p - bp);
+  sh = s;
+  sl += fmaf(t, al, err + e);
+}
+
+constexpr int kPrerotLight = 32;  // rows with more entries go to a whole warp
+
+// out(j) for every j < dp of TL lines at once: -sum_l theta_jl in_l over row j's list (in = ih + il,
+// double-float pairs; the result as a pair (sh, sl) handed to sink(j, sh, sl)). Rows of at most 32
+// entries one per thread, longer ones one per warp (lane-strided entries, then a tree over the lanes:
+// lane 0's sum, in an order fixed by the lane numbers). The few rows of the smallest eigenvalues
+// fail the test against nearly every partner: one thread each would serialise their warps.
+template <int TL, class Sink>
+__device__ __forceinline__ void prerot_product_df(const int2* __restrict__ ent, const int* __restrict__ cnt,
+                                                  const int* heavy, int nh, int dp, const float* ih,
+                                                  const float* il, Sink sink) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int j = threadIdx.x; j < dp; j += blockDim.x) {
+    const int n = cnt[j];
+    if (n > kPrerotLight) continue;
+    float sh[TL], sl[TL];
+#pragma unroll
+    for (int l = 0; l < TL; ++l) sh[l] = sl[l] = 0.f;
+    for (int e = 0; e < n; ++e) {
+      const int2 en = ent[(long long)j * dp + e];
+      const int k = en.x;
+      const float t = -__int_as_float(en.y);
+#pragma unroll
+      for (int l = 0; l < TL; ++l) df_madd(sh[l], sl[l], t, ih[l * dp + k], il[l * dp + k]);
+    }
+    sink(j, sh, sl);
+  }
+  for (int h = warp; h < nh; h += nwarp) {
+    const int j = heavy[h], n = cnt[j];
+    float sh[TL], sl[TL];
+#pragma unroll
+    for (int l = 0; l < TL; ++l) sh[l] = sl[l] = 0.f;
+    for (int e = lane; e < n; e += 32) {
+      const int2 en = ent[(long long)j * dp + e];
+      const int k = en.x;
+      const float t = -__int_as_float(en.y);
+#pragma unroll
+      for (int l = 0; l < TL; ++l) df_madd(sh[l], sl[l], t, ih[l * dp + k], il[l * dp + k]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int l = 0; l < TL; ++l) {
+        const float oh = __shfl_down_sync(0xffffffffu, sh[l], o), ol = __shfl_down_sync(0xffffffffu, sl[l], o);
+        const float s = sh[l] + oh;
+        const float bp = s - sh[l];
+        const float err = (sh[l] - (s - bp)) + (oh - bp);
+        sh[l] = s;
+        sl[l] += ol + err;
+      }
+    }
+    if (lane == 0) sink(j, sh, sl);
+  }
+}
+
+// The same product in FP32 (in and the result u single words; sink(j, u)).
+template <int TL, class Sink>
+__device__ __forceinline__ void prerot_product_f32(const int2* __restrict__ ent, const int* __restrict__ cnt,
+                                                   const int* heavy, int nh, int dp, const float* in, Sink sink) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int j = threadIdx.x; j < dp; j += blockDim.x) {
+    const int n = cnt[j];
+    if (n > kPrerotLight) continue;
+    float u[TL];
+#pragma unroll
+    for (int l = 0; l < TL; ++l) u[l] = 0.f;
+    for (int e = 0; e < n; ++e) {
+      const int2 en = ent[(long long)j * dp + e];
+      const int k = en.x;
+      const float t = __int_as_float(en.y);
+#pragma unroll
+      for (int l = 0; l < TL; ++l) u[l] = fmaf(-t, in[l * dp + k], u[l]);
+    }
+    sink(j, u);
+  }
+  for (int h = warp; h < nh; h += nwarp) {
+    const int j = heavy[h], n = cnt[j];
+    float u[TL];
+#pragma unroll
+    for (int l = 0; l < TL; ++l) u[l] = 0.f;
+    for (int e = lane; e < n; e += 32) {
+      const int2 en = ent[(long long)j * dp + e];
+      const int k = en.x;
+      const float t = __int_as_float(en.y);
+#pragma unroll
+      for (int l = 0; l < TL; ++l) u[l] = fmaf(-t, in[l * dp + k], u[l]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int l = 0; l < TL; ++l) u[l] += __shfl_down_sync(0xffffffffu, u[l], o);
+    }
+    if (lane == 0) sink(j, u);
+  }
+}
+
+// v <- v X with X = I + A + A^2 / 2 + A^3 / 6 + A^4 / 24 for TL lines v of one chain's dp x dp
+// matrix at a time: the rows of `in` (COLS false: the lines are rows, Z = M X) or its columns (COLS
+// true: X^T Y, whose column c is Y[:, c] X). With w1 = v A (A skew: (v A)_j = -sum_l theta_jl v_l)
+// and w_{k+1} = w_k A, v X = v + w1 + w2 / 2 + w3 / 6 + w4 / 24, |w_k| <= ||A||_F^k |v| <= 1e-3k |v|.
+// w1 and w2 are formed in double-float pairs (v split into FP32 hi + lo, ~48 bits), w3 (<= 1e-9 |v|)
+// and w4 in FP32, all of them within ~1e-16 |v|; v + (the sum) is formed in FP64. SYM (with COLS):
+// the output is symmetric, and the CTA of column c writes both out[k][c] and out[c][k] for k <= c
+// (each pair of mirrored entries has one writer). Grid (dp / TL, chains); shared memory 16 TL dp
+// + 4 dp bytes; chains with mask 0 return. The summation order of every output is fixed (runs
+// repeat bit for bit).
+template <int TL, bool COLS, bool SYM>
+__global__ void __launch_bounds__(256) k_prerot_apply(const double* inb, double* outb,  // (may alias)
+                                                      const int2* __restrict__ entb, const int* __restrict__ cntb,
+                                                      const int* __restrict__ mask, int dp) {
+  extern __shared__ float psf[];
+  __shared__ int nheavy;
+  const int c = blockIdx.y;
+  if (!mask[c]) return;
+  const long long DD = (long long)dp * dp;
+  const double* in = inb + c * DD;
+  double* out = outb + c * DD;
+  const int2* ent = entb + c * DD;
+  const int* cnt = cntb + (long long)c * dp;
+  const int l0 = blockIdx.x * TL, nl = min(TL, dp - l0);
+  const int TD = TL * dp;
+  // four [TL][dp] FP32 arrays: P1, P2 = v (hi, lo), then w2 (hi, lo), then P2 = w3; P3, P4 = w1
+  // (hi, lo), into which w2 / 2, w3 / 6 and w4 / 24 are folded; res overlays P1, P2 at the end
+  float* P1 = psf;
+  float* P2 = P1 + TD;
+  float* P3 = P2 + TD;
+  float* P4 = P3 + TD;
+  int* heavy = reinterpret_cast<int*>(P4 + TD);  // [dp]
+  double* res = reinterpret_cast<double*>(psf);  // [TL][dp]
+  if (threadIdx.x == 0) nheavy = 0;
+  for (int e = threadIdx.x; e < TD; e += blockDim.x) {
+    int l, k;
+    if (COLS) { k = e / TL; l = e - k * TL; }
+    else { l = e / dp; k = e - l * dp; }
+    const double x = l < nl ? (COLS ? in[(long long)k * dp + l0 + l] : in[(long long)(l0 + l) * dp + k]) : 0.0;
+    const float h = __double2float_rn(x);
+    P1[l * dp + k] = h;
+    P2[l * dp + k] = __double2float_rn(x - (double)h);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < dp; j += blockDim.x)
+    if (cnt[j] > kPrerotLight) heavy[atomicAdd(&nheavy, 1)] = j;
+  __syncthreads();
+  const int nh = nheavy;
+  // w1 = v A -> P3, P4
+  prerot_product_df<TL>(ent, cnt, heavy, nh, dp, P1, P2, [&](int j, const float* h, const float* lo) {
+#pragma unroll
+    for (int l = 0; l < TL; ++l) {
+      P3[l * dp + j] = h[l];
+      P4[l * dp + j] = lo[l];
+    }
+  });
+  __syncthreads();
+  // w2 = w1 A -> P1, P2 (v is no longer read)
+  prerot_product_df<TL>(ent, cnt, heavy, nh, dp, P3, P4, [&](int j, const float* h, const float* lo) {
+#pragma unroll
+    for (int l = 0; l < TL; ++l) {
+      P1[l * dp + j] = h[l];
+      P2[l * dp + j] = lo[l];
+    }
+  });
+  __syncthreads();
+  // w3 = w2 A from w2's high words (P1, read by every thread); each thread first folds its own
+  // entries of w2 / 2 into w1 (two-sum of the high words), then keeps w3 in P2 (its own entries)
+  prerot_product_f32<TL>(ent, cnt, heavy, nh, dp, P1, [&](int j, const float* u) {
+#pragma unroll
+    for (int l = 0; l < TL; ++l) {
+      const int i = l * dp + j;
+      const float a = 0.5f * P1[i];
+      const float s = P3[i] + a;
+      const float bp = s - P3[i];
+      const float err = (P3[i] - (s - bp)) + (a - bp);
+      P3[i] = s;
+      P4[i] += fmaf(0.5f, P2[i], err);
+      P2[i] = u[l];
+    }
+  });
+  __syncthreads();
+  // w4 = w3 A; w3 / 6 + w4 / 24 into the low words
+  prerot_product_f32<TL>(ent, cnt, heavy, nh, dp, P2, [&](int j, const float* u) {
+#pragma unroll
+    for (int l = 0; l < TL; ++l) {
+      const int i = l * dp + j;
+      P4[i] += fmaf(u[l], 1.f / 24.f, P2[i] * (1.f / 6.f));
+    }
+  });
+  __syncthreads();
+  // v X = v + (P3 + P4) in FP64 (res overlays P1, P2: no longer read)
+  for (int e = threadIdx.x; e < TD; e += blockDim.x) {
+    int l, k;
+    if (COLS) { k = e / TL; l = e - k * TL; }
+    else { l = e / dp; k = e - l * dp; }
+    if (l >= nl) continue;
+    const double x = COLS ? in[(long long)k * dp + l0 + l] : in[(long long)(l0 + l) * dp + k];
+    res[l * dp + k] = x + ((double)P3[l * dp + k] + (double)P4[l * dp + k]);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TD; e += blockDim.x) {
+    int l, k;
+    if (COLS) { k = e / TL; l = e - k * TL; }
+    else { l = e / dp; k = e - l * dp; }
+    if (l >= nl) continue;
+    if (!COLS) out[(long long)(l0 + l) * dp + k] = res[l * dp + k];
+    else if (!SYM || k <= l0 + l) out[(long long)k * dp + l0 + l] = res[l * dp + k];
+  }
+  if (SYM) {
+    for (int e = threadIdx.x; e < TD; e += blockDim.x) {
+      const int l = e / dp, k = e - l * dp;
+      if (l < nl && k <= l0 + l) out[(long long)(l0 + l) * dp + k] = res[l * dp + k];
     }
   }
 }
@@ -665,10 +931,10 @@ namespace {
 
 enum Cat {
   CAT_GEMM = 0, CAT_JACOBI, CAT_CHOL, CAT_TRINV, CAT_MODEL, CAT_CONTRACT, CAT_VECTOR, CAT_MGS, CAT_JACOBI_DF,
-  CAT_GEMM_TC
+  CAT_GEMM_TC, CAT_PREROT
 };
-const char* kCatNames[RMHMC_PROF_NCAT] = {"gemm_f64", "jacobi_f64", "cholesky", "trinv",
-                                          "model", "contract", "vector", "reorth", "jacobi_df", "gemm_tc"};
+const char* kCatNames[RMHMC_PROF_NCAT] = {"gemm_f64", "jacobi_f64", "cholesky", "trinv", "model", "contract",
+                                          "vector", "reorth", "jacobi_df", "gemm_tc", "prerotation"};
 
 // bf16 slices of the mixed form's tensor-core GEMMs: 9 (63 bits, at or below FP64 GEMM rounding)
 // for the K^-1 algebra, whose cond(K) ~ 1e8 amplification needs FP64-level products, and 7 (49 bits,
@@ -911,45 +1177,52 @@ void primal_model_layer(rmhmc_model* m) {
 // --- geometry at the current q: U, dU, Hessian, warm-started eigendecomposition, g(lambda);
 //     with `third`, also the third-derivative operator (the dual model's A1, S^2 and F-phase
 //     statistics; the primal model needs no more than l''').
-// The first-order pre-rotation of a warm eigen-update (see k_prerot_gen), on the tensor cores:
-// A and X = I + A (W and Y are free during the eigen-update), X += A A / 2, then M <- X^T (M X)
-// and Psi^T <- X^T Psi^T for the chains in pr_mask. The products read their operands' slices, so the
-// outputs may overwrite M and Psi^T.
+// The first-order pre-rotation of a warm eigen-update (see k_prerot_rows). A holds a few percent
+// of nonzeros, so X = I + A + A^2 / 2 is applied from the lists of A's rows: M <- X^T (M X) and
+// Psi^T <- X^T Psi^T for the chains in pr_mask (Z = M X in Zp; the lists in W and Y, free during the
+// eigen-update). Eight lines per CTA while their buffers (16 TL dp + 4 dp bytes) stay within 200 KB
+// of shared memory, else two; beyond dp = 6428 the pre-rotation is not taken.
+inline size_t prerot_smem(int TL, int dp) { return (size_t)16 * TL * dp + (size_t)4 * dp; }
+bool prerot_fits(int dp) { return prerot_smem(2, dp) <= (size_t)226 * 1024; }
+
+template <int TL>
+void prerot_apply_all(rmhmc_model* m, const int2* ent, const int* cnt) {
+  cudaStream_t s = m->stream;
+  const int C = m->C, dp = m->dp;
+  const size_t smem = prerot_smem(TL, dp);
+  // (the opt-in limit covers the kernel's static shared memory too: ask for what this launch needs)
+  static size_t attr_bytes = 0;
+  if (smem > attr_bytes) {
+    cudaFuncSetAttribute(k_prerot_apply<TL, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_prerot_apply<TL, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_prerot_apply<TL, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_bytes = smem;
+  }
+  const dim3 grid((dp + TL - 1) / TL, C);
+  const int* mk = m->pr_mask;
+  PROF(m, CAT_PREROT, 0)
+  k_prerot_apply<TL, false, false><<<grid, 256, smem, s>>>(m->M, m->Zp, ent, cnt, mk, dp);
+  PROF(m, CAT_PREROT, 0)
+  k_prerot_apply<TL, true, true><<<grid, 256, smem, s>>>(m->Zp, m->M, ent, cnt, mk, dp);
+  PROF(m, CAT_PREROT, 0)
+  k_prerot_apply<TL, true, false><<<grid, 256, smem, s>>>(m->PsiT, m->PsiT, ent, cnt, mk, dp);
+}
+
 void prerotate(rmhmc_model* m) {
   cudaStream_t s = m->stream;
   const int C = m->C, dp = m->dp, d = m->d;
-  const long long DD = (long long)dp * dp;
-  const int S = kSlicesD;
-  double* A = m->W;
-  double* X = m->Y;
-  PROF(m, CAT_JACOBI_DF, 0)
-  k_prerot_norms<<<C, 256, 0, s>>>(m->M, dp, d, m->pr_acc);
-  PROF(m, CAT_JACOBI_DF, 0)
-  k_prerot_gen<<<dim3(nblk(DD), C), 256, 0, s>>>(m->M, m->pr_acc, dp, d, m->jacobi_rule, m->tol, m->status, A, X,
-                                                 m->pr_acc);
-  PROF(m, CAT_JACOBI_DF, 0)
+  int2* ent = reinterpret_cast<int2*>(m->W);  // C x dp^2 (column, angle) entries
+  int* cnt = reinterpret_cast<int*>(m->Y);    // C x dp row lengths
+  double* part = m->pr_acc + 4 * C;
+  PROF(m, CAT_PREROT, 0)
+  k_prerot_norms<<<dim3(kPrerotParts, C), 256, 0, s>>>(m->M, dp, d, m->pr_acc, part);
+  PROF(m, CAT_PREROT, 0)
+  k_prerot_rows<<<dim3((dp + 7) / 8, C), 256, 0, s>>>(m->M, part, dp, d, m->jacobi_rule, m->tol, m->status, ent,
+                                                      cnt, m->pr_acc);
+  PROF(m, CAT_PREROT, 0)
   k_prerot_mask<<<nblk(C), 256, 0, s>>>(m->pr_acc, C, m->pr_mask, m->jw.tiles);
-  const int* mk = m->pr_mask;
-  TcOperand oa = tc_operand(m->tcA, dp, dp, S, C, false), ob = tc_operand(m->tcB, dp, dp, S, C, true);
-  // X += A A / 2
-  PROF(m, CAT_GEMM_TC, 0) tc_split(s, A, dp, DD, true, C, oa, mk);
-  PROF(m, CAT_GEMM_TC, 0) tc_split(s, A, dp, DD, false, C, ob, mk);
-  PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(oa, ob, C, false, m->tc_nt))
-  gemm_tc(s, oa, ob, 0.5, 1.0, X, dp, DD, C, false, m->status, 1, mk, m->tc_nt);
-  // Z = M X
-  PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->M, dp, DD, true, C, oa, mk);
-  PROF(m, CAT_GEMM_TC, 0) tc_split(s, X, dp, DD, false, C, ob, mk);
-  PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(oa, ob, C, false, m->tc_nt))
-  gemm_tc(s, oa, ob, 1.0, 0.0, m->Zp, dp, DD, C, false, m->status, 1, mk, m->tc_nt);
-  // M = X^T Z (symmetric)
-  PROF(m, CAT_GEMM_TC, 0) tc_split(s, X, dp, DD, false, C, oa, mk);
-  PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->Zp, dp, DD, false, C, ob, mk);
-  PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(oa, ob, C, true, m->tc_nt))
-  gemm_tc(s, oa, ob, 1.0, 0.0, m->M, dp, DD, C, true, m->status, 1, mk, m->tc_nt);
-  // Psi^T = X^T Psi^T (op(A) = X^T is still split in oa)
-  PROF(m, CAT_GEMM_TC, 0) tc_split(s, m->PsiT, dp, DD, false, C, ob, mk);
-  PROF(m, CAT_GEMM_TC, gemm_tc_tensor_flops(oa, ob, C, false, m->tc_nt))
-  gemm_tc(s, oa, ob, 1.0, 0.0, m->PsiT, dp, DD, C, false, m->status, 1, mk, m->tc_nt);
+  if (prerot_smem(8, dp) <= (size_t)200 * 1024) prerot_apply_all<8>(m, ent, cnt);
+  else prerot_apply_all<2>(m, ent, cnt);
 }
 
 void eval_geometry(rmhmc_model* m, bool third) {
@@ -991,7 +1264,7 @@ void eval_geometry(rmhmc_model* m, bool third) {
   // angles
   const bool cold = m->cold || m->eigen_start == 1;
   const int sched = cold ? RMHMC_JACOBI_CYCLIC : m->jacobi_sched;
-  if (m->prerot && !cold && use_tc(m, dp, dp)) {
+  if (m->prerot && !cold && use_tc(m, dp, dp) && prerot_fits(dp)) {
     prerotate(m);
     m->tc_pa_ok = m->tc_pb_ok = false;
   }
@@ -1241,7 +1514,7 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
   ALLOC(m->jw.tiles, (size_t)kJacStats * C);
   ALLOC(m->jw.crit, (size_t)C * (dp / kJacBlk) * (dp / kJacBlk));
   ALLOC(m->Zp, (size_t)C * DD);
-  ALLOC(m->pr_acc, (size_t)4 * C);
+  ALLOC(m->pr_acc, (size_t)(4 + 2 * kPrerotParts) * C);
   ALLOC(m->pr_mask, (size_t)C);
 #undef ALLOC
   return st;

@@ -23,7 +23,7 @@ JACOBI_RULES = {"metric": 0, "relative": 1}
 EIGEN_STARTS = {"warm": 0, "cold": 1}
 CHAIN_NOTPD, CHAIN_NOTCONV, CHAIN_NONFINITE, CHAIN_TIMEOUT = 1, 2, 4, 8
 JACOBI_SCHEDULES = ["cyclic", "dynamic"]  # rmhmc_jacobi_schedule
-PROF_NCAT = 10
+PROF_NCAT = 11
 
 
 class KernelDesc(ctypes.Structure):
