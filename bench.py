@@ -440,7 +440,7 @@ def _tensor_roofline(prof):
 # The pipe whose measured peak bounds each timed category's counted FLOPs: FP64 FMA
 # (rmhmc_fp64_peak), the double-float multiply-add (rmhmc_df_peak), the bf16 tensor rate.
 CATEGORY_PIPE = {"gemm_f64": "fp64", "jacobi_f64": "fp64", "cholesky": "fp64", "trinv": "fp64",
-                 "jacobi_df": "df", "gemm_tc": "bf16"}
+                 "jacobi_df": "df", "gemm_tc": "bf16", "prerotation": "df"}
 
 
 def category_rooflines(prof, peaks, mixed=False):
@@ -489,7 +489,7 @@ def _roofline(rmhmc, prof, C):
     dom_ms, dom_flops, dom_launches = prof[dom]
     if dom == "gemm_tc":
         return _tensor_roofline(prof)
-    if dom == "jacobi_df":
+    if dom in ("jacobi_df", "prerotation"):
         # the double-float multiply-add (Dot2 step: 12 FP32 instructions) measured on this GPU
         peak = rmhmc.df_peak_tflops(300)
         fp32 = rmhmc.fp32_peak_tflops(300)
@@ -505,6 +505,10 @@ def _roofline(rmhmc, prof, C):
         out["achieved_note"] = ("executed work: 16x16x16 rotation-tile products x 8192 flops (skipped identity "
                                 "tiles not counted) + inner rotation rounds x 1952 flops; rotation angles, "
                                 "stopping tests and conversions not counted")
+    elif dom == "prerotation":
+        out["achieved_note"] = ("double-float multiply-adds of the first- and second-order sparse products "
+                                "(2 flops each, 24 dp per pre-rotated pair); the FP32 higher-order products, "
+                                "the coupling test and the element-wise passes not counted")
     if dom in DRAM_BYTES_PER_CHAIN:
         out["traffic"] = DRAM_BYTES_PER_CHAIN[dom] * C
         out["traffic_note"] = "bytes per launch, ncu capture at 8 chains scaled to the chain count"

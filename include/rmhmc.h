@@ -337,7 +337,7 @@ rmhmc_status rmhmc_stream_destroy(void* stream);
  * X = I + A + A^2 / 2 (orthogonal up to A^4 / 4) is applied as M <- X^T M X and Psi <- Psi X
  * from the lists of A's nonzeros (first-order terms in double-float pairs, the sums in FP64), and
  * the Jacobi then checks the stopping rule and rotates whatever is left. Matrices of more than
- * 6428 (padded) rows are left to the Jacobi.
+ * 1701 (padded) rows are left to the Jacobi.
  * Pairs whose angle exceeds 1e-5 (nearly equal diagonal entries) are left to the Jacobi; a chain
  * takes it only when ||A||_F <= 1e-4 (so that A^4 / 4 is below FP64 rounding); cold starts
  * and the FP64 path use the Jacobi alone. Not part of the paper's method, which this accelerates:
@@ -355,7 +355,8 @@ rmhmc_status rmhmc_set_jacobi(rmhmc_model* m, int cluster, int sched);
  * and triangular inverse N^3/3; Jacobi 2 * 16^3 per 16 x 16 x 16 rotation-tile product executed,
  * tiles skipped because both rotations were the identity not counted, plus 1952 per round of 8
  * rotations applied inside a 16 x 16 sub-problem; the pre-rotation's kernels, category
- * "prerotation", with no FLOPs counted). rmhmc_profile(m, 1)
+ * "prerotation": 2 flops per double-float multiply-add of its first- and second-order products,
+ * 24 dp per pre-rotated pair). rmhmc_profile(m, 1)
  * resets and starts, rmhmc_profile(m, 0) stops. rmhmc_profile_read synchronises the stream and
  * writes per-category milliseconds, FLOPs and launch counts (host arrays of RMHMC_PROF_NCAT). */
 #define RMHMC_PROF_NCAT 11

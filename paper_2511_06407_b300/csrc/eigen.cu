@@ -415,7 +415,8 @@ __global__ void __launch_bounds__(NW * 32)
                int* __restrict__ sweeps_acc, double* __restrict__ Vb, double* __restrict__ Db,
                double* __restrict__ slotsb, int* __restrict__ flagsb,
                unsigned long long* __restrict__ tiles, typename E::T* __restrict__ Mwb,
-               typename E::T* __restrict__ Pwb, float* __restrict__ critb, int sched) {
+               typename E::T* __restrict__ Pwb, float* __restrict__ critb, int sched,
+               const int* __restrict__ pre) {
   using T = typename E::T;
   static_assert(sizeof(T) == sizeof(double), "tiles of V and D are stored in double-sized slots");
   cg::cluster_group cluster = cg::this_cluster();
@@ -474,10 +475,12 @@ __global__ void __launch_bounds__(NW * 32)
   __shared__ unsigned char sused[kMaxBlocks];
 
   if constexpr (E::kPairs) {
-    for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
-      E::st(Mw + e, E::split(__ldcg(M + e)));
-      E::st(Pw + e, E::split(__ldcg(P + e)));
-    }
+    // (chains flagged in pre arrive with M and Psi^T already in the pair buffers)
+    if (!(pre && pre[chain]))
+      for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
+        E::st(Mw + e, E::split(__ldcg(M + e)));
+        E::st(Pw + e, E::split(__ldcg(P + e)));
+      }
     cluster.sync();
   }
 
@@ -1064,12 +1067,13 @@ void jacobi_f64(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, in
   }
   launch_cluster(k_jacobi_t<ElemF64>, n_chains, cluster, smem, s, M, PsiT, lam, dp, d, rule, tol, max_sweeps,
                  status, sweeps_out, sweeps_acc, w.V, w.D, w.slots, w.flags, w.tiles, (double*)nullptr,
-                 (double*)nullptr, w.crit, sched);
+                 (double*)nullptr, w.crit, sched, (const int*)nullptr);
 }
 
 void jacobi_df(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,
                int rule, double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
-               JacobiWork w, int cluster, double* pair_scratch_M, double* pair_scratch_P, int sched) {
+               JacobiWork w, int cluster, double* pair_scratch_M, double* pair_scratch_P, int sched,
+               const int* pre) {
   const size_t smem = (size_t)NW * WARP_SMEM * sizeof(double);
   static bool attr_set = false;
   if (!attr_set) {
@@ -1079,7 +1083,7 @@ void jacobi_df(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int
   launch_cluster(k_jacobi_t<ElemDF>, n_chains, cluster, smem, s, M, PsiT, lam, dp, d, rule, tol, max_sweeps,
                  status, sweeps_out, sweeps_acc, w.V, w.D, w.slots, w.flags, w.tiles,
                  reinterpret_cast<float2*>(pair_scratch_M), reinterpret_cast<float2*>(pair_scratch_P), w.crit,
-                 sched);
+                 sched, pre);
 }
 
 void mgs_rows_f64(cudaStream_t s, double* PsiT, int dp, int d, int n_chains, const int* eig_count,
@@ -1142,7 +1146,7 @@ extern "C" rmhmc_status rmhmc_eigh_noalloc(void* cuda_stream, int n, int d, cons
                      max_sweeps, status,
                      sweeps_dev ? sweeps_dev : sweeps, (int*)nullptr, V, D, slots, flags,
                      (unsigned long long*)nullptr, (double*)nullptr, (double*)nullptr, (float*)nullptr,
-                     (int)RMHMC_JACOBI_CYCLIC) != cudaSuccess)
+                     (int)RMHMC_JACOBI_CYCLIC, (const int*)nullptr) != cudaSuccess)
     return RMHMC_ECUDA;
   const long long out = (long long)n * d * d;
   k_noalloc_unpack<<<(unsigned)((out + 255) / 256), 256, 0, s>>>(lamp, P, d, dp, n, lam_dev, Q_dev);

@@ -164,10 +164,14 @@ void jacobi_f64(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, in
                 int rule, double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
                 JacobiWork w, int cluster, int sched);
 // The same eigen-update with the phase-2 rotations in double-float (FP32 pair) arithmetic;
-// pair_scratch_M / pair_scratch_P are n_chains x dp x dp doubles of scratch (used as float2).
+// pair_scratch_M / pair_scratch_P are n_chains x dp x dp doubles of scratch (used as float2, laid
+// out as M and Psi^T). Chains c with pre[c] != 0 (pre may be null) start from the pairs already in
+// the scratch (written by the pre-rotation) instead of converting M and Psi^T; every chain ends with
+// M, Psi^T and lam written from the pairs.
 void jacobi_df(cudaStream_t s, double* M, double* PsiT, double* lam, int dp, int d, int n_chains,
                int rule, double tol, int max_sweeps, int* status, int* sweeps_out, int* sweeps_acc,
-               JacobiWork w, int cluster, double* pair_scratch_M, double* pair_scratch_P, int sched);
+               JacobiWork w, int cluster, double* pair_scratch_M, double* pair_scratch_P, int sched,
+               const int* pre);
 // Modified Gram-Schmidt on the first d rows of PsiT (dp x dp per chain), for chains whose
 // eig_count is a positive multiple of every (0 = never).
 void mgs_rows_f64(cudaStream_t s, double* PsiT, int dp, int d, int n_chains, const int* eig_count,

@@ -426,16 +426,56 @@ __global__ void __launch_bounds__(256) k_prerot_norms(const double* __restrict__
   }
 }
 
+// x as a double-float pair (hi, lo) by integer operations on its bits (B300's FP64 pipe, which also
+// runs the FP64 <-> FP32 conversions, is 1/64 of its FP32 rate): hi = x rounded to 24 significant
+// bits, lo = x - hi rounded to 24 (both ties away from zero), so |x - hi - lo| <= 2^-25 |lo| <=
+// 2^-49 |x|. Zero, subnormal doubles and magnitudes below FP32's normal range give (+-0, 0), and lo
+// is 0 where it would fall below that range (|x| < ~1e-30); beyond the range hi is +-inf, and a NaN
+// stays a NaN.
+__device__ __forceinline__ float2 df_split_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned long long mag = b & 0x7fffffffffffffffull;
+  const int E = (int)(mag >> 52);
+  if (E == 0x7ff)
+    return make_float2(__uint_as_float(sign | 0x7f800000u | ((mag & 0xfffffffffffffull) ? 0x400000u : 0u)), 0.f);
+  if (E < 1023 - 126) return make_float2(__uint_as_float(sign), 0.f);
+  const unsigned low = (unsigned)(mag & 0x1fffffffull);                 // the 29 bits below hi
+  const unsigned up = (low >> 28) & 1u;                                   // round half away from zero
+  const unsigned long long hmag = (mag & ~0x1fffffffull) + ((unsigned long long)up << 29);  // (carries into E)
+  const int Eh = (int)(hmag >> 52);
+  if (Eh > 1023 + 127) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+  const float hi = __uint_as_float(sign | ((unsigned)(Eh - 1023 + 127) << 23) | (unsigned)((hmag >> 29) & 0x7fffffu));
+  const int R = (int)low - (int)(up << 29);  // x - hi in units of 2^(E - 1075), |R| <= 2^28
+  if (R == 0) return make_float2(hi, 0.f);
+  const unsigned r = (unsigned)(R < 0 ? -R : R);
+  const int nb = 32 - __clz(r);
+  const int el = E - 1075 + (nb - 1) + 127;
+  if (el <= 0) return make_float2(hi, 0.f);
+  unsigned m = nb > 24 ? ((r >> (nb - 25)) + 1u) >> 1 : (r << (24 - nb));  // (rounded half up)
+  int ef = el;
+  if (m >> 24) {  // (the rounding carried into a 25th bit)
+    m >>= 1;
+    ++ef;
+  }
+  return make_float2(hi, __uint_as_float((sign ^ (R < 0 ? 0x80000000u : 0u)) | ((unsigned)ef << 23) | (m & 0x7fffffu)));
+}
+
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
 // The rows of A (skew) as lists: for row j, the columns l and angles theta_jl of the pairs that
 // fail the Jacobi's coupling test (METRIC or RELATIVE, with the double-float rounding floor
 // 4 * 2^-48 ||M||_F). One warp per row (grid: row groups of 8, chains); the warp compacts its row
-// with ballots. Per chain, entry e of row j is ent[j * dp + e] = (l, theta_jl as FP32 bits) and
-// cnt[j] the row's length (0 for the padding rows j >= d). The sums of theta^2 and of the entries
-// are reduced per CTA before one atomic each.
-// The angles are FP32: X = I + A + A^2 / 2 is orthogonal up to A^4 / 4 for any skew A, and M and
-// Psi are rotated by the same X, so the angles' rounding only leaves a coupling of ~2^-24 of its
-// size for the Jacobi. theta_lj = -theta_jl exactly (M is symmetric, the FP32 quotient is
-// correctly rounded).
+// with ballots. Per chain, entry e of row j is ent[e * dp + j] = (l, theta_jl as FP32 bits), entry-
+// major so that the warps that walk 32 rows at once read one line per entry, and cnt[j] is the
+// row's length (0 for the padding rows j >= d). The sums of theta^2 and of the entries are reduced
+// per CTA before one atomic each.
+// The angles are FP32: X (exp(A) to fourth order, below) is orthogonal to rounding for any small
+// skew A, and M and Psi are rotated by the same X, so the angles' rounding only leaves a coupling of
+// ~2^-24 of its size for the Jacobi. theta_lj = -theta_jl exactly (M is symmetric, the FP32
+// conversions are sign-symmetric and the FP32 quotient is correctly rounded).
 __global__ void __launch_bounds__(256) k_prerot_rows(const double* __restrict__ Mb, const double* __restrict__ part,
                                                      int dp, int d, int rule, double tol,
                                                      const int* __restrict__ status, int2* __restrict__ entb,
@@ -446,22 +486,30 @@ __global__ void __launch_bounds__(256) k_prerot_rows(const double* __restrict__ 
   const double* M = Mb + c * DD;
   int2* ent = entb + c * DD;
   int* cnt = cntb + (long long)c * dp;
-  float t2 = 0.f;
-  int n = 0;
-  if (j < dp) {
-    const bool live = j < d && status[c] == 0;
-    double nrm2 = 0.0, dmin = 1e308;  // (the partial results in a fixed order)
+  // the test's constants, once per CTA: log2 of the floor, of tol^2 and of min |m_ii|^2 (the
+  // partial results of k_prerot_norms in a fixed order)
+  __shared__ float sfl[3];
+  if (threadIdx.x == 0) {
+    double nrm2 = 0.0, dmin = 1e308;
     for (int b = 0; b < kPrerotParts; ++b) {
       nrm2 += part[((long long)c * kPrerotParts + b) * 2];
       dmin = fmin(dmin, part[((long long)c * kPrerotParts + b) * 2 + 1]);
     }
-    // the stopping rule's test in the log domain (exponent fields and FP32 logarithms: FP64
-    // arithmetic runs at 1/64 of the FP32 rate here), the angle in FP32 for the pairs that fail it
+    sfl[0] = log2_abs(16.0 * 1.2621774483536189e-29 * nrm2);
+    sfl[1] = 2.f * log2_abs(tol);
+    sfl[2] = 2.f * log2_abs(dmin);
+  }
+  __syncthreads();
+  float t2 = 0.f;
+  int n = 0;
+  if (j < dp) {
+    const bool live = j < d && status[c] == 0;
+    // the stopping rule's test in the log domain (exponent fields and FP32 logarithms), the angle in
+    // FP32 for the pairs that fail it
+    const float lfloor2 = sfl[0], ltol2 = sfl[1], ldmin2 = sfl[2];
     const double djj = M[(long long)j * dp + j];
-    const float fjj = (float)djj;
-    const float lfloor2 = log2_abs(16.0 * 1.2621774483536189e-29 * nrm2);
-    const float ltol2 = 2.f * log2_abs(tol), ldmin2 = 2.f * log2_abs(dmin);
     const float lj = log2_abs(djj);
+    const float fjj = df_split_bits(djj).x;
     for (int kb = 0; kb < dp; kb += 32) {
       const int l = kb + lane;
       float th = 0.f;
@@ -477,26 +525,27 @@ __global__ void __launch_bounds__(256) k_prerot_rows(const double* __restrict__ 
           lthr = ltol2 + 2.f * (lj + ll) - fmaxf(ldmin2, -996.578f);
           lfl = lfloor2;
         }
-        if (!isfinite(v) || 2.f * lv > fmaxf(lthr, lfl)) {
-          // theta = atan(x) / 2 ~ x / 2 (x^2 / 3 < 2^-24 here); x = +-inf (equal diagonal entries)
-          // and |x| > 2e-5 are left to the Jacobi; a non-finite coupling or diagonal (or one beyond
-          // the FP32 range) marks the chain (theta = 1: ||A||_F too large)
-          const float x = 2.f * (float)v / ((float)dll - fjj);
-          if (!isfinite(v) || isnan(x)) th = 1.f;
+        const bool fin = finite_bits(v);
+        if (!fin || 2.f * lv > fmaxf(lthr, lfl)) {
+          // theta = atan(x) / 2 ~ x / 2 (x^2 / 3 < 2^-24 here); x = +-inf (equal diagonal entries,
+          // or an entry beyond the FP32 range) and |x| > 2e-5 are left to the Jacobi; a non-finite
+          // coupling or a NaN marks the chain (theta = 1: ||A||_F too large)
+          const float x = 2.f * df_split_bits(v).x / (df_split_bits(dll).x - fjj);
+          if (!fin || isnan(x)) th = 1.f;
           else if (fabsf(x) <= (float)kPrerotMaxX) th = 0.5f * x;
         }
       }
       const unsigned bal = __ballot_sync(0xffffffffu, th != 0.f);
       if (th != 0.f) {
         const int pos = n + __popc(bal & ((1u << lane) - 1u));
-        ent[(long long)j * dp + pos] = make_int2(l, __float_as_int(th));
+        ent[(long long)pos * dp + j] = make_int2(l, __float_as_int(th));
       }
       n += __popc(bal);
       t2 = fmaf(th, th, t2);
     }
     if (lane == 0) cnt[j] = n;
   }
-  // (in FP32: the sum only decides the ||A||_F <= 1e-4 test, and the count is an integer)
+  // (in FP32: the sum only decides the ||A||_F <= 1e-3 test, and the count is an integer)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) t2 += __shfl_xor_sync(0xffffffffu, t2, o);
   __shared__ float r0[8];
@@ -534,45 +583,54 @@ __device__ __forceinline__ void df_madd(float& sh, float& sl, float t, float ah,
   sl += fmaf(t, al, err + e);
 }
 
+constexpr int kPrerotLines = 8;   // lines of the matrix per CTA of k_prerot_apply
 constexpr int kPrerotLight = 32;  // rows with more entries go to a whole warp
 
-// out(j) for every j < dp of TL lines at once: -sum_l theta_jl in_l over row j's list (in = ih + il,
-// double-float pairs; the result as a pair (sh, sl) handed to sink(j, sh, sl)). Rows of at most 32
-// entries one per thread, longer ones one per warp (lane-strided entries, then a tree over the lanes:
-// lane 0's sum, in an order fixed by the lane numbers). The few rows of the smallest eigenvalues
-// fail the test against nearly every partner: one thread each would serialise their warps.
-template <int TL, class Sink>
-__device__ __forceinline__ void prerot_product_df(const int2* __restrict__ ent, const int* __restrict__ cnt,
-                                                  const int* heavy, int nh, int dp, const float* ih,
-                                                  const float* il, Sink sink) {
+// out(j) for every row j < dp of the 8 lines at once: -sum_k theta_jk in(k) over row j's list
+// (in = ih + il, double-float pairs, [dp][8] in shared memory, read four lines at a time; the result
+// as pairs (sh, sl) handed to sink(j, sh, sl)). Rows of at most 32 entries one per thread (the next
+// entry loaded ahead; the entry-major lists give the 32 rows of a warp one line per entry), longer
+// ones one per warp (lane-strided entries, then a tree over the lanes: lane 0's sum, in an order
+// fixed by the lane numbers). The few rows of the smallest eigenvalues fail the test against nearly
+// every partner: one thread each would serialise their warps.
+template <class Sink>
+__device__ __forceinline__ void prerot_product_df(const int2* __restrict__ ent, const int* scnt, const int* heavy,
+                                                  int nh, int dp, const float* ih, const float* il, Sink sink) {
+  constexpr int TL = kPrerotLines;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  auto madd = [&](float* sh, float* sl, int2 en) {
+    const float t = -__int_as_float(en.y);
+    const float4* h4 = reinterpret_cast<const float4*>(ih + en.x * TL);
+    const float4* l4 = reinterpret_cast<const float4*>(il + en.x * TL);
+#pragma unroll
+    for (int q = 0; q < TL / 4; ++q) {
+      const float4 h = h4[q], lo = l4[q];
+      df_madd(sh[4 * q], sl[4 * q], t, h.x, lo.x);
+      df_madd(sh[4 * q + 1], sl[4 * q + 1], t, h.y, lo.y);
+      df_madd(sh[4 * q + 2], sl[4 * q + 2], t, h.z, lo.z);
+      df_madd(sh[4 * q + 3], sl[4 * q + 3], t, h.w, lo.w);
+    }
+  };
   for (int j = threadIdx.x; j < dp; j += blockDim.x) {
-    const int n = cnt[j];
+    const int n = scnt[j];
     if (n > kPrerotLight) continue;
     float sh[TL], sl[TL];
 #pragma unroll
     for (int l = 0; l < TL; ++l) sh[l] = sl[l] = 0.f;
+    int2 nx = n > 0 ? ent[j] : make_int2(0, 0);
     for (int e = 0; e < n; ++e) {
-      const int2 en = ent[(long long)j * dp + e];
-      const int k = en.x;
-      const float t = -__int_as_float(en.y);
-#pragma unroll
-      for (int l = 0; l < TL; ++l) df_madd(sh[l], sl[l], t, ih[l * dp + k], il[l * dp + k]);
+      const int2 en = nx;
+      if (e + 1 < n) nx = ent[(long long)(e + 1) * dp + j];
+      madd(sh, sl, en);
     }
     sink(j, sh, sl);
   }
   for (int h = warp; h < nh; h += nwarp) {
-    const int j = heavy[h], n = cnt[j];
+    const int j = heavy[h], n = scnt[j];
     float sh[TL], sl[TL];
 #pragma unroll
     for (int l = 0; l < TL; ++l) sh[l] = sl[l] = 0.f;
-    for (int e = lane; e < n; e += 32) {
-      const int2 en = ent[(long long)j * dp + e];
-      const int k = en.x;
-      const float t = -__int_as_float(en.y);
-#pragma unroll
-      for (int l = 0; l < TL; ++l) df_madd(sh[l], sl[l], t, ih[l * dp + k], il[l * dp + k]);
-    }
+    for (int e = lane; e < n; e += 32) madd(sh, sl, ent[(long long)e * dp + j]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -590,37 +648,43 @@ __device__ __forceinline__ void prerot_product_df(const int2* __restrict__ ent, 
 }
 
 // The same product in FP32 (in and the result u single words; sink(j, u)).
-template <int TL, class Sink>
-__device__ __forceinline__ void prerot_product_f32(const int2* __restrict__ ent, const int* __restrict__ cnt,
-                                                   const int* heavy, int nh, int dp, const float* in, Sink sink) {
+template <class Sink>
+__device__ __forceinline__ void prerot_product_f32(const int2* __restrict__ ent, const int* scnt, const int* heavy,
+                                                   int nh, int dp, const float* in, Sink sink) {
+  constexpr int TL = kPrerotLines;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  auto madd = [&](float* u, int2 en) {
+    const float t = __int_as_float(en.y);
+    const float4* v4 = reinterpret_cast<const float4*>(in + en.x * TL);
+#pragma unroll
+    for (int q = 0; q < TL / 4; ++q) {
+      const float4 v = v4[q];
+      u[4 * q] = fmaf(-t, v.x, u[4 * q]);
+      u[4 * q + 1] = fmaf(-t, v.y, u[4 * q + 1]);
+      u[4 * q + 2] = fmaf(-t, v.z, u[4 * q + 2]);
+      u[4 * q + 3] = fmaf(-t, v.w, u[4 * q + 3]);
+    }
+  };
   for (int j = threadIdx.x; j < dp; j += blockDim.x) {
-    const int n = cnt[j];
+    const int n = scnt[j];
     if (n > kPrerotLight) continue;
     float u[TL];
 #pragma unroll
     for (int l = 0; l < TL; ++l) u[l] = 0.f;
+    int2 nx = n > 0 ? ent[j] : make_int2(0, 0);
     for (int e = 0; e < n; ++e) {
-      const int2 en = ent[(long long)j * dp + e];
-      const int k = en.x;
-      const float t = __int_as_float(en.y);
-#pragma unroll
-      for (int l = 0; l < TL; ++l) u[l] = fmaf(-t, in[l * dp + k], u[l]);
+      const int2 en = nx;
+      if (e + 1 < n) nx = ent[(long long)(e + 1) * dp + j];
+      madd(u, en);
     }
     sink(j, u);
   }
   for (int h = warp; h < nh; h += nwarp) {
-    const int j = heavy[h], n = cnt[j];
+    const int j = heavy[h], n = scnt[j];
     float u[TL];
 #pragma unroll
     for (int l = 0; l < TL; ++l) u[l] = 0.f;
-    for (int e = lane; e < n; e += 32) {
-      const int2 en = ent[(long long)j * dp + e];
-      const int k = en.x;
-      const float t = __int_as_float(en.y);
-#pragma unroll
-      for (int l = 0; l < TL; ++l) u[l] = fmaf(-t, in[l * dp + k], u[l]);
-    }
+    for (int e = lane; e < n; e += 32) madd(u, ent[(long long)e * dp + j]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -630,78 +694,105 @@ __device__ __forceinline__ void prerot_product_f32(const int2* __restrict__ ent,
   }
 }
 
-// v <- v X with X = I + A + A^2 / 2 + A^3 / 6 + A^4 / 24 for TL lines v of one chain's dp x dp
-// matrix at a time: the rows of `in` (COLS false: the lines are rows, Z = M X) or its columns (COLS
-// true: X^T Y, whose column c is Y[:, c] X). With w1 = v A (A skew: (v A)_j = -sum_l theta_jl v_l)
-// and w_{k+1} = w_k A, v X = v + w1 + w2 / 2 + w3 / 6 + w4 / 24, |w_k| <= ||A||_F^k |v| <= 1e-3k |v|.
-// w1 and w2 are formed in double-float pairs (v split into FP32 hi + lo, ~48 bits), w3 (<= 1e-9 |v|)
-// and w4 in FP32, all of them within ~1e-16 |v|; v + (the sum) is formed in FP64. SYM (with COLS):
-// the output is symmetric, and the CTA of column c writes both out[k][c] and out[c][k] for k <= c
-// (each pair of mirrored entries has one writer). Grid (dp / TL, chains); shared memory 16 TL dp
-// + 4 dp bytes; chains with mask 0 return. The summation order of every output is fixed (runs
-// repeat bit for bit).
-template <int TL, bool COLS, bool SYM>
-__global__ void __launch_bounds__(256) k_prerot_apply(const double* inb, double* outb,  // (may alias)
-                                                      const int2* __restrict__ entb, const int* __restrict__ cntb,
-                                                      const int* __restrict__ mask, int dp) {
-  extern __shared__ float psf[];
+// v <- v X with X = I + A + A^2 / 2 + A^3 / 6 + A^4 / 24 for 8 lines v of one chain's dp x dp matrix
+// at a time: the rows of the input (COLS false: the lines are rows, Z = M X) or its columns (COLS
+// true: X^T Y, whose column c is Y[:, c] X). The input is FP64 (inb) or double-float pairs
+// (IN_PAIRS: in2b); the output is double-float pairs (out2b, laid out as the input), the form the
+// double-float Jacobi works in. With w1 = v A (A skew: (v A)_j = -sum_k theta_jk v_k) and
+// w_{k+1} = w_k A, v X = v + w1 + w2 / 2 + w3 / 6 + w4 / 24, |w_k| <= ||A||_F^k |v| <= 1e-3k |v|:
+// w1 and w2 are formed in double-float pairs (v as hi + lo, ~48 bits), w3 (<= 1e-9 |v|) and w4 in
+// FP32, each within ~1e-16 |v|, and v + (their sum) by a double-float addition. An FP64 input is
+// split once, and its pairs are kept in the output's places for that last addition. SYM (with
+// COLS): the output is symmetric, and the CTA of column c writes both out[k][c] and out[c][k] for
+// k <= c (each pair of mirrored entries has one writer). Grid (dp / 8, chains); shared memory
+// 128 dp + 8 dp bytes; chains with mask 0 return. The summation order of every output is fixed
+// (runs repeat bit for bit).
+template <bool COLS, bool SYM, bool IN_PAIRS>
+__global__ void __launch_bounds__(256) k_prerot_apply(const double* __restrict__ inb, const float2* __restrict__ in2b,
+                                                      float2* __restrict__ out2b, const int2* __restrict__ entb,
+                                                      const int* __restrict__ cntb, const int* __restrict__ mask,
+                                                      int dp) {
+  constexpr int TL = kPrerotLines;
+  extern __shared__ float4 psf4[];
   __shared__ int nheavy;
   const int c = blockIdx.y;
   if (!mask[c]) return;
   const long long DD = (long long)dp * dp;
-  const double* in = inb + c * DD;
-  double* out = outb + c * DD;
+  const double* in = IN_PAIRS ? nullptr : inb + c * DD;
+  const float2* in2 = IN_PAIRS ? in2b + c * DD : nullptr;
+  float2* out = out2b + c * DD;
+  const float2* vsrc = IN_PAIRS ? in2 : out;  // where the final addition reads v's pairs
   const int2* ent = entb + c * DD;
   const int* cnt = cntb + (long long)c * dp;
   const int l0 = blockIdx.x * TL, nl = min(TL, dp - l0);
   const int TD = TL * dp;
-  // four [TL][dp] FP32 arrays: P1, P2 = v (hi, lo), then w2 (hi, lo), then P2 = w3; P3, P4 = w1
-  // (hi, lo), into which w2 / 2, w3 / 6 and w4 / 24 are folded; res overlays P1, P2 at the end
-  float* P1 = psf;
+  // four [dp][8] FP32 arrays: P1, P2 = v (hi, lo), then w2 (hi, lo), then P2 = w3; P3, P4 = w1
+  // (hi, lo), into which w2 / 2, w3 / 6 and w4 / 24 are folded
+  float* P1 = reinterpret_cast<float*>(psf4);
   float* P2 = P1 + TD;
   float* P3 = P2 + TD;
   float* P4 = P3 + TD;
   int* heavy = reinterpret_cast<int*>(P4 + TD);  // [dp]
-  double* res = reinterpret_cast<double*>(psf);  // [TL][dp]
+  int* scnt = heavy + dp;                        // [dp]
   if (threadIdx.x == 0) nheavy = 0;
-  for (int e = threadIdx.x; e < TD; e += blockDim.x) {
-    int l, k;
-    if (COLS) { k = e / TL; l = e - k * TL; }
-    else { l = e / dp; k = e - l * dp; }
-    const double x = l < nl ? (COLS ? in[(long long)k * dp + l0 + l] : in[(long long)(l0 + l) * dp + k]) : 0.0;
-    const float h = __double2float_rn(x);
-    P1[l * dp + k] = h;
-    P2[l * dp + k] = __double2float_rn(x - (double)h);
+  // v: element (k, l) of the lines is input[k][l0 + l] (COLS) or input[l0 + l][k]
+  if (COLS) {
+    for (int e = threadIdx.x; e < TD; e += blockDim.x) {
+      const int k = e >> 3, l = e & 7;
+      const long long i = (long long)k * dp + l0 + l;
+      float2 v = make_float2(0.f, 0.f);
+      if (l < nl) {
+        if (IN_PAIRS) v = in2[i];
+        else out[i] = v = df_split_bits(in[i]);
+      }
+      P1[e] = v.x;
+      P2[e] = v.y;
+    }
+  } else {
+    for (int k = threadIdx.x; k < dp; k += blockDim.x) {
+#pragma unroll
+      for (int l = 0; l < TL; ++l) {
+        const long long i = (long long)(l0 + l) * dp + k;
+        float2 v = make_float2(0.f, 0.f);
+        if (l < nl) {
+          if (IN_PAIRS) v = in2[i];
+          else out[i] = v = df_split_bits(in[i]);
+        }
+        P1[k * TL + l] = v.x;
+        P2[k * TL + l] = v.y;
+      }
+    }
   }
+  for (int j = threadIdx.x; j < dp; j += blockDim.x) scnt[j] = cnt[j];
   __syncthreads();
   for (int j = threadIdx.x; j < dp; j += blockDim.x)
-    if (cnt[j] > kPrerotLight) heavy[atomicAdd(&nheavy, 1)] = j;
+    if (scnt[j] > kPrerotLight) heavy[atomicAdd(&nheavy, 1)] = j;
   __syncthreads();
   const int nh = nheavy;
   // w1 = v A -> P3, P4
-  prerot_product_df<TL>(ent, cnt, heavy, nh, dp, P1, P2, [&](int j, const float* h, const float* lo) {
+  prerot_product_df(ent, scnt, heavy, nh, dp, P1, P2, [&](int j, const float* h, const float* lo) {
 #pragma unroll
     for (int l = 0; l < TL; ++l) {
-      P3[l * dp + j] = h[l];
-      P4[l * dp + j] = lo[l];
+      P3[j * TL + l] = h[l];
+      P4[j * TL + l] = lo[l];
     }
   });
   __syncthreads();
   // w2 = w1 A -> P1, P2 (v is no longer read)
-  prerot_product_df<TL>(ent, cnt, heavy, nh, dp, P3, P4, [&](int j, const float* h, const float* lo) {
+  prerot_product_df(ent, scnt, heavy, nh, dp, P3, P4, [&](int j, const float* h, const float* lo) {
 #pragma unroll
     for (int l = 0; l < TL; ++l) {
-      P1[l * dp + j] = h[l];
-      P2[l * dp + j] = lo[l];
+      P1[j * TL + l] = h[l];
+      P2[j * TL + l] = lo[l];
     }
   });
   __syncthreads();
   // w3 = w2 A from w2's high words (P1, read by every thread); each thread first folds its own
-  // entries of w2 / 2 into w1 (two-sum of the high words), then keeps w3 in P2 (its own entries)
-  prerot_product_f32<TL>(ent, cnt, heavy, nh, dp, P1, [&](int j, const float* u) {
+  // entry of w2 / 2 into w1 (two-sum of the high words), then keeps w3 in P2 (its own entry)
+  prerot_product_f32(ent, scnt, heavy, nh, dp, P1, [&](int j, const float* u) {
 #pragma unroll
     for (int l = 0; l < TL; ++l) {
-      const int i = l * dp + j;
+      const int i = j * TL + l;
       const float a = 0.5f * P1[i];
       const float s = P3[i] + a;
       const float bp = s - P3[i];
@@ -713,36 +804,46 @@ __global__ void __launch_bounds__(256) k_prerot_apply(const double* inb, double*
   });
   __syncthreads();
   // w4 = w3 A; w3 / 6 + w4 / 24 into the low words
-  prerot_product_f32<TL>(ent, cnt, heavy, nh, dp, P2, [&](int j, const float* u) {
+  prerot_product_f32(ent, scnt, heavy, nh, dp, P2, [&](int j, const float* u) {
 #pragma unroll
     for (int l = 0; l < TL; ++l) {
-      const int i = l * dp + j;
+      const int i = j * TL + l;
       P4[i] += fmaf(u[l], 1.f / 24.f, P2[i] * (1.f / 6.f));
     }
   });
   __syncthreads();
-  // v X = v + (P3 + P4) in FP64 (res overlays P1, P2: no longer read)
-  for (int e = threadIdx.x; e < TD; e += blockDim.x) {
-    int l, k;
-    if (COLS) { k = e / TL; l = e - k * TL; }
-    else { l = e / dp; k = e - l * dp; }
-    if (l >= nl) continue;
-    const double x = COLS ? in[(long long)k * dp + l0 + l] : in[(long long)(l0 + l) * dp + k];
-    res[l * dp + k] = x + ((double)P3[l * dp + k] + (double)P4[l * dp + k]);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < TD; e += blockDim.x) {
-    int l, k;
-    if (COLS) { k = e / TL; l = e - k * TL; }
-    else { l = e / dp; k = e - l * dp; }
-    if (l >= nl) continue;
-    if (!COLS) out[(long long)(l0 + l) * dp + k] = res[l * dp + k];
-    else if (!SYM || k <= l0 + l) out[(long long)k * dp + l0 + l] = res[l * dp + k];
-  }
-  if (SYM) {
+  // v X = v + (P3 + P4): two-sum of the high words, the low words and the error added, renormalised
+  auto finish = [&](int k, int l, long long i) -> float2 {
+    const float2 v = vsrc[i];
+    const float dh = P3[k * TL + l], dl = P4[k * TL + l];
+    const float s = v.x + dh;
+    const float bp = s - v.x;
+    const float err = (v.x - (s - bp)) + (dh - bp);
+    const float lo = v.y + dl + err;
+    const float hi = s + lo;
+    return make_float2(hi, lo - (hi - s));
+  };
+  if (COLS) {
     for (int e = threadIdx.x; e < TD; e += blockDim.x) {
-      const int l = e / dp, k = e - l * dp;
-      if (l < nl && k <= l0 + l) out[(long long)(l0 + l) * dp + k] = res[l * dp + k];
+      const int k = e >> 3, l = e & 7;
+      if (l >= nl) continue;
+      const long long i = (long long)k * dp + l0 + l;
+      const float2 r = finish(k, l, i);
+      if (!SYM) {
+        out[i] = r;
+      } else if (k <= l0 + l) {
+        out[i] = r;
+        out[(long long)(l0 + l) * dp + k] = r;
+      }
+    }
+  } else {
+    for (int k = threadIdx.x; k < dp; k += blockDim.x) {
+#pragma unroll
+      for (int l = 0; l < TL; ++l) {
+        if (l >= nl) continue;
+        const long long i = (long long)(l0 + l) * dp + k;
+        out[i] = finish(k, l, i);
+      }
     }
   }
 }
@@ -925,6 +1026,8 @@ struct rmhmc_model {
   double* Zp = nullptr;
   double* pr_acc = nullptr;
   int* pr_mask = nullptr;
+  int2* pr_ent = nullptr;  // the pre-rotation's row lists (C x dp^2 entries, C x dp lengths)
+  int* pr_cnt = nullptr;
 };
 
 namespace {
@@ -1178,51 +1281,51 @@ void primal_model_layer(rmhmc_model* m) {
 //     with `third`, also the third-derivative operator (the dual model's A1, S^2 and F-phase
 //     statistics; the primal model needs no more than l''').
 // The first-order pre-rotation of a warm eigen-update (see k_prerot_rows). A holds a few percent
-// of nonzeros, so X = I + A + A^2 / 2 is applied from the lists of A's rows: M <- X^T (M X) and
-// Psi^T <- X^T Psi^T for the chains in pr_mask (Z = M X in Zp; the lists in W and Y, free during the
-// eigen-update). Eight lines per CTA while their buffers (16 TL dp + 4 dp bytes) stay within 200 KB
-// of shared memory, else two; beyond dp = 6428 the pre-rotation is not taken.
-inline size_t prerot_smem(int TL, int dp) { return (size_t)16 * TL * dp + (size_t)4 * dp; }
-bool prerot_fits(int dp) { return prerot_smem(2, dp) <= (size_t)226 * 1024; }
+// of nonzeros, so X is applied from the lists of A's rows (pr_ent, pr_cnt), for the chains in
+// pr_mask: Z = M X into Zp (double-float pairs), X^T Z into the Jacobi's pair buffer for M (W) and
+// X^T Psi^T into its pair buffer for Psi^T (Y); the double-float Jacobi then starts from those pairs
+// for these chains. Eight lines per CTA, whose buffers (16 TL dp + 8 dp bytes) fit the 226 KB of
+// shared memory up to dp = 1701; beyond it the pre-rotation is not taken.
+inline size_t prerot_smem(int TL, int dp) { return (size_t)16 * TL * dp + (size_t)8 * dp; }
+bool prerot_fits(int dp) { return prerot_smem(kPrerotLines, dp) <= (size_t)226 * 1024; }
 
-template <int TL>
-void prerot_apply_all(rmhmc_model* m, const int2* ent, const int* cnt) {
+void prerot_apply_all(rmhmc_model* m) {
   cudaStream_t s = m->stream;
   const int C = m->C, dp = m->dp;
-  const size_t smem = prerot_smem(TL, dp);
+  const size_t smem = prerot_smem(kPrerotLines, dp);
   // (the opt-in limit covers the kernel's static shared memory too: ask for what this launch needs)
   static size_t attr_bytes = 0;
   if (smem > attr_bytes) {
-    cudaFuncSetAttribute(k_prerot_apply<TL, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_prerot_apply<TL, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_prerot_apply<TL, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_prerot_apply<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_prerot_apply<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_prerot_apply<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_bytes = smem;
   }
-  const dim3 grid((dp + TL - 1) / TL, C);
+  const dim3 grid((dp + kPrerotLines - 1) / kPrerotLines, C);
   const int* mk = m->pr_mask;
+  float2* Z2 = reinterpret_cast<float2*>(m->Zp);
   PROF(m, CAT_PREROT, 0)
-  k_prerot_apply<TL, false, false><<<grid, 256, smem, s>>>(m->M, m->Zp, ent, cnt, mk, dp);
+  k_prerot_apply<false, false, false><<<grid, 256, smem, s>>>(m->M, nullptr, Z2, m->pr_ent, m->pr_cnt, mk, dp);
   PROF(m, CAT_PREROT, 0)
-  k_prerot_apply<TL, true, true><<<grid, 256, smem, s>>>(m->Zp, m->M, ent, cnt, mk, dp);
+  k_prerot_apply<true, true, true><<<grid, 256, smem, s>>>(nullptr, Z2, reinterpret_cast<float2*>(m->W), m->pr_ent,
+                                                           m->pr_cnt, mk, dp);
   PROF(m, CAT_PREROT, 0)
-  k_prerot_apply<TL, true, false><<<grid, 256, smem, s>>>(m->PsiT, m->PsiT, ent, cnt, mk, dp);
+  k_prerot_apply<true, false, false><<<grid, 256, smem, s>>>(m->PsiT, nullptr, reinterpret_cast<float2*>(m->Y),
+                                                             m->pr_ent, m->pr_cnt, mk, dp);
 }
 
 void prerotate(rmhmc_model* m) {
   cudaStream_t s = m->stream;
   const int C = m->C, dp = m->dp, d = m->d;
-  int2* ent = reinterpret_cast<int2*>(m->W);  // C x dp^2 (column, angle) entries
-  int* cnt = reinterpret_cast<int*>(m->Y);    // C x dp row lengths
   double* part = m->pr_acc + 4 * C;
   PROF(m, CAT_PREROT, 0)
   k_prerot_norms<<<dim3(kPrerotParts, C), 256, 0, s>>>(m->M, dp, d, m->pr_acc, part);
   PROF(m, CAT_PREROT, 0)
-  k_prerot_rows<<<dim3((dp + 7) / 8, C), 256, 0, s>>>(m->M, part, dp, d, m->jacobi_rule, m->tol, m->status, ent,
-                                                      cnt, m->pr_acc);
+  k_prerot_rows<<<dim3((dp + 7) / 8, C), 256, 0, s>>>(m->M, part, dp, d, m->jacobi_rule, m->tol, m->status,
+                                                      m->pr_ent, m->pr_cnt, m->pr_acc);
   PROF(m, CAT_PREROT, 0)
   k_prerot_mask<<<nblk(C), 256, 0, s>>>(m->pr_acc, C, m->pr_mask, m->jw.tiles);
-  if (prerot_smem(8, dp) <= (size_t)200 * 1024) prerot_apply_all<8>(m, ent, cnt);
-  else prerot_apply_all<2>(m, ent, cnt);
+  prerot_apply_all(m);
 }
 
 void eval_geometry(rmhmc_model* m, bool third) {
@@ -1264,15 +1367,15 @@ void eval_geometry(rmhmc_model* m, bool third) {
   // angles
   const bool cold = m->cold || m->eigen_start == 1;
   const int sched = cold ? RMHMC_JACOBI_CYCLIC : m->jacobi_sched;
-  if (m->prerot && !cold && use_tc(m, dp, dp) && prerot_fits(dp)) {
-    prerotate(m);
-    m->tc_pa_ok = m->tc_pb_ok = false;
-  }
+  // (the pre-rotation is for the mixed form, whose Jacobi works in double-float pairs)
+  const bool pre = m->prerot && !cold && use_tc(m, dp, dp) && prerot_fits(dp);
+  if (pre) prerotate(m);
   if (m->precision == RMHMC_MIXED) {
-    // rotations in double-float pairs; W and Y serve as the pair buffers (free during the update)
+    // rotations in double-float pairs; W and Y serve as the pair buffers (free during the update),
+    // already filled by the pre-rotation for the chains in pr_mask
     PROF(m, CAT_JACOBI_DF, 0)
     jacobi_df(s, m->M, m->PsiT, m->lam, dp, d, C, m->jacobi_rule, m->tol, m->max_sweeps, m->status,
-              m->sweeps_last, m->sweeps_acc, m->jw, m->cluster, m->W, m->Y, sched);
+              m->sweeps_last, m->sweeps_acc, m->jw, m->cluster, m->W, m->Y, sched, pre ? m->pr_mask : nullptr);
   } else {
     PROF(m, CAT_JACOBI, 0)
     jacobi_f64(s, m->M, m->PsiT, m->lam, dp, d, C, m->jacobi_rule, m->tol, m->max_sweeps, m->status,
@@ -1516,6 +1619,8 @@ rmhmc_status allocate_model(rmhmc_model* m, int n_cov) {
   ALLOC(m->Zp, (size_t)C * DD);
   ALLOC(m->pr_acc, (size_t)(4 + 2 * kPrerotParts) * C);
   ALLOC(m->pr_mask, (size_t)C);
+  ALLOC(m->pr_ent, (size_t)C * DD);
+  ALLOC(m->pr_cnt, (size_t)C * dp);
 #undef ALLOC
   return st;
 }
@@ -1884,17 +1989,23 @@ rmhmc_status rmhmc_profile_read(rmhmc_model* m, double* ms_host, double* flops_h
   // 2 flops each like the DFMA peak)
   std::vector<unsigned long long> tl((size_t)kJacStats * m->C);
   cudaMemcpy(tl.data(), m->jw.tiles, tl.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
-  double tiles = 0.0, rounds = 0.0;
+  double tiles = 0.0, rounds = 0.0, prerot_pairs = 0.0;
   for (int c = 0; c < m->C; ++c) {
     tiles += (double)tl[(size_t)kJacStats * c];
     rounds += (double)tl[(size_t)kJacStats * c + 1];
+    prerot_pairs += (double)tl[(size_t)kJacStats * c + 7];
   }
+  // pre-rotation work = the double-float multiply-adds of its first- and second-order products:
+  // per pre-rotated chain, 2 entries of A per pair x dp lines x 2 products x 3 applications, 2 flops
+  // each (the FP32 third- and fourth-order products and the element-wise passes are not counted)
+  const double prerot_flops = prerot_pairs * 2.0 * m->dp * 2.0 * 3.0 * 2.0;
   for (int i = 0; i < RMHMC_PROF_NCAT; ++i) {
     if (ms_host) ms_host[i] = ms[i];
     if (flops_host)
       flops_host[i] = (i == CAT_JACOBI || i == CAT_JACOBI_DF)
                           ? (m->prof_launch[i] ? tiles * 8192.0 + rounds * 1952.0 : 0.0)
-                          : m->prof_flops[i];
+                      : i == CAT_PREROT ? (m->prof_launch[i] ? prerot_flops : 0.0)
+                                        : m->prof_flops[i];
     if (launches_host) launches_host[i] = m->prof_launch[i];
   }
   return RMHMC_OK;
