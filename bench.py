@@ -40,7 +40,7 @@ N_INPUTS, N_CHAINS, EPS, N_FP, N_LEAPFROG = 400, 64, 0.001, 6, 10
 # dram__bytes_write.sum of single-kernel captures at 8 chains of this workload (traffic grows
 # with the number of chains, so a 64-chain launch is scaled by 64 / 8). A kernel enters here only
 # with counters taken from its current code.
-DRAM_BYTES_PER_CHAIN = {"jacobi_df": 22.37568e6 / 8}  # k_jacobi_t<ElemDF>, warm update, 8 chains
+DRAM_BYTES_PER_CHAIN = {}  # (k_jacobi_t<ElemDF>'s last capture predates its current criterion reads)
 SUBSTEPS_PER_LEAPFROG = 2 * N_FP + 1
 # The paper's settings for its simulated primal-model runs (Sec. 2.5): step size, and kappa of the
 # map g(lambda) = sqrt(kappa^2 + lambda^2) (passed as alpha = 1 / kappa).

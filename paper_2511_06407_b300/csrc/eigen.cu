@@ -330,6 +330,9 @@ struct ElemF64 {
   static __device__ __forceinline__ void st(T* p, T v) { __stcg(p, v); }
   static __device__ __forceinline__ double join(T v) { return v; }
   static __device__ __forceinline__ T split(double v) { return v; }
+  // the value the coupling criterion (a log-domain test to FP32 rounding) reads
+  using CV = double;
+  static __device__ __forceinline__ CV cv(T v) { return v; }
   static __device__ __forceinline__ void transform(const T* X, const T* Vp, const T* Vq, T* Tt, T* Y) {
     tile_transform(X, Vp, Vq, Tt, Y);
   }
@@ -343,6 +346,11 @@ struct ElemDF {
   static __device__ __forceinline__ void st(T* p, T v) { __stcg(p, v); }
   static __device__ __forceinline__ double join(T v) { return df_join(v); }
   static __device__ __forceinline__ T split(double v) { return df_split(v); }
+  // the value the coupling criterion reads: hi + lo rounded to FP32 (within 2^-24 of the pair's
+  // value, below the criterion's own FP32-logarithm rounding; no FP64 instruction, whose pipe is
+  // 1/64 of the FP32 rate; an unnormalised pair with hi = 0 still gives its lo)
+  using CV = float;
+  static __device__ __forceinline__ CV cv(T v) { return v.x + v.y; }
   static __device__ __forceinline__ void transform(const T* X, const T* Vp, const T* Vq, T* Tt, T* Y) {
     tile_transform_df(X, Vp, Vq, Tt, Y);
   }
@@ -366,9 +374,26 @@ struct CritConst {
 // rounding of the logarithms, ~1e-6 relative in the ratio). den = (m_jj m_ll)^2 / d_min^2 (METRIC)
 // or |m_jj m_ll| (RELATIVE); the floor is the rule's (stop_floor2). A non-finite entry gives +inf
 // (the caller treats it as a failed update).
+// log2 |x| for a finite float, from its exponent field and the FP32 log2 of its significand; zero
+// gives -2000, a subnormal the log2 of 2^-127.
+__device__ __forceinline__ float log2_abs(float x) {
+  const unsigned b = __float_as_uint(x) & 0x7fffffffu;
+  if (b == 0) return -2000.f;
+  const int e = (int)(b >> 23) - 127;
+  return (float)e + __log2f(__uint_as_float(0x3f800000u | (b & 0x7fffffu)));
+}
+
+__device__ __forceinline__ float coupling_log_ratio_l(float lv, float lj, float ll, const CritConst& k);
+// (double: the FP64 kernel's values; float: the double-float kernel's pairs as FP32 values)
 __device__ __forceinline__ float coupling_log_ratio(double v, double djj, double dll, const CritConst& k) {
   if (!isfinite(v)) return INFINITY;
-  const float lv = log2_abs(v), lj = log2_abs(djj), ll = log2_abs(dll);
+  return coupling_log_ratio_l(log2_abs(v), log2_abs(djj), log2_abs(dll), k);
+}
+__device__ __forceinline__ float coupling_log_ratio(float v, float djj, float dll, const CritConst& k) {
+  if (!isfinite(v)) return INFINITY;
+  return coupling_log_ratio_l(log2_abs(v), log2_abs(djj), log2_abs(dll), k);
+}
+__device__ __forceinline__ float coupling_log_ratio_l(float lv, float lj, float ll, const CritConst& k) {
   float lthr, lfl;
   if (k.rule == RMHMC_JACOBI_METRIC) {
     lthr = k.ltol2 + 2.f * (lj + ll) - k.ldmin2;
@@ -465,7 +490,7 @@ __global__ void __launch_bounds__(NW * 32)
   __shared__ unsigned char sneed[kMaxPairs];  // pair p is solved in phase 1 of this round
   __shared__ short ssolve[kMaxPairs];         // the pairs solved, in order
   __shared__ int snsolve, snmatch, sbad;
-  __shared__ double sdg[NW][2 * SB];          // phase 2: new diagonal of a tile's rows and columns
+  __shared__ typename E::CV sdg[NW][2 * SB];  // phase 2: new diagonal of a tile's rows and columns
   // dynamic matching
   __shared__ float stopv[kMaxBlocks][kTop];
   __shared__ short stopj[kMaxBlocks][kTop];
@@ -502,8 +527,10 @@ __global__ void __launch_bounds__(NW * 32)
     //      still poisons tot)
     double tot = 0.0, dmin = 1e308;
     if (pass == 0) {
+      // (pairs: the FP32 values, one FP64 conversion and FMA each for ||M||_F^2, which only sets
+      // the rounding floor)
       for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
-        const double v = E::join(E::ld(Mw + e));
+        const double v = E::kPairs ? (double)E::cv(E::ld(Mw + e)) : E::join(E::ld(Mw + e));
         tot = fma(v, v, tot);
         const int i = (int)(e / dp);
         if (i < d && (long long)i * dp + i == e) dmin = fmin(dmin, fabs(v));
@@ -553,11 +580,11 @@ __global__ void __launch_bounds__(NW * 32)
           const int a = e / BL, b = e % BL;
           if (I == J && a >= b) continue;
           const int j = I * BL + a, l = J * BL + b;
-          const double v = E::join(E::ld(Mw + (long long)j * dp + l));
-          if (v == 0.0) continue;
+          const typename E::CV v = E::cv(E::ld(Mw + (long long)j * dp + l));
+          if (v == 0) continue;
           if (!isfinite(v)) { nf = true; continue; }
-          const double djj = E::join(E::ld(Mw + (long long)j * dp + j));
-          const double dll = E::join(E::ld(Mw + (long long)l * dp + l));
+          const typename E::CV djj = E::cv(E::ld(Mw + (long long)j * dp + j));
+          const typename E::CV dll = E::cv(E::ld(Mw + (long long)l * dp + l));
           rmax = fmaxf(rmax, coupling_log_ratio(v, djj, dll, ck));
         }
         rmax = warp_max(rmax);
@@ -573,13 +600,23 @@ __global__ void __launch_bounds__(NW * 32)
       for (long long e = (long long)rank * blockDim.x + tid; e < DD; e += (long long)C * blockDim.x) {
         const int j = (int)(e / dp), l = (int)(e % dp);
         if (j >= l) continue;  // M is kept symmetric: the upper triangle decides
-        const double v = E::join(E::ld(Mw + e));
-        if (v == 0.0) continue;
-        if (!isfinite(v)) bad = 1.0;
-        const double djj = E::join(E::ld(Mw + (long long)j * dp + j));
-        const double dll = E::join(E::ld(Mw + (long long)l * dp + l));
-        if (pair_unconverged(v, djj, dll, tol2, stop_floor2(djj, dll, floor2, rule), rule, dmin2))
-          critv = 1.0;
+        if constexpr (E::kPairs) {
+          // the log-domain criterion on the pairs' FP32 values (as the dynamic schedule's test)
+          const float v = E::cv(E::ld(Mw + e));
+          if (v == 0.f) continue;
+          if (!isfinite(v)) bad = 1.0;
+          if (coupling_log_ratio(v, E::cv(E::ld(Mw + (long long)j * dp + j)),
+                                 E::cv(E::ld(Mw + (long long)l * dp + l)), ck) > 0.f)
+            critv = 1.0;
+        } else {
+          const double v = E::join(E::ld(Mw + e));
+          if (v == 0.0) continue;
+          if (!isfinite(v)) bad = 1.0;
+          const double djj = E::join(E::ld(Mw + (long long)j * dp + j));
+          const double dll = E::join(E::ld(Mw + (long long)l * dp + l));
+          if (pair_unconverged(v, djj, dll, tol2, stop_floor2(djj, dll, floor2, rule), rule, dmin2))
+            critv = 1.0;
+        }
       }
     }
 #pragma unroll
@@ -816,10 +853,9 @@ __global__ void __launch_bounds__(NW * 32)
             for (int e = lane; e < SB * SB; e += 32) {
               const int a = e / SB, b = e % SB;
               if (a >= b) continue;
-              const double v = E::join(E::ld(Dp + e));
-              if (v == 0.0) continue;
-              const float rr = coupling_log_ratio(v, E::join(E::ld(Dp + a * SB + a)),
-                                                  E::join(E::ld(Dp + b * SB + b)), ck);
+              const typename E::CV v = E::cv(E::ld(Dp + e));
+              if (v == 0) continue;
+              const float rr = coupling_log_ratio(v, E::cv(E::ld(Dp + a * SB + a)), E::cv(E::ld(Dp + b * SB + b)), ck);
               if (b < BL) r00 = fmaxf(r00, rr);
               else if (a >= BL) r11 = fmaxf(r11, rr);
               else r01 = fmaxf(r01, rr);
@@ -846,8 +882,8 @@ __global__ void __launch_bounds__(NW * 32)
             const int pq = lane < SB ? Pp : Q, a = lane & (SB - 1);
             const bool fr = lane < SB ? fP : fQ;
             const int I = lane < SB ? I1 : I2, J = lane < SB ? J1 : J2;
-            sdg[warp][lane] = fr ? E::join(E::ld(D + (long long)pq * SB * SB + a * SB + a))
-                                 : E::join(E::ld(Mw + (long long)gidx(I, J, a) * dp + gidx(I, J, a)));
+            sdg[warp][lane] = fr ? E::cv(E::ld(D + (long long)pq * SB * SB + a * SB + a))
+                                 : E::cv(E::ld(Mw + (long long)gidx(I, J, a) * dp + gidx(I, J, a)));
           }
           __syncwarp();
           E::transform(X, fP ? Va : nullptr, fQ ? Vq : nullptr, Tt, X);
@@ -863,12 +899,11 @@ __global__ void __launch_bounds__(NW * 32)
             // lane (t, u0) covers 8 entries of one 8 x 8 block: rows of block (t < 8 ? I1 : J1),
             // columns of block (u0 < 8 ? I2 : J2); lanes 2, 4, 8 apart share it
             float rr = -INFINITY;
-            const double djj = sdg[warp][t];
+            const typename E::CV djj = sdg[warp][t];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              const double v = E::join(X[t * SBP + u0 + j]);
-              if (v != 0.0)
-                rr = fmaxf(rr, coupling_log_ratio(v, djj, sdg[warp][SB + u0 + j], ck));
+              const typename E::CV v = E::cv(X[t * SBP + u0 + j]);
+              if (v != 0) rr = fmaxf(rr, coupling_log_ratio(v, djj, sdg[warp][SB + u0 + j], ck));
             }
             rr = fmaxf(rr, __shfl_xor_sync(0xffffffffu, rr, 2));
             rr = fmaxf(rr, __shfl_xor_sync(0xffffffffu, rr, 4));
