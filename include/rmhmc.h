@@ -332,16 +332,16 @@ rmhmc_status rmhmc_stream_create(void** stream_out);
 rmhmc_status rmhmc_stream_destroy(void* stream);
 /* First-order pre-rotation of warm eigen-updates in the RMHMC_MIXED form (on by default; enable 0
  * or 1, else EINVAL). After a warm start M = Psi^T H Psi is diagonal up to small couplings: every
- * pair (j, l) that fails the Jacobi stopping rule gets the angle theta_jl = atan(2 m_jl / (m_ll -
- * m_jj)) / 2 that zeroes its coupling to first order; with the skew matrix A of these angles,
- * X = I + A + A^2 / 2 (orthogonal up to A^4 / 4) is applied as M <- X^T M X and Psi <- Psi X
- * from the lists of A's nonzeros (first-order terms in double-float pairs, the sums in FP64), and
- * the Jacobi then checks the stopping rule and rotates whatever is left. Matrices of more than
- * 1701 (padded) rows are left to the Jacobi.
- * Pairs whose angle exceeds 1e-5 (nearly equal diagonal entries) are left to the Jacobi; a chain
- * takes it only when ||A||_F <= 1e-4 (so that A^4 / 4 is below FP64 rounding); cold starts
- * and the FP64 path use the Jacobi alone. Not part of the paper's method, which this accelerates:
- * the eigen-update's result still satisfies the same stopping rule. */
+ * pair (j, l) that fails the Jacobi stopping rule gets the angle x / 2, x = 2 m_jl / (m_ll - m_jj)
+ * (atan(x) / 2 to FP32 rounding), which zeroes its coupling to first order; with the skew matrix A
+ * of these angles, X = I + A + A^2 / 2 + A^3 / 6 + A^4 / 24 (exp(A) to fourth order, orthogonal up
+ * to A^6 / 72) is applied as M <- X^T M X and Psi <- Psi X from the lists of A's nonzeros (the
+ * first- and second-order terms in double-float pairs), and the double-float Jacobi then starts
+ * from the result, checks the stopping rule and rotates whatever is left. Pairs with |x| > 2e-5
+ * (nearly equal diagonal entries) are left to the Jacobi; a chain takes it only when
+ * ||A||_F <= 1e-3 (so that A^6 / 72 is below 1e-19); cold starts, matrices of more than 1701
+ * (padded) rows and the FP64 path use the Jacobi alone. Not part of the paper's method, which this
+ * accelerates: the eigen-update's result still satisfies the same stopping rule. */
 rmhmc_status rmhmc_set_prerotation(rmhmc_model* m, int enable);
 /* Set the Jacobi cluster size (1, 2, 4, 8, or 0 for the default) and rotation schedule directly. */
 rmhmc_status rmhmc_set_jacobi(rmhmc_model* m, int cluster, int sched);
