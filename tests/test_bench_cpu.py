@@ -53,6 +53,32 @@ def test_category_rooflines_of_a_measured_mixed_run():
     assert st["frac"] < st["frac_counted"] < 1.0
 
 
+def test_prerotation_is_rated_against_the_double_float_peak():
+    """The pre-rotation's counted work (double-float multiply-adds) is rated against the measured
+    Dot2 peak, per category and, when it dominates the step, in the headline roofline (whose traffic
+    stays null: no capture of it feeds the table of DRAM bytes)."""
+    ms = {"gemm_tc": 203.472, "jacobi_df": 185.624, "cholesky": 152.726, "prerotation": 139.724}
+    tf = {"gemm_tc": 647.136, "jacobi_df": 0.85686, "prerotation": 0.92389}
+    prof = {k: (v, tf.get(k, 0.0) * 1e12 * v * 1e-3, 61) for k, v in ms.items()}
+    out = bench.category_rooflines(prof, {"fp64": 1.2, "df": 6.45, "bf16": 1372.4}, mixed=True)
+    c = out["categories"]["prerotation"]
+    assert c["pipe"] == "df" and abs(c["frac"] - 0.92389 / 6.45) < 1e-9
+
+    class PeakProbes:
+        def df_peak_tflops(self, n):
+            return 6.45
+
+        def fp32_peak_tflops(self, n):
+            return 75.0
+
+        def fp64_peak_tflops(self, n):
+            return 1.2
+
+    r = bench._roofline(PeakProbes(), {"prerotation": prof["prerotation"], "vector": (52.6, 0.0, 61)}, 64)
+    assert r["kernel"] == "prerotation" and r["peak"] == 6.45 and r["traffic"] is None
+    assert abs(r["frac"] - 0.92389 / 6.45) < 1e-6
+
+
 def test_category_rooflines_fp64_run_uses_the_fp64_pipe():
     prof = {"gemm_f64": (1370.0, 0.8465e12 * 1.370, 40), "cholesky": (102.0, 0.4e12 * 0.102, 13),
             "model": (27.0, 0.0, 30)}
